@@ -1,0 +1,600 @@
+/*
+ * Plain FP64 CPU oracle of the explicit PIC cycle (test infrastructure only; see
+ * pic_oracle.h). Loops are written in the order of the published definitions with
+ * no blocking, fusion or reordering, so that each function can be checked by eye:
+ *
+ *   step:  B^n = (B^{n-1/2} + B^{n+1/2})/2 (kept from the previous step)
+ *          for every particle: order-2 interpolation of E^n, B^n at x^n,
+ *                              Boris  u^{n-1/2} -> u^{n+1/2},
+ *                              move   x^{n+1} = x^n + dt u/gamma,
+ *                              Esirkepov deposit of J^{n+1/2} from x^n -> x^{n+1}
+ *          particle boundaries (periodic wrap; window: absorb outside [0, Lx))
+ *          Ampere   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J^{n+1/2})
+ *          Faraday  B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1};  B^{n+1} = average
+ *          moving window: shift by one cell when floor(step dt/dx) increments,
+ *          drop particles with x < 0, inject a cold lattice column on the right.
+ *
+ * The paper (Sec. 2.1) names only "a traditional 2nd order scheme"; the schemes are
+ * the textbook ones: Yee 1966; Boris 1970; Esirkepov 2001 (Comput. Phys. Commun.
+ * 135, 144), Eqs. for W and the cumulative current; quadratic B-spline shapes.
+ */
+#include "pic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* stagger bits (x, y, z) of Ex, Ey, Ez, Bx, By, Bz; J uses the first three */
+static const int STAG[6][3] = {
+    {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+struct orc_sim {
+    orc_config c;
+    long long ncell;
+    double* E[3];
+    double* Bh[3]; /* B^{n+1/2} */
+    double* Bn[3]; /* B^n, used by the push */
+    double* J[3];
+    double* rho_bg;
+    long long np, cap;
+    double *x, *y, *z, *ux, *uy, *uz, *w;
+    int* id;
+    long long step, nshift, next_id;
+};
+
+/* ------------------------------------------------------------------ helpers */
+
+static long wrap(long i, long n) { return ((i % n) + n) % n; }
+
+/* flat index of (i, j, k) with the boundary rule; -1 = outside a window x axis */
+static long long flat(const orc_config* c, long i, long j, long k) {
+    if (c->window) {
+        if (i < 0 || i >= c->n[0]) return -1;
+    } else {
+        i = wrap(i, c->n[0]);
+    }
+    j = wrap(j, c->n[1]);
+    k = wrap(k, c->n[2]);
+    return ((long long)k * c->n[1] + j) * c->n[0] + i;
+}
+
+static double at(const orc_config* c, const double* a, long i, long j, long k) {
+    long long t = flat(c, i, j, k);
+    return t < 0 ? 0.0 : a[t];
+}
+
+static void add_at(const orc_config* c, double* a, long i, long j, long k, double v) {
+    long long t = flat(c, i, j, k);
+    if (t >= 0) a[t] += v;
+}
+
+long long orc_shift_count(const orc_config* c, long long step) {
+    return (long long)floor((double)step * c->dt / c->d[0]);
+}
+
+/* ------------------------------------------------------------------ shapes */
+
+long orc_shape2(double xi, double S[3]) {
+    double node = floor(xi + 0.5);
+    double delta = xi - node; /* in [-1/2, 1/2] */
+    S[0] = 0.5 * (0.5 - delta) * (0.5 - delta);
+    S[1] = 0.75 - delta * delta;
+    S[2] = 0.5 * (0.5 + delta) * (0.5 + delta);
+    return (long)node;
+}
+
+/* ------------------------------------------------------------------ Boris */
+
+void orc_boris(double q, double m, double dt, const double E[3], const double B[3],
+               double u[3]) {
+    double eps = q * dt / (2.0 * m);
+    double um[3], t[3], s[3], up[3], uq[3];
+    for (int a = 0; a < 3; a++) um[a] = u[a] + eps * E[a];
+    double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    for (int a = 0; a < 3; a++) t[a] = eps * B[a] / gm;
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int a = 0; a < 3; a++) s[a] = 2.0 * t[a] / (1.0 + t2);
+    /* u' = u- + u- x t */
+    up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    /* u+ = u- + u' x s */
+    uq[0] = um[0] + (up[1] * s[2] - up[2] * s[1]);
+    uq[1] = um[1] + (up[2] * s[0] - up[0] * s[2]);
+    uq[2] = um[2] + (up[0] * s[1] - up[1] * s[0]);
+    for (int a = 0; a < 3; a++) u[a] = uq[a] + eps * E[a];
+}
+
+/* ------------------------------------------------------------------ interpolation */
+
+void orc_interp(const orc_config* c, const double* const F[6], const double pos[3],
+                double out[6]) {
+    for (int comp = 0; comp < 6; comp++) {
+        long node[3] = {0, 0, 0};
+        double S[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
+        for (int a = 0; a < c->dims; a++) {
+            double xi = pos[a] / c->d[a] - 0.5 * STAG[comp][a];
+            node[a] = orc_shape2(xi, S[a]);
+        }
+        int kz = c->dims == 3 ? 1 : 0;
+        double sum = 0.0;
+        for (int k = -kz; k <= kz; k++)
+            for (int j = -1; j <= 1; j++)
+                for (int i = -1; i <= 1; i++)
+                    sum += S[0][i + 1] * S[1][j + 1] * S[2][k + 1] *
+                           at(c, F[comp], node[0] + i, node[1] + j, node[2] + k);
+        out[comp] = sum;
+    }
+}
+
+/* ------------------------------------------------------------------ Esirkepov */
+
+/* S0, S1 on the five primal nodes node0-2 .. node0+2 around the old nearest node;
+ * returns 0, or -1 if the particle moved by more than one node. */
+static int esirkepov_shapes(double xi0, double xi1, long* node0, double S0[5],
+                            double DS[5]) {
+    double s[3], S1[5] = {0, 0, 0, 0, 0};
+    *node0 = orc_shape2(xi0, s);
+    S0[0] = 0.0;
+    S0[1] = s[0];
+    S0[2] = s[1];
+    S0[3] = s[2];
+    S0[4] = 0.0;
+    long node1 = orc_shape2(xi1, s);
+    long shift = node1 - *node0;
+    if (shift < -1 || shift > 1) return -1;
+    for (int b = 0; b < 3; b++) S1[shift + 1 + b] = s[b];
+    for (int k = 0; k < 5; k++) DS[k] = S1[k] - S0[k];
+    return 0;
+}
+
+static int deposit2d(const orc_config* c, const double pos0[3], const double pos1[3],
+                     double vz, double qw, double* const J[3]) {
+    long n0[2];
+    double S0[2][5], DS[2][5];
+    for (int a = 0; a < 2; a++)
+        if (esirkepov_shapes(pos0[a] / c->d[a], pos1[a] / c->d[a], &n0[a], S0[a], DS[a]))
+            return -1;
+    double dV = c->d[0] * c->d[1];
+    double cx = -qw / dV * c->d[0] / c->dt;
+    double cy = -qw / dV * c->d[1] / c->dt;
+    double cz = qw / dV * vz;
+    /* Jx at (i+1/2, j): running sum of Wx = DSx (S0y + DSy/2) along +x */
+    for (int l = 0; l < 5; l++) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; k++) {
+            acc += DS[0][k] * (S0[1][l] + 0.5 * DS[1][l]);
+            add_at(c, J[0], n0[0] + k - 2, n0[1] + l - 2, 0, cx * acc);
+        }
+    }
+    /* Jy at (i, j+1/2): running sum of Wy = DSy (S0x + DSx/2) along +y */
+    for (int k = 0; k < 5; k++) {
+        double acc = 0.0;
+        for (int l = 0; l < 4; l++) {
+            acc += DS[1][l] * (S0[0][k] + 0.5 * DS[0][k]);
+            add_at(c, J[1], n0[0] + k - 2, n0[1] + l - 2, 0, cy * acc);
+        }
+    }
+    /* Jz at nodes: vz times the path-averaged shape Wz */
+    for (int l = 0; l < 5; l++)
+        for (int k = 0; k < 5; k++) {
+            double wz = S0[0][k] * S0[1][l] + 0.5 * DS[0][k] * S0[1][l] +
+                        0.5 * S0[0][k] * DS[1][l] + DS[0][k] * DS[1][l] / 3.0;
+            add_at(c, J[2], n0[0] + k - 2, n0[1] + l - 2, 0, cz * wz);
+        }
+    return 0;
+}
+
+/* 3D: W_a = DS_a (S0_b S0_c + DS_b S0_c/2 + S0_b DS_c/2 + DS_b DS_c/3) for the two
+ * other axes b, c; J_a is the running sum of -(qw/dV)(d_a/dt) W_a along +a. */
+static int deposit3d(const orc_config* c, const double pos0[3], const double pos1[3],
+                     double qw, double* const J[3]) {
+    long n0[3];
+    double S0[3][5], DS[3][5];
+    for (int a = 0; a < 3; a++)
+        if (esirkepov_shapes(pos0[a] / c->d[a], pos1[a] / c->d[a], &n0[a], S0[a], DS[a]))
+            return -1;
+    double dV = c->d[0] * c->d[1] * c->d[2];
+    for (int a = 0; a < 3; a++) {
+        int b = (a + 1) % 3, e = (a + 2) % 3;
+        double coef = -qw / dV * c->d[a] / c->dt;
+        for (int ie = 0; ie < 5; ie++)
+            for (int ib = 0; ib < 5; ib++) {
+                double acc = 0.0;
+                for (int ia = 0; ia < 4; ia++) {
+                    double w = DS[a][ia] *
+                               (S0[b][ib] * S0[e][ie] + 0.5 * DS[b][ib] * S0[e][ie] +
+                                0.5 * S0[b][ib] * DS[e][ie] + DS[b][ib] * DS[e][ie] / 3.0);
+                    acc += w;
+                    long idx[3];
+                    idx[a] = n0[a] + ia - 2;
+                    idx[b] = n0[b] + ib - 2;
+                    idx[e] = n0[e] + ie - 2;
+                    add_at(c, J[a], idx[0], idx[1], idx[2], coef * acc);
+                }
+            }
+    }
+    return 0;
+}
+
+void orc_deposit(const orc_config* c, const double pos0[3], const double pos1[3],
+                 double vz, double qw, double* const J[3]) {
+    if (c->dims == 2)
+        deposit2d(c, pos0, pos1, vz, qw, J);
+    else
+        deposit3d(c, pos0, pos1, qw, J);
+}
+
+void orc_rho(const orc_config* c, long long n, const double* x, const double* y,
+             const double* z, const double* w, double q, double* rho) {
+    double dV = c->d[0] * c->d[1] * (c->dims == 3 ? c->d[2] : 1.0);
+    for (long long p = 0; p < n; p++) {
+        double pos[3] = {x[p], y[p], c->dims == 3 ? z[p] : 0.0};
+        long node[3] = {0, 0, 0};
+        double S[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
+        for (int a = 0; a < c->dims; a++) node[a] = orc_shape2(pos[a] / c->d[a], S[a]);
+        int kz = c->dims == 3 ? 1 : 0;
+        for (int k = -kz; k <= kz; k++)
+            for (int j = -1; j <= 1; j++)
+                for (int i = -1; i <= 1; i++)
+                    add_at(c, rho, node[0] + i, node[1] + j, node[2] + k,
+                           q * w[p] / dV * S[0][i + 1] * S[1][j + 1] * S[2][k + 1]);
+    }
+}
+
+/* ------------------------------------------------------------------ Yee */
+
+void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
+               const double* const J[3]) {
+    double dt = c->dt, dx = c->d[0], dy = c->d[1], dz = c->d[2];
+    int d3 = c->dims == 3;
+    for (long k = 0; k < c->n[2]; k++)
+        for (long j = 0; j < c->n[1]; j++)
+            for (long i = 0; i < c->n[0]; i++) {
+                long long t = flat(c, i, j, k);
+                const double *Bx = B[0], *By = B[1], *Bz = B[2];
+                double cx = (at(c, Bz, i, j, k) - at(c, Bz, i, j - 1, k)) / dy;
+                double cy = -(at(c, Bz, i, j, k) - at(c, Bz, i - 1, j, k)) / dx;
+                double cz = (at(c, By, i, j, k) - at(c, By, i - 1, j, k)) / dx -
+                            (at(c, Bx, i, j, k) - at(c, Bx, i, j - 1, k)) / dy;
+                if (d3) {
+                    cx -= (at(c, By, i, j, k) - at(c, By, i, j, k - 1)) / dz;
+                    cy += (at(c, Bx, i, j, k) - at(c, Bx, i, j, k - 1)) / dz;
+                }
+                E[0][t] += dt * (cx - J[0][t]);
+                E[1][t] += dt * (cy - J[1][t]);
+                E[2][t] += dt * (cz - J[2][t]);
+            }
+}
+
+void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]) {
+    double dt = c->dt, dx = c->d[0], dy = c->d[1], dz = c->d[2];
+    int d3 = c->dims == 3;
+    for (long k = 0; k < c->n[2]; k++)
+        for (long j = 0; j < c->n[1]; j++)
+            for (long i = 0; i < c->n[0]; i++) {
+                long long t = flat(c, i, j, k);
+                const double *Ex = E[0], *Ey = E[1], *Ez = E[2];
+                double cx = (at(c, Ez, i, j + 1, k) - at(c, Ez, i, j, k)) / dy;
+                double cy = -(at(c, Ez, i + 1, j, k) - at(c, Ez, i, j, k)) / dx;
+                double cz = (at(c, Ey, i + 1, j, k) - at(c, Ey, i, j, k)) / dx -
+                            (at(c, Ex, i, j + 1, k) - at(c, Ex, i, j, k)) / dy;
+                if (d3) {
+                    cx -= (at(c, Ey, i, j, k + 1) - at(c, Ey, i, j, k)) / dz;
+                    cy += (at(c, Ex, i, j, k + 1) - at(c, Ex, i, j, k)) / dz;
+                }
+                B[0][t] -= dt * cx;
+                B[1][t] -= dt * cy;
+                B[2][t] -= dt * cz;
+            }
+}
+
+void orc_div_e(const orc_config* c, const double* const E[3], double* out) {
+    for (long k = 0; k < c->n[2]; k++)
+        for (long j = 0; j < c->n[1]; j++)
+            for (long i = 0; i < c->n[0]; i++) {
+                double v = (at(c, E[0], i, j, k) - at(c, E[0], i - 1, j, k)) / c->d[0] +
+                           (at(c, E[1], i, j, k) - at(c, E[1], i, j - 1, k)) / c->d[1];
+                if (c->dims == 3)
+                    v += (at(c, E[2], i, j, k) - at(c, E[2], i, j, k - 1)) / c->d[2];
+                out[flat(c, i, j, k)] = v;
+            }
+}
+
+/* ------------------------------------------------------------------ simulation */
+
+static int valid_config(const orc_config* c) {
+    if (c->dims != 2 && c->dims != 3) return 0;
+    if (c->dims == 2 && c->n[2] != 1) return 0;
+    for (int a = 0; a < c->dims; a++)
+        if (c->n[a] < 1 || !(c->d[a] > 0)) return 0;
+    if (!(c->dt > 0) || !(c->m > 0)) return 0;
+    for (int a = 0; a < c->dims; a++)
+        if (c->dt >= c->d[a]) return 0; /* displacement must stay below one cell */
+    return 1;
+}
+
+orc_sim* orc_create(const orc_config* c, long long capacity) {
+    if (!valid_config(c) || capacity < 0) return NULL;
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    s->c = *c;
+    s->ncell = (long long)c->n[0] * c->n[1] * c->n[2];
+    for (int a = 0; a < 3; a++) {
+        s->E[a] = (double*)calloc(s->ncell, sizeof(double));
+        s->Bh[a] = (double*)calloc(s->ncell, sizeof(double));
+        s->Bn[a] = (double*)calloc(s->ncell, sizeof(double));
+        s->J[a] = (double*)calloc(s->ncell, sizeof(double));
+    }
+    s->rho_bg = (double*)calloc(s->ncell, sizeof(double));
+    s->cap = capacity;
+    long long m = capacity > 0 ? capacity : 1;
+    s->x = (double*)calloc(m, sizeof(double));
+    s->y = (double*)calloc(m, sizeof(double));
+    s->z = (double*)calloc(m, sizeof(double));
+    s->ux = (double*)calloc(m, sizeof(double));
+    s->uy = (double*)calloc(m, sizeof(double));
+    s->uz = (double*)calloc(m, sizeof(double));
+    s->w = (double*)calloc(m, sizeof(double));
+    s->id = (int*)calloc(m, sizeof(int));
+    return s;
+}
+
+void orc_destroy(orc_sim* s) {
+    if (!s) return;
+    for (int a = 0; a < 3; a++) {
+        free(s->E[a]);
+        free(s->Bh[a]);
+        free(s->Bn[a]);
+        free(s->J[a]);
+    }
+    free(s->rho_bg);
+    free(s->x);
+    free(s->y);
+    free(s->z);
+    free(s->ux);
+    free(s->uy);
+    free(s->uz);
+    free(s->w);
+    free(s->id);
+    free(s);
+}
+
+int orc_set_particles(orc_sim* s, long long n, const double* x, const double* y,
+                      const double* z, const double* ux, const double* uy,
+                      const double* uz, const double* w, const int* id) {
+    if (n < 0 || n > s->cap) return -1;
+    s->np = n;
+    int maxid = -1;
+    for (long long p = 0; p < n; p++) {
+        s->x[p] = x[p];
+        s->y[p] = y[p];
+        s->z[p] = z ? z[p] : 0.0;
+        s->ux[p] = ux[p];
+        s->uy[p] = uy[p];
+        s->uz[p] = uz[p];
+        s->w[p] = w[p];
+        s->id[p] = id[p];
+        if (id[p] > maxid) maxid = id[p];
+    }
+    s->next_id = (long long)maxid + 1;
+    return 0;
+}
+
+long long orc_num_particles(const orc_sim* s) { return s->np; }
+long long orc_steps_done(const orc_sim* s) { return s->step; }
+long long orc_shifts_done(const orc_sim* s) { return s->nshift; }
+
+int orc_get_particles(const orc_sim* s, double* x, double* y, double* z, double* ux,
+                      double* uy, double* uz, double* w, int* id) {
+    for (long long p = 0; p < s->np; p++) {
+        x[p] = s->x[p];
+        y[p] = s->y[p];
+        z[p] = s->z[p];
+        ux[p] = s->ux[p];
+        uy[p] = s->uy[p];
+        uz[p] = s->uz[p];
+        w[p] = s->w[p];
+        id[p] = s->id[p];
+    }
+    return 0;
+}
+
+int orc_set_fields(orc_sim* s, const double* Ex, const double* Ey, const double* Ez,
+                   const double* Bx, const double* By, const double* Bz) {
+    const double* E[3] = {Ex, Ey, Ez};
+    const double* B[3] = {Bx, By, Bz};
+    size_t bytes = (size_t)s->ncell * sizeof(double);
+    for (int a = 0; a < 3; a++) {
+        memcpy(s->E[a], E[a], bytes);
+        memcpy(s->Bh[a], B[a], bytes);
+        memcpy(s->Bn[a], B[a], bytes);
+    }
+    return 0;
+}
+
+int orc_get_fields(const orc_sim* s, double* out12) {
+    size_t nc = (size_t)s->ncell;
+    for (int a = 0; a < 3; a++) {
+        memcpy(out12 + (0 + a) * nc, s->E[a], nc * sizeof(double));
+        memcpy(out12 + (3 + a) * nc, s->Bh[a], nc * sizeof(double));
+        memcpy(out12 + (6 + a) * nc, s->Bn[a], nc * sizeof(double));
+        memcpy(out12 + (9 + a) * nc, s->J[a], nc * sizeof(double));
+    }
+    return 0;
+}
+
+int orc_set_rho_bg(orc_sim* s, const double* rho_bg) {
+    if (rho_bg) {
+        memcpy(s->rho_bg, rho_bg, (size_t)s->ncell * sizeof(double));
+    } else {
+        memset(s->rho_bg, 0, (size_t)s->ncell * sizeof(double));
+        orc_rho(&s->c, s->np, s->x, s->y, s->z, s->w, s->c.q, s->rho_bg);
+        for (long long t = 0; t < s->ncell; t++) s->rho_bg[t] = -s->rho_bg[t];
+    }
+    return 0;
+}
+
+/* stable compaction: keep particle p iff keep[p] != 0 */
+static void compact(orc_sim* s, const unsigned char* keep) {
+    long long o = 0;
+    for (long long p = 0; p < s->np; p++) {
+        if (!keep[p]) continue;
+        s->x[o] = s->x[p];
+        s->y[o] = s->y[p];
+        s->z[o] = s->z[p];
+        s->ux[o] = s->ux[p];
+        s->uy[o] = s->uy[p];
+        s->uz[o] = s->uz[p];
+        s->w[o] = s->w[p];
+        s->id[o] = s->id[p];
+        o++;
+    }
+    s->np = o;
+}
+
+static double density(const orc_config* c, double x_lab) {
+    double f = (x_lab - c->ramp_x0) / c->ramp_len;
+    if (f < 0.0) f = 0.0;
+    if (f > 1.0) f = 1.0;
+    return c->n0 * f;
+}
+
+/* Window shift by one cell: fields move one cell towards -x, the uncovered column
+ * is zero; particles move by -dx, those with x < 0 are dropped; the new rightmost
+ * cell column is filled with a cold lattice weighted by the lab-frame density. */
+static int window_shift(orc_sim* s) {
+    const orc_config* c = &s->c;
+    long nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    double* arrays[9] = {s->E[0], s->E[1], s->E[2], s->Bh[0], s->Bh[1],
+                         s->Bh[2], s->Bn[0], s->Bn[1], s->Bn[2]};
+    for (int a = 0; a < 9; a++)
+        for (long k = 0; k < nz; k++)
+            for (long j = 0; j < ny; j++) {
+                double* row = arrays[a] + ((long long)k * ny + j) * nx;
+                for (long i = 0; i < nx - 1; i++) row[i] = row[i + 1];
+                row[nx - 1] = 0.0;
+            }
+    s->nshift++;
+    unsigned char* keep = (unsigned char*)malloc((size_t)(s->np > 0 ? s->np : 1));
+    for (long long p = 0; p < s->np; p++) {
+        s->x[p] -= c->d[0];
+        keep[p] = s->x[p] >= 0.0;
+    }
+    compact(s, keep);
+    free(keep);
+    int px = c->inject_ppc[0], py = c->inject_ppc[1];
+    int pz = c->dims == 3 ? c->inject_ppc[2] : 1;
+    long nzz = c->dims == 3 ? nz : 1;
+    double dV = c->d[0] * c->d[1] * (c->dims == 3 ? c->d[2] : 1.0);
+    double ppc = (double)px * py * pz;
+    for (long k = 0; k < nzz; k++)
+        for (long j = 0; j < ny; j++)
+            for (int cz = 0; cz < pz; cz++)
+                for (int b = 0; b < py; b++)
+                    for (int a = 0; a < px; a++) {
+                        double xw = ((double)(nx - 1) + ((double)a + 0.5) / px) * c->d[0];
+                        double xl = xw + (double)s->nshift * c->d[0];
+                        double dens = density(c, xl);
+                        if (!(dens > 0.0)) continue;
+                        if (s->np >= s->cap) return -1;
+                        long long lat = (((long long)(k * ny + j) * pz + cz) * py + b) * px + a;
+                        long long p = s->np++;
+                        s->x[p] = xw;
+                        s->y[p] = ((double)j + ((double)b + 0.5) / py) * c->d[1];
+                        s->z[p] = c->dims == 3
+                                      ? ((double)k + ((double)cz + 0.5) / pz) * c->d[2]
+                                      : 0.0;
+                        s->ux[p] = s->uy[p] = s->uz[p] = 0.0;
+                        s->w[p] = dens * dV / ppc;
+                        s->id[p] = (int)(s->next_id + lat);
+                    }
+    s->next_id += (long long)nzz * ny * pz * py * px;
+    return 0;
+}
+
+static void wrap_pos(double* v, double L) {
+    if (*v < 0.0) *v += L;
+    if (*v >= L) *v -= L;
+}
+
+int orc_step(orc_sim* s, int nsteps) {
+    const orc_config* c = &s->c;
+    int dims = c->dims;
+    double L[3] = {c->n[0] * c->d[0], c->n[1] * c->d[1], c->n[2] * c->d[2]};
+    double* Bold[3];
+    for (int a = 0; a < 3; a++) Bold[a] = (double*)malloc((size_t)s->ncell * sizeof(double));
+    int rc = 0;
+    for (int it = 0; it < nsteps && rc == 0; it++) {
+        for (int a = 0; a < 3; a++) memset(s->J[a], 0, (size_t)s->ncell * sizeof(double));
+        const double* F[6] = {s->E[0], s->E[1], s->E[2], s->Bn[0], s->Bn[1], s->Bn[2]};
+        for (long long p = 0; p < s->np; p++) {
+            double pos0[3] = {s->x[p], s->y[p], s->z[p]};
+            double EB[6];
+            orc_interp(c, F, pos0, EB);
+            double u[3] = {s->ux[p], s->uy[p], s->uz[p]};
+            orc_boris(c->q, c->m, c->dt, EB, EB + 3, u);
+            double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            double pos1[3] = {pos0[0], pos0[1], pos0[2]};
+            for (int a = 0; a < dims; a++) pos1[a] = pos0[a] + c->dt * u[a] / gamma;
+            int bad = dims == 2 ? deposit2d(c, pos0, pos1, u[2] / gamma, c->q * s->w[p], s->J)
+                                : deposit3d(c, pos0, pos1, c->q * s->w[p], s->J);
+            if (bad) rc = -2;
+            s->x[p] = pos1[0];
+            s->y[p] = pos1[1];
+            s->z[p] = pos1[2];
+            s->ux[p] = u[0];
+            s->uy[p] = u[1];
+            s->uz[p] = u[2];
+        }
+        unsigned char* keep = (unsigned char*)malloc((size_t)(s->np > 0 ? s->np : 1));
+        for (long long p = 0; p < s->np; p++) {
+            keep[p] = 1;
+            if (c->window)
+                keep[p] = s->x[p] >= 0.0 && s->x[p] < L[0];
+            else
+                wrap_pos(&s->x[p], L[0]);
+            wrap_pos(&s->y[p], L[1]);
+            if (dims == 3) wrap_pos(&s->z[p], L[2]);
+        }
+        compact(s, keep);
+        free(keep);
+        orc_yee_e(c, s->E, (const double* const*)s->Bh, (const double* const*)s->J);
+        for (int a = 0; a < 3; a++) memcpy(Bold[a], s->Bh[a], (size_t)s->ncell * sizeof(double));
+        orc_yee_b(c, (const double* const*)s->E, s->Bh);
+        for (int a = 0; a < 3; a++)
+            for (long long t = 0; t < s->ncell; t++) s->Bn[a][t] = 0.5 * (Bold[a][t] + s->Bh[a][t]);
+        s->step++;
+        if (c->window && orc_shift_count(c, s->step) > orc_shift_count(c, s->step - 1))
+            if (window_shift(s)) rc = -3;
+    }
+    for (int a = 0; a < 3; a++) free(Bold[a]);
+    return rc;
+}
+
+void orc_energy(const orc_sim* s, double out[3]) {
+    const orc_config* c = &s->c;
+    double dV = c->d[0] * c->d[1] * (c->dims == 3 ? c->d[2] : 1.0);
+    double we = 0, wb = 0, wk = 0;
+    for (long long t = 0; t < s->ncell; t++) {
+        for (int a = 0; a < 3; a++) {
+            we += s->E[a][t] * s->E[a][t];
+            wb += s->Bn[a][t] * s->Bn[a][t];
+        }
+    }
+    for (long long p = 0; p < s->np; p++) {
+        double g = sqrt(1.0 + s->ux[p] * s->ux[p] + s->uy[p] * s->uy[p] + s->uz[p] * s->uz[p]);
+        wk += s->w[p] * c->m * (g - 1.0);
+    }
+    out[0] = 0.5 * we * dV;
+    out[1] = 0.5 * wb * dV;
+    out[2] = wk;
+}
+
+void orc_gauss(const orc_sim* s, double* out) {
+    const orc_config* c = &s->c;
+    double* rho = (double*)calloc((size_t)s->ncell, sizeof(double));
+    orc_rho(c, s->np, s->x, s->y, s->z, s->w, c->q, rho);
+    orc_div_e(c, (const double* const*)s->E, out);
+    for (long long t = 0; t < s->ncell; t++) out[t] -= rho[t] + s->rho_bg[t];
+    free(rho);
+}

@@ -1,0 +1,117 @@
+/*
+ * Plain, slow FP64 CPU oracle for the explicit electromagnetic particle-in-cell
+ * (PIC) cycle of patch-based PIC codes (Sec. 3, "The importance of computational
+ * load-management", and Sec. 3.1 "Dynamic load balancing": a PIC code whose cost is
+ * the per-super-particle (SP) loop plus the field update).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may include, link, call or
+ * execute this code; only the test suite, the smoke check and the bench's CPU
+ * baseline do. It shares no code with the CUDA implementation.
+ *
+ * The paper names the field solver only as "a traditional 2nd order scheme" (Sec. 2.1)
+ * and prints no PIC equations, so every formula here is the standard published form:
+ *   - Yee (1966) staggered FDTD for Faraday and Ampere,
+ *   - quadratic B-spline (order-2) shape functions,
+ *   - the relativistic Boris (1970) rotation,
+ *   - Esirkepov (2001) charge-conserving current deposition.
+ * Each function below says which of these it follows. Units are normalised:
+ * c = eps0 = 1; dE/dt = curl B - J, dB/dt = -curl E, div E = rho.
+ *
+ * Layout: every field component is a plain row-major array [nz][ny][nx] (x fastest;
+ * nz = 1 in 2D) with NO guard cells. Array index i of a component stands for the
+ * position (i + s/2) * d, where s is that component's stagger bit along the axis:
+ *      Ex (1,0,0)  Ey (0,1,0)  Ez (0,0,1)   (J like E)
+ *      Bx (0,1,1)  By (1,0,1)  Bz (1,1,0)   (rho on nodes: (0,0,0))
+ * Periodic axes wrap indices; along a moving-window x axis a value outside [0, nx)
+ * is zero (fields) or dropped (current).
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_config {
+    int dims;           /* 2 (2D3V) or 3 (3D3V) */
+    int n[3];           /* cells per axis (n[2] = 1 in 2D) */
+    double d[3];        /* cell sizes */
+    double dt;          /* time step */
+    int window;         /* 0: x periodic; 1: x is a moving window at c (y, z periodic) */
+    double q, m;        /* species charge and mass (electrons: -1, 1) */
+    double n0;          /* injected plasma density (window only) */
+    double ramp_x0;     /* lab-frame x where the linear density ramp starts */
+    double ramp_len;    /* ramp length; n(x) = n0 * clamp((x - ramp_x0)/ramp_len, 0, 1) */
+    int inject_ppc[3];  /* injected lattice per cell (window only) */
+} orc_config;
+
+typedef struct orc_sim orc_sim;
+
+/* ---- building blocks (each used by the full step and pinned on its own) ---- */
+
+/* Quadratic B-spline weights of a particle at coordinate xi (in cell units, already
+ * shifted by -1/2 for a dual axis): nearest node i = floor(xi + 1/2),
+ * delta = xi - i, S[0..2] = weights of nodes i-1, i, i+1. Returns i. */
+long orc_shape2(double xi, double S[3]);
+
+/* Relativistic Boris rotation: u^{n-1/2} -> u^{n+1/2} in the fields E, B. */
+void orc_boris(double q, double m, double dt, const double E[3], const double B[3],
+               double u[3]);
+
+/* Order-2 interpolation of the six staggered components at a position.
+ * F = {Ex,Ey,Ez,Bx,By,Bz}; out = the six values. */
+void orc_interp(const orc_config* c, const double* const F[6], const double pos[3],
+                double out[6]);
+
+/* Esirkepov deposition of one particle moving pos0 -> pos1 (physical units,
+ * |displacement| < one cell per axis), charge*weight qw, in-plane-unresolved
+ * velocity vz (2D only). Adds into J = {Jx,Jy,Jz}. */
+void orc_deposit(const orc_config* c, const double pos0[3], const double pos1[3],
+                 double vz, double qw, double* const J[3]);
+
+/* Order-2 charge density of n particles (adds into rho). */
+void orc_rho(const orc_config* c, long long n, const double* x, const double* y,
+             const double* z, const double* w, double q, double* rho);
+
+/* Yee half-updates: E += dt (curl B - J); B -= dt curl E. In place. */
+void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
+               const double* const J[3]);
+void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]);
+
+/* div E on nodes (backward differences of the staggered E). */
+void orc_div_e(const orc_config* c, const double* const E[3], double* out);
+
+/* Number of window shifts after `step` steps: floor(step * dt / dx[0]). */
+long long orc_shift_count(const orc_config* c, long long step);
+
+/* ---- a whole simulation ---- */
+orc_sim* orc_create(const orc_config* c, long long capacity);
+void orc_destroy(orc_sim* s);
+/* Particles: physical positions (z ignored in 2D), momenta u = gamma v, weights, ids. */
+int orc_set_particles(orc_sim* s, long long n, const double* x, const double* y,
+                      const double* z, const double* ux, const double* uy,
+                      const double* uz, const double* w, const int* id);
+long long orc_num_particles(const orc_sim* s);
+int orc_get_particles(const orc_sim* s, double* x, double* y, double* z, double* ux,
+                      double* uy, double* uz, double* w, int* id);
+/* E at t = 0 and B at t = +dt/2; the first push uses that B at integer time too. */
+int orc_set_fields(orc_sim* s, const double* Ex, const double* Ey, const double* Ez,
+                   const double* Bx, const double* By, const double* Bz);
+/* Copies out E^n, B^{n+1/2}, B^n (= the average used by the push) and the last
+ * step's J^{n-1/2}: 12 arrays of ncell each, in that order. */
+int orc_get_fields(const orc_sim* s, double* out12);
+/* Background (immobile ion) charge density on nodes; NULL = minus the electron
+ * density at the time of the call. */
+int orc_set_rho_bg(orc_sim* s, const double* rho_bg);
+int orc_step(orc_sim* s, int nsteps);
+long long orc_steps_done(const orc_sim* s);
+long long orc_shifts_done(const orc_sim* s);
+/* {W_E, W_B, W_kin} at integer time (B^n for W_B). */
+void orc_energy(const orc_sim* s, double out[3]);
+/* div E - rho_e - rho_bg on nodes (ncell values). */
+void orc_gauss(const orc_sim* s, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
