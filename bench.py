@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Particle pushes/s of the GB300 patch-PIC hot path on the 2D LWFA workload.
+
+One "step" is one pass of the whole hot path (work-queue build, particle
+interpolation + Boris push + Esirkepov deposition, window injection, particle
+exchange, Yee E and B) over the 2048 x 512-cell LWFA window: 4 particles per cell,
+window full of plasma (4 194 304 particles), a0 = 4 Gaussian laser. Prints one JSON
+line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the sim's
+stream with a synchronize (and a barrier under torchrun) on both sides; the
+working set (particles + fields) is larger than the 129 MB L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle pushes/s (interp+push+deposit) vs HBM roofline; served p50/p99 sim latency"
+UNIT = "pushes/s"
+# FP64 dense rate of GB300 from the unit counts and clock (nominal 1.25 TFLOP/s)
+FP64_NOMINAL_TFLOPS = 1.25
+# Algorithmic FP64 flops of one 2D push (FMA = 2 flops), counted from the kernel:
+# shapes 40, interpolation 126, Boris 70, move 7, new shapes + DS 30, deposit 97.
+FLOPS_PER_PUSH_2D = 370
+# Algorithmic HBM bytes of the particle kernel per push (read + write of the state once,
+# weight read once; fields read once and J written once per cell, at 4 particles/cell)
+BYTES_PER_PUSH = {"f64": 2 * (16 + 24) + 8 + (48 + 24) / 4.0,
+                  "f32": 2 * (4 + 8 + 12) + 4 + (24 + 24) / 4.0}
+KERNELS_PER_STEP = 7  # queue, push, inject, exchange, yee_e, yee_b, end_step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-variant", action="store_true", help="skip the other precision")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(nx, ny):
+    from paper_1511_03878_gb300 import inputs
+
+    # the window full of plasma: density ramp placed before x = 0
+    w = inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
+    return w
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed work runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if n_gpus > 1 else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        dist.barrier(device_ids=[torch.cuda.current_device()])
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(args, w, precision, K, W, world, clocks=None):
+    """Returns timing + roofline of one precision on this rank's GPU."""
+    import torch
+
+    from paper_1511_03878_gb300 import binding
+
+    prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=prec, capacity=3 * n, chunk=args.chunk)
+    sim.load(w)
+    stream = sim.stream
+    sim.step(W)
+    sim.sync()
+    n0 = sim.num_particles()
+    if clocks:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    if clocks:
+        clocks.stop()
+    sim.sync()  # raises on any latched device error
+    n1 = sim.num_particles()
+    ms = max_over_ranks(ms, world)
+    pushes = K * 0.5 * (n0 + n1)
+    # per-kernel CUDA-event pass (same kernels, same launch shapes) for the roofline
+    prof = sim.profile(K)
+    push_ms = prof["push"] / K
+    dt = "f64" if precision == "fp64" else "f32"
+    n_push = 0.5 * (n0 + n1)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    if precision == "fp64":
+        achieved = FLOPS_PER_PUSH_2D * n_push / (push_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "push2d_kernel<double>",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit counts x clock)",
+                "hbm_frac_of_measured": (BYTES_PER_PUSH[dt] * n_push / (push_ms * 1e-3) / 1e9 / hbm)
+                if hbm else None}
+    else:
+        achieved = BYTES_PER_PUSH[dt] * n_push / (push_ms * 1e-3) / 1e9
+        peak = hbm if hbm else 6800.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "push2d_kernel<float>",
+                "peak_source": "measured" if hbm else "fallback"}
+    out = dict(ms=ms, pushes=pushes, n=n_push, profile={k: v / K for k, v in prof.items()},
+               roofline=roof, push_ms=push_ms)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(args, w, precision, K):
+    """Same metric through the public C ABI with host buffers: load (H2D), K steps,
+    read back the energy and the axis wake field (D2H), all inside the timed region."""
+    import torch
+
+    from paper_1511_03878_gb300 import binding
+
+    prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=prec, capacity=3 * n, chunk=args.chunk)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.load(w)
+    sim.step(K)
+    e = sim.energy()
+    ax = sim.ex_axis()
+    t1 = time.perf_counter()
+    es = 8 if precision == "fp64" else 4
+    cap = 3 * n
+    per_slot = es * (2 + 3 + 1) + 4 + (4 if precision == "fp32" else 0)
+    cfg = sim.cfg
+    fstride = (cfg.n[0] + 4) * (cfg.n[1] + 3)
+    h2d = cap * per_slot + 9 * fstride * es + 5 * sim.npatch * 4
+    d2h = e.nbytes + ax.nbytes
+    sim.close()
+    return dict(value=n * K / (t1 - t0), h2d=h2d / K, d2h=d2h / K, seconds=t1 - t0)
+
+
+def oracle_rate(w, seconds_budget, max_steps=50):
+    """Pushes/s of the FP64 CPU oracle (single thread, as it stands) on a bounded
+    number of steps of the same workload."""
+    import oracle as orc
+
+    p = w["params"]
+    c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+                        m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
+                        inject_ppc=p["inject_ppc"])
+    n = len(w["particles"]["x"])
+    o = orc.OracleSim(c, n + 2 * (max_steps + 2) * p["n"][1] * 4)
+    o.set_particles(w["particles"])
+    o.set_fields(w["E"], w["B"])
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    steps = 1
+    budget_steps = int(max(0, min(max_steps - 1, seconds_budget / max(t1 - t0, 1e-6) - 1)))
+    pushes = n
+    if budget_steps > 0:
+        n1 = o.num_particles()
+        t2 = time.perf_counter()
+        o.step(budget_steps)
+        t3 = time.perf_counter()
+        steps += budget_steps
+        pushes += n1 * budget_steps
+        t1 = t1 + (t3 - t2)
+    return pushes / (t1 - t0), steps, n
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.nx, args.ny)
+    import oracle as orc
+
+    orc.build()
+    p = w["params"]
+    n = len(w["particles"]["x"])
+    c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+                        m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
+                        inject_ppc=p["inject_ppc"])
+    total = args.steps + args.warmup
+    o = orc.OracleSim(c, n + 4 * (total + 2) * p["n"][1] * 4)
+    o.set_particles(w["particles"])
+    o.set_fields(w["E"], w["B"])
+    t0 = time.perf_counter()
+    o.step(1)
+    t_step = time.perf_counter() - t0
+    # each step is a bounded sample: fewer rows of the same window if K+W full steps
+    # would exceed about three minutes
+    frac = min(1.0, 180.0 / max(total * t_step, 1e-9))
+    sample = "full window"
+    if frac < 1.0:
+        ny = max(32, int(p["n"][1] * frac) // 32 * 32)
+        w = workload(args.nx, ny)
+        p = w["params"]
+        n = len(w["particles"]["x"])
+        c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+                            m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
+                            inject_ppc=p["inject_ppc"])
+        o = orc.OracleSim(c, n + 4 * (total + 2) * p["n"][1] * 4)
+        o.set_particles(w["particles"])
+        o.set_fields(w["E"], w["B"])
+        sample = f"{args.nx}x{ny} rows of the window ({n} particles)"
+    o.step(max(0, args.warmup - 1))
+    n0 = o.num_particles()
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    n1 = o.num_particles()
+    value = args.steps * 0.5 * (n0 + n1) / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded LWFA-shaped initial condition)",
+        "config": config_dict(args, "fp64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 C oracle, single thread, {sample}, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, precision):
+    return {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
+            "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
+            "patch": [32, 32], "laser_a0": 4.0, "precision": precision,
+            "mapping": "persistent work queue (largest chunk first)",
+            "chunk": args.chunk or 2048,
+            "l2": "inputs larger than L2 (particles + fields > 129 MB), no flush",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    if rank != 0:
+        __graft_entry__.build()
+
+    w = workload(args.nx, args.ny)
+    clocks = ClockSampler(local)
+    main_run = run_gpu(args, w, args.precision, args.steps, args.warmup, world, clocks)
+    other = "fp32" if args.precision == "fp64" else "fp64"
+    variant = None
+    if not args.no_variant:
+        variant = run_gpu(args, w, other, args.steps, args.warmup, world)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, args.precision, args.steps)
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        rate, steps, n = oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 C oracle, single thread, {steps} steps of the same "
+                         f"LWFA window ({n} particles)"}
+    if rank != 0:
+        return
+    value = world * main_run["pushes"] / (main_run["ms"] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic (seeded LWFA-shaped initial condition, no dataset)",
+        "config": config_dict(args, args.precision),
+        "roofline": main_run["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": ({"value": world * e2e["value"], "unit": UNIT,
+                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+                if e2e else None),
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks.summary(),
+        "kernel_ms_per_step": main_run["profile"],
+        "particles": main_run["n"],
+    }
+    if variant:
+        line["variants"] = {other: {
+            "value": world * variant["pushes"] / (variant["ms"] * 1e-3),
+            "ms_per_step": variant["ms"] / args.steps, "roofline": variant["roofline"],
+            "kernel_ms_per_step": variant["profile"],
+            "dtype": "f64" if other == "fp64" else "f32"}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * pic.h - C ABI of the GB300 (sm_103a) patch-based particle-in-cell hot path.
+ *
+ * What the library computes: the explicit electromagnetic PIC cycle of a patch-based
+ * code (Sec. 3, "The importance of computational load-management"; Sec. 3.1,
+ * "Dynamic load balancing": the simulation domain is cut into many small patches,
+ * each holding the fields and the super-particles (SP) of a sub-domain, and the
+ * load of a patch is its SP count). One step is
+ *   order-2 interpolation of E, B from the Yee grid at each SP, relativistic Boris
+ *   push, Esirkepov charge-conserving current deposition, exchange of SP between
+ *   neighbouring patches, Yee FDTD update of E and B ("a traditional 2nd order
+ *   scheme", Sec. 2.1), and for laser-wakefield runs a moving window with plasma
+ *   injection (Sec. 2.2 setup: laser focused at the foot of a density ramp).
+ * The paper's load-imbalance problem (Sec. 3: up to 40 times the initial SP count
+ * in some regions, Fig. 2 caption) is handled on one GPU by a persistent kernel that
+ * pulls patch chunks from a device work queue ordered by SP count.
+ *
+ * Units are normalised: c = eps0 = 1, dE/dt = curl B - J, dB/dt = -curl E.
+ * Grid staggering (array index i of a component stands for position (i + s/2) d):
+ *   Ex (1,0,0) Ey (0,1,0) Ez (0,0,1) Bx (0,1,1) By (1,0,1) Bz (1,1,0); J like E.
+ * Host field arrays are plain row-major [nz][ny][nx] float64 (nz = 1 in 2D).
+ *
+ * Memory: the caller owns all device memory. pic_required_bytes() gives the size
+ * of one device arena; pic_create() carves everything out of it and never calls
+ * cudaMalloc. The arena must stay valid until pic_destroy(). Host buffers passed
+ * to the library are read or written during the call only and never retained.
+ *
+ * Errors: no exception crosses the ABI. Every call returns a pic_status. Errors
+ * raised on the device (capacity overflow, non-finite particles, an expired
+ * bounded wait) latch in a device status word and are returned by the next call
+ * that synchronises (pic_diag, pic_sync). A failed call leaves the sim destroyable.
+ * pic_last_error() gives a one-line description.
+ *
+ * Threading: a sim is used by one host thread at a time; all its work is ordered
+ * on the CUDA stream given at creation.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_sim pic_sim;
+typedef struct pic_batch pic_batch;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_INVALID = -1,  /* bad argument or configuration */
+    PIC_ERR_NOMEM = -2,    /* arena or output buffer too small */
+    PIC_ERR_CAPACITY = -3, /* a patch or exchange buffer overflowed on the device */
+    PIC_ERR_CUDA = -4,     /* a CUDA runtime call failed */
+    PIC_ERR_NUMERIC = -5,  /* non-finite particle state or a move of a cell or more */
+    PIC_ERR_TIMEOUT = -6   /* a bounded device-side wait expired */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_FP32 = 1 };
+
+/* Work distribution of the particle kernel. */
+enum {
+    PIC_MAP_QUEUE = 0, /* persistent CTAs pull chunks, largest first (default) */
+    PIC_MAP_STATIC = 1 /* one CTA per patch, no chunking (baseline for comparison) */
+};
+
+typedef struct {
+    int dims;           /* 2 (2D3V) or 3 (3D3V) */
+    int n[3];           /* cells per axis; n[2] = 1 in 2D */
+    double d[3];        /* cell sizes */
+    double dt;          /* time step; must be below every d[a] */
+    int patch[3];       /* cells per patch per axis: a multiple of 4, dividing n[a] */
+    int precision;      /* PIC_FP64: FP64 everywhere.  PIC_FP32: FP32 fields and
+                           particles (cell index + FP32 offset), FP64 global current */
+    int window;         /* 0: all axes periodic.  1: x is a moving window at c
+                           (fields zero outside, particles absorbed), y/z periodic */
+    double n0;          /* window only: injected density n(x) = n0 *        */
+    double ramp_x0;     /*   clamp((x_lab - ramp_x0)/ramp_len, 0, 1)          */
+    double ramp_len;    /*                                                    */
+    int inject_ppc[3];  /* window only: injected lattice per cell per axis */
+    double q, m;        /* species charge and mass (electrons: -1, 1) */
+    long long capacity; /* particle slots in the arena (>= the largest count held) */
+    int chunk;          /* work-queue chunk size in particles (0 = 2048) */
+    int mapping;        /* PIC_MAP_QUEUE or PIC_MAP_STATIC */
+} pic_config;
+
+/* Device bytes one arena needs for this configuration (0 if the config is invalid). */
+size_t pic_required_bytes(const pic_config* cfg);
+
+/* Create a sim in a caller-owned device arena (>= pic_required_bytes, 256-byte
+ * aligned). cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all
+ * work of this sim is ordered. On success *out owns host-side state only. */
+pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
+                      void* cuda_stream, pic_sim** out);
+
+/* Load n particles from host SoA arrays (float64 physical positions, momenta
+ * u = gamma v, weights; int32 ids, unique and >= 0). z may be NULL in 2D. Positions
+ * must lie in [0, n[a] d[a]). Particles are binned by patch on the host and copied;
+ * per-patch capacities split the free slots half by count, half evenly.
+ * Returns PIC_ERR_CAPACITY if n > capacity. Resets the step counter to 0. */
+pic_status pic_load_particles(pic_sim* sim, long long n, const double* x, const double* y,
+                              const double* z, const double* ux, const double* uy,
+                              const double* uz, const double* w, const int* id);
+
+/* Load fields from host arrays [nz][ny][nx]: E at t = 0, B at t = +dt/2 (the first
+ * push uses that B at integer time too). rho_bg: immobile background charge on
+ * nodes for the Gauss diagnostic; NULL = minus the charge density of the particles
+ * loaded now. Zeroes the current. */
+pic_status pic_load_fields(pic_sim* sim, const double* const E[3], const double* const B[3],
+                           const double* rho_bg);
+
+/* Enqueue nsteps steps on the sim's stream (asynchronous: returns before the GPU
+ * finishes). Each step is one replay of a CUDA graph of the kernels above. */
+pic_status pic_step(pic_sim* sim, int nsteps);
+
+/* Wait for the sim's stream; returns any latched device error. */
+pic_status pic_sync(pic_sim* sim);
+
+/* Diagnostics (synchronise first, then copy to the host buffer out of out_bytes;
+ * *written = bytes written). Kinds: */
+enum {
+    PIC_DIAG_ENERGY = 0,        /* 3 float64: W_E, W_B (with B^n), W_kin          */
+    PIC_DIAG_GAUSS = 1,         /* ncell float64: div E - rho - rho_bg on nodes    */
+    PIC_DIAG_FIELDS = 2,        /* 12 * ncell float64: E^n, B^{n+1/2}, B^n, last J */
+    PIC_DIAG_PARTICLES = 3,     /* n * 7 float64 (x,y,z,ux,uy,uz,w, each array of n)
+                                   then n int32 ids; sorted by id; x in the window
+                                   frame                                          */
+    PIC_DIAG_NUM_PARTICLES = 4, /* 1 int64                                        */
+    PIC_DIAG_PATCH_COUNTS = 5,  /* npatch int32 (x fastest)                        */
+    PIC_DIAG_STEP = 6,          /* 2 int64: steps taken, window shifts            */
+    PIC_DIAG_EX_AXIS = 7        /* nx float64: Ex on the row (and plane) ny/2      */
+};
+pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);
+
+/* Instrumentation (per-kernel timing): runs nsteps steps with one plain launch per
+ * kernel (no graph) and CUDA events around each kernel on the sim's stream, then
+ * synchronises. ms[0..6] receive the summed times in milliseconds of: work-queue
+ * build, particle push/deposit, window injection, particle exchange, Yee E+B, end of
+ * step, and the whole steps. n_ms must be >= 7. Same kernels and launch shapes as
+ * pic_step; the state advances by nsteps. */
+pic_status pic_profile(pic_sim* sim, int nsteps, double* ms, int n_ms);
+
+/* Destroy the host-side state (synchronises; does not free the arena). */
+pic_status pic_destroy(pic_sim* sim);
+
+/* One-line description of the last error on this sim (never NULL). */
+const char* pic_last_error(const pic_sim* sim);
+
+/* ---- batching: many sims stepped together, one persistent particle launch ----
+ * All sims of a batch share dims and precision; each keeps its own arena, state
+ * and step counter. The batch needs a small arena of its own (work queue). */
+size_t pic_batch_required_bytes(pic_sim* const* sims, int nsims);
+pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
+                            size_t arena_bytes, void* cuda_stream, pic_batch** out);
+pic_status pic_batch_step(pic_batch* batch, int nsteps);
+pic_status pic_batch_destroy(pic_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,315 @@
+"""Thin ctypes binding of libpic.so (include/pic.h): same names, argument
+marshalling only. Every step of the PIC cycle runs in the CUDA library; there is
+no CPU fallback - if the library or a GPU is missing, calls raise.
+
+PyTorch provides the device arena (a uint8 tensor) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpic.so")
+
+PIC_OK, PIC_ERR_INVALID, PIC_ERR_NOMEM, PIC_ERR_CAPACITY = 0, -1, -2, -3
+PIC_ERR_CUDA, PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT = -4, -5, -6
+PIC_FP64, PIC_FP32 = 0, 1
+PIC_MAP_QUEUE, PIC_MAP_STATIC = 0, 1
+(PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_FIELDS, PIC_DIAG_PARTICLES,
+ PIC_DIAG_NUM_PARTICLES, PIC_DIAG_PATCH_COUNTS, PIC_DIAG_STEP, PIC_DIAG_EX_AXIS) = range(8)
+
+STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
+                -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NUMERIC",
+                -6: "PIC_ERR_TIMEOUT"}
+
+# every symbol include/pic.h declares
+EXPORTS = ("pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
+           "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
+           "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
+           "pic_batch_destroy")
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("d", ctypes.c_double * 3),
+        ("dt", ctypes.c_double),
+        ("patch", ctypes.c_int * 3),
+        ("precision", ctypes.c_int),
+        ("window", ctypes.c_int),
+        ("n0", ctypes.c_double),
+        ("ramp_x0", ctypes.c_double),
+        ("ramp_len", ctypes.c_double),
+        ("inject_ppc", ctypes.c_int * 3),
+        ("q", ctypes.c_double),
+        ("m", ctypes.c_double),
+        ("capacity", ctypes.c_longlong),
+        ("chunk", ctypes.c_int),
+        ("mapping", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libpic.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        cfgp = ctypes.POINTER(PicConfig)
+        L.pic_required_bytes.restype = ctypes.c_size_t
+        L.pic_required_bytes.argtypes = [cfgp]
+        L.pic_create.restype = ctypes.c_int
+        L.pic_create.argtypes = [cfgp, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.pic_load_particles.restype = ctypes.c_int
+        L.pic_load_particles.argtypes = [vp, ctypes.c_longlong] + [dp] * 7 + [ip]
+        L.pic_load_fields.restype = ctypes.c_int
+        L.pic_load_fields.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), dp]
+        L.pic_step.restype = ctypes.c_int
+        L.pic_step.argtypes = [vp, ctypes.c_int]
+        L.pic_sync.restype = ctypes.c_int
+        L.pic_sync.argtypes = [vp]
+        L.pic_diag.restype = ctypes.c_int
+        L.pic_diag.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.pic_profile.restype = ctypes.c_int
+        L.pic_profile.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+        L.pic_destroy.restype = ctypes.c_int
+        L.pic_destroy.argtypes = [vp]
+        L.pic_last_error.restype = ctypes.c_char_p
+        L.pic_last_error.argtypes = [vp]
+        L.pic_batch_required_bytes.restype = ctypes.c_size_t
+        L.pic_batch_required_bytes.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        L.pic_batch_create.restype = ctypes.c_int
+        L.pic_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.c_size_t, vp,
+                                       ctypes.POINTER(vp)]
+        L.pic_batch_step.restype = ctypes.c_int
+        L.pic_batch_step.argtypes = [vp, ctypes.c_int]
+        L.pic_batch_destroy.restype = ctypes.c_int
+        L.pic_batch_destroy.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _check(rc, handle=None):
+    if rc != PIC_OK:
+        msg = lib().pic_last_error(handle).decode() if handle else ""
+        raise PicError(rc, msg)
+
+
+# ------------------------------------------------------------------ same-name wrappers
+
+def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chunk: int = 0,
+                mapping: int = PIC_MAP_QUEUE) -> PicConfig:
+    c = PicConfig()
+    c.dims = int(params["dims"])
+    for a in range(3):
+        c.n[a] = int(params["n"][a]) if a < len(params["n"]) else 1
+        c.d[a] = float(params["d"][a]) if a < len(params["d"]) else 1.0
+        pt = params.get("patch", (32, 32, 32))
+        c.patch[a] = int(pt[a]) if a < len(pt) else 1
+        ip = params.get("inject_ppc", (1, 1, 1))
+        c.inject_ppc[a] = int(ip[a]) if a < len(ip) else 1
+    if c.dims == 2:
+        c.n[2] = 1
+    c.dt = float(params["dt"])
+    c.precision = int(precision)
+    c.window = 1 if params.get("window") else 0
+    c.n0 = float(params.get("n0", 0.0))
+    c.ramp_x0 = float(params.get("ramp_x0", 0.0))
+    c.ramp_len = float(params.get("ramp_len", 1.0))
+    c.q = float(params.get("q", -1.0))
+    c.m = float(params.get("m", 1.0))
+    c.capacity = int(capacity)
+    c.chunk = int(chunk)
+    c.mapping = int(mapping)
+    return c
+
+
+def pic_required_bytes(cfg: PicConfig) -> int:
+    return int(lib().pic_required_bytes(ctypes.byref(cfg)))
+
+
+def pic_create(cfg: PicConfig, arena_ptr: int, arena_bytes: int, stream_ptr: int):
+    h = ctypes.c_void_p()
+    _check(lib().pic_create(ctypes.byref(cfg), ctypes.c_void_p(arena_ptr), arena_bytes,
+                            ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h
+
+
+def pic_load_particles(h, p: dict):
+    n = len(p["x"])
+    arrs = [np.ascontiguousarray(p.get(k, np.zeros(n)), dtype=np.float64)
+            for k in ("x", "y", "z", "ux", "uy", "uz", "w")]
+    ids = np.ascontiguousarray(p["id"], dtype=np.int32)
+    _check(lib().pic_load_particles(h, n, *[_dp(a) for a in arrs], _ip(ids)), h)
+
+
+def pic_load_fields(h, E, B, rho_bg=None):
+    E = [np.ascontiguousarray(a, dtype=np.float64) for a in E]
+    B = [np.ascontiguousarray(a, dtype=np.float64) for a in B]
+    Ep = (ctypes.POINTER(ctypes.c_double) * 3)(*[_dp(a) for a in E])
+    Bp = (ctypes.POINTER(ctypes.c_double) * 3)(*[_dp(a) for a in B])
+    rb = np.ascontiguousarray(rho_bg, dtype=np.float64) if rho_bg is not None else None
+    _check(lib().pic_load_fields(h, Ep, Bp, _dp(rb)), h)
+
+
+def pic_step(h, nsteps: int):
+    _check(lib().pic_step(h, int(nsteps)), h)
+
+
+def pic_sync(h):
+    _check(lib().pic_sync(h), h)
+
+
+def pic_diag(h, kind: int, nbytes: int) -> bytes:
+    buf = ctypes.create_string_buffer(nbytes)
+    written = ctypes.c_size_t(0)
+    _check(lib().pic_diag(h, kind, buf, nbytes, ctypes.byref(written)), h)
+    return buf.raw[: written.value]
+
+
+PROFILE_KERNELS = ("queue_build", "push", "inject", "exchange", "yee", "end_step", "step")
+
+
+def pic_profile(h, nsteps: int) -> dict:
+    ms = np.zeros(7)
+    _check(lib().pic_profile(h, int(nsteps), _dp(ms), 7), h)
+    return dict(zip(PROFILE_KERNELS, ms.tolist()))
+
+
+def pic_destroy(h):
+    _check(lib().pic_destroy(h))
+
+
+def pic_last_error(h) -> str:
+    return lib().pic_last_error(h).decode()
+
+
+def pic_batch_required_bytes(handles) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    return int(lib().pic_batch_required_bytes(arr, len(handles)))
+
+
+def pic_batch_create(handles, arena_ptr: int, arena_bytes: int, stream_ptr: int):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    _check(lib().pic_batch_create(arr, len(handles), ctypes.c_void_p(arena_ptr), arena_bytes,
+                                  ctypes.c_void_p(stream_ptr), ctypes.byref(b)))
+    return b
+
+
+def pic_batch_step(b, nsteps: int):
+    _check(lib().pic_batch_step(b, int(nsteps)))
+
+
+def pic_batch_destroy(b):
+    _check(lib().pic_batch_destroy(b))
+
+
+# ------------------------------------------------------------------ convenience object
+
+class Sim:
+    """One simulation resident on the GPU: arena from torch, work on a torch stream."""
+
+    def __init__(self, params: dict, precision: int = PIC_FP64, capacity: int = 0,
+                 chunk: int = 0, mapping: int = PIC_MAP_QUEUE, stream=None, device="cuda"):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (the library has no CPU path)")
+        self.params = params
+        self.cfg = make_config(params, precision, capacity, chunk, mapping)
+        self.nbytes = pic_required_bytes(self.cfg)
+        if self.nbytes == 0:
+            raise PicError(PIC_ERR_INVALID, "invalid configuration")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.arena = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        ptr = self.arena.data_ptr()
+        ptr = (ptr + 255) // 256 * 256
+        self.h = pic_create(self.cfg, ptr, self.nbytes, self.stream.cuda_stream)
+        n = self.cfg.n
+        self.fshape = (n[2], n[1], n[0]) if self.cfg.dims == 3 else (n[1], n[0])
+        self.ncell = int(np.prod(self.fshape))
+        self.npatch = int(np.prod([n[a] // self.cfg.patch[a] for a in range(self.cfg.dims)]))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, workload: dict, rho_bg=None):
+        pic_load_particles(self.h, workload["particles"])
+        pic_load_fields(self.h, workload["E"], workload["B"], rho_bg)
+
+    def step(self, n: int = 1):
+        pic_step(self.h, n)
+
+    def sync(self):
+        pic_sync(self.h)
+
+    def profile(self, nsteps: int) -> dict:
+        return pic_profile(self.h, nsteps)
+
+    def energy(self):
+        return np.frombuffer(pic_diag(self.h, PIC_DIAG_ENERGY, 24), dtype=np.float64).copy()
+
+    def gauss(self):
+        b = pic_diag(self.h, PIC_DIAG_GAUSS, 8 * self.ncell)
+        return np.frombuffer(b, dtype=np.float64).reshape(self.fshape).copy()
+
+    def fields(self) -> dict:
+        b = pic_diag(self.h, PIC_DIAG_FIELDS, 12 * 8 * self.ncell)
+        a = np.frombuffer(b, dtype=np.float64).reshape((12,) + self.fshape)
+        names = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bnx", "Bny", "Bnz", "Jx", "Jy", "Jz"]
+        return {k: a[i].copy() for i, k in enumerate(names)}
+
+    def num_particles(self) -> int:
+        return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_NUM_PARTICLES, 8), dtype=np.int64)[0])
+
+    def particles(self) -> dict:
+        n = self.num_particles()
+        b = pic_diag(self.h, PIC_DIAG_PARTICLES, n * 60)
+        d = np.frombuffer(b[: 56 * n], dtype=np.float64).reshape(7, n)
+        out = {k: d[i].copy() for i, k in enumerate(("x", "y", "z", "ux", "uy", "uz", "w"))}
+        out["id"] = np.frombuffer(b[56 * n:], dtype=np.int32).copy()
+        return out
+
+    def patch_counts(self):
+        return np.frombuffer(pic_diag(self.h, PIC_DIAG_PATCH_COUNTS, 4 * self.npatch),
+                             dtype=np.int32).copy()
+
+    def step_info(self):
+        s, k = np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 16), dtype=np.int64)
+        return int(s), int(k)
+
+    def ex_axis(self):
+        return np.frombuffer(pic_diag(self.h, PIC_DIAG_EX_AXIS, 8 * self.cfg.n[0]),
+                             dtype=np.float64).copy()

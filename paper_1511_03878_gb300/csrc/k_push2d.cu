@@ -1,0 +1,476 @@
+// 2D3V particle kernel: per patch chunk, order-2 interpolation of E and B^n from a
+// TMA-staged field tile, relativistic Boris push, Esirkepov deposition into a
+// shared-memory current tile, flush of the tile to the global FP64 current with
+// atomics, and hand-off of particles that left the patch to the neighbour's
+// exchange buffer. Work items come from a device queue (largest first) pulled by
+// persistent CTAs, so no CTA idles while dense patches are pushed.
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+template <typename T>
+struct JType;
+template <>
+struct JType<double> {
+    using type = double;
+};
+template <>
+struct JType<float> {
+    using type = float;
+};
+
+// Per-axis Esirkepov data on the five nodes node0-2 .. node0+2.
+template <typename T>
+struct Axis5 {
+    T S0[5], DS[5];
+    int lo, hi;  // non-zero range of DS (and of S0 + DS/2)
+};
+
+template <typename T>
+__device__ __forceinline__ void esirkepov_axis(const T s0[3], T delta1, int shift, Axis5<T>& a) {
+    T s1[3];
+    shape3(delta1, s1);
+    const bool m = shift < 0, z = shift == 0, p = shift > 0;
+    T S1[5];
+    S1[0] = m ? s1[0] : T(0);
+    S1[1] = m ? s1[1] : (z ? s1[0] : T(0));
+    S1[2] = m ? s1[2] : (z ? s1[1] : s1[0]);
+    S1[3] = p ? s1[1] : (z ? s1[2] : T(0));
+    S1[4] = p ? s1[2] : T(0);
+    a.S0[0] = T(0);
+    a.S0[1] = s0[0];
+    a.S0[2] = s0[1];
+    a.S0[3] = s0[2];
+    a.S0[4] = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; k++) a.DS[k] = S1[k] - a.S0[k];
+    a.lo = m ? 0 : 1;
+    a.hi = p ? 4 : 3;
+}
+
+// Gather of one staggered component: Sx/Sy are the three weights, (tx, ty) the tile
+// index of the first tap.
+template <typename T>
+__device__ __forceinline__ T gather9(const T* __restrict__ f, int BX, const T Sx[3],
+                                     const T Sy[3]) {
+    T r = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const T* row = f + b * BX;
+        r += Sy[b] * (Sx[0] * row[0] + Sx[1] * row[1] + Sx[2] * row[2]);
+    }
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __restrict__ bd,
+                                                           int static_map) {
+    using JT = typename JType<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    int loaded_sim = -1, loaded_patch = -1, loaded_gen = -1;
+    int next_static = blockIdx.x;
+
+    for (;;) {
+        __syncthreads();  // the previous item's tiles are no longer read
+        if (tid == 0) s_item = static_map ? next_static : atomicAdd(bd->head, 1);
+        next_static += gridDim.x;
+        __syncthreads();
+        const int it = s_item;
+        if (it >= *bd->nitems || it >= bd->max_items) break;
+        const int4 item = bd->items[it];
+        const SimDev& S = bd->sims[item.x];
+        const int patch = item.y;
+
+        const int P0 = S.P[0], P1 = S.P[1];
+        const int BX = S.BX, BY = S.BY;
+        const int JX = P0 + 5, JY = P1 + 5;
+        const int nx = S.n[0], ny = S.n[1];
+        const int NX = S.NX;
+        const int px0 = (patch % S.np[0]) * P0;
+        const int py0 = (patch / S.np[0]) * P1;
+        const int gen = S.st->gen;
+        const int shift = S.st->shift;
+        const int window = S.window;
+
+        T* Ft = reinterpret_cast<T*>(smem);
+        const int fbytes = 6 * BX * BY * (int)sizeof(T);
+        JT* Jt = reinterpret_cast<JT*>(smem + ((fbytes + 127) & ~127));
+        const int jplane = JX * JY;
+
+        for (int e = tid; e < 3 * jplane; e += blockDim.x) Jt[e] = JT(0);
+
+        if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, (uint32_t)fbytes);
+                // box origin: interior index (px0 - 1, py0 - 1) = padded (px0, py0)
+                tma_load_3d(Ft, S.tmap + gen, &mbar, px0 - 1 + kGuard, py0 - 1 + kGuard, 0);
+            }
+            const bool ok = mbar_wait_bounded(&mbar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(S.status, ST_TIMEOUT);
+                return;
+            }
+            loaded_sim = item.x;
+            loaded_patch = patch;
+            loaded_gen = gen;
+        }
+        __syncthreads();  // J tile zeroed
+
+        // per-sim constants in the working precision
+        const T dtdx = T(S.dt / S.d[0]), dtdy = T(S.dt / S.d[1]);
+        const T eps = T(S.q * S.dt / (2.0 * S.m));
+        const double qdv = S.q / (S.d[0] * S.d[1]);
+        const T cjx = T(-qdv * S.d[0] / S.dt);
+        const T cjy = T(-qdv * S.d[1] / S.dt);
+        const T cjz = T(qdv);
+
+        const int base = S.pbase[patch] + item.z;
+        const int cnt = item.w;
+        const T* W = reinterpret_cast<const T*>(S.w);
+        T* U0 = reinterpret_cast<T*>(S.u[0]);
+        T* U1 = reinterpret_cast<T*>(S.u[1]);
+        T* U2 = reinterpret_cast<T*>(S.u[2]);
+
+        for (int k0 = 0; k0 < cnt; k0 += blockDim.x) {
+            const int k = k0 + tid;
+            const bool valid = k < cnt;
+            const int slot = base + (valid ? k : 0);
+
+            // ---- position: integer cell + offset per axis
+            int ix = 0, iy = 0;
+            T fx = T(0), fy = T(0);
+            double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
+            if (valid) {
+                if constexpr (sizeof(T) == 8) {
+                    xi0 = reinterpret_cast<const double*>(S.xi[0])[slot];
+                    eta0 = reinterpret_cast<const double*>(S.xi[1])[slot];
+                    const double fxd = floor(xi0), fyd = floor(eta0);
+                    ix = (int)fxd;
+                    iy = (int)fyd;
+                    fx = xi0 - fxd;
+                    fy = eta0 - fyd;
+                } else {
+                    const int c = S.cell[slot];
+                    ix = c & 0xFFFF;
+                    iy = (c >> 16) & 0xFFFF;
+                    fx = reinterpret_cast<const float*>(S.xi[0])[slot];
+                    fy = reinterpret_cast<const float*>(S.xi[1])[slot];
+                }
+            }
+            T u[3] = {T(0), T(0), T(0)};
+            T w = T(0);
+            if (valid) {
+                u[0] = U0[slot];
+                u[1] = U1[slot];
+                u[2] = U2[slot];
+                w = W[slot];
+            }
+            // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
+            const int hx = fx >= T(0.5), hy = fy >= T(0.5);
+            const int nxp = ix + hx, nyp = iy + hy;
+            const T dxp = fx - T(hx), dyp = fy - T(hy);
+            const T dxd = fx - T(0.5), dyd = fy - T(0.5);
+            // tile-local first-tap indices (field tile origin at px0 - 1, py0 - 1)
+            const int txp = nxp - px0, txd = ix - px0;
+            const int typ = nyp - py0, tyd = iy - py0;
+            bool ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
+                      (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
+
+            bool leave = false;
+            int dest = patch;
+            if (ok) {
+                T Sxp[3], Sxd[3], Syp[3], Syd[3];
+                shape3(dxp, Sxp);
+                shape3(dxd, Sxd);
+                shape3(dyp, Syp);
+                shape3(dyd, Syd);
+                const int pl = BX * BY;
+                T E[3], B[3];
+                E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
+                E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
+                B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
+                B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+
+                const T ig = boris(eps, E, B, u);
+                const T vx = u[0] * ig, vy = u[1] * ig, vz = u[2] * ig;
+
+                // ---- move: new node and delta per axis
+                int nxp1, nyp1, ix1, iy1;
+                T dxp1, dyp1, fx1, fy1;
+                double xi1 = 0.0, eta1 = 0.0;
+                if constexpr (sizeof(T) == 8) {
+                    xi1 = xi0 + dtdx * vx;
+                    eta1 = eta0 + dtdy * vy;
+                    const double nx1d = floor(xi1 + 0.5), ny1d = floor(eta1 + 0.5);
+                    nxp1 = (int)nx1d;
+                    nyp1 = (int)ny1d;
+                    dxp1 = xi1 - nx1d;
+                    dyp1 = eta1 - ny1d;
+                    ix1 = (int)floor(xi1);
+                    iy1 = (int)floor(eta1);
+                    fx1 = fy1 = T(0);
+                } else {
+                    fx1 = fx + dtdx * vx;
+                    fy1 = fy + dtdy * vy;
+                    ix1 = ix;
+                    iy1 = iy;
+                    if (fx1 < T(0)) {
+                        fx1 += T(1);
+                        ix1 -= 1;
+                        if (fx1 >= T(1)) { fx1 = T(0); ix1 += 1; }
+                    } else if (fx1 >= T(1)) {
+                        fx1 -= T(1);
+                        ix1 += 1;
+                    }
+                    if (fy1 < T(0)) {
+                        fy1 += T(1);
+                        iy1 -= 1;
+                        if (fy1 >= T(1)) { fy1 = T(0); iy1 += 1; }
+                    } else if (fy1 >= T(1)) {
+                        fy1 -= T(1);
+                        iy1 += 1;
+                    }
+                    const int h1x = fx1 >= T(0.5), h1y = fy1 >= T(0.5);
+                    nxp1 = ix1 + h1x;
+                    nyp1 = iy1 + h1y;
+                    dxp1 = fx1 - T(h1x);
+                    dyp1 = fy1 - T(h1y);
+                }
+                const int sx = nxp1 - nxp, sy = nyp1 - nyp;
+                ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
+                if (ok) {
+                    // ---- Esirkepov deposition into the shared tile (origin px0-2, py0-2)
+                    Axis5<T> ax, ay;
+                    esirkepov_axis(Sxp, dxp1, sx, ax);
+                    esirkepov_axis(Syp, dyp1, sy, ay);
+                    const T qx = cjx * w, qy = cjy * w, qz = cjz * w * vz;
+                    JT* jxt = Jt + txp;           // stencil k = 0 at tile x = nxp - px0
+                    JT* jyt = Jt + jplane + txp;
+                    JT* jzt = Jt + 2 * jplane + txp;
+                    const int r0 = typ * JX;
+#pragma unroll
+                    for (int l = 0; l < 5; l++) {
+                        if (l >= ay.lo && l <= ay.hi) {
+                            const T wy = ay.S0[l] + T(0.5) * ay.DS[l];
+                            const T wz = T(0.5) * ay.S0[l] + ay.DS[l] * T(1.0 / 3.0);
+                            T acc = T(0);
+                            const int r = r0 + l * JX;
+#pragma unroll
+                            for (int kk = 0; kk < 4; kk++) {
+                                if (kk >= ax.lo && kk < ax.hi) {
+                                    acc += ax.DS[kk] * wy;
+                                    atomicAdd(jxt + r + kk, JT(qx * acc));
+                                }
+                            }
+#pragma unroll
+                            for (int kk = 0; kk < 5; kk++) {
+                                if (kk >= ax.lo && kk <= ax.hi) {
+                                    const T wzk = ax.S0[kk] * wy + ax.DS[kk] * wz;
+                                    atomicAdd(jzt + r + kk, JT(qz * wzk));
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 5; kk++) {
+                        if (kk >= ax.lo && kk <= ax.hi) {
+                            const T wx = ax.S0[kk] + T(0.5) * ax.DS[kk];
+                            T acc = T(0);
+#pragma unroll
+                            for (int l = 0; l < 4; l++) {
+                                if (l >= ay.lo && l < ay.hi) {
+                                    acc += ay.DS[l] * wx;
+                                    atomicAdd(jyt + r0 + l * JX + kk, JT(qy * acc));
+                                }
+                            }
+                        }
+                    }
+
+                    // ---- boundaries and destination patch
+                    bool del = false;
+                    if constexpr (sizeof(T) == 8) {
+                        double xs = xi1 - (double)shift;
+                        if (window) {
+                            del = xi1 < 0.0 || xi1 >= (double)nx || xs < 0.0;
+                        } else {
+                            if (xs < 0.0) xs += (double)nx;
+                            if (xs >= (double)nx) xs -= (double)nx;
+                        }
+                        if (eta1 < 0.0) eta1 += (double)ny;
+                        if (eta1 >= (double)ny) eta1 -= (double)ny;
+                        xi1 = xs;
+                        ix1 = (int)floor(xi1);
+                        iy1 = (int)floor(eta1);
+                    } else {
+                        if (window) {
+                            del = ix1 < 0 || ix1 >= nx;
+                            ix1 -= shift;
+                            del = del || ix1 < 0;
+                        } else {
+                            ix1 = wrapi(ix1, nx);
+                        }
+                        iy1 = wrapi(iy1, ny);
+                    }
+                    if (!del) {
+                        const int dpx = ix1 / P0, dpy = iy1 / P1;
+                        dest = dpx + S.np[0] * dpy;
+                        leave = dest != patch;
+                        if (!leave) {
+                            if constexpr (sizeof(T) == 8) {
+                                reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
+                                reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
+                            } else {
+                                S.cell[slot] = ix1 | (iy1 << 16);
+                                reinterpret_cast<float*>(S.xi[0])[slot] = fx1;
+                                reinterpret_cast<float*>(S.xi[1])[slot] = fy1;
+                            }
+                            U0[slot] = u[0];
+                            U1[slot] = u[1];
+                            U2[slot] = u[2];
+                        }
+                    } else {
+                        dest = -1;
+                        leave = true;
+                    }
+                    // leavers: stash the new state in registers for the mailbox write
+                    if (leave && dest >= 0) {
+                        if constexpr (sizeof(T) == 8) {
+                            fx = (T)xi1;
+                            fy = (T)eta1;
+                        } else {
+                            fx = fx1;
+                            fy = fy1;
+                            ix = ix1;
+                            iy = iy1;
+                        }
+                    }
+                }
+            }
+            if (valid && !ok) {
+                // corrupted or non-finite particle: report and drop it
+                atomicOr(S.status, ST_NUMERIC);
+                leave = true;
+                dest = -1;
+            }
+
+            // ---- exchange hand-off (warp-aggregated counters)
+            const int hslot = warp_claim(S.hcount, patch, valid && leave, 0xffffffffu);
+            const bool send = valid && leave && dest >= 0;
+            const int mslot = warp_claim(S.mcount, send ? dest : 0, send, 0xffffffffu);
+            if (valid && leave) {
+                S.holes[S.pbase[patch] + hslot] = slot;
+                const int pid = S.id[slot];
+                S.id[slot] = -1;
+                if (send) {
+                    if (mslot < S.mcap[dest]) {
+                        const int m = S.mbase[dest] + mslot;
+                        if constexpr (sizeof(T) == 8) {
+                            reinterpret_cast<double*>(S.mxi[0])[m] = fx;
+                            reinterpret_cast<double*>(S.mxi[1])[m] = fy;
+                        } else {
+                            S.mcell[m] = ix | (iy << 16);
+                            reinterpret_cast<float*>(S.mxi[0])[m] = fx;
+                            reinterpret_cast<float*>(S.mxi[1])[m] = fy;
+                        }
+                        reinterpret_cast<T*>(S.mu[0])[m] = u[0];
+                        reinterpret_cast<T*>(S.mu[1])[m] = u[1];
+                        reinterpret_cast<T*>(S.mu[2])[m] = u[2];
+                        reinterpret_cast<T*>(S.mw)[m] = w;
+                        S.mid[m] = pid;
+                    } else {
+                        atomicOr(S.status, ST_MAILBOX);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- flush the current tile (origin px0-2, py0-2) into the global FP64 J
+        double* Jg = S.J[gen];
+        const long long fs = S.fstride;
+        for (int e = tid; e < 3 * jplane; e += blockDim.x) {
+            const JT v = Jt[e];
+            if (v == JT(0)) continue;
+            const int comp = e / jplane;
+            const int r = e - comp * jplane;
+            const int ty = r / JX, tx = r - ty * JX;
+            int gi = px0 - 2 + tx, gj = py0 - 2 + ty;
+            if (window) {
+                if (gi < 0 || gi >= nx) continue;
+            } else {
+                gi = wrapi(gi, nx);
+            }
+            gj = wrapi(gj, ny);
+            atomicAdd(Jg + comp * fs + (long long)(gj + kGuard) * NX + (gi + kGuard), (double)v);
+        }
+    }
+}
+
+template <typename T>
+static int smem_bytes_2d(int P0, int P1) {
+    const int BX = ((P0 + 3) + 3) & ~3, BY = P1 + 3;
+    const int fb = 6 * BX * BY * (int)sizeof(T);
+    const int jb = 3 * (P0 + 5) * (P1 + 5) * (int)sizeof(typename JType<T>::type);
+    return ((fb + 127) & ~127) + jb;
+}
+
+int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) {
+    (void)P2;
+    if (dims != 2) return 0;
+    int blocks = 0;
+    if (prec == 0) {
+        const int sb = smem_bytes_2d<double>(P0, P1);
+        *smem_bytes = sb;
+        if (cudaFuncSetAttribute(push2d_kernel<double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<double>,
+                                                          kThreads, sb) != cudaSuccess)
+            return 0;
+    } else {
+        const int sb = smem_bytes_2d<float>(P0, P1);
+        *smem_bytes = sb;
+        if (cudaFuncSetAttribute(push2d_kernel<float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<float>,
+                                                          kThreads, sb) != cudaSuccess)
+            return 0;
+    }
+    return blocks;
+}
+
+cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping, int P0,
+                        int P1, int P2, int grid, cudaStream_t s) {
+    (void)P2;
+    if (dims != 2) return cudaErrorInvalidValue;
+    const int static_map = mapping == 1;
+    if (prec == 0) {
+        const int sb = smem_bytes_2d<double>(P0, P1);
+        push2d_kernel<double><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
+    } else {
+        const int sb = smem_bytes_2d<float>(P0, P1);
+        push2d_kernel<float><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pic

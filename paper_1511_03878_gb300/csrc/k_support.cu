@@ -1,0 +1,618 @@
+// Support kernels of one PIC step:
+//   queue_build  - per-step work queue: patch chunks of at most `chunk` particles,
+//                  full chunks first then remainders in descending size (an
+//                  approximate longest-processing-time order), so the persistent
+//                  particle kernel starts the heaviest work first (the single-GPU
+//                  form of the patch load balancing of Sec. 3.1).
+//   exchange     - moves particles that changed patch (and injected ones) into their
+//                  new patch, filling the holes they left; one CTA per patch.
+//   inject       - moving window: cold lattice column on the uncovered edge.
+//   yee_e/yee_b  - Yee FDTD half-updates with the window shift folded into the write
+//                  index, periodic guard cells, and zeroing of the next current buffer.
+//   end_step     - advances the device-side step state.
+//   diagnostics  - energy sums, charge deposition for Gauss's law, field unpadding.
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+// ================================================================ work queue
+
+__global__ void __launch_bounds__(kQueueThreads) queue_build_kernel(const BatchDev* __restrict__ bd) {
+    __shared__ int warp_sums[32];
+    __shared__ int bucket_cnt[kBuckets];
+    __shared__ int bucket_off[kBuckets];
+    __shared__ int s_full_total;
+    const int tid = threadIdx.x;
+    const int nsims = bd->nsims;
+    const int chunk = bd->chunk;
+    const int total = bd->total_patches;
+    const int static_map = bd->sims[0].mapping == 1;
+
+    // begin-of-step state per sim: shift decision and buffer generation
+    for (int s = tid; s < nsims; s += blockDim.x) {
+        StepState* st = bd->sims[s].st;
+        const SimDev& S = bd->sims[s];
+        const long long n = st->step;
+        int shift = 0;
+        if (S.window) {
+            const double a = floor((double)(n + 1) * S.dt / S.d[0]);
+            const double b = floor((double)n * S.dt / S.d[0]);
+            shift = a > b;
+        }
+        st->shift = shift;
+        st->gen = (int)(n & 1);
+    }
+    for (int b = tid; b < kBuckets; b += blockDim.x) bucket_cnt[b] = 0;
+    __syncthreads();
+
+    // pass 1: full chunks (scan-ordered by global patch index) + remainder histogram
+    int carry = 0;
+    for (int g0 = 0; g0 < total; g0 += blockDim.x) {
+        const int g = g0 + tid;
+        int sim = 0, p = 0, cnt = 0;
+        if (g < total) {
+            while (sim + 1 < nsims && bd->patch_prefix[sim + 1] <= g) sim++;
+            p = g - bd->patch_prefix[sim];
+            cnt = bd->sims[sim].pcount[p];
+        }
+        int full = static_map ? 0 : cnt / chunk;
+        int tot;
+        const int ex = block_exclusive_scan(full, warp_sums, &tot);
+        for (int c = 0; c < full; c++) {
+            const int pos = carry + ex + c;
+            if (pos < bd->max_items) bd->items[pos] = make_int4(sim, p, c * chunk, chunk);
+        }
+        if (!static_map) {
+            const int rem = cnt - full * chunk;
+            if (rem > 0) {
+                const int b = kBuckets - 1 - (int)((long long)rem * kBuckets / (chunk + 1));
+                atomicAdd(&bucket_cnt[b < 0 ? 0 : b], 1);
+            }
+        }
+        carry += tot;
+    }
+    if (tid == 0) s_full_total = carry;
+    __syncthreads();
+    if (static_map) {
+        // one item per non-empty patch, in patch order
+        int c2 = 0;
+        for (int g0 = 0; g0 < total; g0 += blockDim.x) {
+            const int g = g0 + tid;
+            int sim = 0, p = 0, cnt = 0;
+            if (g < total) {
+                while (sim + 1 < nsims && bd->patch_prefix[sim + 1] <= g) sim++;
+                p = g - bd->patch_prefix[sim];
+                cnt = bd->sims[sim].pcount[p];
+            }
+            int tot;
+            const int ex = block_exclusive_scan(cnt > 0, warp_sums, &tot);
+            if (cnt > 0 && c2 + ex < bd->max_items) bd->items[c2 + ex] = make_int4(sim, p, 0, cnt);
+            c2 += tot;
+        }
+        if (tid == 0) {
+            *bd->nitems = c2 < bd->max_items ? c2 : bd->max_items;
+            if (c2 > bd->max_items) atomicOr(bd->sims[0].status, ST_QUEUE);
+            *bd->head = 0;
+        }
+        return;
+    }
+    if (tid == 0) {
+        int acc = s_full_total;
+        for (int b = 0; b < kBuckets; b++) {
+            bucket_off[b] = acc;
+            acc += bucket_cnt[b];
+        }
+        *bd->nitems = acc < bd->max_items ? acc : bd->max_items;
+        if (acc > bd->max_items) atomicOr(bd->sims[0].status, ST_QUEUE);
+        *bd->head = 0;
+    }
+    __syncthreads();
+    // pass 2: remainder chunks into their bucket (largest bucket first)
+    for (int g = tid; g < total; g += blockDim.x) {
+        int sim = 0;
+        while (sim + 1 < nsims && bd->patch_prefix[sim + 1] <= g) sim++;
+        const int p = g - bd->patch_prefix[sim];
+        const int cnt = bd->sims[sim].pcount[p];
+        const int full = cnt / chunk;
+        const int rem = cnt - full * chunk;
+        if (rem > 0) {
+            int b = kBuckets - 1 - (int)((long long)rem * kBuckets / (chunk + 1));
+            b = b < 0 ? 0 : b;
+            const int pos = atomicAdd(&bucket_off[b], 1);
+            if (pos < bd->max_items) bd->items[pos] = make_int4(sim, p, full * chunk, rem);
+        }
+    }
+}
+
+cudaError_t launch_queue_build(const BatchDev* bd, cudaStream_t s) {
+    queue_build_kernel<<<1, kQueueThreads, 0, s>>>(bd);
+    return cudaGetLastError();
+}
+
+// ================================================================ exchange
+
+template <typename T>
+__device__ __forceinline__ void copy_particle(const SimDev& S, int dims, int dst, int src,
+                                              bool from_mailbox) {
+    if (from_mailbox) {
+        if constexpr (sizeof(T) == 4) S.cell[dst] = S.mcell[src];
+        for (int a = 0; a < dims; a++)
+            reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.mxi[a])[src];
+        for (int a = 0; a < 3; a++)
+            reinterpret_cast<T*>(S.u[a])[dst] = reinterpret_cast<const T*>(S.mu[a])[src];
+        reinterpret_cast<T*>(S.w)[dst] = reinterpret_cast<const T*>(S.mw)[src];
+        S.id[dst] = S.mid[src];
+    } else {
+        if constexpr (sizeof(T) == 4) S.cell[dst] = S.cell[src];
+        for (int a = 0; a < dims; a++)
+            reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.xi[a])[src];
+        for (int a = 0; a < 3; a++)
+            reinterpret_cast<T*>(S.u[a])[dst] = reinterpret_cast<const T*>(S.u[a])[src];
+        reinterpret_cast<T*>(S.w)[dst] = reinterpret_cast<const T*>(S.w)[src];
+        S.id[dst] = S.id[src];
+    }
+}
+
+// One CTA per patch. Holes (slots of particles that left, id = -1) below the new
+// count are filled first with arrivals from the mailbox, then with live particles
+// moved down from the tail; extra arrivals are appended.
+template <typename T>
+__global__ void __launch_bounds__(256) exchange_kernel(const BatchDev* __restrict__ bd) {
+    __shared__ int warp_sums[32];
+    __shared__ int s_n, s_nh, s_nm, s_new;
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int p = blockIdx.x;
+    if (p >= S.npatch) return;
+    const int tid = threadIdx.x;
+    const int base = S.pbase[p];
+    if (tid == 0) {
+        const int n = S.pcount[p];
+        const int nh = S.hcount[p];
+        int nm = S.mcount[p];
+        const int mc = S.mcap[p];
+        if (nm > mc) nm = mc;
+        int nn = n - nh + nm;
+        const int cap = S.pcap[p];
+        if (nn > cap) {
+            atomicOr(S.status, ST_CAPACITY);
+            nm -= nn - cap;
+            nn = cap;
+        }
+        s_n = n;
+        s_nh = nh;
+        s_nm = nm;
+        s_new = nn;
+        S.hcount[p] = 0;
+        S.mcount[p] = 0;
+        S.pcount[p] = nn;
+    }
+    __syncthreads();
+    const int n = s_n, nh = s_nh, nm = s_nm, nn = s_new;
+    if (nh == 0 && nm == 0) return;
+    int* holes = S.holes + base;
+    int* aux = S.aux + base;
+    const int mb = S.mbase[p];
+
+    // targets T1: holes below the new count, compacted into aux[0..t1)
+    int t1 = 0;
+    for (int k0 = 0; k0 < nh; k0 += blockDim.x) {
+        const int k = k0 + tid;
+        int h = -1;
+        if (k < nh) h = holes[k];
+        const bool keep = k < nh && (h - base) < nn;
+        int tot;
+        const int ex = block_exclusive_scan(keep, warp_sums, &tot);
+        if (keep) aux[t1 + ex] = h;
+        t1 += tot;
+    }
+    __syncthreads();
+    // sources S2: live slots in [nn, n), compacted into holes[0..s2)
+    int s2 = 0;
+    for (int k0 = nn; k0 < n; k0 += blockDim.x) {
+        const int k = k0 + tid;
+        const bool live = k < n && S.id[base + k] >= 0;
+        int tot;
+        const int ex = block_exclusive_scan(live, warp_sums, &tot);
+        if (live) holes[s2 + ex] = base + k;
+        s2 += tot;
+    }
+    __syncthreads();
+    const int ntarget = t1 + (nn > n ? nn - n : 0);
+    for (int k = tid; k < ntarget; k += blockDim.x) {
+        const int dst = k < t1 ? aux[k] : base + n + (k - t1);
+        if (k < nm)
+            copy_particle<T>(S, S.dims, dst, mb + k, true);
+        else if (k - nm < s2)
+            copy_particle<T>(S, S.dims, dst, holes[k - nm], false);
+    }
+}
+
+cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int prec,
+                            cudaStream_t s) {
+    dim3 grid(max_patches, nsims);
+    if (prec == 0)
+        exchange_kernel<double><<<grid, 256, 0, s>>>(bd);
+    else
+        exchange_kernel<float><<<grid, 256, 0, s>>>(bd);
+    return cudaGetLastError();
+}
+
+// ================================================================ moving-window injection
+
+// Lattice point t of the uncovered column (2D): row j varies fastest so that the
+// lanes of a warp sit in different cells (no shared-memory atomic collisions in the
+// next push). Lattice index (id offset) = (j * py + b) * px + a.
+template <typename T>
+__global__ void inject2d_kernel(const BatchDev* __restrict__ bd) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    if (!S.window || !S.st->shift) return;
+    const int ny = S.n[1], nx = S.n[0];
+    const int px = S.ippc[0], py = S.ippc[1];
+    const int npts = ny * px * py;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts) return;
+    const int j = t % ny;
+    const int r = t / ny;
+    const int b = r % py;
+    const int a = r / py;
+    const double dx = S.d[0], dy = S.d[1];
+    const double xw = ((double)(nx - 1) + ((double)a + 0.5) / px) * dx;
+    const double xl = xw + (double)(S.st->nshift + 1) * dx;
+    double f = (xl - S.ramp_x0) / S.ramp_len;
+    f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+    const double dens = S.n0 * f;
+    if (!(dens > 0.0)) return;
+    const double wgt = dens * (dx * dy) / ((double)px * py * 1.0);
+    const long long lat = ((long long)j * py + b) * px + a;
+    const int dest = ((nx - 1) / S.P[0]) + S.np[0] * (j / S.P[1]);
+    const int slot = atomicAdd(S.mcount + dest, 1);
+    if (slot >= S.mcap[dest]) {
+        atomicOr(S.status, ST_MAILBOX);
+        return;
+    }
+    const int m = S.mbase[dest] + slot;
+    const double ox = ((double)a + 0.5) / px, oy = ((double)b + 0.5) / py;
+    if constexpr (sizeof(T) == 8) {
+        reinterpret_cast<double*>(S.mxi[0])[m] = (double)(nx - 1) + ox;
+        reinterpret_cast<double*>(S.mxi[1])[m] = (double)j + oy;
+    } else {
+        S.mcell[m] = (nx - 1) | (j << 16);
+        reinterpret_cast<float*>(S.mxi[0])[m] = (float)ox;
+        reinterpret_cast<float*>(S.mxi[1])[m] = (float)oy;
+    }
+    reinterpret_cast<T*>(S.mu[0])[m] = T(0);
+    reinterpret_cast<T*>(S.mu[1])[m] = T(0);
+    reinterpret_cast<T*>(S.mu[2])[m] = T(0);
+    reinterpret_cast<T*>(S.mw)[m] = (T)wgt;
+    S.mid[m] = (int)(S.st->next_id + lat);
+}
+
+cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int prec,
+                          cudaStream_t s) {
+    if (max_column_pts <= 0) return cudaSuccess;
+    dim3 grid((max_column_pts + 255) / 256, nsims);
+    if (prec == 0)
+        inject2d_kernel<double><<<grid, 256, 0, s>>>(bd);
+    else
+        inject2d_kernel<float><<<grid, 256, 0, s>>>(bd);
+    return cudaGetLastError();
+}
+
+// ================================================================ Yee (2D)
+
+// Writes v at interior (i, j) of a padded component and at its periodic images in
+// the guard cells (x images only when x is periodic).
+template <typename T>
+__device__ __forceinline__ void put2d(T* a, int NX, int i, int j, int nx, int ny, bool px, T v) {
+    int xs[2] = {i + kGuard, -1}, ys[2] = {j + kGuard, -1};
+    if (px) {
+        if (i == nx - 1) xs[1] = 0;
+        else if (i == 0) xs[1] = nx + kGuard;
+        else if (i == 1) xs[1] = nx + 1 + kGuard;
+    }
+    if (j == ny - 1) ys[1] = 0;
+    else if (j == 0) ys[1] = ny + kGuard;
+    else if (j == 1) ys[1] = ny + 1 + kGuard;
+#pragma unroll
+    for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+        for (int b2 = 0; b2 < 2; b2++)
+            if (xs[a2] >= 0 && ys[b2] >= 0) a[(long long)ys[b2] * NX + xs[a2]] = v;
+}
+
+// E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2}); output written shifted by the
+// window shift of this step; the next step's current buffer is zeroed.
+template <typename T>
+__global__ void __launch_bounds__(256) yee_e2d_kernel(const BatchDev* __restrict__ bd) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int nx = S.n[0], ny = S.n[1];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nx * ny) return;
+    const int ox = idx % nx, oy = idx / nx;
+    const int g = S.st->gen, s = S.st->shift;
+    const int NX = S.NX;
+    const long long fs = S.fstride;
+    const bool win = S.window != 0;
+    const T* Ein = reinterpret_cast<const T*>(S.F[g]);
+    T* Eout = reinterpret_cast<T*>(S.F[1 - g]);
+    const T* Hin = reinterpret_cast<const T*>(S.H[g]);
+    const double* Jin = S.J[g];
+    double* Jnext = S.J[1 - g];
+    const long long po = (long long)(oy + kGuard) * NX + (ox + kGuard);
+    Jnext[po] = 0.0;
+    Jnext[fs + po] = 0.0;
+    Jnext[2 * fs + po] = 0.0;
+    const int i = ox + s, j = oy;
+    T ex = T(0), ey = T(0), ez = T(0);
+    if (i < nx) {
+        const T dt = T(S.dt), idx_ = T(1.0 / S.d[0]), idy = T(1.0 / S.d[1]);
+        const int jm = j == 0 ? ny - 1 : j - 1;
+        const bool has_im = !(win && i == 0);
+        const int im = i == 0 ? nx - 1 : i - 1;
+        auto at = [&](const T* a, int c, int ii, int jj) {
+            return a[c * fs + (long long)(jj + kGuard) * NX + (ii + kGuard)];
+        };
+        const long long pi = (long long)(j + kGuard) * NX + (i + kGuard);
+        const T bz = at(Hin, 2, i, j), bzjm = at(Hin, 2, i, jm);
+        const T bzim = has_im ? at(Hin, 2, im, j) : T(0);
+        const T by = at(Hin, 1, i, j), byim = has_im ? at(Hin, 1, im, j) : T(0);
+        const T bx = at(Hin, 0, i, j), bxjm = at(Hin, 0, i, jm);
+        ex = Ein[pi] + dt * ((bz - bzjm) * idy - T(Jin[pi]));
+        ey = Ein[fs + pi] + dt * (-(bz - bzim) * idx_ - T(Jin[fs + pi]));
+        ez = Ein[2 * fs + pi] + dt * ((by - byim) * idx_ - (bx - bxjm) * idy - T(Jin[2 * fs + pi]));
+    }
+    put2d(Eout, NX, ox, oy, nx, ny, !win, ex);
+    put2d(Eout + fs, NX, ox, oy, nx, ny, !win, ey);
+    put2d(Eout + 2 * fs, NX, ox, oy, nx, ny, !win, ez);
+}
+
+// B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1};  B^{n+1} = (B^{n+1/2} + B^{n+3/2}) / 2.
+template <typename T>
+__global__ void __launch_bounds__(256) yee_b2d_kernel(const BatchDev* __restrict__ bd) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int nx = S.n[0], ny = S.n[1];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nx * ny) return;
+    const int ox = idx % nx, oy = idx / nx;
+    const int g = S.st->gen, s = S.st->shift;
+    const int NX = S.NX;
+    const long long fs = S.fstride;
+    const bool win = S.window != 0;
+    const T* E = reinterpret_cast<const T*>(S.F[1 - g]);  // E^{n+1}, output frame
+    T* Bn = reinterpret_cast<T*>(S.F[1 - g]) + 3 * fs;
+    const T* Hin = reinterpret_cast<const T*>(S.H[g]);
+    T* Hout = reinterpret_cast<T*>(S.H[1 - g]);
+    const int i = ox + s, j = oy;
+    T hx = T(0), hy = T(0), hz = T(0), nbx = T(0), nby = T(0), nbz = T(0);
+    if (i < nx) {
+        const T dt = T(S.dt), idx_ = T(1.0 / S.d[0]), idy = T(1.0 / S.d[1]);
+        auto at = [&](const T* a, int c, int ii, int jj) {
+            return a[c * fs + (long long)(jj + kGuard) * NX + (ii + kGuard)];
+        };
+        const int jp = oy == ny - 1 ? 0 : oy + 1;
+        const bool has_ip = !(win && ox + 1 >= nx);
+        const int ip = ox + 1 >= nx ? 0 : ox + 1;
+        const T ez = at(E, 2, ox, oy), ezjp = at(E, 2, ox, jp);
+        const T ezip = has_ip ? at(E, 2, ip, oy) : T(0);
+        const T ey = at(E, 1, ox, oy), eyip = has_ip ? at(E, 1, ip, oy) : T(0);
+        const T ex = at(E, 0, ox, oy), exjp = at(E, 0, ox, jp);
+        const T h0x = at(Hin, 0, i, j), h0y = at(Hin, 1, i, j), h0z = at(Hin, 2, i, j);
+        hx = h0x - dt * ((ezjp - ez) * idy);
+        hy = h0y + dt * ((ezip - ez) * idx_);
+        hz = h0z - dt * ((eyip - ey) * idx_ - (exjp - ex) * idy);
+        nbx = T(0.5) * (h0x + hx);
+        nby = T(0.5) * (h0y + hy);
+        nbz = T(0.5) * (h0z + hz);
+    }
+    const long long po = (long long)(oy + kGuard) * NX + (ox + kGuard);
+    Hout[po] = hx;
+    Hout[fs + po] = hy;
+    Hout[2 * fs + po] = hz;
+    put2d(Bn, NX, ox, oy, nx, ny, !win, nbx);
+    put2d(Bn + fs, NX, ox, oy, nx, ny, !win, nby);
+    put2d(Bn + 2 * fs, NX, ox, oy, nx, ny, !win, nbz);
+}
+
+cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
+                       cudaStream_t s) {
+    if (dims != 2) return cudaErrorInvalidValue;
+    dim3 grid((max_ncell + 255) / 256, nsims);
+    if (prec == 0) {
+        yee_e2d_kernel<double><<<grid, 256, 0, s>>>(bd);
+        yee_b2d_kernel<double><<<grid, 256, 0, s>>>(bd);
+    } else {
+        yee_e2d_kernel<float><<<grid, 256, 0, s>>>(bd);
+        yee_b2d_kernel<float><<<grid, 256, 0, s>>>(bd);
+    }
+    return cudaGetLastError();
+}
+
+// ================================================================ end of step
+
+__global__ void end_step_kernel(const BatchDev* __restrict__ bd) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bd->nsims) return;
+    const SimDev& S = bd->sims[s];
+    StepState* st = S.st;
+    st->step += 1;
+    if (st->shift) {
+        st->nshift += 1;
+        long long pts = (long long)S.n[1] * S.ippc[0] * S.ippc[1];
+        if (S.dims == 3) pts *= (long long)S.n[2] * S.ippc[2];
+        st->next_id += pts;
+    }
+    st->shift = 0;
+}
+
+cudaError_t launch_end_step(const BatchDev* bd, int nsims, cudaStream_t s) {
+    end_step_kernel<<<(nsims + 127) / 128, 128, 0, s>>>(bd);
+    return cudaGetLastError();
+}
+
+// ================================================================ diagnostics
+
+template <typename T>
+__global__ void energy_kernel(const SimDev* __restrict__ sd, long long ncell, long long cap) {
+    const SimDev& S = *sd;
+    __shared__ double sh[3][256 / 32];
+    const int g = (int)(S.st->step & 1);  // fields of the current time level
+    const T* F = reinterpret_cast<const T*>(S.F[g]);
+    double we = 0, wb = 0, wk = 0;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += stride) {
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((long long)nx * ny));
+        const long long pi = ((long long)(S.dims == 3 ? k + kGuard : 0) * S.NY + (j + kGuard)) * S.NX +
+                             (i + kGuard);
+        (void)nz;
+        for (int a = 0; a < 3; a++) {
+            const double e = (double)F[a * S.fstride + pi];
+            const double b = (double)F[(3 + a) * S.fstride + pi];
+            we += e * e;
+            wb += b * b;
+        }
+    }
+    // particles: live slots of each patch (grid-stride over patches, block over slots)
+    const T* U0 = reinterpret_cast<const T*>(S.u[0]);
+    const T* U1 = reinterpret_cast<const T*>(S.u[1]);
+    const T* U2 = reinterpret_cast<const T*>(S.u[2]);
+    const T* W = reinterpret_cast<const T*>(S.w);
+    for (int p = blockIdx.x; p < S.npatch; p += gridDim.x) {
+        const int b0 = S.pbase[p], cnt = S.pcount[p];
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const int sidx = b0 + k;
+            const double ux = U0[sidx], uy = U1[sidx], uz = U2[sidx];
+            wk += (double)W[sidx] * S.m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        }
+    }
+    (void)cap;
+    for (int o = 16; o > 0; o >>= 1) {
+        we += __shfl_down_sync(0xffffffffu, we, o);
+        wb += __shfl_down_sync(0xffffffffu, wb, o);
+        wk += __shfl_down_sync(0xffffffffu, wk, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = we;
+        sh[1][threadIdx.x >> 5] = wb;
+        sh[2][threadIdx.x >> 5] = wk;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); w2++) v += sh[threadIdx.x][w2];
+        atomicAdd(S.red + threadIdx.x, v);
+    }
+}
+
+cudaError_t launch_energy(const SimDev* sd, long long ncell, long long cap, int prec,
+                          cudaStream_t s) {
+    int grid = 152 * 4;
+    if (prec == 0)
+        energy_kernel<double><<<grid, 256, 0, s>>>(sd, ncell, cap);
+    else
+        energy_kernel<float><<<grid, 256, 0, s>>>(sd, ncell, cap);
+    return cudaGetLastError();
+}
+
+// Order-2 charge density of every live particle, FP64 atomics into rho (unpadded).
+template <typename T>
+__global__ void rho2d_kernel(const SimDev* __restrict__ sd, double* rho, double sign) {
+    const SimDev& S = *sd;
+    const int p = blockIdx.x;
+    if (p >= S.npatch) return;
+    const int b0 = S.pbase[p], cnt = S.pcount[p];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int t = b0 + k;
+    const int nx = S.n[0], ny = S.n[1];
+    int ix, iy;
+    double fx, fy;
+    if constexpr (sizeof(T) == 8) {
+        const double xi = reinterpret_cast<const double*>(S.xi[0])[t];
+        const double eta = reinterpret_cast<const double*>(S.xi[1])[t];
+        ix = (int)floor(xi);
+        iy = (int)floor(eta);
+        fx = xi - ix;
+        fy = eta - iy;
+    } else {
+        const int c = S.cell[t];
+        ix = c & 0xFFFF;
+        iy = (c >> 16) & 0xFFFF;
+        fx = reinterpret_cast<const float*>(S.xi[0])[t];
+        fy = reinterpret_cast<const float*>(S.xi[1])[t];
+    }
+    const int hx = fx >= 0.5, hy = fy >= 0.5;
+    double Sx[3], Sy[3];
+    shape3(fx - hx, Sx);
+    shape3(fy - hy, Sy);
+    const double qw = sign * S.q * (double)reinterpret_cast<const T*>(S.w)[t] / (S.d[0] * S.d[1]);
+    for (int b = 0; b < 3; b++) {
+        const int j = wrapi(iy + hy + b - 1, ny);
+        for (int a = 0; a < 3; a++) {
+            int i = ix + hx + a - 1;
+            if (S.window) {
+                if (i < 0 || i >= nx) continue;
+            } else {
+                i = wrapi(i, nx);
+            }
+            atomicAdd(rho + (long long)j * nx + i, qw * Sx[a] * Sy[b]);
+        }
+    }
+    }
+}
+
+// mode 0: rho_bg = -rho_e (into S.rho_bg);  mode 1: out = div E - rho_e - rho_bg (into S.rho)
+template <typename T>
+__global__ void gauss2d_kernel(const SimDev* __restrict__ sd) {
+    const SimDev& S = *sd;
+    const int nx = S.n[0], ny = S.n[1];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nx * ny) return;
+    const int i = idx % nx, j = idx / nx;
+    const T* E = reinterpret_cast<const T*>(S.F[S.st->step & 1]);  // current time level
+    const long long fs = S.fstride;
+    auto at = [&](int c, int ii, int jj) -> double {
+        if (S.window && (ii < 0 || ii >= nx)) return 0.0;
+        ii = wrapi(ii, nx);
+        jj = wrapi(jj, ny);
+        return (double)E[c * fs + (long long)(jj + kGuard) * S.NX + (ii + kGuard)];
+    };
+    const double div = (at(0, i, j) - at(0, i - 1, j)) / S.d[0] + (at(1, i, j) - at(1, i, j - 1)) / S.d[1];
+    S.rho[idx] = div - S.rho[idx] - S.rho_bg[idx];
+}
+
+cudaError_t launch_gauss(const SimDev* sd, const SimDev& hs, int prec, int mode, cudaStream_t s) {
+    const long long nc = hs.ncell;
+    double* target = mode == 0 ? hs.rho_bg : hs.rho;
+    cudaError_t e = cudaMemsetAsync(target, 0, nc * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const int g1 = hs.npatch;
+    const double sign = mode == 0 ? -1.0 : 1.0;
+    if (hs.dims != 2) return cudaErrorInvalidValue;
+    if (prec == 0)
+        rho2d_kernel<double><<<g1, 256, 0, s>>>(sd, target, sign);
+    else
+        rho2d_kernel<float><<<g1, 256, 0, s>>>(sd, target, sign);
+    if (mode == 1) {
+        const int g2 = (int)((nc + 255) / 256);
+        if (prec == 0)
+            gauss2d_kernel<double><<<g2, 256, 0, s>>>(sd);
+        else
+            gauss2d_kernel<float><<<g2, 256, 0, s>>>(sd);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pic

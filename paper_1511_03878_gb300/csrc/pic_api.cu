@@ -1,0 +1,976 @@
+// Host side of the C ABI declared in include/pic.h: arena carving, TMA tensor maps,
+// host binning of particles into patches, CUDA-graph capture of one step, and
+// diagnostics. Device memory is never allocated here: everything lives in the
+// caller's arena.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pic.h"
+#include "pic_internal.h"
+
+using namespace pic;
+
+namespace {
+
+// Everything carved out of one sim arena.
+struct Layout {
+    SimDev S{};          // host copy of the device descriptor
+    SimDev* ds = nullptr;   // device copy
+    BatchDev B{};        // single-sim batch descriptor (host copy)
+    BatchDev* db = nullptr; // device copy
+    int* prefix = nullptr;  // [2] patch prefix of the single-sim batch
+    size_t bytes = 0;
+};
+
+struct Carver {
+    char* base;
+    bool dry;
+    size_t off = 0;
+    template <class T>
+    T* take(long long count, size_t align = 256) {
+        off = (off + align - 1) / align * align;
+        T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+        off += (size_t)std::max(count, 0LL) * sizeof(T);
+        return p;
+    }
+};
+
+int default_chunk(const pic_config* c) {
+    if (c->mapping == PIC_MAP_STATIC) return 1 << 30;
+    return c->chunk > 0 ? c->chunk : 2048;
+}
+
+}  // namespace
+
+struct pic_sim {
+    pic_config cfg{};
+    Layout L;
+    char* arena = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap0 = nullptr, cap1 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int push_grid = 0;
+    int column_pts = 0;
+    std::vector<int> h_pbase, h_pcap;
+    std::string err;
+};
+
+struct pic_batch {
+    std::vector<pic_sim*> sims;
+    BatchDev hb{};
+    BatchDev* db = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap0 = nullptr, cap1 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+const char* validate(const pic_config* c) {
+    if (!c) return "null config";
+    if (c->dims != 2 && c->dims != 3) return "dims must be 2 or 3";
+    if (c->dims == 3) return "3D3V is not available in this build";
+    if (c->precision != PIC_FP64 && c->precision != PIC_FP32) return "bad precision";
+    if (c->window != 0 && c->window != 1) return "bad window flag";
+    if (c->mapping != PIC_MAP_QUEUE && c->mapping != PIC_MAP_STATIC) return "bad mapping";
+    for (int a = 0; a < c->dims; a++) {
+        if (c->n[a] < 4) return "each axis needs at least 4 cells";
+        if (!(c->d[a] > 0) || !std::isfinite(c->d[a])) return "cell sizes must be positive";
+        if (c->patch[a] < 4 || c->patch[a] % 4 != 0 || c->patch[a] > 64)
+            return "patch sides must be multiples of 4 in [4, 64]";
+        if (c->n[a] % c->patch[a] != 0) return "patch sides must divide the grid";
+        if (!(c->dt < c->d[a])) return "dt must be below every cell size";
+    }
+    if (c->dims == 2 && c->n[2] != 1) return "2D needs n[2] = 1";
+    if (c->dims == 2 && (c->n[0] >= 65536 || c->n[1] >= 32768)) return "grid too large";
+    if (!(c->dt > 0) || !std::isfinite(c->dt)) return "dt must be positive";
+    if (!(c->m > 0)) return "mass must be positive";
+    if (c->capacity < 0 || c->capacity > (1LL << 31) - (1LL << 24)) return "bad capacity";
+    if (c->chunk < 0) return "bad chunk";
+    if (c->window) {
+        if (!(c->ramp_len > 0)) return "ramp_len must be positive";
+        for (int a = 0; a < c->dims; a++)
+            if (c->inject_ppc[a] < 1 || c->inject_ppc[a] > 16) return "inject_ppc in [1,16]";
+    }
+    return nullptr;
+}
+
+// Geometry + arena carve (base == nullptr: dry run for the byte count).
+Layout plan(const pic_config* c, char* base) {
+    Layout L;
+    Carver cv{base, base == nullptr};
+    SimDev& S = L.S;
+    S.dims = c->dims;
+    S.prec = c->precision;
+    S.window = c->window;
+    S.mapping = c->mapping;
+    for (int a = 0; a < 3; a++) {
+        S.n[a] = a < c->dims ? c->n[a] : 1;
+        S.P[a] = a < c->dims ? c->patch[a] : 1;
+        S.np[a] = S.n[a] / S.P[a];
+        S.d[a] = a < c->dims ? c->d[a] : 1.0;
+        S.ippc[a] = a < c->dims ? std::max(1, c->inject_ppc[a]) : 1;
+    }
+    S.npatch = S.np[0] * S.np[1] * S.np[2];
+    // TMA box: interior [p0-1, p0+P+3) in x (P + 4 columns, 16-byte rows), P + 3 rows
+    S.BX = S.P[0] + 4;
+    S.BY = S.P[1] + 3;
+    S.BZ = c->dims == 3 ? S.P[2] + 3 : 1;
+    S.NX = S.n[0] + 4;
+    S.NY = S.n[1] + 3;
+    S.NZ = c->dims == 3 ? S.n[2] + 3 : 1;
+    S.fstride = (long long)S.NX * S.NY * S.NZ;
+    S.dt = c->dt;
+    S.q = c->q;
+    S.m = c->m;
+    S.n0 = c->n0;
+    S.ramp_x0 = c->ramp_x0;
+    S.ramp_len = c->ramp_len;
+    S.ncell = (long long)S.n[0] * S.n[1] * S.n[2];
+    const long long es = c->precision == PIC_FP64 ? 8 : 4;
+    const long long cap = c->capacity;
+    S.capacity = cap;
+
+    L.ds = cv.take<SimDev>(1);
+    L.db = cv.take<BatchDev>(1);
+    L.prefix = cv.take<int>(2);
+    S.tmap = cv.take<CUtensorMap>(2, 128);
+    S.st = cv.take<StepState>(1);
+    S.status = cv.take<int>(1);
+    S.red = cv.take<double>(8);
+    for (int g = 0; g < 2; g++) S.F[g] = cv.take<char>(6 * S.fstride * es);
+    for (int g = 0; g < 2; g++) S.H[g] = cv.take<char>(3 * S.fstride * es);
+    for (int g = 0; g < 2; g++) S.J[g] = cv.take<double>(3 * S.fstride);
+    S.rho = cv.take<double>(S.ncell);
+    S.rho_bg = cv.take<double>(S.ncell);
+    S.cell = c->precision == PIC_FP32 ? cv.take<int>(cap) : nullptr;
+    for (int a = 0; a < 3; a++) S.xi[a] = a < c->dims ? cv.take<char>(cap * es) : nullptr;
+    for (int a = 0; a < 3; a++) S.u[a] = cv.take<char>(cap * es);
+    S.w = cv.take<char>(cap * es);
+    S.id = cv.take<int>(cap);
+    S.holes = cv.take<int>(cap);
+    S.aux = cv.take<int>(cap);
+    S.pbase = cv.take<int>(S.npatch);
+    S.pcap = cv.take<int>(S.npatch);
+    S.pcount = cv.take<int>(S.npatch);
+    S.hcount = cv.take<int>(S.npatch);
+    S.mbase = cv.take<int>(S.npatch);
+    S.mcap = cv.take<int>(S.npatch);
+    S.mcount = cv.take<int>(S.npatch);
+    S.mtotal = cap / 4 + 64LL * S.npatch;
+    S.mcell = c->precision == PIC_FP32 ? cv.take<int>(S.mtotal) : nullptr;
+    for (int a = 0; a < 3; a++) S.mxi[a] = a < c->dims ? cv.take<char>(S.mtotal * es) : nullptr;
+    for (int a = 0; a < 3; a++) S.mu[a] = cv.take<char>(S.mtotal * es);
+    S.mw = cv.take<char>(S.mtotal * es);
+    S.mid = cv.take<int>(S.mtotal);
+
+    BatchDev& B = L.B;
+    B.nsims = 1;
+    B.chunk = default_chunk(c);
+    B.max_items = (int)std::min<long long>(S.npatch + cap / std::max(1, B.chunk) + 64, 1LL << 30);
+    B.total_patches = S.npatch;
+    B.max_patches = S.npatch;
+    B.max_ncell = (int)S.ncell;
+    B.items = cv.take<int4>(B.max_items);
+    B.nitems = cv.take<int>(1);
+    B.head = cv.take<int>(1);
+    B.sims = L.ds;
+    B.patch_prefix = L.prefix;
+    L.bytes = cv.off + 256;
+    return L;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// One tensor map per field generation: the six components E, B^n of F[g] as a
+// (x, y, component) tensor; the box is one patch tile plus guards.
+bool encode_field_maps(const SimDev& S, CUtensorMap out[2]) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const CUtensorMapDataType dt =
+        S.prec == PIC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    for (int g = 0; g < 2; g++) {
+        if (S.dims != 2) return false;
+        cuuint64_t dims[3] = {(cuuint64_t)S.NX, (cuuint64_t)S.NY, 6};
+        cuuint64_t strides[2] = {(cuuint64_t)S.NX * es, (cuuint64_t)S.NX * S.NY * es};
+        cuuint32_t box[3] = {(cuuint32_t)S.BX, (cuuint32_t)S.BY, 6};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = fn(&out[g], dt, 3, S.F[g], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+pic_status fail(std::string* err, pic_status st, const std::string& msg) {
+    if (err) *err = msg;
+    return st;
+}
+
+pic_status cuda_fail(std::string* err, cudaError_t e, const char* where) {
+    return fail(err, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                                \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(&s->err, e_, where);   \
+    } while (0)
+
+pic_status status_to_error(std::string* err, int st) {
+    if (st == 0) return PIC_OK;
+    if (st & ST_TIMEOUT) return fail(err, PIC_ERR_TIMEOUT, "a bounded device wait expired");
+    if (st & ST_NUMERIC)
+        return fail(err, PIC_ERR_NUMERIC, "non-finite particle state or a move of a cell or more");
+    if (st & ST_CAPACITY) return fail(err, PIC_ERR_CAPACITY, "a patch overflowed its capacity");
+    if (st & ST_MAILBOX) return fail(err, PIC_ERR_CAPACITY, "an exchange buffer overflowed");
+    if (st & ST_QUEUE) return fail(err, PIC_ERR_CAPACITY, "the work queue overflowed");
+    return fail(err, PIC_ERR_CUDA, "unknown device status");
+}
+
+struct GraphOwner {
+    cudaStream_t* cap0;
+    cudaStream_t* cap1;
+    cudaEvent_t* ev_fork;
+    cudaEvent_t* ev_join;
+    cudaGraph_t* graph;
+    cudaGraphExec_t* gexec;
+};
+
+// Captures one step into a graph: queue build -> particle kernel -> (Yee on a
+// second branch) | (injection -> exchange) -> end of step.
+cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_patches,
+                         int max_ncell, int max_column, int dims, int prec, int mapping,
+                         const int P[3], int grid, bool window) {
+    cudaError_t e;
+    if (!*o.cap0) {
+        if ((e = cudaStreamCreateWithFlags(o.cap0, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(o.cap1, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(o.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(o.ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaStreamBeginCapture(*o.cap0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+    cudaError_t le = launch_queue_build(db, *o.cap0);
+    if (le == cudaSuccess) le = launch_push(db, dims, prec, mapping, P[0], P[1], P[2], grid, *o.cap0);
+    if (le == cudaSuccess) le = cudaEventRecord(*o.ev_fork, *o.cap0);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap1, *o.ev_fork, 0);
+    if (le == cudaSuccess) le = launch_yee(db, nsims, max_ncell, dims, prec, *o.cap1);
+    if (le == cudaSuccess) le = cudaEventRecord(*o.ev_join, *o.cap1);
+    if (le == cudaSuccess && window) le = launch_inject(db, nsims, max_column, prec, *o.cap0);
+    if (le == cudaSuccess) le = launch_exchange(db, nsims, max_patches, prec, *o.cap0);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap0, *o.ev_join, 0);
+    if (le == cudaSuccess) le = launch_end_step(db, nsims, *o.cap0);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(*o.cap0, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    if (*o.gexec) cudaGraphExecDestroy(*o.gexec);
+    if (*o.graph) cudaGraphDestroy(*o.graph);
+    *o.graph = g;
+    *o.gexec = nullptr;
+    return cudaGraphInstantiate(o.gexec, g, 0);
+}
+
+void destroy_graph_owner(GraphOwner o) {
+    if (*o.gexec) cudaGraphExecDestroy(*o.gexec);
+    if (*o.graph) cudaGraphDestroy(*o.graph);
+    if (*o.ev_fork) cudaEventDestroy(*o.ev_fork);
+    if (*o.ev_join) cudaEventDestroy(*o.ev_join);
+    if (*o.cap0) cudaStreamDestroy(*o.cap0);
+    if (*o.cap1) cudaStreamDestroy(*o.cap1);
+}
+
+// Grid of the particle kernel: one CTA per patch (static mapping) or the number of
+// CTAs resident at once (persistent queue). Also sets the kernel's shared-memory
+// attribute, which every launch needs.
+int push_grid_size(int dims, int prec, const int P[3], bool static_map, int npatch) {
+    int dev = 0, nsm = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per = push_occupancy(dims, prec, P[0], P[1], P[2], &smem);
+    if (per < 1) per = 1;
+    return static_map ? std::max(1, npatch) : nsm * per;
+}
+
+// Padded device layout of a host [nz][ny][nx] array (guards: periodic images, or
+// zero along a window axis).
+template <typename T>
+void pad_field(const SimDev& S, const double* src, T* dst) {
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const bool px = !S.window;
+    const int zlo = S.dims == 3 ? -1 : 0, zhi = S.dims == 3 ? nz + 2 : 1;
+    for (int kp = zlo; kp < zhi; kp++) {
+        if (S.dims == 3 && kp + kGuard >= S.NZ) continue;
+        const int k = S.dims == 3 ? ((kp % nz) + nz) % nz : 0;
+        const long long zoff = S.dims == 3 ? (long long)(kp + kGuard) * S.NY * S.NX : 0;
+        for (int jp = -1; jp < ny + 2; jp++) {
+            const int j = ((jp % ny) + ny) % ny;
+            for (int ip = -1; ip < S.NX - 1; ip++) {
+                double v = 0.0;
+                if (ip >= 0 && ip < nx) {
+                    v = src[((long long)k * ny + j) * nx + ip];
+                } else if (px && ip < nx + 2) {
+                    const int i = ((ip % nx) + nx) % nx;
+                    v = src[((long long)k * ny + j) * nx + i];
+                }
+                dst[zoff + (long long)(jp + kGuard) * S.NX + (ip + kGuard)] = (T)v;
+            }
+        }
+    }
+}
+
+template <typename T>
+void unpad_field(const SimDev& S, const T* src, double* dst) {
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const long long pi =
+                    ((long long)(S.dims == 3 ? k + kGuard : 0) * S.NY + (j + kGuard)) * S.NX +
+                    (i + kGuard);
+                dst[((long long)k * ny + j) * nx + i] = (double)src[pi];
+            }
+}
+
+uint64_t mix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" size_t pic_required_bytes(const pic_config* cfg) {
+    if (validate(cfg)) return 0;
+    return plan(cfg, nullptr).bytes;
+}
+
+extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
+                                 void* cuda_stream, pic_sim** out) {
+    if (!out) return PIC_ERR_INVALID;
+    *out = nullptr;
+    if (validate(cfg)) return PIC_ERR_INVALID;
+    if (!dev_arena || (reinterpret_cast<uintptr_t>(dev_arena) & 255)) return PIC_ERR_INVALID;
+    if (arena_bytes < plan(cfg, nullptr).bytes) return PIC_ERR_NOMEM;
+    pic_sim* s = new (std::nothrow) pic_sim();
+    if (!s) return PIC_ERR_NOMEM;
+    s->cfg = *cfg;
+    s->arena = static_cast<char*>(dev_arena);
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->L = plan(cfg, s->arena);
+    const SimDev& S = s->L.S;
+    s->column_pts = cfg->window ? S.n[1] * S.ippc[0] * S.ippc[1] : 0;
+    auto bail = [&](pic_status st) {
+        GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
+        destroy_graph_owner(o);
+        delete s;
+        return st;
+    };
+    if (cudaMemsetAsync(s->arena, 0, s->L.bytes - 256, s->stream) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+    CUtensorMap maps[2];
+    if (!encode_field_maps(S, maps)) return bail(PIC_ERR_CUDA);
+    int prefix[2] = {0, S.npatch};
+    if (cudaMemcpyAsync((void*)S.tmap, maps, sizeof(maps), cudaMemcpyHostToDevice, s->stream) ||
+        cudaMemcpyAsync(s->L.ds, &S, sizeof(SimDev), cudaMemcpyHostToDevice, s->stream) ||
+        cudaMemcpyAsync(s->L.db, &s->L.B, sizeof(BatchDev), cudaMemcpyHostToDevice, s->stream) ||
+        cudaMemcpyAsync(s->L.prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice, s->stream))
+        return bail(PIC_ERR_CUDA);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bail(PIC_ERR_CUDA);
+    s->push_grid = push_grid_size(S.dims, S.prec, S.P, cfg->mapping == PIC_MAP_STATIC, S.npatch);
+    GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
+    if (capture_step(o, s->L.db, 1, S.npatch, (int)S.ncell, s->column_pts, S.dims, S.prec,
+                     S.mapping, S.P, s->push_grid, S.window != 0) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+    *out = s;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* x,
+                                         const double* y, const double* z, const double* ux,
+                                         const double* uy, const double* uz, const double* w,
+                                         const int* id) {
+    if (!s) return PIC_ERR_INVALID;
+    const SimDev& S = s->L.S;
+    if (n < 0) return fail(&s->err, PIC_ERR_INVALID, "negative particle count");
+    if (n > S.capacity) return fail(&s->err, PIC_ERR_CAPACITY, "more particles than capacity");
+    if (n > 0 && (!x || !y || !ux || !uy || !uz || !w || !id || (S.dims == 3 && !z)))
+        return fail(&s->err, PIC_ERR_INVALID, "null particle array");
+    CK(cudaStreamSynchronize(s->stream), "sync before load");
+    const int dims = S.dims;
+    const double* pos[3] = {x, y, z};
+    std::vector<int> ip(n * 3);
+    std::vector<double> xi(n * 3);
+    std::vector<int> patch(n);
+    std::vector<int> counts(S.npatch, 0);
+    int maxid = -1;
+    for (long long p = 0; p < n; p++) {
+        int pc[3] = {0, 0, 0};
+        for (int a = 0; a < dims; a++) {
+            const double v = pos[a][p];
+            const double L = S.n[a] * S.d[a];
+            if (!std::isfinite(v) || v < 0.0 || v >= L)
+                return fail(&s->err, PIC_ERR_INVALID, "particle position outside the grid");
+            double c = v / S.d[a];
+            if (c >= (double)S.n[a]) c = std::nextafter((double)S.n[a], 0.0);
+            const int i = (int)std::floor(c);
+            xi[p * 3 + a] = c;
+            ip[p * 3 + a] = i;
+            pc[a] = i / S.P[a];
+        }
+        if (!std::isfinite(ux[p]) || !std::isfinite(uy[p]) || !std::isfinite(uz[p]) ||
+            !std::isfinite(w[p]))
+            return fail(&s->err, PIC_ERR_NUMERIC, "non-finite particle momentum or weight");
+        if (id[p] < 0) return fail(&s->err, PIC_ERR_INVALID, "negative particle id");
+        maxid = std::max(maxid, id[p]);
+        patch[p] = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
+        counts[patch[p]]++;
+    }
+    // per-patch capacity: the free slots are shared half by count, half evenly
+    const long long spare = S.capacity - n;
+    std::vector<int> pcap(S.npatch), pbase(S.npatch), mcap(S.npatch), mbase(S.npatch);
+    long long acc = 0, macc = 0;
+    for (int p = 0; p < S.npatch; p++) {
+        double share = n > 0 ? 0.5 * (double)counts[p] / (double)n + 0.5 / S.npatch : 1.0 / S.npatch;
+        long long c = counts[p] + (long long)std::floor((double)spare * share);
+        pcap[p] = (int)c;
+        pbase[p] = (int)acc;
+        acc += c;
+        mcap[p] = std::max(64, pcap[p] / 4);
+        mbase[p] = (int)macc;
+        macc += mcap[p];
+    }
+    if (acc > S.capacity || macc > S.mtotal)
+        return fail(&s->err, PIC_ERR_CAPACITY, "capacity split failed");
+    // stable binning, then a fixed pseudo-random order inside each patch so that the
+    // lanes of a warp rarely share a cell (spreads shared-memory atomics)
+    std::vector<long long> order(n);
+    {
+        std::vector<long long> cursor(S.npatch);
+        long long a = 0;
+        for (int p = 0; p < S.npatch; p++) {
+            cursor[p] = a;
+            a += counts[p];
+        }
+        std::vector<long long> start(cursor);
+        for (long long p = 0; p < n; p++) order[cursor[patch[p]]++] = p;
+        for (int p = 0; p < S.npatch; p++) {
+            const long long b0 = start[p], c = counts[p];
+            for (long long k = c - 1; k > 0; k--) {
+                const long long r = (long long)(mix64(((uint64_t)p << 32) ^ (uint64_t)k) % (uint64_t)(k + 1));
+                std::swap(order[b0 + k], order[b0 + r]);
+            }
+        }
+    }
+    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const long long cap = S.capacity;
+    std::vector<char> hx[3], hu[3], hw;
+    std::vector<int> hid(cap, -1), hcell;
+    for (int a = 0; a < dims; a++) hx[a].assign(cap * es, 0);
+    for (int a = 0; a < 3; a++) hu[a].assign(cap * es, 0);
+    hw.assign(cap * es, 0);
+    if (S.prec == PIC_FP32) hcell.assign(cap, 0);
+    {
+        long long k = 0;
+        for (int p = 0; p < S.npatch; p++) {
+            for (int c = 0; c < counts[p]; c++, k++) {
+                const long long src = order[k];
+                const long long dst = pbase[p] + c;
+                const double uu[3] = {ux[src], uy[src], uz[src]};
+                if (S.prec == PIC_FP64) {
+                    for (int a = 0; a < dims; a++)
+                        reinterpret_cast<double*>(hx[a].data())[dst] = xi[src * 3 + a];
+                    for (int a = 0; a < 3; a++) reinterpret_cast<double*>(hu[a].data())[dst] = uu[a];
+                    reinterpret_cast<double*>(hw.data())[dst] = w[src];
+                } else {
+                    int cellv = 0;
+                    for (int a = 0; a < dims; a++) {
+                        int i = ip[src * 3 + a];
+                        float f = (float)(xi[src * 3 + a] - (double)i);
+                        if (f >= 1.0f) {  // rounding up to the next cell
+                            f = 0.0f;
+                            i += 1;
+                        }
+                        reinterpret_cast<float*>(hx[a].data())[dst] = f;
+                        cellv |= i << (16 * a);
+                    }
+                    hcell[dst] = cellv;
+                    for (int a = 0; a < 3; a++) reinterpret_cast<float*>(hu[a].data())[dst] = (float)uu[a];
+                    reinterpret_cast<float*>(hw.data())[dst] = (float)w[src];
+                }
+                hid[dst] = id[src];
+            }
+        }
+    }
+    for (int a = 0; a < dims; a++)
+        CK(cudaMemcpyAsync(S.xi[a], hx[a].data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy x");
+    for (int a = 0; a < 3; a++)
+        CK(cudaMemcpyAsync(S.u[a], hu[a].data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy u");
+    CK(cudaMemcpyAsync(S.w, hw.data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy w");
+    CK(cudaMemcpyAsync(S.id, hid.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream), "copy id");
+    if (S.prec == PIC_FP32)
+        CK(cudaMemcpyAsync(S.cell, hcell.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream),
+           "copy cell");
+    const size_t pb = S.npatch * sizeof(int);
+    CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
+    CK(cudaMemcpyAsync(S.pcap, pcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcap");
+    CK(cudaMemcpyAsync(S.pcount, counts.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcount");
+    CK(cudaMemcpyAsync(S.mbase, mbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mbase");
+    CK(cudaMemcpyAsync(S.mcap, mcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mcap");
+    CK(cudaMemsetAsync(S.hcount, 0, pb, s->stream), "zero hcount");
+    CK(cudaMemsetAsync(S.mcount, 0, pb, s->stream), "zero mcount");
+    StepState st{};
+    st.next_id = (long long)maxid + 1;
+    CK(cudaMemcpyAsync(S.st, &st, sizeof(st), cudaMemcpyHostToDevice, s->stream), "copy state");
+    CK(cudaMemsetAsync(S.status, 0, sizeof(int), s->stream), "zero status");
+    CK(cudaStreamSynchronize(s->stream), "load particles");
+    s->h_pbase = pbase;
+    s->h_pcap = pcap;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], const double* const B[3],
+                                      const double* rho_bg) {
+    if (!s || !E || !B) return PIC_ERR_INVALID;
+    for (int a = 0; a < 3; a++)
+        if (!E[a] || !B[a]) return fail(&s->err, PIC_ERR_INVALID, "null field array");
+    const SimDev& S = s->L.S;
+    CK(cudaStreamSynchronize(s->stream), "sync before fields");
+    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const long long fs = S.fstride;
+    std::vector<char> hF(6 * fs * es, 0), hH(3 * fs * es, 0);
+    for (int a = 0; a < 3; a++) {
+        if (S.prec == PIC_FP64) {
+            pad_field(S, E[a], reinterpret_cast<double*>(hF.data()) + a * fs);
+            pad_field(S, B[a], reinterpret_cast<double*>(hF.data()) + (3 + a) * fs);
+            pad_field(S, B[a], reinterpret_cast<double*>(hH.data()) + a * fs);
+        } else {
+            pad_field(S, E[a], reinterpret_cast<float*>(hF.data()) + a * fs);
+            pad_field(S, B[a], reinterpret_cast<float*>(hF.data()) + (3 + a) * fs);
+            pad_field(S, B[a], reinterpret_cast<float*>(hH.data()) + a * fs);
+        }
+    }
+    CK(cudaMemcpyAsync(S.F[0], hF.data(), hF.size(), cudaMemcpyHostToDevice, s->stream), "copy F");
+    CK(cudaMemcpyAsync(S.H[0], hH.data(), hH.size(), cudaMemcpyHostToDevice, s->stream), "copy H");
+    CK(cudaMemsetAsync(S.F[1], 0, hF.size(), s->stream), "zero F1");
+    CK(cudaMemsetAsync(S.H[1], 0, hH.size(), s->stream), "zero H1");
+    CK(cudaMemsetAsync(S.J[0], 0, 3 * fs * sizeof(double), s->stream), "zero J0");
+    CK(cudaMemsetAsync(S.J[1], 0, 3 * fs * sizeof(double), s->stream), "zero J1");
+    // the fields belong to step 0
+    StepState st{};
+    CK(cudaMemcpyAsync(&st, S.st, sizeof(st), cudaMemcpyDeviceToHost, s->stream), "read state");
+    CK(cudaStreamSynchronize(s->stream), "read state");
+    st.step = 0;
+    st.nshift = 0;
+    st.gen = 0;
+    st.shift = 0;
+    CK(cudaMemcpyAsync(S.st, &st, sizeof(st), cudaMemcpyHostToDevice, s->stream), "write state");
+    if (rho_bg) {
+        CK(cudaMemcpyAsync(S.rho_bg, rho_bg, S.ncell * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream),
+           "copy rho_bg");
+    } else {
+        CK(launch_gauss(s->L.ds, S, S.prec, 0, s->stream), "rho_bg");
+    }
+    CK(cudaStreamSynchronize(s->stream), "load fields");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_step(pic_sim* s, int nsteps) {
+    if (!s || nsteps < 0) return PIC_ERR_INVALID;
+    for (int i = 0; i < nsteps; i++) CK(cudaGraphLaunch(s->gexec, s->stream), "graph launch");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sync(pic_sim* s) {
+    if (!s) return PIC_ERR_INVALID;
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    int st = 0;
+    CK(cudaMemcpy(&st, s->L.S.status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    return status_to_error(&s->err, st);
+}
+
+extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes, size_t* written) {
+    if (!s) return PIC_ERR_INVALID;
+    if (written) *written = 0;
+    pic_status rc = pic_sync(s);
+    if (rc != PIC_OK) return rc;
+    const SimDev& S = s->L.S;
+    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    auto need = [&](size_t b) { return out && out_bytes >= b; };
+    StepState st{};
+    CK(cudaMemcpy(&st, S.st, sizeof(st), cudaMemcpyDeviceToHost), "read state");
+    const int g = (int)(st.step & 1);
+    std::vector<int> counts(S.npatch);
+    auto read_counts = [&]() -> cudaError_t {
+        return cudaMemcpy(counts.data(), S.pcount, S.npatch * sizeof(int), cudaMemcpyDeviceToHost);
+    };
+    switch (kind) {
+        case PIC_DIAG_ENERGY: {
+            if (!need(3 * sizeof(double))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            CK(cudaMemsetAsync(S.red, 0, 8 * sizeof(double), s->stream), "zero red");
+            CK(launch_energy(s->L.ds, S.ncell, S.capacity, S.prec, s->stream), "energy");
+            double r[3];
+            CK(cudaMemcpyAsync(r, S.red, sizeof(r), cudaMemcpyDeviceToHost, s->stream), "read red");
+            CK(cudaStreamSynchronize(s->stream), "energy");
+            const double dV = S.d[0] * S.d[1] * (S.dims == 3 ? S.d[2] : 1.0);
+            double* o = static_cast<double*>(out);
+            o[0] = 0.5 * r[0] * dV;
+            o[1] = 0.5 * r[1] * dV;
+            o[2] = r[2];
+            if (written) *written = 3 * sizeof(double);
+            return PIC_OK;
+        }
+        case PIC_DIAG_GAUSS: {
+            const size_t b = S.ncell * sizeof(double);
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            CK(launch_gauss(s->L.ds, S, S.prec, 1, s->stream), "gauss");
+            CK(cudaMemcpyAsync(out, S.rho, b, cudaMemcpyDeviceToHost, s->stream), "read gauss");
+            CK(cudaStreamSynchronize(s->stream), "gauss");
+            if (written) *written = b;
+            return PIC_OK;
+        }
+        case PIC_DIAG_FIELDS:
+        case PIC_DIAG_EX_AXIS: {
+            const long long nc = S.ncell, fs = S.fstride;
+            const size_t b = kind == PIC_DIAG_FIELDS ? 12 * nc * sizeof(double) : S.n[0] * sizeof(double);
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            std::vector<char> hF(6 * fs * es), hH(3 * fs * es);
+            std::vector<double> hJ(3 * fs);
+            CK(cudaMemcpy(hF.data(), S.F[g], hF.size(), cudaMemcpyDeviceToHost), "read F");
+            CK(cudaMemcpy(hH.data(), S.H[g], hH.size(), cudaMemcpyDeviceToHost), "read H");
+            CK(cudaMemcpy(hJ.data(), S.J[1 - g], hJ.size() * sizeof(double), cudaMemcpyDeviceToHost),
+               "read J");
+            std::vector<double> all(12 * nc);
+            for (int a = 0; a < 3; a++) {
+                if (S.prec == PIC_FP64) {
+                    unpad_field(S, reinterpret_cast<double*>(hF.data()) + a * fs, &all[(0 + a) * nc]);
+                    unpad_field(S, reinterpret_cast<double*>(hH.data()) + a * fs, &all[(3 + a) * nc]);
+                    unpad_field(S, reinterpret_cast<double*>(hF.data()) + (3 + a) * fs, &all[(6 + a) * nc]);
+                } else {
+                    unpad_field(S, reinterpret_cast<float*>(hF.data()) + a * fs, &all[(0 + a) * nc]);
+                    unpad_field(S, reinterpret_cast<float*>(hH.data()) + a * fs, &all[(3 + a) * nc]);
+                    unpad_field(S, reinterpret_cast<float*>(hF.data()) + (3 + a) * fs, &all[(6 + a) * nc]);
+                }
+                unpad_field(S, hJ.data() + a * fs, &all[(9 + a) * nc]);
+            }
+            if (kind == PIC_DIAG_FIELDS) {
+                memcpy(out, all.data(), b);
+            } else {
+                const long long row = ((long long)(S.n[2] / 2) * S.n[1] + S.n[1] / 2) * S.n[0];
+                memcpy(out, &all[row], b);
+            }
+            if (written) *written = b;
+            return PIC_OK;
+        }
+        case PIC_DIAG_NUM_PARTICLES: {
+            if (!need(sizeof(long long))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            CK(read_counts(), "read counts");
+            long long n = 0;
+            for (int c : counts) n += c;
+            *static_cast<long long*>(out) = n;
+            if (written) *written = sizeof(long long);
+            return PIC_OK;
+        }
+        case PIC_DIAG_PATCH_COUNTS: {
+            const size_t b = S.npatch * sizeof(int);
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            CK(read_counts(), "read counts");
+            memcpy(out, counts.data(), b);
+            if (written) *written = b;
+            return PIC_OK;
+        }
+        case PIC_DIAG_STEP: {
+            if (!need(2 * sizeof(long long))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            long long* o = static_cast<long long*>(out);
+            o[0] = st.step;
+            o[1] = st.nshift;
+            if (written) *written = 2 * sizeof(long long);
+            return PIC_OK;
+        }
+        case PIC_DIAG_PARTICLES: {
+            CK(read_counts(), "read counts");
+            long long n = 0;
+            for (int c : counts) n += c;
+            const size_t b = (size_t)n * (7 * sizeof(double) + sizeof(int));
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            const long long cap = S.capacity;
+            std::vector<char> hx[3], hu[3], hw(cap * es);
+            std::vector<int> hid(cap), hcell;
+            for (int a = 0; a < S.dims; a++) {
+                hx[a].resize(cap * es);
+                CK(cudaMemcpy(hx[a].data(), S.xi[a], cap * es, cudaMemcpyDeviceToHost), "read x");
+            }
+            for (int a = 0; a < 3; a++) {
+                hu[a].resize(cap * es);
+                CK(cudaMemcpy(hu[a].data(), S.u[a], cap * es, cudaMemcpyDeviceToHost), "read u");
+            }
+            CK(cudaMemcpy(hw.data(), S.w, cap * es, cudaMemcpyDeviceToHost), "read w");
+            CK(cudaMemcpy(hid.data(), S.id, cap * sizeof(int), cudaMemcpyDeviceToHost), "read id");
+            if (S.prec == PIC_FP32) {
+                hcell.resize(cap);
+                CK(cudaMemcpy(hcell.data(), S.cell, cap * sizeof(int), cudaMemcpyDeviceToHost), "read cell");
+            }
+            std::vector<std::pair<int, long long>> live;
+            live.reserve(n);
+            for (int p = 0; p < S.npatch; p++)
+                for (int c = 0; c < counts[p]; c++) {
+                    const long long sl = (long long)s->h_pbase[p] + c;
+                    live.emplace_back(hid[sl], sl);
+                }
+            std::sort(live.begin(), live.end());
+            double* o = static_cast<double*>(out);
+            int* oid = reinterpret_cast<int*>(o + 7 * n);
+            for (long long k = 0; k < n; k++) {
+                const long long sl = live[k].second;
+                double pos[3] = {0, 0, 0}, uu[3], ww;
+                for (int a = 0; a < S.dims; a++) {
+                    if (S.prec == PIC_FP64) {
+                        pos[a] = reinterpret_cast<double*>(hx[a].data())[sl] * S.d[a];
+                    } else {
+                        const int i = (hcell[sl] >> (16 * a)) & 0xFFFF;
+                        pos[a] = ((double)i + (double)reinterpret_cast<float*>(hx[a].data())[sl]) * S.d[a];
+                    }
+                }
+                for (int a = 0; a < 3; a++)
+                    uu[a] = S.prec == PIC_FP64 ? reinterpret_cast<double*>(hu[a].data())[sl]
+                                               : (double)reinterpret_cast<float*>(hu[a].data())[sl];
+                ww = S.prec == PIC_FP64 ? reinterpret_cast<double*>(hw.data())[sl]
+                                        : (double)reinterpret_cast<float*>(hw.data())[sl];
+                o[0 * n + k] = pos[0];
+                o[1 * n + k] = pos[1];
+                o[2 * n + k] = pos[2];
+                o[3 * n + k] = uu[0];
+                o[4 * n + k] = uu[1];
+                o[5 * n + k] = uu[2];
+                o[6 * n + k] = ww;
+                oid[k] = live[k].first;
+            }
+            if (written) *written = b;
+            return PIC_OK;
+        }
+        default:
+            return fail(&s->err, PIC_ERR_INVALID, "unknown diagnostic kind");
+    }
+}
+
+extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) {
+    if (!s || nsteps < 0 || !ms || n_ms < 7) return PIC_ERR_INVALID;
+    const SimDev& S = s->L.S;
+    cudaEvent_t ev[7];
+    for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ev[i]), "event create");
+    for (int i = 0; i < 7; i++) ms[i] = 0.0;
+    pic_status rc = PIC_OK;
+    for (int it = 0; it < nsteps && rc == PIC_OK; it++) {
+        cudaError_t e = cudaEventRecord(ev[0], s->stream);
+        if (e == cudaSuccess) e = launch_queue_build(s->L.db, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s->stream);
+        if (e == cudaSuccess)
+            e = launch_push(s->L.db, S.dims, S.prec, S.mapping, S.P[0], S.P[1], S.P[2], s->push_grid,
+                            s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], s->stream);
+        if (e == cudaSuccess && S.window) e = launch_inject(s->L.db, 1, s->column_pts, S.prec, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], s->stream);
+        if (e == cudaSuccess) e = launch_exchange(s->L.db, 1, S.npatch, S.prec, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
+        if (e == cudaSuccess) e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
+        if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[6], s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(&s->err, e, "profile");
+            break;
+        }
+        for (int k = 0; k < 6; k++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms[k] += t;
+        }
+        float tt = 0.f;
+        cudaEventElapsedTime(&tt, ev[0], ev[6]);
+        ms[6] += tt;
+    }
+    for (int i = 0; i < 7; i++) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+extern "C" pic_status pic_destroy(pic_sim* s) {
+    if (!s) return PIC_ERR_INVALID;
+    cudaStreamSynchronize(s->stream);
+    GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
+    destroy_graph_owner(o);
+    delete s;
+    return PIC_OK;
+}
+
+extern "C" const char* pic_last_error(const pic_sim* s) {
+    if (!s) return "null sim";
+    return s->err.c_str();
+}
+
+// ===================================================================== batches
+
+namespace {
+struct BatchLayout {
+    SimDev* sims;
+    int* prefix;
+    BatchDev* db;
+    int4* items;
+    int* nitems;
+    int* head;
+    int max_items;
+    size_t bytes;
+};
+
+BatchLayout plan_batch(pic_sim* const* sims, int nsims, char* base) {
+    Carver cv{base, base == nullptr};
+    BatchLayout b{};
+    b.sims = cv.take<SimDev>(nsims);
+    b.prefix = cv.take<int>(nsims + 1);
+    b.db = cv.take<BatchDev>(1);
+    long long items = 64;
+    for (int i = 0; i < nsims; i++) {
+        const SimDev& S = sims[i]->L.S;
+        items += S.npatch + S.capacity / std::max(1, default_chunk(&sims[0]->cfg));
+    }
+    b.max_items = (int)std::min<long long>(items, 1LL << 30);
+    b.items = cv.take<int4>(b.max_items);
+    b.nitems = cv.take<int>(1);
+    b.head = cv.take<int>(1);
+    b.bytes = cv.off + 256;
+    return b;
+}
+
+const char* batch_check(pic_sim* const* sims, int nsims) {
+    if (!sims || nsims < 1) return "empty batch";
+    for (int i = 0; i < nsims; i++) {
+        if (!sims[i]) return "null sim";
+        if (sims[i]->L.S.dims != sims[0]->L.S.dims || sims[i]->L.S.prec != sims[0]->L.S.prec)
+            return "sims of a batch must share dims and precision";
+        if (sims[i]->L.S.P[0] != sims[0]->L.S.P[0] || sims[i]->L.S.P[1] != sims[0]->L.S.P[1] ||
+            sims[i]->L.S.P[2] != sims[0]->L.S.P[2])
+            return "sims of a batch must share the patch size";
+        if (sims[i]->cfg.mapping != sims[0]->cfg.mapping) return "sims must share the mapping";
+    }
+    return nullptr;
+}
+}  // namespace
+
+extern "C" size_t pic_batch_required_bytes(pic_sim* const* sims, int nsims) {
+    if (batch_check(sims, nsims)) return 0;
+    return plan_batch(sims, nsims, nullptr).bytes;
+}
+
+extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
+                                       size_t arena_bytes, void* cuda_stream, pic_batch** out) {
+    if (!out) return PIC_ERR_INVALID;
+    *out = nullptr;
+    if (batch_check(sims, nsims)) return PIC_ERR_INVALID;
+    if (!dev_arena || (reinterpret_cast<uintptr_t>(dev_arena) & 255)) return PIC_ERR_INVALID;
+    BatchLayout bl = plan_batch(sims, nsims, nullptr);
+    if (arena_bytes < bl.bytes) return PIC_ERR_NOMEM;
+    bl = plan_batch(sims, nsims, static_cast<char*>(dev_arena));
+    pic_batch* b = new (std::nothrow) pic_batch();
+    if (!b) return PIC_ERR_NOMEM;
+    b->sims.assign(sims, sims + nsims);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<SimDev> hsims(nsims);
+    std::vector<int> prefix(nsims + 1, 0);
+    int max_patches = 0, max_ncell = 0, max_column = 0;
+    bool any_window = false;
+    for (int i = 0; i < nsims; i++) {
+        hsims[i] = sims[i]->L.S;
+        prefix[i + 1] = prefix[i] + hsims[i].npatch;
+        max_patches = std::max(max_patches, hsims[i].npatch);
+        max_ncell = std::max(max_ncell, (int)hsims[i].ncell);
+        max_column = std::max(max_column, sims[i]->column_pts);
+        any_window = any_window || hsims[i].window;
+    }
+    BatchDev& B = b->hb;
+    B.nsims = nsims;
+    B.chunk = default_chunk(&sims[0]->cfg);
+    B.max_items = bl.max_items;
+    B.total_patches = prefix[nsims];
+    B.max_patches = max_patches;
+    B.max_ncell = max_ncell;
+    B.sims = bl.sims;
+    B.patch_prefix = bl.prefix;
+    B.items = bl.items;
+    B.nitems = bl.nitems;
+    B.head = bl.head;
+    b->db = bl.db;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nsims && e == cudaSuccess; i++) e = cudaStreamSynchronize(sims[i]->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bl.sims, hsims.data(), nsims * sizeof(SimDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bl.prefix, prefix.data(), (nsims + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bl.db, &B, sizeof(B), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    const SimDev& S0 = hsims[0];
+    const int grid = push_grid_size(S0.dims, S0.prec, S0.P, sims[0]->cfg.mapping == PIC_MAP_STATIC,
+                                    prefix[nsims]);
+    GraphOwner o{&b->cap0, &b->cap1, &b->ev_fork, &b->ev_join, &b->graph, &b->gexec};
+    if (e == cudaSuccess)
+        e = capture_step(o, bl.db, nsims, max_patches, max_ncell, max_column, S0.dims, S0.prec,
+                         sims[0]->cfg.mapping, S0.P, grid, any_window);
+    if (e != cudaSuccess) {
+        destroy_graph_owner(o);
+        delete b;
+        return PIC_ERR_CUDA;
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_step(pic_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return PIC_ERR_INVALID;
+    for (int i = 0; i < nsteps; i++)
+        if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return PIC_ERR_CUDA;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_destroy(pic_batch* b) {
+    if (!b) return PIC_ERR_INVALID;
+    cudaStreamSynchronize(b->stream);
+    GraphOwner o{&b->cap0, &b->cap1, &b->ev_fork, &b->ev_join, &b->graph, &b->gexec};
+    destroy_graph_owner(o);
+    delete b;
+    return PIC_OK;
+}

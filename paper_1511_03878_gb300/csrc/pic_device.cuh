@@ -1,0 +1,174 @@
+// Device-side building blocks: mbarrier + TMA inline PTX (sm_103a), order-2
+// B-spline shapes, relativistic Boris rotation, block-level scans.
+#pragma once
+#include <stdint.h>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+// ---------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// order earlier generic-proxy accesses of shared memory before async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2^31 SM clocks (about a
+// second) so that a lost transfer turns into a status flag, never a hang.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+    return true;
+}
+
+// TMA tiled load of a 3D box (x, y, component) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// TMA tiled load of a 4D box (x, y, z, component) into shared memory.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------- numerics
+
+// Quadratic B-spline weights of nodes (i-1, i, i+1) for delta = xi - i in [-1/2, 1/2].
+template <typename T>
+__device__ __forceinline__ void shape3(T delta, T S[3]) {
+    const T a = T(0.5) - delta, b = T(0.5) + delta;
+    S[0] = T(0.5) * a * a;
+    S[1] = T(0.75) - delta * delta;
+    S[2] = T(0.5) * b * b;
+}
+
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+// Relativistic Boris rotation (Boris 1970): u^{n-1/2} -> u^{n+1/2}; eps = q dt/(2m).
+// Returns 1/gamma^{n+1/2}.
+template <typename T>
+__device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
+    T um0 = u[0] + eps * E[0], um1 = u[1] + eps * E[1], um2 = u[2] + eps * E[2];
+    const T ig = rsqrt_t(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
+    const T t0 = eps * B[0] * ig, t1 = eps * B[1] * ig, t2 = eps * B[2] * ig;
+    const T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    const T up0 = um0 + (um1 * t2 - um2 * t1);
+    const T up1 = um1 + (um2 * t0 - um0 * t2);
+    const T up2 = um2 + (um0 * t1 - um1 * t0);
+    um0 += up1 * s2 - up2 * s1;
+    um1 += up2 * s0 - up0 * s2;
+    um2 += up0 * s1 - up1 * s0;
+    u[0] = um0 + eps * E[0];
+    u[1] = um1 + eps * E[1];
+    u[2] = um2 + eps * E[2];
+    return rsqrt_t(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// ---------------------------------------------------------------- scans
+
+// Exclusive block scan of one int per thread; blockDim.x a multiple of 32, <= 1024.
+// `warp_sums` must hold 32 ints of shared memory. Returns the exclusive prefix and
+// writes the block total to *total (all threads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    const int before = wid > 0 ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-aggregated atomicAdd of 1 on counter[key] for every active lane of `mask`
+// that holds `active`; returns this lane's slot. All lanes of `mask` must call it.
+__device__ __forceinline__ int warp_claim(int* counter_base, int key, bool active,
+                                          unsigned mask) {
+    const unsigned act = __ballot_sync(mask, active);
+    int slot = 0;
+    if (active) {
+        const unsigned peers = __match_any_sync(act, key);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & lanemask_lt());
+        int base = 0;
+        if ((threadIdx.x & 31) == leader) base = atomicAdd(counter_base + key, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        slot = base + rank;
+    }
+    return slot;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+}  // namespace pic

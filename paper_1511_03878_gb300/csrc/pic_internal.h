@@ -1,0 +1,115 @@
+// Internal device-visible data model of the patch-PIC library (host + device).
+//
+// Fields: every component is a padded array [NZ][NY][NX] with one guard cell
+// below each axis (interior index i is stored at i + 1). The particle kernel
+// stages a patch tile of E and B^n (6 components, contiguous) with one TMA box;
+// periodic axes keep their guard cells filled with periodic images.
+// Particles: patch-sorted SoA. Patch p owns slots [pbase[p], pbase[p] + pcap[p]),
+// the first pcount[p] of them live. FP64 path: positions are float64 in cell units
+// (xi = x / d). FP32 path: a global linear cell index plus float32 offsets in [0,1).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int kGuard = 1;        // guard cells below each axis in the padded field arrays
+constexpr int kThreads = 256;    // threads per CTA of the particle kernel
+constexpr int kQueueThreads = 1024;
+constexpr int kBuckets = 64;     // remainder buckets of the approximate LPT order
+
+// status bits latched by device code
+enum : int {
+    ST_CAPACITY = 1,   // patch overflow in the exchange
+    ST_MAILBOX = 2,    // exchange buffer overflow
+    ST_TIMEOUT = 4,    // bounded wait expired
+    ST_NUMERIC = 8,    // non-finite or too-large move
+    ST_QUEUE = 16,     // work queue overflow
+};
+
+struct StepState {
+    long long step;     // steps completed
+    long long nshift;   // window shifts completed
+    long long next_id;  // next particle id handed to injected particles
+    int shift;          // 1 if the current step ends with a window shift
+    int gen;            // field buffer generation read by the current step (step & 1)
+    int pad[2];
+};
+
+struct SimDev {
+    int dims, prec, window, mapping;
+    int n[3];        // cells
+    int P[3];        // cells per patch
+    int np[3];       // patches per axis
+    int npatch;
+    int NX, NY, NZ;  // padded extents
+    int BX, BY, BZ;  // TMA box extents
+    long long fstride;  // elements per padded component
+    double d[3], dt, q, m;
+    double n0, ramp_x0, ramp_len;
+    int ippc[3];
+    int pad0;
+    // fields
+    void* F[2];      // [6][NZ][NY][NX]: Ex Ey Ez Bnx Bny Bnz (B^n for the push)
+    void* H[2];      // [3][...]: B^{n+1/2}
+    double* J[2];    // [3][...] (guards unused)
+    const CUtensorMap* tmap;  // [2], in global memory
+    // particles
+    int* cell;       // FP32 only
+    void* xi[3];     // FP64: double positions in cell units; FP32: float offsets
+    void* u[3];
+    void* w;
+    int* id;
+    int* pbase; int* pcap; int* pcount;
+    int* hcount; int* holes; int* aux;
+    // exchange mailboxes (same SoA layout)
+    int* mbase; int* mcap; int* mcount;
+    int* mcell;
+    void* mxi[3];
+    void* mu[3];
+    void* mw;
+    int* mid;
+    long long capacity, mtotal;
+    // state and scratch
+    StepState* st;
+    int* status;
+    double* red;     // 8 reduction slots
+    double* rho;     // [ncell] scratch for the Gauss diagnostic
+    double* rho_bg;  // [ncell]
+    long long ncell;
+};
+
+struct BatchDev {
+    int nsims;
+    int chunk;
+    int max_items;
+    int total_patches;
+    int max_patches;     // largest npatch over sims
+    int max_ncell;
+    const SimDev* sims;  // device array [nsims]
+    const int* patch_prefix;  // [nsims + 1]
+    int4* items;         // {sim, patch, first, count}
+    int* nitems;
+    int* head;
+};
+
+// ---- launchers (each enqueues on the given stream) ----
+cudaError_t launch_queue_build(const BatchDev* bd, cudaStream_t s);
+cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping,
+                        int P0, int P1, int P2, int grid, cudaStream_t s);
+int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes);
+cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int prec,
+                          cudaStream_t s);
+cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int prec,
+                            cudaStream_t s);
+cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
+                       cudaStream_t s);
+cudaError_t launch_end_step(const BatchDev* bd, int nsims, cudaStream_t s);
+// diagnostics on one sim
+cudaError_t launch_energy(const SimDev* sd, long long ncell, long long cap, int prec,
+                          cudaStream_t s);
+cudaError_t launch_gauss(const SimDev* sd, const SimDev& hs, int prec, int mode,
+                         cudaStream_t s);
+
+}  // namespace pic

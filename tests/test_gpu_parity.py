@@ -1,0 +1,281 @@
+"""GPU (CUDA, sm_103a) vs CPU FP64 oracle, element by element, through the C ABI.
+
+Tolerances (normwise per array, max|a - b| / max|b|, particles matched by id):
+  FP64, 1 step   : 1e-12     FP64, <= 20 steps : 1e-9
+  FP32 (FP64 J)  : stated error, gated loosely (see each test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1511_03878_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELD_KEYS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bnx", "Bny", "Bnz", "Jx", "Jy", "Jz")
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1511_03878_gb300 import binding as b, build
+
+    build.build()
+    return b
+
+
+def normwise(a, b):
+    den = np.abs(b).max()
+    if den == 0:
+        return float(np.abs(a).max())
+    return float(np.abs(a - b).max() / den)
+
+
+def wrapdiff(a, b, L):
+    return (a - b + 0.5 * L) % L - 0.5 * L
+
+
+def make_oracle(w, cap=None):
+    p = w["params"]
+    c = orc.make_config(p["dims"], p["n"][:p["dims"]], p["d"][:p["dims"]], p["dt"],
+                        window=p["window"], q=p["q"], m=p["m"], n0=p["n0"],
+                        ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
+                        inject_ppc=p["inject_ppc"])
+    n = len(w["particles"]["x"])
+    o = orc.OracleSim(c, cap or max(4 * n, 100000))
+    o.set_particles(w["particles"])
+    o.set_fields(w["E"], w["B"])
+    o.set_rho_bg(None)
+    return o
+
+
+def compare(sim, o, params, tol, keys=FIELD_KEYS, check_particles=True):
+    f = sim.fields()
+    fo = o.get_fields()
+    errs = {}
+    for k in keys:
+        errs[k] = normwise(f[k], fo[k])
+    if check_particles:
+        q = sim.particles()
+        qo = o.get_particles()
+        assert len(q["id"]) == len(qo["id"])
+        assert np.array_equal(q["id"], qo["id"])
+        Lx = params["n"][0] * params["d"][0]
+        Ly = params["n"][1] * params["d"][1]
+        dx = wrapdiff(q["x"], qo["x"], Lx) if not params["window"] else q["x"] - qo["x"]
+        dy = wrapdiff(q["y"], qo["y"], Ly)
+        errs["x"] = float(np.abs(dx).max() / max(np.abs(qo["x"]).max(), 1e-300))
+        errs["y"] = float(np.abs(dy).max() / max(np.abs(qo["y"]).max(), 1e-300))
+        for k in ("ux", "uy", "uz", "w"):
+            errs[k] = normwise(q[k], qo[k])
+    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def small_lwfa(**kw):
+    args = dict(nx=256, ny=128, dx=0.125, dy=0.5, ppc=(2, 2), n0=0.01, ramp_cells=16,
+                a0=4.0, w0=15.0, tau=8.0, laser_back=12.0, patch=(32, 32))
+    args.update(kw)
+    w = inputs.lwfa2d(**args)
+    # plasma already around the pulse: ramp from 8 units behind the laser centre
+    if "ramp_x0" not in kw:
+        w = inputs.lwfa2d(**args, ramp_x0=w["params"]["xc"] - 8.0)
+    return w
+
+
+# ------------------------------------------------------------------ FP64 parity
+
+@pytest.mark.parametrize("steps,tol", [(1, 1e-12), (20, 1e-9)])
+def test_thermal_fp64_full_size(binding, steps, tol):
+    """configs[0]-sized thermal plasma: 128x128, 16 ppc (262 144 particles)."""
+    w = inputs.thermal2d(seed=1511)
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim.load(w)
+    sim.step(steps)
+    o = make_oracle(w)
+    o.step(steps)
+    compare(sim, o, w["params"], tol)
+    assert sim.step_info() == (steps, 0)
+
+
+@pytest.mark.parametrize("steps,tol", [(1, 1e-12), (20, 1e-9)])
+def test_lwfa_small_fp64_window(binding, steps, tol):
+    """Moving window + injection + laser: shrunk LWFA (256x128, same dx, dy, dt)."""
+    w = small_lwfa()
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=8 * n + 100000)
+    sim.load(w)
+    sim.step(steps)
+    o = make_oracle(w)
+    o.step(steps)
+    compare(sim, o, w["params"], tol)
+    s, k = sim.step_info()
+    assert s == steps and k == o.shifts == orc.shift_count(o.c, steps)
+
+
+def test_patch_size_and_chunking_variants(binding):
+    """Several tiles, ragged chunks and both work mappings give the same answer."""
+    w = inputs.thermal2d(nx=96, ny=64, d=0.1, ppc_side=3, uth=0.1, seed=5, patch=(16, 32))
+    n = len(w["particles"]["x"])
+    o = make_oracle(w)
+    o.step(3)
+    for chunk, mapping in ((0, 0), (100, 0), (977, 0), (0, 1)):
+        sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n,
+                          chunk=chunk, mapping=mapping)
+        sim.load(w)
+        sim.step(3)
+        compare(sim, o, w["params"], 1e-11)
+        sim.close()
+
+
+def test_gauss_law_on_gpu(binding):
+    """Esirkepov + Yee keep div E - rho at round-off on the GPU too (100 steps)."""
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, uth=0.1, seed=8, patch=(16, 16))
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim.load(w)
+    g0 = sim.gauss()
+    assert np.abs(g0).max() < 1e-12
+    sim.step(100)
+    g = sim.gauss()
+    assert np.abs(g - g0).max() < 1e-11
+    assert np.abs(sim.fields()["Ex"]).max() > 1e-4
+
+
+def test_energy_diag_matches_oracle(binding):
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, seed=9, patch=(16, 16))
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim.load(w)
+    sim.step(10)
+    o = make_oracle(w)
+    o.step(10)
+    e, eo = sim.energy(), o.energy()
+    assert np.allclose(e, eo, rtol=1e-10, atol=1e-14)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_empty_and_single_particle(binding):
+    w = inputs.thermal2d(nx=32, ny=32, d=0.1, seed=1, patch=(16, 16))
+    empty = {k: v[:0] for k, v in w["particles"].items()}
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=1000)
+    sim.load(dict(w, particles=empty))
+    sim.step(5)
+    assert sim.num_particles() == 0
+    assert np.abs(sim.fields()["Jx"]).max() == 0.0
+    sim.close()
+    # one fast particle crossing patch corners diagonally, periodic wrap
+    one = dict(x=np.array([1.599]), y=np.array([1.599]), z=np.zeros(1),
+               ux=np.array([3.0]), uy=np.array([3.0]), uz=np.array([0.5]),
+               w=np.array([0.01]), id=np.array([7], np.int32))
+    w1 = dict(w, particles=one)
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=1000)
+    sim.load(w1)
+    o = make_oracle(w1)
+    for _ in range(6):
+        sim.step(5)
+        o.step(5)
+        compare(sim, o, w["params"], 1e-10)
+
+
+def test_one_heavy_patch(binding):
+    """Most particles in one patch: chunked queue vs static mapping, same result."""
+    rng = np.random.default_rng(4)
+    N = 40000
+    x = np.concatenate([rng.uniform(0.0, 1.6, N - 2000), rng.uniform(0, 6.4, 2000)])
+    y = np.concatenate([rng.uniform(0.0, 1.6, N - 2000), rng.uniform(0, 6.4, 2000)])
+    p = dict(x=x, y=y, z=np.zeros(N), ux=rng.normal(0, 0.1, N), uy=rng.normal(0, 0.1, N),
+             uz=rng.normal(0, 0.1, N), w=np.full(N, 1e-3), id=np.arange(N, dtype=np.int32))
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, seed=2, patch=(16, 16))
+    w = dict(w, particles=p)
+    o = make_oracle(w)
+    o.step(4)
+    for mapping in (0, 1):
+        sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=3 * N,
+                          chunk=512, mapping=mapping)
+        sim.load(w)
+        sim.step(4)
+        compare(sim, o, w["params"], 1e-10)
+        counts = sim.patch_counts()
+        assert counts.sum() == N and counts.max() > 30000
+        sim.close()
+
+
+def test_capacity_overflow_is_reported(binding):
+    """A patch that cannot take its arrivals latches PIC_ERR_CAPACITY (no fault)."""
+    w = inputs.thermal2d(nx=32, ny=32, d=0.1, ppc_side=4, seed=1, patch=(16, 16))
+    # everything drifts to +x at high speed: the right patches overflow a tight capacity
+    p = dict(w["particles"])
+    n = len(p["x"])
+    p["ux"] = np.full(n, 5.0)
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=n + 8)
+    sim.load(dict(w, particles=p))
+    sim.step(40)
+    with pytest.raises(binding.PicError) as e:
+        sim.sync()
+    assert e.value.code == binding.PIC_ERR_CAPACITY
+
+
+def test_invalid_particles_rejected(binding):
+    w = inputs.thermal2d(nx=32, ny=32, d=0.1, seed=1, patch=(16, 16))
+    p = dict(w["particles"])
+    p["x"] = p["x"].copy()
+    p["x"][3] = 99.0
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * len(p["x"]))
+    with pytest.raises(binding.PicError) as e:
+        binding.pic_load_particles(sim.h, p)
+    assert e.value.code == binding.PIC_ERR_INVALID
+    p["x"][3] = 0.5
+    p["ux"] = p["ux"].copy()
+    p["ux"][5] = np.nan
+    with pytest.raises(binding.PicError) as e:
+        binding.pic_load_particles(sim.h, p)
+    assert e.value.code == binding.PIC_ERR_NUMERIC
+
+
+# ------------------------------------------------------------------ FP32 path
+
+def test_thermal_fp32_error_stated(binding):
+    """FP32 particles/fields, FP64 J: error against the FP64 oracle after 20 steps."""
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, seed=12, patch=(16, 16))
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP32, capacity=2 * n)
+    sim.load(w)
+    sim.step(20)
+    o = make_oracle(w)
+    o.step(20)
+    q, qo = sim.particles(), o.get_particles()
+    assert np.array_equal(q["id"], qo["id"])
+    ux_err = normwise(q["ux"], qo["ux"])
+    x_err = np.abs(wrapdiff(q["x"], qo["x"], 6.4)).max() / 0.1  # in cells
+    f, fo = sim.fields(), o.get_fields()
+    ex_err = normwise(f["Ex"], fo["Ex"])
+    print(f"FP32 thermal 20 steps: ux {ux_err:.2e}, x {x_err:.2e} cells, Ex {ex_err:.2e}")
+    assert ux_err < 1e-4 and x_err < 1e-4 and ex_err < 1e-2
+    e, eo = sim.energy(), o.energy()
+    assert abs(e.sum() - eo.sum()) / eo.sum() < 1e-3
+
+
+def test_lwfa_fp32_window(binding):
+    w = small_lwfa()
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP32, capacity=8 * n + 100000)
+    sim.load(w)
+    sim.step(20)
+    o = make_oracle(w)
+    o.step(20)
+    assert sim.num_particles() == o.num_particles()
+    f, fo = sim.fields(), o.get_fields()
+    ey_err = normwise(f["Ey"], fo["Ey"])
+    e, eo = sim.energy(), o.energy()
+    print(f"FP32 LWFA 20 steps: Ey {ey_err:.2e}, energy {abs(e.sum() / eo.sum() - 1):.2e}")
+    assert ey_err < 1e-4
+    assert abs(e.sum() - eo.sum()) / eo.sum() < 1e-3

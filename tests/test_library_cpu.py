@@ -1,0 +1,52 @@
+"""Host-side checks of the C-ABI library that need no GPU: every symbol the header
+declares is exported, and configuration validation / arena sizing behave."""
+import re
+
+import pytest
+
+from paper_1511_03878_gb300 import binding, build, inputs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def test_header_symbols_exported(lib):
+    hdr = open(build.INCLUDE + "/pic.h").read()
+    declared = set(re.findall(r"\b(pic_[a-z_]+)\s*\(", hdr))
+    assert declared == set(binding.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_required_bytes_and_validation(lib):
+    p = inputs.thermal2d(nx=64, ny=64, patch=(16, 16))["params"]
+    cfg = binding.make_config(p, capacity=100000)
+    nb = binding.pic_required_bytes(cfg)
+    assert nb > 100000 * (16 + 24 + 8 + 4)
+    # FP32 arena is smaller
+    cfg32 = binding.make_config(p, precision=binding.PIC_FP32, capacity=100000)
+    assert 0 < binding.pic_required_bytes(cfg32) < nb
+    # invalid: patch does not divide the grid, dt above a cell, bad dims
+    bad = dict(p, patch=(24, 16))
+    assert binding.pic_required_bytes(binding.make_config(bad, capacity=10)) == 0
+    bad = dict(p, dt=0.2)
+    assert binding.pic_required_bytes(binding.make_config(bad, capacity=10)) == 0
+    bad = dict(p, dims=4)
+    assert binding.pic_required_bytes(binding.make_config(bad, capacity=10)) == 0
+
+
+def test_create_rejects_bad_arguments(lib):
+    import ctypes
+    p = inputs.thermal2d(nx=64, ny=64, patch=(16, 16))["params"]
+    cfg = binding.make_config(p, capacity=1000)
+    h = ctypes.c_void_p()
+    # null arena and misaligned arena are rejected before any CUDA call
+    assert lib.pic_create(ctypes.byref(cfg), None, 1 << 30, None, ctypes.byref(h)) == binding.PIC_ERR_INVALID
+    assert lib.pic_create(ctypes.byref(cfg), ctypes.c_void_p(4096 + 8), 1 << 30, None,
+                          ctypes.byref(h)) == binding.PIC_ERR_INVALID
+    # too small an arena
+    assert lib.pic_create(ctypes.byref(cfg), ctypes.c_void_p(4096), 16, None,
+                          ctypes.byref(h)) == binding.PIC_ERR_NOMEM
