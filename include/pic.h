@@ -155,6 +155,39 @@ pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
 pic_status pic_batch_step(pic_batch* batch, int nsteps);
 pic_status pic_batch_destroy(pic_batch* batch);
 
+/* ---- allocation-free entry point (the paper has no counterpart) ----
+ * Gauss's-law residual div E - rho_e - rho_bg on the nodes of a 2D grid, computed
+ * from caller-owned device arrays, for callers that cannot allocate device memory:
+ * code that runs inside another framework's memory pool or under a fixed device
+ * budget, where a cudaMalloc would fail, fragment the pool, or implicitly
+ * synchronise the device in the middle of asynchronous work. This call allocates
+ * nothing: its charge-density accumulator is a file-scope static device array of
+ * PIC_STATIC_MAX_CELLS float64 (8 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *   x, y, w : n particle positions (physical, in [0, nx dx) x [0, ny dy)) and
+ *             weights, device float64; particles outside the grid are skipped.
+ *   q       : species charge.
+ *   Ex, Ey  : device float64 [ny][nx], Yee staggering (Ex at (i+1/2, j), Ey at
+ *             (i, j+1/2)).
+ *   rho_bg  : device float64 [ny][nx] background charge, or NULL for none.
+ *   out     : device float64 [ny][nx], written completely.
+ *   window  : 0 = x periodic; 1 = values outside [0, nx) along x are zero.
+ * y is periodic. The work is enqueued on cuda_stream and returns before it runs.
+ * Returns PIC_ERR_NOMEM if nx * ny > PIC_STATIC_MAX_CELLS (nothing is launched),
+ * PIC_ERR_INVALID for bad arguments, PIC_ERR_CUDA if a lookup or launch fails.
+ * Every call shares the scratch array, which keeps the last call's contents; each
+ * call clears the part it uses before depositing. Calls that overlap on the GPU
+ * (other streams, other host threads) race on that array: serialise them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. */
+#define PIC_STATIC_MAX_CELLS (1 << 20)
+pic_status pic_gauss_residual_2d_static(long long n, const double* x, const double* y,
+                                        const double* w, double q, const double* Ex,
+                                        const double* Ey, const double* rho_bg, double* out,
+                                        int nx, int ny, double dx, double dy, int window,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

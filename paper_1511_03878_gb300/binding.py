@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
 EXPORTS = ("pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
            "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
            "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
-           "pic_batch_destroy")
+           "pic_batch_destroy", "pic_gauss_residual_2d_static")
+PIC_STATIC_MAX_CELLS = 1 << 20
 
 
 class PicError(RuntimeError):
@@ -100,6 +101,10 @@ def lib():
         L.pic_batch_step.argtypes = [vp, ctypes.c_int]
         L.pic_batch_destroy.restype = ctypes.c_int
         L.pic_batch_destroy.argtypes = [vp]
+        L.pic_gauss_residual_2d_static.restype = ctypes.c_int
+        L.pic_gauss_residual_2d_static.argtypes = (
+            [ctypes.c_longlong, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, ctypes.c_int,
+             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp])
         _lib = L
     return _lib
 
@@ -226,6 +231,17 @@ def pic_batch_step(b, nsteps: int):
 
 def pic_batch_destroy(b):
     _check(lib().pic_batch_destroy(b))
+
+
+def pic_gauss_residual_2d_static(n, x_ptr, y_ptr, w_ptr, q, ex_ptr, ey_ptr, rho_bg_ptr, out_ptr,
+                                 nx, ny, dx, dy, window, stream_ptr) -> int:
+    """Allocation-free Gauss residual on caller-owned device pointers (ints); returns
+    the pic_status code (the call allocates nothing, see include/pic.h)."""
+    vp = ctypes.c_void_p
+    return int(lib().pic_gauss_residual_2d_static(
+        int(n), vp(x_ptr), vp(y_ptr), vp(w_ptr), float(q), vp(ex_ptr), vp(ey_ptr),
+        vp(rho_bg_ptr) if rho_bg_ptr else None, vp(out_ptr), int(nx), int(ny), float(dx),
+        float(dy), int(window), vp(stream_ptr) if stream_ptr else None))
 
 
 # ------------------------------------------------------------------ convenience object

@@ -15,7 +15,7 @@ def lib():
 
 def test_header_symbols_exported(lib):
     hdr = open(build.INCLUDE + "/pic.h").read()
-    declared = set(re.findall(r"\b(pic_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", hdr))
     assert declared == set(binding.EXPORTS)
     for name in declared:
         assert hasattr(lib, name), name
