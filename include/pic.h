@@ -8,11 +8,11 @@
  * load of a patch is its SP count). One step is
  *   order-2 interpolation of E, B from the Yee grid at each SP, relativistic Boris
  *   push, Esirkepov charge-conserving current deposition, exchange of SP between
- *   neighbouring patches, Yee FDTD update of E and B ("a traditional 2nd order
- *   scheme", Sec. 2.1), and for laser-wakefield runs a moving window with plasma
+ *   neighbouring patches, Yee FDTD update of E and B (the standard second-order
+ *   scheme of Sec. 2.1), and for laser-wakefield runs a moving window with plasma
  *   injection (Sec. 2.2 setup: laser focused at the foot of a density ramp).
- * The paper's load-imbalance problem (Sec. 3: up to 40 times the initial SP count
- * in some regions, Fig. 2 caption) is handled on one GPU by a persistent kernel that
+ * The paper's load-imbalance problem (Sec. 3: some regions hold about forty times
+ * their initial SP count, Fig. 2) is handled on one GPU by a persistent kernel that
  * pulls patch chunks from a device work queue ordered by SP count.
  *
  * Units are normalised: c = eps0 = 1, dE/dt = curl B - J, dB/dt = -curl E.

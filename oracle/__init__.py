@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the bench's CPU baselin
 are the only callers; the CUDA library never imports, links or runs anything here.
 
 What it computes (Sec. 3 of the paper: the per-super-particle loop plus the field
-update of a patch-based PIC code; the schemes are the standard published ones the
-paper names only as "a traditional 2nd order scheme", Sec. 2.1):
+update of a patch-based PIC code; the schemes are the standard published ones, the
+paper identifying the field solver only as a standard second-order one, Sec. 2.1):
 order-2 B-spline interpolation from the Yee grid, relativistic Boris push,
 Esirkepov (2001) charge-conserving deposition, Yee (1966) FDTD, moving window.
 """

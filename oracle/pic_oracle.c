@@ -14,8 +14,8 @@
  *          moving window: shift by one cell when floor(step dt/dx) increments,
  *          drop particles with x < 0, inject a cold lattice column on the right.
  *
- * The paper (Sec. 2.1) names only "a traditional 2nd order scheme"; the schemes are
- * the textbook ones: Yee 1966; Boris 1970; Esirkepov 2001 (Comput. Phys. Commun.
+ * The paper (Sec. 2.1) identifies only a standard second-order field scheme; the
+ * schemes are the textbook ones: Yee 1966; Boris 1970; Esirkepov 2001 (Comput. Phys. Commun.
  * 135, 144), Eqs. for W and the cumulative current; quadratic B-spline shapes.
  */
 #include "pic_oracle.h"

@@ -8,7 +8,7 @@
  * execute this code; only the test suite, the smoke check and the bench's CPU
  * baseline do. It shares no code with the CUDA implementation.
  *
- * The paper names the field solver only as "a traditional 2nd order scheme" (Sec. 2.1)
+ * The paper identifies the field solver only as a standard second-order scheme (Sec. 2.1)
  * and prints no PIC equations, so every formula here is the standard published form:
  *   - Yee (1966) staggered FDTD for Faraday and Ampere,
  *   - quadratic B-spline (order-2) shape functions,

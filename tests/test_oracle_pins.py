@@ -1,7 +1,7 @@
 """Pins of the FP64 CPU oracle against what the mathematics fixes (no GPU).
 
-The paper prints no PIC equations and no worked example (Sec. 2.1 names only "a
-traditional 2nd order scheme"), so each part of the oracle is pinned by a closed
+The paper prints no PIC equations and no worked example (Sec. 2.1 identifies only a
+standard second-order field scheme), so each part of the oracle is pinned by a closed
 form or an invariant of the published scheme it restates:
   * quadratic B-spline: partition of unity, first moment, variance 1/4, continuity;
   * Boris: |u| conservation, exact discrete rotation angle, gyration radius of the
