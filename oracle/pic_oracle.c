@@ -44,7 +44,12 @@ struct orc_sim {
 
 /* ------------------------------------------------------------------ helpers */
 
-static long wrap(long i, long n) { return ((i % n) + n) % n; }
+static long wrap(long i, long n) {
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    if (i < 0 || i >= n) i = ((i % n) + n) % n;  /* more than one period away */
+    return i;
+}
 
 /* flat index of (i, j, k) with the boundary rule; -1 = outside a window x axis */
 static long long flat(const orc_config* c, long i, long j, long k) {

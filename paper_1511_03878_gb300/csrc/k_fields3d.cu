@@ -1,0 +1,200 @@
+// 3D Yee FDTD half-updates (periodic on all axes) and the 3D diagnostics kernels.
+//   E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2})
+//   B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1},  B^{n+1} = (B^{n+1/2} + B^{n+3/2}) / 2
+// Staggering: Ex (i+1/2,j,k) Ey (i,j+1/2,k) Ez (i,j,k+1/2) Bx (i,j+1/2,k+1/2)
+// By (i+1/2,j,k+1/2) Bz (i+1/2,j+1/2,k).
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+__device__ __forceinline__ long long pidx3(const SimDev& S, int i, int j, int k) {
+    return ((long long)(k + kGuard) * S.NY + (j + kGuard)) * S.NX + (i + kGuard);
+}
+
+// value at interior (i, j, k) and its periodic images in the guard cells
+template <typename T>
+__device__ __forceinline__ void put3d(const SimDev& S, T* a, int i, int j, int k, T v) {
+    int xs[2] = {i + kGuard, -1}, ys[2] = {j + kGuard, -1}, zs[2] = {k + kGuard, -1};
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    if (i == nx - 1) xs[1] = 0; else if (i == 0) xs[1] = nx + kGuard; else if (i == 1) xs[1] = nx + 1 + kGuard;
+    if (j == ny - 1) ys[1] = 0; else if (j == 0) ys[1] = ny + kGuard; else if (j == 1) ys[1] = ny + 1 + kGuard;
+    if (k == nz - 1) zs[1] = 0; else if (k == 0) zs[1] = nz + kGuard; else if (k == 1) zs[1] = nz + 1 + kGuard;
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int a2 = 0; a2 < 2; a2++)
+                if (xs[a2] >= 0 && ys[b] >= 0 && zs[c] >= 0)
+                    a[((long long)zs[c] * S.NY + ys[b]) * S.NX + xs[a2]] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) yee_e3d_kernel(const BatchDev* __restrict__ bd) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= S.ncell) return;
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int g = S.st->gen;
+    const long long fs = S.fstride;
+    const T* Ein = reinterpret_cast<const T*>(S.F[g]);
+    T* Eout = reinterpret_cast<T*>(S.F[1 - g]);
+    const T* H = reinterpret_cast<const T*>(S.H[g]);
+    const double* Jin = S.J[g];
+    double* Jnext = S.J[1 - g];
+    const long long p = pidx3(S, i, j, k);
+    Jnext[p] = 0.0;
+    Jnext[fs + p] = 0.0;
+    Jnext[2 * fs + p] = 0.0;
+    const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
+    const T dt = T(S.dt), ix = T(1.0 / S.d[0]), iy = T(1.0 / S.d[1]), iz = T(1.0 / S.d[2]);
+    const T bx = H[p], by = H[fs + p], bz = H[2 * fs + p];
+    const T bx_jm = H[pidx3(S, i, jm, k)], bx_km = H[pidx3(S, i, j, km)];
+    const T by_im = H[fs + pidx3(S, im, j, k)], by_km = H[fs + pidx3(S, i, j, km)];
+    const T bz_im = H[2 * fs + pidx3(S, im, j, k)], bz_jm = H[2 * fs + pidx3(S, i, jm, k)];
+    const T ex = Ein[p] + dt * ((bz - bz_jm) * iy - (by - by_km) * iz - T(Jin[p]));
+    const T ey = Ein[fs + p] + dt * ((bx - bx_km) * iz - (bz - bz_im) * ix - T(Jin[fs + p]));
+    const T ez = Ein[2 * fs + p] + dt * ((by - by_im) * ix - (bx - bx_jm) * iy - T(Jin[2 * fs + p]));
+    put3d(S, Eout, i, j, k, ex);
+    put3d(S, Eout + fs, i, j, k, ey);
+    put3d(S, Eout + 2 * fs, i, j, k, ez);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) yee_b3d_kernel(const BatchDev* __restrict__ bd) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= S.ncell) return;
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int g = S.st->gen;
+    const long long fs = S.fstride;
+    const T* E = reinterpret_cast<const T*>(S.F[1 - g]);
+    T* Bn = reinterpret_cast<T*>(S.F[1 - g]) + 3 * fs;
+    const T* H = reinterpret_cast<const T*>(S.H[g]);
+    T* Hout = reinterpret_cast<T*>(S.H[1 - g]);
+    const long long p = pidx3(S, i, j, k);
+    const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1, kp = k == nz - 1 ? 0 : k + 1;
+    const T dt = T(S.dt), ix = T(1.0 / S.d[0]), iy = T(1.0 / S.d[1]), iz = T(1.0 / S.d[2]);
+    const T ex = E[p], ey = E[fs + p], ez = E[2 * fs + p];
+    const T ex_jp = E[pidx3(S, i, jp, k)], ex_kp = E[pidx3(S, i, j, kp)];
+    const T ey_ip = E[fs + pidx3(S, ip, j, k)], ey_kp = E[fs + pidx3(S, i, j, kp)];
+    const T ez_ip = E[2 * fs + pidx3(S, ip, j, k)], ez_jp = E[2 * fs + pidx3(S, i, jp, k)];
+    const T h0x = H[p], h0y = H[fs + p], h0z = H[2 * fs + p];
+    const T hx = h0x - dt * ((ez_jp - ez) * iy - (ey_kp - ey) * iz);
+    const T hy = h0y - dt * ((ex_kp - ex) * iz - (ez_ip - ez) * ix);
+    const T hz = h0z - dt * ((ey_ip - ey) * ix - (ex_jp - ex) * iy);
+    Hout[p] = hx;
+    Hout[fs + p] = hy;
+    Hout[2 * fs + p] = hz;
+    put3d(S, Bn, i, j, k, T(0.5) * (h0x + hx));
+    put3d(S, Bn + fs, i, j, k, T(0.5) * (h0y + hy));
+    put3d(S, Bn + 2 * fs, i, j, k, T(0.5) * (h0z + hz));
+}
+
+cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,
+                         cudaStream_t s) {
+    dim3 grid((unsigned)((max_ncell + 255) / 256), nsims);
+    if (prec == 0) {
+        yee_e3d_kernel<double><<<grid, 256, 0, s>>>(bd);
+        yee_b3d_kernel<double><<<grid, 256, 0, s>>>(bd);
+    } else {
+        yee_e3d_kernel<float><<<grid, 256, 0, s>>>(bd);
+        yee_b3d_kernel<float><<<grid, 256, 0, s>>>(bd);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics (3D)
+
+template <typename T>
+__global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double sign) {
+    const SimDev& S = *sd;
+    const int p = blockIdx.x;
+    if (p >= S.npatch) return;
+    const int b0 = S.pbase[p], cnt = S.pcount[p];
+    const int n[3] = {S.n[0], S.n[1], S.n[2]};
+    const double qdv = sign * S.q / (S.d[0] * S.d[1] * S.d[2]);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int t = b0 + k;
+        int ic[3];
+        double f[3];
+        if constexpr (sizeof(T) == 8) {
+            for (int a = 0; a < 3; a++) {
+                const double xi = reinterpret_cast<const double*>(S.xi[a])[t];
+                ic[a] = (int)floor(xi);
+                f[a] = xi - ic[a];
+            }
+        } else {
+            const int c = S.cell[t];
+            ic[0] = c & 0x7FF;
+            ic[1] = (c >> 11) & 0x7FF;
+            ic[2] = (c >> 22) & 0x3FF;
+            for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const float*>(S.xi[a])[t];
+        }
+        double Sw[3][3];
+        int nd[3];
+        for (int a = 0; a < 3; a++) {
+            const int h = f[a] >= 0.5;
+            nd[a] = ic[a] + h;
+            shape3(f[a] - h, Sw[a]);
+        }
+        const double qw = qdv * (double)reinterpret_cast<const T*>(S.w)[t];
+        for (int c3 = 0; c3 < 3; c3++) {
+            const int kk = wrapi(nd[2] + c3 - 1, n[2]);
+            for (int b = 0; b < 3; b++) {
+                const int jj = wrapi(nd[1] + b - 1, n[1]);
+                for (int a = 0; a < 3; a++) {
+                    const int ii = wrapi(nd[0] + a - 1, n[0]);
+                    atomicAdd(rho + ((long long)kk * n[1] + jj) * n[0] + ii,
+                              qw * Sw[0][a] * Sw[1][b] * Sw[2][c3]);
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void gauss3d_kernel(const SimDev* __restrict__ sd) {
+    const SimDev& S = *sd;
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= S.ncell) return;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const T* E = reinterpret_cast<const T*>(S.F[S.st->step & 1]);  // current time level
+    const long long fs = S.fstride;
+    const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
+    const double div = ((double)E[pidx3(S, i, j, k)] - (double)E[pidx3(S, im, j, k)]) / S.d[0] +
+                       ((double)E[fs + pidx3(S, i, j, k)] - (double)E[fs + pidx3(S, i, jm, k)]) / S.d[1] +
+                       ((double)E[2 * fs + pidx3(S, i, j, k)] - (double)E[2 * fs + pidx3(S, i, j, km)]) / S.d[2];
+    S.rho[c] = div - S.rho[c] - S.rho_bg[c];
+}
+
+cudaError_t launch_gauss3d(const SimDev* sd, const SimDev& hs, int prec, int mode, cudaStream_t s) {
+    double* target = mode == 0 ? hs.rho_bg : hs.rho;
+    cudaError_t e = cudaMemsetAsync(target, 0, hs.ncell * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const double sign = mode == 0 ? -1.0 : 1.0;
+    if (prec == 0)
+        rho3d_kernel<double><<<hs.npatch, 256, 0, s>>>(sd, target, sign);
+    else
+        rho3d_kernel<float><<<hs.npatch, 256, 0, s>>>(sd, target, sign);
+    if (mode == 1) {
+        const unsigned g2 = (unsigned)((hs.ncell + 255) / 256);
+        if (prec == 0)
+            gauss3d_kernel<double><<<g2, 256, 0, s>>>(sd);
+        else
+            gauss3d_kernel<float><<<g2, 256, 0, s>>>(sd);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pic

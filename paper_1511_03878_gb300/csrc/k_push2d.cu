@@ -11,46 +11,6 @@
 
 namespace pic {
 
-template <typename T>
-struct JType;
-template <>
-struct JType<double> {
-    using type = double;
-};
-template <>
-struct JType<float> {
-    using type = float;
-};
-
-// Per-axis Esirkepov data on the five nodes node0-2 .. node0+2.
-template <typename T>
-struct Axis5 {
-    T S0[5], DS[5];
-    int lo, hi;  // non-zero range of DS (and of S0 + DS/2)
-};
-
-template <typename T>
-__device__ __forceinline__ void esirkepov_axis(const T s0[3], T delta1, int shift, Axis5<T>& a) {
-    T s1[3];
-    shape3(delta1, s1);
-    const bool m = shift < 0, z = shift == 0, p = shift > 0;
-    T S1[5];
-    S1[0] = m ? s1[0] : T(0);
-    S1[1] = m ? s1[1] : (z ? s1[0] : T(0));
-    S1[2] = m ? s1[2] : (z ? s1[1] : s1[0]);
-    S1[3] = p ? s1[1] : (z ? s1[2] : T(0));
-    S1[4] = p ? s1[2] : T(0);
-    a.S0[0] = T(0);
-    a.S0[1] = s0[0];
-    a.S0[2] = s0[1];
-    a.S0[3] = s0[2];
-    a.S0[4] = T(0);
-#pragma unroll
-    for (int k = 0; k < 5; k++) a.DS[k] = S1[k] - a.S0[k];
-    a.lo = m ? 0 : 1;
-    a.hi = p ? 4 : 3;
-}
-
 // Gather of one staggered component: Sx/Sy are the three weights, (tx, ty) the tile
 // index of the first tap.
 template <typename T>
@@ -65,9 +25,90 @@ __device__ __forceinline__ T gather9(const T* __restrict__ f, int BX, const T Sx
     return r;
 }
 
+// Esirkepov deposition, 2D, when the particle stays on its nearest nodes along both
+// axes (the common case): S0 and DS live on the stencil nodes 1..3 only, the running
+// sums have two non-zero entries, 6 + 6 + 9 shared-memory atomics.
+template <typename T, typename JT>
+__device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
+                                               const T S0y[3], T dx1, T dy1, T qx, T qy, T qz) {
+    T S1x[3], S1y[3], a[3], b[3], wy[3], wz[3], wx[3];
+    shape3(dx1, S1x);
+    shape3(dy1, S1y);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        a[k] = S1x[k] - S0x[k];
+        b[k] = S1y[k] - S0y[k];
+        wy[k] = S0y[k] + T(0.5) * b[k];
+        wz[k] = T(0.5) * S0y[k] + b[k] * T(1.0 / 3.0);
+        wx[k] = S0x[k] + T(0.5) * a[k];
+    }
+    const T ax1 = qx * a[0], ax2 = qx * (a[0] + a[1]);
+    const T by1 = qy * b[0], by2 = qy * (b[0] + b[1]);
+    // stencil nodes 1..3 start one tile cell in: pointers already at (1, 1)
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+        atomicAdd(jx + l * JX + 0, JT(ax1 * wy[l]));
+        atomicAdd(jx + l * JX + 1, JT(ax2 * wy[l]));
+#pragma unroll
+        for (int k = 0; k < 3; k++) atomicAdd(jz + l * JX + k, JT(qz * (S0x[k] * wy[l] + a[k] * wz[l])));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        atomicAdd(jy + 0 * JX + k, JT(by1 * wx[k]));
+        atomicAdd(jy + 1 * JX + k, JT(by2 * wx[k]));
+    }
+}
+
+// General 2D Esirkepov deposition on the five-node stencil (any shift in {-1,0,1}).
+template <typename T, typename JT>
+__device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
+                                                  const T S0y[3], T dx1, T dy1, int sx, int sy,
+                                                  T qx, T qy, T qz) {
+    Axis5<T> ax, ay;
+    esirkepov_axis(S0x, dx1, sx, ax);
+    esirkepov_axis(S0y, dy1, sy, ay);
+#pragma unroll
+    for (int l = 0; l < 5; l++) {
+        if (l >= ay.lo && l <= ay.hi) {
+            const T wy = ay.S0[l] + T(0.5) * ay.DS[l];
+            const T wz = T(0.5) * ay.S0[l] + ay.DS[l] * T(1.0 / 3.0);
+            T acc = T(0);
+            const int r = l * JX;
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) {
+                if (kk >= ax.lo && kk < ax.hi) {
+                    acc += ax.DS[kk] * wy;
+                    atomicAdd(jx + r + kk, JT(qx * acc));
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 5; kk++) {
+                if (kk >= ax.lo && kk <= ax.hi) {
+                    const T wzk = ax.S0[kk] * wy + ax.DS[kk] * wz;
+                    atomicAdd(jz + r + kk, JT(qz * wzk));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 5; kk++) {
+        if (kk >= ax.lo && kk <= ax.hi) {
+            const T wx = ax.S0[kk] + T(0.5) * ax.DS[kk];
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                if (l >= ay.lo && l < ay.hi) {
+                    acc += ay.DS[l] * wx;
+                    atomicAdd(jy + l * JX + kk, JT(qy * acc));
+                }
+            }
+        }
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __restrict__ bd,
-                                                           int static_map) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+    push2d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -132,13 +173,15 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
         }
         __syncthreads();  // J tile zeroed
 
-        // per-sim constants in the working precision
-        const T dtdx = T(S.dt / S.d[0]), dtdy = T(S.dt / S.d[1]);
-        const T eps = T(S.q * S.dt / (2.0 * S.m));
-        const double qdv = S.q / (S.d[0] * S.d[1]);
-        const T cjx = T(-qdv * S.d[0] / S.dt);
-        const T cjy = T(-qdv * S.d[1] / S.dt);
-        const T cjz = T(qdv);
+        // per-sim constants in the working precision (precomputed on the host)
+        T dtdx, dtdy, eps, cjx, cjy, cjz;
+        if constexpr (sizeof(T) == 8) {
+            dtdx = S.c_dtd[0], dtdy = S.c_dtd[1], eps = S.c_eps;
+            cjx = S.c_j[0], cjy = S.c_j[1], cjz = S.c_j[2];
+        } else {
+            dtdx = S.f_dtd[0], dtdy = S.f_dtd[1], eps = S.f_eps;
+            cjx = S.f_j[0], cjy = S.f_j[1], cjz = S.f_j[2];
+        }
 
         const int base = S.pbase[patch] + item.z;
         const int cnt = item.w;
@@ -152,10 +195,12 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
             const bool valid = k < cnt;
             const int slot = base + (valid ? k : 0);
 
-            // ---- position: integer cell + offset per axis
+            // ---- A. load: integer cell + offset per axis
             int ix = 0, iy = 0;
             T fx = T(0), fy = T(0);
             double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
+            T u[3] = {T(0), T(0), T(0)};
+            T w = T(0);
             if (valid) {
                 if constexpr (sizeof(T) == 8) {
                     xi0 = reinterpret_cast<const double*>(S.xi[0])[slot];
@@ -172,19 +217,15 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                     fx = reinterpret_cast<const float*>(S.xi[0])[slot];
                     fy = reinterpret_cast<const float*>(S.xi[1])[slot];
                 }
-            }
-            T u[3] = {T(0), T(0), T(0)};
-            T w = T(0);
-            if (valid) {
                 u[0] = U0[slot];
                 u[1] = U1[slot];
                 u[2] = U2[slot];
                 w = W[slot];
             }
             // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
-            const int hx = fx >= T(0.5), hy = fy >= T(0.5);
-            const int nxp = ix + hx, nyp = iy + hy;
-            const T dxp = fx - T(hx), dyp = fy - T(hy);
+            const bool hx = fx >= T(0.5), hy = fy >= T(0.5);
+            const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
+            const T dxp = hx ? fx - T(1) : fx, dyp = hy ? fy - T(1) : fy;
             const T dxd = fx - T(0.5), dyd = fy - T(0.5);
             // tile-local first-tap indices (field tile origin at px0 - 1, py0 - 1)
             const int txp = nxp - px0, txd = ix - px0;
@@ -192,10 +233,13 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
             bool ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
                       (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
 
-            bool leave = false;
-            int dest = patch;
+            // ---- B. interpolate, push, move
+            T Sxp[3], Syp[3];
+            T dxp1 = T(0), dyp1 = T(0), fx1 = T(0), fy1 = T(0), vz = T(0);
+            int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
+            double xi1 = 0.0, eta1 = 0.0;
             if (ok) {
-                T Sxp[3], Sxd[3], Syp[3], Syd[3];
+                T Sxd[3], Syd[3];
                 shape3(dxp, Sxp);
                 shape3(dxd, Sxd);
                 shape3(dyp, Syp);
@@ -210,12 +254,9 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                 B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
 
                 const T ig = boris(eps, E, B, u);
-                const T vx = u[0] * ig, vy = u[1] * ig, vz = u[2] * ig;
-
-                // ---- move: new node and delta per axis
-                int nxp1, nyp1, ix1, iy1;
-                T dxp1, dyp1, fx1, fy1;
-                double xi1 = 0.0, eta1 = 0.0;
+                const T vx = u[0] * ig, vy = u[1] * ig;
+                vz = u[2] * ig;
+                int nxp1, nyp1;
                 if constexpr (sizeof(T) == 8) {
                     xi1 = xi0 + dtdx * vx;
                     eta1 = eta0 + dtdy * vy;
@@ -224,9 +265,6 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                     nyp1 = (int)ny1d;
                     dxp1 = xi1 - nx1d;
                     dyp1 = eta1 - ny1d;
-                    ix1 = (int)floor(xi1);
-                    iy1 = (int)floor(eta1);
-                    fx1 = fy1 = T(0);
                 } else {
                     fx1 = fx + dtdx * vx;
                     fy1 = fy + dtdy * vy;
@@ -248,120 +286,78 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                         fy1 -= T(1);
                         iy1 += 1;
                     }
-                    const int h1x = fx1 >= T(0.5), h1y = fy1 >= T(0.5);
-                    nxp1 = ix1 + h1x;
-                    nyp1 = iy1 + h1y;
-                    dxp1 = fx1 - T(h1x);
-                    dyp1 = fy1 - T(h1y);
+                    const bool h1x = fx1 >= T(0.5), h1y = fy1 >= T(0.5);
+                    nxp1 = ix1 + (h1x ? 1 : 0);
+                    nyp1 = iy1 + (h1y ? 1 : 0);
+                    dxp1 = h1x ? fx1 - T(1) : fx1;
+                    dyp1 = h1y ? fy1 - T(1) : fy1;
                 }
-                const int sx = nxp1 - nxp, sy = nyp1 - nyp;
+                sx = nxp1 - nxp;
+                sy = nyp1 - nyp;
                 ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
-                if (ok) {
-                    // ---- Esirkepov deposition into the shared tile (origin px0-2, py0-2)
-                    Axis5<T> ax, ay;
-                    esirkepov_axis(Sxp, dxp1, sx, ax);
-                    esirkepov_axis(Syp, dyp1, sy, ay);
-                    const T qx = cjx * w, qy = cjy * w, qz = cjz * w * vz;
-                    JT* jxt = Jt + txp;           // stencil k = 0 at tile x = nxp - px0
-                    JT* jyt = Jt + jplane + txp;
-                    JT* jzt = Jt + 2 * jplane + txp;
-                    const int r0 = typ * JX;
-#pragma unroll
-                    for (int l = 0; l < 5; l++) {
-                        if (l >= ay.lo && l <= ay.hi) {
-                            const T wy = ay.S0[l] + T(0.5) * ay.DS[l];
-                            const T wz = T(0.5) * ay.S0[l] + ay.DS[l] * T(1.0 / 3.0);
-                            T acc = T(0);
-                            const int r = r0 + l * JX;
-#pragma unroll
-                            for (int kk = 0; kk < 4; kk++) {
-                                if (kk >= ax.lo && kk < ax.hi) {
-                                    acc += ax.DS[kk] * wy;
-                                    atomicAdd(jxt + r + kk, JT(qx * acc));
-                                }
-                            }
-#pragma unroll
-                            for (int kk = 0; kk < 5; kk++) {
-                                if (kk >= ax.lo && kk <= ax.hi) {
-                                    const T wzk = ax.S0[kk] * wy + ax.DS[kk] * wz;
-                                    atomicAdd(jzt + r + kk, JT(qz * wzk));
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int kk = 0; kk < 5; kk++) {
-                        if (kk >= ax.lo && kk <= ax.hi) {
-                            const T wx = ax.S0[kk] + T(0.5) * ax.DS[kk];
-                            T acc = T(0);
-#pragma unroll
-                            for (int l = 0; l < 4; l++) {
-                                if (l >= ay.lo && l < ay.hi) {
-                                    acc += ay.DS[l] * wx;
-                                    atomicAdd(jyt + r0 + l * JX + kk, JT(qy * acc));
-                                }
-                            }
-                        }
-                    }
+            }
 
-                    // ---- boundaries and destination patch
-                    bool del = false;
-                    if constexpr (sizeof(T) == 8) {
-                        double xs = xi1 - (double)shift;
-                        if (window) {
-                            del = xi1 < 0.0 || xi1 >= (double)nx || xs < 0.0;
-                        } else {
-                            if (xs < 0.0) xs += (double)nx;
-                            if (xs >= (double)nx) xs -= (double)nx;
-                        }
-                        if (eta1 < 0.0) eta1 += (double)ny;
-                        if (eta1 >= (double)ny) eta1 -= (double)ny;
-                        xi1 = xs;
-                        ix1 = (int)floor(xi1);
-                        iy1 = (int)floor(eta1);
+            // ---- C. Esirkepov deposition into the shared tile (origin px0-2, py0-2);
+            // warp-uniform choice of the no-crossing fast path
+            const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
+            bool leave = false;
+            int dest = patch;
+            if (ok) {
+                const T qx = cjx * w, qy = cjy * w, qz = cjz * w * vz;
+                const int t0 = typ * JX + txp;  // stencil node 0 of both axes
+                if (fast) {
+                    const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
+                    deposit2d_fast<T, JT>(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX, Sxp,
+                                          Syp, dxp1, dyp1, qx, qy, qz);
+                } else {
+                    deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0, JX,
+                                             Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
+                }
+
+                // ---- D. boundaries and destination patch
+                bool del = false;
+                if constexpr (sizeof(T) == 8) {
+                    double xs = xi1 - (double)shift;
+                    if (window) {
+                        del = xi1 < 0.0 || xi1 >= (double)nx || xs < 0.0;
                     } else {
-                        if (window) {
-                            del = ix1 < 0 || ix1 >= nx;
-                            ix1 -= shift;
-                            del = del || ix1 < 0;
-                        } else {
-                            ix1 = wrapi(ix1, nx);
-                        }
-                        iy1 = wrapi(iy1, ny);
+                        if (xs < 0.0) xs += (double)nx;
+                        if (xs >= (double)nx) xs -= (double)nx;
                     }
-                    if (!del) {
-                        const int dpx = ix1 / P0, dpy = iy1 / P1;
-                        dest = dpx + S.np[0] * dpy;
-                        leave = dest != patch;
-                        if (!leave) {
-                            if constexpr (sizeof(T) == 8) {
-                                reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
-                                reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
-                            } else {
-                                S.cell[slot] = ix1 | (iy1 << 16);
-                                reinterpret_cast<float*>(S.xi[0])[slot] = fx1;
-                                reinterpret_cast<float*>(S.xi[1])[slot] = fy1;
-                            }
-                            U0[slot] = u[0];
-                            U1[slot] = u[1];
-                            U2[slot] = u[2];
-                        }
+                    if (eta1 < 0.0) eta1 += (double)ny;
+                    if (eta1 >= (double)ny) eta1 -= (double)ny;
+                    xi1 = xs;
+                    ix1 = (int)floor(xi1);
+                    iy1 = (int)floor(eta1);
+                } else {
+                    if (window) {
+                        del = ix1 < 0 || ix1 >= nx;
+                        ix1 -= shift;
+                        del = del || ix1 < 0;
                     } else {
-                        dest = -1;
-                        leave = true;
+                        ix1 = wrapi(ix1, nx);
                     }
-                    // leavers: stash the new state in registers for the mailbox write
-                    if (leave && dest >= 0) {
+                    iy1 = wrapi(iy1, ny);
+                }
+                if (!del) {
+                    dest = ix1 / P0 + S.np[0] * (iy1 / P1);
+                    leave = dest != patch;
+                    if (!leave) {
                         if constexpr (sizeof(T) == 8) {
-                            fx = (T)xi1;
-                            fy = (T)eta1;
+                            reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
+                            reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
                         } else {
-                            fx = fx1;
-                            fy = fy1;
-                            ix = ix1;
-                            iy = iy1;
+                            S.cell[slot] = ix1 | (iy1 << 16);
+                            reinterpret_cast<float*>(S.xi[0])[slot] = fx1;
+                            reinterpret_cast<float*>(S.xi[1])[slot] = fy1;
                         }
+                        U0[slot] = u[0];
+                        U1[slot] = u[1];
+                        U2[slot] = u[2];
                     }
+                } else {
+                    dest = -1;
+                    leave = true;
                 }
             }
             if (valid && !ok) {
@@ -371,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                 dest = -1;
             }
 
-            // ---- exchange hand-off (warp-aggregated counters)
+            // ---- E. exchange hand-off (warp-aggregated counters)
             const int hslot = warp_claim(S.hcount, patch, valid && leave, 0xffffffffu);
             const bool send = valid && leave && dest >= 0;
             const int mslot = warp_claim(S.mcount, send ? dest : 0, send, 0xffffffffu);
@@ -383,12 +379,12 @@ __global__ void __launch_bounds__(kThreads) push2d_kernel(const BatchDev* __rest
                     if (mslot < S.mcap[dest]) {
                         const int m = S.mbase[dest] + mslot;
                         if constexpr (sizeof(T) == 8) {
-                            reinterpret_cast<double*>(S.mxi[0])[m] = fx;
-                            reinterpret_cast<double*>(S.mxi[1])[m] = fy;
+                            reinterpret_cast<double*>(S.mxi[0])[m] = xi1;
+                            reinterpret_cast<double*>(S.mxi[1])[m] = eta1;
                         } else {
-                            S.mcell[m] = ix | (iy << 16);
-                            reinterpret_cast<float*>(S.mxi[0])[m] = fx;
-                            reinterpret_cast<float*>(S.mxi[1])[m] = fy;
+                            S.mcell[m] = ix1 | (iy1 << 16);
+                            reinterpret_cast<float*>(S.mxi[0])[m] = fx1;
+                            reinterpret_cast<float*>(S.mxi[1])[m] = fy1;
                         }
                         reinterpret_cast<T*>(S.mu[0])[m] = u[0];
                         reinterpret_cast<T*>(S.mu[1])[m] = u[1];
@@ -433,7 +429,7 @@ static int smem_bytes_2d(int P0, int P1) {
 }
 
 int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) {
-    (void)P2;
+    if (dims == 3) return push3d_occupancy(prec, P0, P1, P2, smem_bytes);
     if (dims != 2) return 0;
     int blocks = 0;
     if (prec == 0) {
@@ -442,6 +438,8 @@ int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) 
         if (cudaFuncSetAttribute(push2d_kernel<double>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
             return 0;
+        cudaFuncSetAttribute(push2d_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<double>,
                                                           kThreads, sb) != cudaSuccess)
             return 0;
@@ -451,6 +449,8 @@ int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) 
         if (cudaFuncSetAttribute(push2d_kernel<float>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
             return 0;
+        cudaFuncSetAttribute(push2d_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<float>,
                                                           kThreads, sb) != cudaSuccess)
             return 0;
@@ -460,7 +460,7 @@ int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) 
 
 cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping, int P0,
                         int P1, int P2, int grid, cudaStream_t s) {
-    (void)P2;
+    if (dims == 3) return launch_push3d(bd_dev, prec, mapping, P0, P1, P2, grid, s);
     if (dims != 2) return cudaErrorInvalidValue;
     const int static_map = mapping == 1;
     if (prec == 0) {

@@ -1,0 +1,448 @@
+// 3D3V particle kernel: the 2D kernel's structure with a 4D TMA box (x, y, z,
+// component), 27-tap order-2 interpolation and the 3D Esirkepov weights
+//   W_a = DS_a ((S0_b + DS_b/2) S0_c + (S0_b/2 + DS_b/3) DS_c),
+// J_a the running sum of -(q w/dV)(d_a/dt) W_a along +a. All axes periodic.
+// FP32 cells pack (ix | iy << 11 | iz << 22).
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+template <typename T>
+__device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, const T Sx[3],
+                                      const T Sy[3], const T Sz[3]) {
+    T r = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        T plane = T(0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const T* row = f + c * BXY + b * BX;
+            plane += Sy[b] * (Sx[0] * row[0] + Sx[1] * row[1] + Sx[2] * row[2]);
+        }
+        r += Sz[c] * plane;
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T f[3],
+                                          double xi[3]) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            xi[a] = reinterpret_cast<const double*>(S.xi[a])[slot];
+            const double fl = floor(xi[a]);
+            i[a] = (int)fl;
+            f[a] = xi[a] - fl;
+        }
+    } else {
+        const int c = S.cell[slot];
+        i[0] = c & 0x7FF;
+        i[1] = (c >> 11) & 0x7FF;
+        i[2] = (c >> 22) & 0x3FF;
+#pragma unroll
+        for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const float*>(S.xi[a])[slot];
+    }
+}
+
+// 3D deposition when no axis changes its nearest node: S0 and DS live on stencil
+// nodes 1..3 of every axis, each running sum has two non-zero entries (54 atomics).
+// `jt[a]` point at stencil node (1, 1, 1) of component a.
+template <typename T, typename JT>
+__device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY, const T S0[3][3],
+                                               const T d1[3], const T q[3]) {
+    T DS[3][3], wa[3][3], wb[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        T S1[3];
+        shape3(d1[a], S1);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            DS[a][k] = S1[k] - S0[a][k];
+            wa[a][k] = S0[a][k] + T(0.5) * DS[a][k];
+            wb[a][k] = T(0.5) * S0[a][k] + DS[a][k] * T(1.0 / 3.0);
+        }
+    }
+    const int st[3] = {1, JX, JXY};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const T c1 = q[a] * DS[a][0], c2 = q[a] * (DS[a][0] + DS[a][1]);
+#pragma unroll
+        for (int kc = 0; kc < 3; kc++)
+#pragma unroll
+            for (int kb = 0; kb < 3; kb++) {
+                const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
+                JT* p = jt[a] + kb * st[b] + kc * st[c];
+                atomicAdd(p, JT(c1 * A));
+                atomicAdd(p + st[a], JT(c2 * A));
+            }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
+    push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
+    using JT = typename JType<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    int loaded_sim = -1, loaded_patch = -1, loaded_gen = -1;
+    int next_static = blockIdx.x;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = static_map ? next_static : atomicAdd(bd->head, 1);
+        next_static += gridDim.x;
+        __syncthreads();
+        const int it = s_item;
+        if (it >= *bd->nitems || it >= bd->max_items) break;
+        const int4 item = bd->items[it];
+        const SimDev& S = bd->sims[item.x];
+        const int patch = item.y;
+
+        const int P[3] = {S.P[0], S.P[1], S.P[2]};
+        const int BX = S.BX, BY = S.BY, BZ = S.BZ;
+        const int BXY = BX * BY;
+        const int JX = P[0] + 5, JY = P[1] + 5, JZ = P[2] + 5;
+        const int JXY = JX * JY;
+        const int n[3] = {S.n[0], S.n[1], S.n[2]};
+        const int p0[3] = {(patch % S.np[0]) * P[0], ((patch / S.np[0]) % S.np[1]) * P[1],
+                           (patch / (S.np[0] * S.np[1])) * P[2]};
+        const int gen = S.st->gen;
+
+        T* Ft = reinterpret_cast<T*>(smem);
+        const int fbytes = 6 * BXY * BZ * (int)sizeof(T);
+        JT* Jt = reinterpret_cast<JT*>(smem + ((fbytes + 127) & ~127));
+        const int jvol = JXY * JZ;
+
+        for (int e = tid; e < 3 * jvol; e += blockDim.x) Jt[e] = JT(0);
+
+        if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, (uint32_t)fbytes);
+                tma_load_4d(Ft, S.tmap + gen, &mbar, p0[0] - 1 + kGuard, p0[1] - 1 + kGuard,
+                            p0[2] - 1 + kGuard, 0);
+            }
+            const bool ok = mbar_wait_bounded(&mbar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(S.status, ST_TIMEOUT);
+                return;
+            }
+            loaded_sim = item.x;
+            loaded_patch = patch;
+            loaded_gen = gen;
+        }
+        __syncthreads();
+
+        T dtd[3], cj[3], eps;
+        if constexpr (sizeof(T) == 8) {
+            for (int a = 0; a < 3; a++) dtd[a] = S.c_dtd[a], cj[a] = S.c_j[a];
+            eps = S.c_eps;
+        } else {
+            for (int a = 0; a < 3; a++) dtd[a] = S.f_dtd[a], cj[a] = S.f_j[a];
+            eps = S.f_eps;
+        }
+        const int base = S.pbase[patch] + item.z;
+        const int cnt = item.w;
+        T* U0 = reinterpret_cast<T*>(S.u[0]);
+        T* U1 = reinterpret_cast<T*>(S.u[1]);
+        T* U2 = reinterpret_cast<T*>(S.u[2]);
+        const T* W = reinterpret_cast<const T*>(S.w);
+
+        for (int k0 = 0; k0 < cnt; k0 += blockDim.x) {
+            const int k = k0 + tid;
+            const bool valid = k < cnt;
+            const int slot = base + (valid ? k : 0);
+            int ic[3] = {0, 0, 0};
+            T f[3] = {T(0), T(0), T(0)};
+            double xi0[3] = {0.0, 0.0, 0.0};
+            T u[3] = {T(0), T(0), T(0)};
+            T w = T(0);
+            if (valid) {
+                split_pos<T>(S, slot, ic, f, xi0);
+                u[0] = U0[slot];
+                u[1] = U1[slot];
+                u[2] = U2[slot];
+                w = W[slot];
+            }
+            int np_[3], tp[3], td[3];
+            T dp[3], dd[3];
+            bool ok = valid;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const bool h = f[a] >= T(0.5);
+                np_[a] = ic[a] + (h ? 1 : 0);
+                dp[a] = h ? f[a] - T(1) : f[a];
+                dd[a] = f[a] - T(0.5);
+                tp[a] = np_[a] - p0[a];
+                td[a] = ic[a] - p0[a];
+                ok = ok && (unsigned)tp[a] <= (unsigned)P[a] && (unsigned)td[a] < (unsigned)P[a];
+            }
+            bool leave = false;
+            int dest = patch;
+            int icn[3] = {0, 0, 0};
+            T fn[3] = {T(0), T(0), T(0)};
+            double xin[3] = {0.0, 0.0, 0.0};
+            T S0keep[3][3] = {}, d1keep[3] = {T(0), T(0), T(0)};
+            int shkeep[3] = {0, 0, 0};
+            if (ok) {
+                T Sp[3][3], Sd[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    shape3(dp[a], Sp[a]);
+                    shape3(dd[a], Sd[a]);
+                }
+                T E[3], B[3];
+                // Ex (d,p,p) Ey (p,d,p) Ez (p,p,d) Bx (p,d,d) By (d,p,d) Bz (d,d,p)
+                E[0] = gather27(Ft + 0 * BXY * BZ + tp[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sp[2]);
+                E[1] = gather27(Ft + 1 * BXY * BZ + tp[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sp[2]);
+                E[2] = gather27(Ft + 2 * BXY * BZ + td[2] * BXY + tp[1] * BX + tp[0], BX, BXY, Sp[0], Sp[1], Sd[2]);
+                B[0] = gather27(Ft + 3 * BXY * BZ + td[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sd[2]);
+                B[1] = gather27(Ft + 4 * BXY * BZ + td[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sd[2]);
+                B[2] = gather27(Ft + 5 * BXY * BZ + tp[2] * BXY + td[1] * BX + td[0], BX, BXY, Sd[0], Sd[1], Sp[2]);
+                const T ig = boris(eps, E, B, u);
+                const T v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
+                int np1[3], sh[3];
+                T dp1[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if constexpr (sizeof(T) == 8) {
+                        xin[a] = xi0[a] + dtd[a] * v[a];
+                        const double nd = floor(xin[a] + 0.5);
+                        np1[a] = (int)nd;
+                        dp1[a] = xin[a] - nd;
+                    } else {
+                        T g = f[a] + dtd[a] * v[a];
+                        int i1 = ic[a];
+                        if (g < T(0)) {
+                            g += T(1);
+                            i1 -= 1;
+                            if (g >= T(1)) { g = T(0); i1 += 1; }
+                        } else if (g >= T(1)) {
+                            g -= T(1);
+                            i1 += 1;
+                        }
+                        const bool h1 = g >= T(0.5);
+                        np1[a] = i1 + (h1 ? 1 : 0);
+                        dp1[a] = h1 ? g - T(1) : g;
+                        icn[a] = i1;
+                        fn[a] = g;
+                    }
+                    sh[a] = np1[a] - np_[a];
+                    ok = ok && sh[a] >= -1 && sh[a] <= 1;
+                }
+                for (int a = 0; a < 3; a++) {
+                    for (int q = 0; q < 3; q++) S0keep[a][q] = Sp[a][q];
+                    d1keep[a] = dp1[a];
+                    shkeep[a] = sh[a];
+                }
+            }
+            // warp-uniform choice of the no-crossing deposition
+            const bool fast = __all_sync(0xffffffffu, !ok || (shkeep[0] == 0 && shkeep[1] == 0 &&
+                                                              shkeep[2] == 0));
+            if (ok) {
+                {
+                    const T* dp1 = d1keep;
+                    const int* sh = shkeep;
+                    T Sp[3][3];
+                    for (int a = 0; a < 3; a++)
+                        for (int q = 0; q < 3; q++) Sp[a][q] = S0keep[a][q];
+                    if (fast) {
+                        JT* jt3[3];
+                        const T q3[3] = {cj[0] * w, cj[1] * w, cj[2] * w};
+                        const int t111 = (tp[2] + 1) * JXY + (tp[1] + 1) * JX + (tp[0] + 1);
+                        for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
+                        deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3);
+                    } else {
+                    Axis5<T> ax[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) esirkepov_axis(Sp[a], dp1[a], sh[a], ax[a]);
+                    // (S0 + DS/2) and (S0/2 + DS/3) per axis
+                    T wa[3][5], wb[3][5];
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+#pragma unroll
+                        for (int q = 0; q < 5; q++) {
+                            wa[a][q] = ax[a].S0[q] + T(0.5) * ax[a].DS[q];
+                            wb[a][q] = T(0.5) * ax[a].S0[q] + ax[a].DS[q] * T(1.0 / 3.0);
+                        }
+                    // tile origin p0 - 2: stencil index 0 at tile index tp[a]
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const int b = (a + 1) % 3, c = (a + 2) % 3;
+                        const T qa = cj[a] * w;
+                        JT* jt = Jt + a * jvol;
+#pragma unroll
+                        for (int kc = 0; kc < 5; kc++) {
+                            if (kc < ax[c].lo || kc > ax[c].hi) continue;
+#pragma unroll
+                            for (int kb = 0; kb < 5; kb++) {
+                                if (kb < ax[b].lo || kb > ax[b].hi) continue;
+                                const T A = wa[b][kb] * ax[c].S0[kc] + wb[b][kb] * ax[c].DS[kc];
+                                T acc = T(0);
+#pragma unroll
+                                for (int ka = 0; ka < 4; ka++) {
+                                    if (ka < ax[a].lo || ka >= ax[a].hi) continue;
+                                    acc += ax[a].DS[ka] * A;
+                                    int t[3];
+                                    t[a] = tp[a] + ka;
+                                    t[b] = tp[b] + kb;
+                                    t[c] = tp[c] + kc;
+                                    atomicAdd(jt + t[2] * JXY + t[1] * JX + t[0], JT(qa * acc));
+                                }
+                            }
+                        }
+                    }
+                    }
+                }
+                    // periodic wrap and destination patch
+                    int dp_[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        if constexpr (sizeof(T) == 8) {
+                            if (xin[a] < 0.0) xin[a] += (double)n[a];
+                            if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
+                            icn[a] = (int)floor(xin[a]);
+                        } else {
+                            icn[a] = wrapi(icn[a], n[a]);
+                        }
+                        dp_[a] = icn[a] / P[a];
+                    }
+                    dest = dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
+                    leave = dest != patch;
+                    if (!leave) {
+                        if constexpr (sizeof(T) == 8) {
+                            for (int a = 0; a < 3; a++)
+                                reinterpret_cast<double*>(S.xi[a])[slot] = xin[a];
+                        } else {
+                            S.cell[slot] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
+                            for (int a = 0; a < 3; a++)
+                                reinterpret_cast<float*>(S.xi[a])[slot] = fn[a];
+                        }
+                        U0[slot] = u[0];
+                        U1[slot] = u[1];
+                        U2[slot] = u[2];
+                    }
+            }
+            if (valid && !ok) {
+                atomicOr(S.status, ST_NUMERIC);
+                leave = true;
+                dest = -1;
+            }
+            const int hslot = warp_claim(S.hcount, patch, valid && leave, 0xffffffffu);
+            const bool send = valid && leave && dest >= 0;
+            const int mslot = warp_claim(S.mcount, send ? dest : 0, send, 0xffffffffu);
+            if (valid && leave) {
+                S.holes[S.pbase[patch] + hslot] = slot;
+                const int pid = S.id[slot];
+                S.id[slot] = -1;
+                if (send) {
+                    if (mslot < S.mcap[dest]) {
+                        const int m = S.mbase[dest] + mslot;
+                        if constexpr (sizeof(T) == 8) {
+                            for (int a = 0; a < 3; a++)
+                                reinterpret_cast<double*>(S.mxi[a])[m] = xin[a];
+                        } else {
+                            S.mcell[m] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
+                            for (int a = 0; a < 3; a++)
+                                reinterpret_cast<float*>(S.mxi[a])[m] = fn[a];
+                        }
+                        reinterpret_cast<T*>(S.mu[0])[m] = u[0];
+                        reinterpret_cast<T*>(S.mu[1])[m] = u[1];
+                        reinterpret_cast<T*>(S.mu[2])[m] = u[2];
+                        reinterpret_cast<T*>(S.mw)[m] = w;
+                        S.mid[m] = pid;
+                    } else {
+                        atomicOr(S.status, ST_MAILBOX);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // flush the current tile (origin p0 - 2) into the global FP64 J (periodic)
+        double* Jg = S.J[gen];
+        const long long fs = S.fstride;
+        for (int e = tid; e < 3 * jvol; e += blockDim.x) {
+            const JT v = Jt[e];
+            if (v == JT(0)) continue;
+            const int comp = e / jvol;
+            const int r = e - comp * jvol;
+            const int tz = r / JXY;
+            const int r2 = r - tz * JXY;
+            const int ty = r2 / JX, tx = r2 - ty * JX;
+            const int gi = wrapi(p0[0] - 2 + tx, n[0]);
+            const int gj = wrapi(p0[1] - 2 + ty, n[1]);
+            const int gk = wrapi(p0[2] - 2 + tz, n[2]);
+            atomicAdd(Jg + comp * fs + ((long long)(gk + kGuard) * S.NY + (gj + kGuard)) * S.NX +
+                          (gi + kGuard),
+                      (double)v);
+        }
+    }
+}
+
+template <typename T>
+int smem_bytes_3d(int P0, int P1, int P2) {
+    const int BX = P0 + 4, BY = P1 + 3, BZ = P2 + 3;
+    const int fb = 6 * BX * BY * BZ * (int)sizeof(T);
+    const int jb = 3 * (P0 + 5) * (P1 + 5) * (P2 + 5) * (int)sizeof(typename JType<T>::type);
+    return ((fb + 127) & ~127) + jb;
+}
+
+int push3d_smem(int prec, int P0, int P1, int P2) {
+    return prec == 0 ? smem_bytes_3d<double>(P0, P1, P2) : smem_bytes_3d<float>(P0, P1, P2);
+}
+
+int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes) {
+    int blocks = 0;
+    const int sb = push3d_smem(prec, P0, P1, P2);
+    *smem_bytes = sb;
+    if (prec == 0) {
+        if (cudaFuncSetAttribute(push3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 sb) != cudaSuccess)
+            return 0;
+        cudaFuncSetAttribute(push3d_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<double>, kThreads,
+                                                          sb) != cudaSuccess)
+            return 0;
+    } else {
+        if (cudaFuncSetAttribute(push3d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 sb) != cudaSuccess)
+            return 0;
+        cudaFuncSetAttribute(push3d_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<float>, kThreads,
+                                                          sb) != cudaSuccess)
+            return 0;
+    }
+    return blocks;
+}
+
+cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0, int P1, int P2,
+                          int grid, cudaStream_t s) {
+    const int sb = push3d_smem(prec, P0, P1, P2);
+    const int static_map = mapping == 1;
+    if (prec == 0)
+        push3d_kernel<double><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
+    else
+        push3d_kernel<float><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

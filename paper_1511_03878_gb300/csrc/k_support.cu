@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(256) yee_b2d_kernel(const BatchDev* __restrict
 
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
                        cudaStream_t s) {
+    if (dims == 3) return launch_yee3d(bd, nsims, max_ncell, prec, s);
     if (dims != 2) return cudaErrorInvalidValue;
     dim3 grid((max_ncell + 255) / 256, nsims);
     if (prec == 0) {
@@ -594,6 +595,7 @@ __global__ void gauss2d_kernel(const SimDev* __restrict__ sd) {
 }
 
 cudaError_t launch_gauss(const SimDev* sd, const SimDev& hs, int prec, int mode, cudaStream_t s) {
+    if (hs.dims == 3) return launch_gauss3d(sd, hs, prec, mode, s);
     const long long nc = hs.ncell;
     double* target = mode == 0 ? hs.rho_bg : hs.rho;
     cudaError_t e = cudaMemsetAsync(target, 0, nc * sizeof(double), s);

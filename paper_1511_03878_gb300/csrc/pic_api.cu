@@ -83,7 +83,6 @@ namespace {
 const char* validate(const pic_config* c) {
     if (!c) return "null config";
     if (c->dims != 2 && c->dims != 3) return "dims must be 2 or 3";
-    if (c->dims == 3) return "3D3V is not available in this build";
     if (c->precision != PIC_FP64 && c->precision != PIC_FP32) return "bad precision";
     if (c->window != 0 && c->window != 1) return "bad window flag";
     if (c->mapping != PIC_MAP_QUEUE && c->mapping != PIC_MAP_STATIC) return "bad mapping";
@@ -97,6 +96,12 @@ const char* validate(const pic_config* c) {
     }
     if (c->dims == 2 && c->n[2] != 1) return "2D needs n[2] = 1";
     if (c->dims == 2 && (c->n[0] >= 65536 || c->n[1] >= 32768)) return "grid too large";
+    if (c->dims == 3) {
+        if (c->n[0] > 2048 || c->n[1] > 2048 || c->n[2] > 1024) return "3D grid too large";
+        if (c->window) return "the moving window is 2D only";
+        if (push3d_smem(c->precision, c->patch[0], c->patch[1], c->patch[2]) > 227 * 1024)
+            return "3D patch tile does not fit in shared memory";
+    }
     if (!(c->dt > 0) || !std::isfinite(c->dt)) return "dt must be positive";
     if (!(c->m > 0)) return "mass must be positive";
     if (c->capacity < 0 || c->capacity > (1LL << 31) - (1LL << 24)) return "bad capacity";
@@ -141,6 +146,21 @@ Layout plan(const pic_config* c, char* base) {
     S.ramp_x0 = c->ramp_x0;
     S.ramp_len = c->ramp_len;
     S.ncell = (long long)S.n[0] * S.n[1] * S.n[2];
+    {
+        const double dV = S.d[0] * S.d[1] * (c->dims == 3 ? S.d[2] : 1.0);
+        const double qdv = S.q / dV;
+        for (int a = 0; a < 3; a++) {
+            S.c_dtd[a] = S.dt / S.d[a];
+            S.c_j[a] = -qdv * S.d[a] / S.dt;
+        }
+        if (c->dims == 2) S.c_j[2] = qdv;
+        S.c_eps = S.q * S.dt / (2.0 * S.m);
+        for (int a = 0; a < 3; a++) {
+            S.f_dtd[a] = (float)S.c_dtd[a];
+            S.f_j[a] = (float)S.c_j[a];
+        }
+        S.f_eps = (float)S.c_eps;
+    }
     const long long es = c->precision == PIC_FP64 ? 8 : 4;
     const long long cap = c->capacity;
     S.capacity = cap;
@@ -216,14 +236,26 @@ bool encode_field_maps(const SimDev& S, CUtensorMap out[2]) {
     const CUtensorMapDataType dt =
         S.prec == PIC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int g = 0; g < 2; g++) {
-        if (S.dims != 2) return false;
-        cuuint64_t dims[3] = {(cuuint64_t)S.NX, (cuuint64_t)S.NY, 6};
-        cuuint64_t strides[2] = {(cuuint64_t)S.NX * es, (cuuint64_t)S.NX * S.NY * es};
-        cuuint32_t box[3] = {(cuuint32_t)S.BX, (cuuint32_t)S.BY, 6};
-        cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = fn(&out[g], dt, 3, S.F[g], dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r;
+        if (S.dims == 2) {
+            cuuint64_t dims[3] = {(cuuint64_t)S.NX, (cuuint64_t)S.NY, 6};
+            cuuint64_t strides[2] = {(cuuint64_t)S.NX * es, (cuuint64_t)S.NX * S.NY * es};
+            cuuint32_t box[3] = {(cuuint32_t)S.BX, (cuuint32_t)S.BY, 6};
+            cuuint32_t estr[3] = {1, 1, 1};
+            r = fn(&out[g], dt, 3, S.F[g], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            // (x, y, z, component) with a 4D box: one patch tile of all six components
+            cuuint64_t dims[4] = {(cuuint64_t)S.NX, (cuuint64_t)S.NY, (cuuint64_t)S.NZ, 6};
+            cuuint64_t strides[3] = {(cuuint64_t)S.NX * es, (cuuint64_t)S.NX * S.NY * es,
+                                     (cuuint64_t)S.NX * S.NY * S.NZ * es};
+            cuuint32_t box[4] = {(cuuint32_t)S.BX, (cuuint32_t)S.BY, (cuuint32_t)S.BZ, 6};
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            r = fn(&out[g], dt, 4, S.F[g], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
         if (r != CUDA_SUCCESS) return false;
     }
     return true;
@@ -519,14 +551,11 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
                 } else {
                     int cellv = 0;
                     for (int a = 0; a < dims; a++) {
-                        int i = ip[src * 3 + a];
+                        const int i = ip[src * 3 + a];
                         float f = (float)(xi[src * 3 + a] - (double)i);
-                        if (f >= 1.0f) {  // rounding up to the next cell
-                            f = 0.0f;
-                            i += 1;
-                        }
+                        if (f >= 1.0f) f = std::nextafter(1.0f, 0.0f);  // stay in the cell
                         reinterpret_cast<float*>(hx[a].data())[dst] = f;
-                        cellv |= i << (16 * a);
+                        cellv |= i << (dims == 2 ? 16 * a : 11 * a);
                     }
                     hcell[dst] = cellv;
                     for (int a = 0; a < 3; a++) reinterpret_cast<float*>(hu[a].data())[dst] = (float)uu[a];
@@ -762,7 +791,9 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
                     if (S.prec == PIC_FP64) {
                         pos[a] = reinterpret_cast<double*>(hx[a].data())[sl] * S.d[a];
                     } else {
-                        const int i = (hcell[sl] >> (16 * a)) & 0xFFFF;
+                        const int sh = S.dims == 2 ? 16 * a : 11 * a;
+                        const int mask = S.dims == 2 ? 0xFFFF : (a < 2 ? 0x7FF : 0x3FF);
+                        const int i = (hcell[sl] >> sh) & mask;
                         pos[a] = ((double)i + (double)reinterpret_cast<float*>(hx[a].data())[sl]) * S.d[a];
                     }
                 }

@@ -111,6 +111,46 @@ __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     return rsqrt_t(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 }
 
+template <typename T>
+struct JType;
+template <>
+struct JType<double> {
+    using type = double;
+};
+template <>
+struct JType<float> {
+    using type = float;
+};
+
+// Per-axis Esirkepov data on the five nodes node0-2 .. node0+2.
+template <typename T>
+struct Axis5 {
+    T S0[5], DS[5];
+    int lo, hi;  // non-zero range of DS (and of S0 + DS/2)
+};
+
+template <typename T>
+__device__ __forceinline__ void esirkepov_axis(const T s0[3], T delta1, int shift, Axis5<T>& a) {
+    T s1[3];
+    shape3(delta1, s1);
+    const bool m = shift < 0, z = shift == 0, p = shift > 0;
+    T S1[5];
+    S1[0] = m ? s1[0] : T(0);
+    S1[1] = m ? s1[1] : (z ? s1[0] : T(0));
+    S1[2] = m ? s1[2] : (z ? s1[1] : s1[0]);
+    S1[3] = p ? s1[1] : (z ? s1[2] : T(0));
+    S1[4] = p ? s1[2] : T(0);
+    a.S0[0] = T(0);
+    a.S0[1] = s0[0];
+    a.S0[2] = s0[1];
+    a.S0[3] = s0[2];
+    a.S0[4] = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; k++) a.DS[k] = S1[k] - a.S0[k];
+    a.lo = m ? 0 : 1;
+    a.hi = p ? 4 : 3;
+}
+
 // ---------------------------------------------------------------- scans
 
 // Exclusive block scan of one int per thread; blockDim.x a multiple of 32, <= 1024.

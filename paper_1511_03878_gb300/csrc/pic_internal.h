@@ -50,6 +50,11 @@ struct SimDev {
     double n0, ramp_x0, ramp_len;
     int ippc[3];
     int pad0;
+    // per-step constants of the particle kernel, computed once on the host
+    double c_dtd[3];   // dt / d[a]
+    double c_eps;      // q dt / (2 m)
+    double c_j[3];     // 2D: -q/dV d[a]/dt for Jx, Jy and q/dV for Jz (times v_z)
+    float f_dtd[3], f_eps, f_j[3];
     // fields
     void* F[2];      // [6][NZ][NY][NX]: Ex Ey Ez Bnx Bny Bnz (B^n for the push)
     void* H[2];      // [3][...]: B^{n+1/2}
@@ -106,6 +111,14 @@ cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int 
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
                        cudaStream_t s);
 cudaError_t launch_end_step(const BatchDev* bd, int nsims, cudaStream_t s);
+// 3D variants
+int push3d_smem(int prec, int P0, int P1, int P2);
+int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes);
+cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0, int P1, int P2,
+                          int grid, cudaStream_t s);
+cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,
+                         cudaStream_t s);
+cudaError_t launch_gauss3d(const SimDev* sd, const SimDev& hs, int prec, int mode, cudaStream_t s);
 // diagnostics on one sim
 cudaError_t launch_energy(const SimDev* sd, long long ncell, long long cap, int prec,
                           cudaStream_t s);

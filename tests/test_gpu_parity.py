@@ -279,3 +279,79 @@ def test_lwfa_fp32_window(binding):
     print(f"FP32 LWFA 20 steps: Ey {ey_err:.2e}, energy {abs(e.sum() / eo.sum() - 1):.2e}")
     assert ey_err < 1e-4
     assert abs(e.sum() - eo.sum()) / eo.sum() < 1e-3
+
+
+# ------------------------------------------------------------------ 3D3V
+
+def stress3d_small(seed=13, total=40000, patch=(8, 8, 8)):
+    """32^3 slice with the statistics of the 3D stress case: log-normal counts over
+    16^3 blocks (sigma = 1.5), uniform positions, u_th = 0.05; 8^3 patches."""
+    w = inputs.stress3d(n=(32, 32, 32), d=0.1, patch=(16, 16, 16), total=total, sigma=1.5,
+                        uth=0.05, seed=seed)
+    w["params"] = dict(w["params"], patch=patch)
+    return w
+
+
+def compare3d(sim, o, params, tol):
+    errs = compare(sim, o, params, tol)
+    q, qo = sim.particles(), o.get_particles()
+    Lz = params["n"][2] * params["d"][2]
+    ez = float(np.abs(wrapdiff(q["z"], qo["z"], Lz)).max() / np.abs(qo["z"]).max())
+    assert ez <= tol, ez
+    return errs
+
+
+@pytest.mark.parametrize("steps,tol", [(1, 1e-12), (10, 1e-9)])
+def test_stress3d_fp64(binding, steps, tol):
+    w = stress3d_small()
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim.load(w)
+    sim.step(steps)
+    o = make_oracle(w)
+    o.step(steps)
+    compare3d(sim, o, w["params"], tol)
+
+
+def test_stress3d_static_mapping_and_chunks(binding):
+    w = stress3d_small(seed=14)
+    n = len(w["particles"]["x"])
+    o = make_oracle(w)
+    o.step(3)
+    for chunk, mapping in ((300, 0), (0, 1)):
+        sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n, chunk=chunk,
+                          mapping=mapping)
+        sim.load(w)
+        sim.step(3)
+        compare3d(sim, o, w["params"], 1e-11)
+        sim.close()
+
+
+def test_gauss_law_3d_gpu(binding):
+    w = stress3d_small(seed=15, total=20000)
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim.load(w)
+    g0 = sim.gauss()
+    sim.step(30)
+    assert np.abs(sim.gauss() - g0).max() < 1e-10
+
+
+def test_stress3d_fp32_error_stated(binding):
+    w = stress3d_small(seed=16)
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP32, capacity=2 * n)
+    sim.load(w)
+    sim.step(10)
+    o = make_oracle(w)
+    o.step(10)
+    q, qo = sim.particles(), o.get_particles()
+    assert np.array_equal(q["id"], qo["id"])
+    ux_err = normwise(q["ux"], qo["ux"])
+    f, fo = sim.fields(), o.get_fields()
+    jx_err = normwise(f["Jx"], fo["Jx"])
+    e, eo = sim.energy(), o.energy()
+    print(f"FP32 3D 10 steps: ux {ux_err:.2e}, Jx {jx_err:.2e}, "
+          f"energy {abs(e.sum() / eo.sum() - 1):.2e}")
+    assert ux_err < 1e-4 and jx_err < 1e-3
+    assert abs(e.sum() - eo.sum()) / eo.sum() < 1e-3
