@@ -36,10 +36,21 @@ FP64_NOMINAL_TFLOPS = 1.25
 # Algorithmic FP64 flops of one 2D push (FMA = 2 flops), counted from the kernel:
 # shapes 40, interpolation 126, Boris 70, move 7, new shapes + DS 30, deposit 97.
 FLOPS_PER_PUSH_2D = 370
-# Algorithmic HBM bytes of the particle kernel per push (read + write of the state once,
-# weight read once; fields read once and J written once per cell, at 4 particles/cell)
-BYTES_PER_PUSH = {"f64": 2 * (16 + 24) + 8 + (48 + 24) / 4.0,
-                  "f32": 2 * (4 + 8 + 12) + 4 + (24 + 24) / 4.0}
+# 3D: shapes 60, interpolation 6 x 57, Boris 70, move 10, new shapes + DS 45,
+# deposition (no crossing) 3 x 9 x 7 + 12
+FLOPS_PER_PUSH_3D = 660
+
+
+def bytes_per_push(dt, w):
+    """Algorithmic HBM bytes of the particle kernel per push: particle state read and
+    written once, weight read once; E and B^n read once and J (FP64) written once per
+    cell, shared by the particles per cell."""
+    p = w["params"]
+    dims = p["dims"]
+    es = 8 if dt == "f64" else 4
+    pos = dims * es + (4 if dt == "f32" else 0)
+    ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
+    return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
 KERNELS_PER_STEP = 7  # queue, push, inject, exchange, yee_e, yee_b, end_step
 
 
@@ -53,6 +64,12 @@ def parse():
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--workload", default="lwfa", choices=["lwfa", "stress3d", "thermal", "serve"])
+    ap.add_argument("--requests", type=int, default=256, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget")
+    ap.add_argument("--mapping", default="queue", choices=["queue", "static"])
+    ap.add_argument("--total", type=int, default=64 * 2 ** 20, help="stress3d particles")
     ap.add_argument("--no-variant", action="store_true", help="skip the other precision")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -60,12 +77,18 @@ def parse():
     return ap.parse_args()
 
 
-def workload(nx, ny):
+def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20):
     from paper_1511_03878_gb300 import inputs
 
+    if kind == "stress3d":
+        # 256x128x128 cells, log-normal counts per 16^3 block, 8^3 patches
+        w = inputs.stress3d(total=total)
+        w["params"] = dict(w["params"], patch=(8, 8, 8))
+        return w
+    if kind == "thermal":
+        return inputs.thermal2d(seed=1511)
     # the window full of plasma: density ramp placed before x = 0
-    w = inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
-    return w
+    return inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
 
 
 def measured_peaks():
@@ -172,7 +195,9 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
 
     prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=prec, capacity=3 * n, chunk=args.chunk)
+    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
+    mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=args.chunk, mapping=mapping)
     sim.load(w)
     stream = sim.stream
     sim.step(W)
@@ -194,6 +219,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
         clocks.stop()
     sim.sync()  # raises on any latched device error
     n1 = sim.num_particles()
+    repacks = sim.repacks()
     ms = max_over_ranks(ms, world)
     pushes = K * 0.5 * (n0 + n1)
     # per-kernel CUDA-event pass (same kernels, same launch shapes) for the roofline
@@ -203,22 +229,24 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
     n_push = 0.5 * (n0 + n1)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
+    dims = w["params"]["dims"]
     if precision == "fp64":
-        achieved = FLOPS_PER_PUSH_2D * n_push / (push_ms * 1e-3) / 1e12
+        fl = FLOPS_PER_PUSH_2D if dims == 2 else FLOPS_PER_PUSH_3D
+        achieved = fl * n_push / (push_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "push2d_kernel<double>",
+                "kernel": f"push{dims}d_kernel<double>",
                 "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit counts x clock)",
-                "hbm_frac_of_measured": (BYTES_PER_PUSH[dt] * n_push / (push_ms * 1e-3) / 1e9 / hbm)
-                if hbm else None}
+                "hbm_frac_of_measured": (bytes_per_push(dt, w) * n_push / (push_ms * 1e-3) / 1e9
+                                         / hbm) if hbm else None}
     else:
-        achieved = BYTES_PER_PUSH[dt] * n_push / (push_ms * 1e-3) / 1e9
+        achieved = bytes_per_push(dt, w) * n_push / (push_ms * 1e-3) / 1e9
         peak = hbm if hbm else 6800.0
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "push2d_kernel<float>",
+                "frac": achieved / peak, "traffic": None, "kernel": f"push{dims}d_kernel<float>",
                 "peak_source": "measured" if hbm else "fallback"}
     out = dict(ms=ms, pushes=pushes, n=n_push, profile={k: v / K for k, v in prof.items()},
-               roofline=roof, push_ms=push_ms)
+               roofline=roof, push_ms=push_ms, repacks=repacks)
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -234,7 +262,8 @@ def run_e2e(args, w, precision, K):
 
     prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=prec, capacity=3 * n, chunk=args.chunk)
+    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=args.chunk)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.load(w)
@@ -243,10 +272,10 @@ def run_e2e(args, w, precision, K):
     ax = sim.ex_axis()
     t1 = time.perf_counter()
     es = 8 if precision == "fp64" else 4
-    cap = 3 * n
-    per_slot = es * (2 + 3 + 1) + 4 + (4 if precision == "fp32" else 0)
+    dims = w["params"]["dims"]
+    per_slot = es * (dims + 3 + 1) + 4 + (4 if precision == "fp32" else 0)
     cfg = sim.cfg
-    fstride = (cfg.n[0] + 4) * (cfg.n[1] + 3)
+    fstride = (cfg.n[0] + 4) * (cfg.n[1] + 3) * ((cfg.n[2] + 3) if dims == 3 else 1)
     h2d = cap * per_slot + 9 * fstride * es + 5 * sim.npatch * 4
     d2h = e.nbytes + ax.nbytes
     sim.close()
@@ -259,7 +288,12 @@ def oracle_rate(w, seconds_budget, max_steps=50):
     import oracle as orc
 
     p = w["params"]
-    c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+    n_all = len(w["particles"]["x"])
+    if n_all > 5_000_000:  # bounded sample: every k-th particle of the same grid
+        k = -(-n_all // 5_000_000)
+        w = dict(w, particles={key: v[::k].copy() for key, v in w["particles"].items()})
+    dims = p["dims"]
+    c = orc.make_config(dims, p["n"][:dims], p["d"][:dims], p["dt"], window=p["window"], q=p["q"],
                         m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
                         inject_ppc=p["inject_ppc"])
     n = len(w["particles"]["x"])
@@ -287,13 +321,14 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.nx, args.ny)
+    w = workload(args.nx, args.ny, args.workload, args.total)
     import oracle as orc
 
     orc.build()
     p = w["params"]
     n = len(w["particles"]["x"])
-    c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+    c = orc.make_config(p["dims"], p["n"][:p["dims"]], p["d"][:p["dims"]], p["dt"],
+                        window=p["window"], q=p["q"],
                         m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
                         inject_ppc=p["inject_ppc"])
     total = args.steps + args.warmup
@@ -309,10 +344,11 @@ def reference_arm(args):
     sample = "full window"
     if frac < 1.0:
         ny = max(32, int(p["n"][1] * frac) // 32 * 32)
-        w = workload(args.nx, ny)
+        w = workload(args.nx, ny, args.workload, args.total)
         p = w["params"]
         n = len(w["particles"]["x"])
-        c = orc.make_config(2, p["n"][:2], p["d"][:2], p["dt"], window=p["window"], q=p["q"],
+        c = orc.make_config(p["dims"], p["n"][:p["dims"]], p["d"][:p["dims"]], p["dt"],
+                        window=p["window"], q=p["q"],
                             m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
                             inject_ppc=p["inject_ppc"])
         o = orc.OracleSim(c, n + 4 * (total + 2) * p["n"][1] * 4)
@@ -340,19 +376,85 @@ def reference_arm(args):
 
 
 def config_dict(args, precision):
-    return {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
-            "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
-            "patch": [32, 32], "laser_a0": 4.0, "precision": precision,
-            "mapping": "persistent work queue (largest chunk first)",
+    if args.workload == "stress3d":
+        base = {"workload": "stress3d-256x128x128-lognormal1.5", "grid": [256, 128, 128],
+                "dx": 0.1, "particles": args.total, "patch": [8, 8, 8]}
+    elif args.workload == "thermal":
+        base = {"workload": "thermal2d-128x128-ppc16", "grid": [128, 128], "dx": 0.1,
+                "particles_per_cell": 16, "patch": [32, 32]}
+    else:
+        base = {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
+                "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
+                "patch": [32, 32], "laser_a0": 4.0}
+    return {**base, "precision": precision,
+            "mapping": ("persistent work queue (largest chunk first)" if args.mapping == "queue"
+                        else "static: one CTA per patch"),
             "chunk": args.chunk or 2048,
             "l2": "inputs larger than L2 (particles + fields > 129 MB), no flush",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def serve_arm(args):
+    """Served parameter scan: Poisson arrivals, HBM-budget admission, continuous
+    batching; value = aggregate pushes/s, with p50/p99 time-to-completion."""
+    import torch
+
+    import __graft_entry__
+    from paper_1511_03878_gb300 import binding, serve
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    reqs = serve.scan_requests(n=args.requests, rate=args.rate)
+    # warm-up: one small request through the same server path
+    serve.Server(budget_bytes=8 << 30).run([serve.Request(rid=0, nx=256, ny=128, a0=3.0, n0=0.01,
+                                                          ppc=2, steps=20)])
+    clocks = ClockSampler(0)
+    clocks.start()
+    srv = serve.Server(budget_bytes=int(args.budget_gb * (1 << 30)), quantum=25)
+    res = srv.run(reqs)
+    clocks.stop()
+    summ = serve.summarize(res)
+    # the plain FP64 single-simulation path on the largest scan grid, for comparison
+    w = serve.request_workload(serve.Request(rid=0, nx=2048, ny=512, a0=4.0, n0=0.01, ppc=4,
+                                             steps=0))
+    w = dict(w, particles=workload(2048, 512)["particles"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64,
+                      capacity=3 * len(w["particles"]["x"]))
+    sim.load(w)
+    sim.step(3)
+    sim.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    sim.step(50)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    fp64_rate = 50 * sim.num_particles() / (ev0.elapsed_time(ev1) * 1e-3)
+    sim.close()
+    line = {
+        "metric": METRIC, "value": summ["aggregate_pushes_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": int(sum(r.steps for r in reqs)), "warmup": 1,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded LWFA parameter scan)",
+        "config": {"workload": f"served-lwfa-scan-{args.requests}req-{args.rate}per_s",
+                   "grids": ["256x128", "512x256", "1024x256", "2048x512"], "a0": [2, 6],
+                   "n0": [0.003, 0.02], "ppc": [1, 2, 4, 8], "steps": [500, 2000],
+                   "budget_gb": args.budget_gb, "precision": "fp32",
+                   "l2": "inputs larger than L2 for the large grids, no flush"},
+        "serving": {**summ, "max_resident": srv.max_resident,
+                    "fp64_single_sim_pushes_per_s": fp64_rate,
+                    "served_over_fp64_single": summ["aggregate_pushes_per_s"] / fp64_rate},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "serve":
+        serve_arm(args)
         return
     import torch
 
@@ -366,7 +468,7 @@ def main():
     if rank != 0:
         __graft_entry__.build()
 
-    w = workload(args.nx, args.ny)
+    w = workload(args.nx, args.ny, args.workload, args.total)
     clocks = ClockSampler(local)
     main_run = run_gpu(args, w, args.precision, args.steps, args.warmup, world, clocks)
     other = "fp32" if args.precision == "fp64" else "fp64"
@@ -402,6 +504,7 @@ def main():
         "clocks": clocks.summary(),
         "kernel_ms_per_step": main_run["profile"],
         "particles": main_run["n"],
+        "capacity_repacks": main_run["repacks"],
     }
     if variant:
         line["variants"] = {other: {

@@ -127,7 +127,9 @@ enum {
                                    frame                                          */
     PIC_DIAG_NUM_PARTICLES = 4, /* 1 int64                                        */
     PIC_DIAG_PATCH_COUNTS = 5,  /* npatch int32 (x fastest)                        */
-    PIC_DIAG_STEP = 6,          /* 2 int64: steps taken, window shifts            */
+    PIC_DIAG_STEP = 6,          /* 3 int64: steps taken, window shifts, capacity
+                                   repacks (per-patch capacities re-split on the
+                                   device when a patch nears its capacity)        */
     PIC_DIAG_EX_AXIS = 7        /* nx float64: Ex on the row (and plane) ny/2      */
 };
 pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);

@@ -323,8 +323,11 @@ class Sim:
                              dtype=np.int32).copy()
 
     def step_info(self):
-        s, k = np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 16), dtype=np.int64)
+        s, k, _ = np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)
         return int(s), int(k)
+
+    def repacks(self) -> int:
+        return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)[2])
 
     def ex_axis(self):
         return np.frombuffer(pic_diag(self.h, PIC_DIAG_EX_AXIS, 8 * self.cfg.n[0]),

@@ -190,38 +190,56 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
         T* U1 = reinterpret_cast<T*>(S.u[1]);
         T* U2 = reinterpret_cast<T*>(S.u[2]);
 
+        // raw particle state of the next iteration, loaded one iteration ahead so the
+        // global-memory latency overlaps the current particle's arithmetic
+        double nx0 = 0.0, ny0 = 0.0;  // FP64 positions
+        int nc = 0;                   // FP32 packed cell
+        T nfx = T(0), nfy = T(0), nu0 = T(0), nu1 = T(0), nu2 = T(0), nw = T(0);
+        auto fetch = [&](int kk) {
+            const int sl = base + kk;
+            if constexpr (sizeof(T) == 8) {
+                nx0 = reinterpret_cast<const double*>(S.xi[0])[sl];
+                ny0 = reinterpret_cast<const double*>(S.xi[1])[sl];
+            } else {
+                nc = S.cell[sl];
+                nfx = reinterpret_cast<const float*>(S.xi[0])[sl];
+                nfy = reinterpret_cast<const float*>(S.xi[1])[sl];
+            }
+            nu0 = U0[sl];
+            nu1 = U1[sl];
+            nu2 = U2[sl];
+            nw = W[sl];
+        };
+        if (tid < cnt) fetch(tid);
+
         for (int k0 = 0; k0 < cnt; k0 += blockDim.x) {
             const int k = k0 + tid;
             const bool valid = k < cnt;
             const int slot = base + (valid ? k : 0);
 
-            // ---- A. load: integer cell + offset per axis
+            // ---- A. take the prefetched state, start loading the next one
             int ix = 0, iy = 0;
             T fx = T(0), fy = T(0);
             double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
-            T u[3] = {T(0), T(0), T(0)};
-            T w = T(0);
+            T u[3] = {nu0, nu1, nu2};
+            T w = nw;
             if (valid) {
                 if constexpr (sizeof(T) == 8) {
-                    xi0 = reinterpret_cast<const double*>(S.xi[0])[slot];
-                    eta0 = reinterpret_cast<const double*>(S.xi[1])[slot];
+                    xi0 = nx0;
+                    eta0 = ny0;
                     const double fxd = floor(xi0), fyd = floor(eta0);
                     ix = (int)fxd;
                     iy = (int)fyd;
                     fx = xi0 - fxd;
                     fy = eta0 - fyd;
                 } else {
-                    const int c = S.cell[slot];
-                    ix = c & 0xFFFF;
-                    iy = (c >> 16) & 0xFFFF;
-                    fx = reinterpret_cast<const float*>(S.xi[0])[slot];
-                    fy = reinterpret_cast<const float*>(S.xi[1])[slot];
+                    ix = nc & 0xFFFF;
+                    iy = (nc >> 16) & 0xFFFF;
+                    fx = nfx;
+                    fy = nfy;
                 }
-                u[0] = U0[slot];
-                u[1] = U1[slot];
-                u[2] = U2[slot];
-                w = W[slot];
             }
+            if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
             // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
             const bool hx = fx >= T(0.5), hy = fy >= T(0.5);
             const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
@@ -415,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
                 gi = wrapi(gi, nx);
             }
             gj = wrapi(gj, ny);
-            atomicAdd(Jg + comp * fs + (long long)(gj + kGuard) * NX + (gi + kGuard), (double)v);
+            atomicAdd(Jg + comp * fs + (long long)(gj + kGuard) * NX + (gi + kGuard), widen_f32(v));
         }
     }
 }

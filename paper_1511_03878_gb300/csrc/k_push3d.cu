@@ -164,22 +164,32 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         T* U2 = reinterpret_cast<T*>(S.u[2]);
         const T* W = reinterpret_cast<const T*>(S.w);
 
+        // next iteration's raw state, loaded one iteration ahead
+        int nic[3] = {0, 0, 0};
+        T nf[3] = {T(0), T(0), T(0)};
+        double nxi[3] = {0.0, 0.0, 0.0};
+        T nu[3] = {T(0), T(0), T(0)};
+        T nw = T(0);
+        auto fetch = [&](int kk) {
+            const int sl = base + kk;
+            split_pos<T>(S, sl, nic, nf, nxi);
+            nu[0] = U0[sl];
+            nu[1] = U1[sl];
+            nu[2] = U2[sl];
+            nw = W[sl];
+        };
+        if (tid < cnt) fetch(tid);
+
         for (int k0 = 0; k0 < cnt; k0 += blockDim.x) {
             const int k = k0 + tid;
             const bool valid = k < cnt;
             const int slot = base + (valid ? k : 0);
-            int ic[3] = {0, 0, 0};
-            T f[3] = {T(0), T(0), T(0)};
-            double xi0[3] = {0.0, 0.0, 0.0};
-            T u[3] = {T(0), T(0), T(0)};
-            T w = T(0);
-            if (valid) {
-                split_pos<T>(S, slot, ic, f, xi0);
-                u[0] = U0[slot];
-                u[1] = U1[slot];
-                u[2] = U2[slot];
-                w = W[slot];
-            }
+            int ic[3] = {nic[0], nic[1], nic[2]};
+            T f[3] = {nf[0], nf[1], nf[2]};
+            double xi0[3] = {nxi[0], nxi[1], nxi[2]};
+            T u[3] = {nu[0], nu[1], nu[2]};
+            T w = nw;
+            if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
             int np_[3], tp[3], td[3];
             T dp[3], dd[3];
             bool ok = valid;
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
             const int gk = wrapi(p0[2] - 2 + tz, n[2]);
             atomicAdd(Jg + comp * fs + ((long long)(gk + kGuard) * S.NY + (gj + kGuard)) * S.NX +
                           (gi + kGuard),
-                      (double)v);
+                      widen_f32(v));
         }
     }
 }

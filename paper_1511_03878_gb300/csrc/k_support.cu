@@ -47,7 +47,6 @@ __global__ void __launch_bounds__(kQueueThreads) queue_build_kernel(const BatchD
     }
     for (int b = tid; b < kBuckets; b += blockDim.x) bucket_cnt[b] = 0;
     __syncthreads();
-
     // pass 1: full chunks (scan-ordered by global patch index) + remainder histogram
     int carry = 0;
     for (int g0 = 0; g0 < total; g0 += blockDim.x) {
@@ -176,13 +175,20 @@ __global__ void __launch_bounds__(256) exchange_kernel(const BatchDev* __restric
         int nm = S.mcount[p];
         const int mc = S.mcap[p];
         if (nm > mc) nm = mc;
-        int nn = n - nh + nm;
         const int cap = S.pcap[p];
-        if (nn > cap) {
-            atomicOr(S.status, ST_CAPACITY);
-            nm -= nn - cap;
-            nn = cap;
+        // arrivals beyond the free room stay in the exchange buffer; the repack at the
+        // end of this step enlarges the patch and places them
+        const int room = cap - (n - nh);
+        int pend = 0;
+        if (nm > room) {
+            pend = nm - room;
+            nm = room;
         }
+        S.mpend[p] = pend;
+        S.mpoff[p] = nm;
+        const int nn = n - nh + nm;
+        // ask for a repack before a patch or its exchange buffer runs out
+        if (pend > 0 || nn > cap - cap / 8 - 16 || S.mcount[p] > mc / 2) atomicOr(&S.st->repack, 1);
         s_n = n;
         s_nh = nh;
         s_nm = nm;
@@ -439,13 +445,143 @@ cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, i
     return cudaGetLastError();
 }
 
+// ================================================================ capacity repack
+
+// New per-patch capacities from the current counts (free slots shared half by count,
+// half evenly, as at load) and their prefix bases. One CTA per sim.
+__global__ void __launch_bounds__(1024) repack_plan_kernel(const BatchDev* __restrict__ bd) {
+    __shared__ int warp_sums[32];
+    __shared__ long long s_total;
+    const SimDev& S = bd->sims[blockIdx.x];
+    if (blockIdx.x >= bd->nsims || !S.st->repack) return;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_total = 0;
+    __syncthreads();
+    long long part = 0;
+    for (int p = tid; p < S.npatch; p += blockDim.x) part += S.pcount[p] + S.mpend[p];
+    atomicAdd((unsigned long long*)&s_total, (unsigned long long)part);
+    __syncthreads();
+    const long long N = s_total;
+    if (N > S.capacity) {  // more particles (with pending arrivals) than slots
+        if (tid == 0) {
+            atomicOr(S.status, ST_CAPACITY);
+            S.st->repack = 2;
+        }
+        return;
+    }
+    const double spare = (double)(S.capacity - N);
+    int carry = 0, mcarry = 0;
+    for (int p0 = 0; p0 < S.npatch; p0 += blockDim.x) {
+        const int p = p0 + tid;
+        int cap = 0, mc = 0;
+        if (p < S.npatch) {
+            const int c = S.pcount[p] + S.mpend[p];
+            const double share = N > 0 ? 0.5 * (double)c / (double)N + 0.5 / S.npatch : 1.0 / S.npatch;
+            cap = c + (int)floor(spare * share);
+            mc = cap / 4 > kMailboxMin ? cap / 4 : kMailboxMin;
+        }
+        int tot, mtot;
+        const int ex = block_exclusive_scan(cap, warp_sums, &tot);
+        const int mex = block_exclusive_scan(mc, warp_sums, &mtot);
+        if (p < S.npatch) {
+            S.pcap_new[p] = cap;
+            S.pbase_new[p] = carry + ex;
+            S.mcap_new[p] = mc;
+            S.mbase_new[p] = mcarry + mex;
+        }
+        carry += tot;
+        mcarry += mtot;
+    }
+    if (tid == 0 && (carry > S.capacity || mcarry > S.mtotal)) {
+        atomicOr(S.status, ST_CAPACITY);
+        S.st->repack = 2;  // failed: keep the current layout, drop the pending arrivals
+    }
+}
+
+// Live particles of patch p -> scratch buffer at the new base (move), then back to
+// the primary arrays at the same new offsets (back).
+template <typename T>
+__global__ void __launch_bounds__(256) repack_copy_kernel(const BatchDev* __restrict__ bd, int back) {
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    if (S.st->repack != 1) return;
+    const int p = blockIdx.x;
+    if (p >= S.npatch) return;
+    const int cnt = S.pcount[p];
+    const int from = back ? S.pbase_new[p] : S.pbase[p];
+    const int to = S.pbase_new[p];
+    const int pend = S.mpend[p];
+    if ((long long)to + cnt + pend > S.capacity || (long long)from + cnt > S.capacity) return;
+    if (back && pend > 0) {  // arrivals that did not fit before: append after the live ones
+        const int m0 = S.mbase[p] + S.mpoff[p];
+        for (int k = threadIdx.x; k < pend; k += blockDim.x)
+            copy_particle<T>(S, S.dims, to + cnt + k, m0 + k, true);
+    }
+    const int dims = S.dims;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int a0 = from + k, b0 = to + k;
+        if (back) {
+            if constexpr (sizeof(T) == 4) S.cell[b0] = S.acell[a0];
+            for (int a = 0; a < dims; a++)
+                reinterpret_cast<T*>(S.xi[a])[b0] = reinterpret_cast<const T*>(S.axi[a])[a0];
+            for (int a = 0; a < 3; a++)
+                reinterpret_cast<T*>(S.u[a])[b0] = reinterpret_cast<const T*>(S.au[a])[a0];
+            reinterpret_cast<T*>(S.w)[b0] = reinterpret_cast<const T*>(S.aw)[a0];
+            S.id[b0] = S.aid[a0];
+        } else {
+            if constexpr (sizeof(T) == 4) S.acell[b0] = S.cell[a0];
+            for (int a = 0; a < dims; a++)
+                reinterpret_cast<T*>(S.axi[a])[b0] = reinterpret_cast<const T*>(S.xi[a])[a0];
+            for (int a = 0; a < 3; a++)
+                reinterpret_cast<T*>(S.au[a])[b0] = reinterpret_cast<const T*>(S.u[a])[a0];
+            reinterpret_cast<T*>(S.aw)[b0] = reinterpret_cast<const T*>(S.w)[a0];
+            S.aid[b0] = S.id[a0];
+        }
+    }
+}
+
+cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int prec,
+                          cudaStream_t s) {
+    repack_plan_kernel<<<nsims, 1024, 0, s>>>(bd);
+    dim3 grid(max_patches, nsims);
+    for (int back = 0; back < 2; back++) {
+        if (prec == 0)
+            repack_copy_kernel<double><<<grid, 256, 0, s>>>(bd, back);
+        else
+            repack_copy_kernel<float><<<grid, 256, 0, s>>>(bd, back);
+    }
+    return cudaGetLastError();
+}
+
 // ================================================================ end of step
 
+// End of step, one CTA per sim: install the layout of a repack done in this step
+// (bases, capacities, counts including placed arrivals), then advance the state.
 __global__ void end_step_kernel(const BatchDev* __restrict__ bd) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x;
     if (s >= bd->nsims) return;
     const SimDev& S = bd->sims[s];
     StepState* st = S.st;
+    const int rp = st->repack;
+    if (rp == 1) {
+        for (int p = threadIdx.x; p < S.npatch; p += blockDim.x) {
+            S.pbase[p] = S.pbase_new[p];
+            S.pcap[p] = S.pcap_new[p];
+            S.mbase[p] = S.mbase_new[p];
+            S.mcap[p] = S.mcap_new[p];
+            S.pcount[p] += S.mpend[p];
+            S.mpend[p] = 0;
+        }
+    } else if (rp == 2) {  // failed repack (status latched): the pending arrivals are lost
+        for (int p = threadIdx.x; p < S.npatch; p += blockDim.x) S.mpend[p] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (rp) {
+        st->repack = 0;
+        st->nrepack += rp == 1;
+    }
     st->step += 1;
     if (st->shift) {
         st->nshift += 1;
@@ -456,8 +592,9 @@ __global__ void end_step_kernel(const BatchDev* __restrict__ bd) {
     st->shift = 0;
 }
 
-cudaError_t launch_end_step(const BatchDev* bd, int nsims, cudaStream_t s) {
-    end_step_kernel<<<(nsims + 127) / 128, 128, 0, s>>>(bd);
+cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cudaStream_t s) {
+    (void)max_patches;
+    end_step_kernel<<<nsims, 256, 0, s>>>(bd);
     return cudaGetLastError();
 }
 

@@ -62,7 +62,6 @@ struct pic_sim {
     cudaGraphExec_t gexec = nullptr;
     int push_grid = 0;
     int column_pts = 0;
-    std::vector<int> h_pbase, h_pcap;
     std::string err;
 };
 
@@ -191,12 +190,23 @@ Layout plan(const pic_config* c, char* base) {
     S.mbase = cv.take<int>(S.npatch);
     S.mcap = cv.take<int>(S.npatch);
     S.mcount = cv.take<int>(S.npatch);
-    S.mtotal = cap / 4 + 64LL * S.npatch;
+    S.mtotal = cap / 4 + (long long)kMailboxMin * S.npatch;
     S.mcell = c->precision == PIC_FP32 ? cv.take<int>(S.mtotal) : nullptr;
     for (int a = 0; a < 3; a++) S.mxi[a] = a < c->dims ? cv.take<char>(S.mtotal * es) : nullptr;
     for (int a = 0; a < 3; a++) S.mu[a] = cv.take<char>(S.mtotal * es);
     S.mw = cv.take<char>(S.mtotal * es);
     S.mid = cv.take<int>(S.mtotal);
+    S.acell = c->precision == PIC_FP32 ? cv.take<int>(cap) : nullptr;
+    for (int a = 0; a < 3; a++) S.axi[a] = a < c->dims ? cv.take<char>(cap * es) : nullptr;
+    for (int a = 0; a < 3; a++) S.au[a] = cv.take<char>(cap * es);
+    S.aw = cv.take<char>(cap * es);
+    S.aid = cv.take<int>(cap);
+    S.pbase_new = cv.take<int>(S.npatch);
+    S.pcap_new = cv.take<int>(S.npatch);
+    S.mbase_new = cv.take<int>(S.npatch);
+    S.mcap_new = cv.take<int>(S.npatch);
+    S.mpend = cv.take<int>(S.npatch);
+    S.mpoff = cv.take<int>(S.npatch);
 
     BatchDev& B = L.B;
     B.nsims = 1;
@@ -279,11 +289,12 @@ pic_status cuda_fail(std::string* err, cudaError_t e, const char* where) {
 pic_status status_to_error(std::string* err, int st) {
     if (st == 0) return PIC_OK;
     if (st & ST_TIMEOUT) return fail(err, PIC_ERR_TIMEOUT, "a bounded device wait expired");
-    if (st & ST_NUMERIC)
-        return fail(err, PIC_ERR_NUMERIC, "non-finite particle state or a move of a cell or more");
-    if (st & ST_CAPACITY) return fail(err, PIC_ERR_CAPACITY, "a patch overflowed its capacity");
+    if (st & ST_CAPACITY)
+        return fail(err, PIC_ERR_CAPACITY, "more particles than the arena's capacity");
     if (st & ST_MAILBOX) return fail(err, PIC_ERR_CAPACITY, "an exchange buffer overflowed");
     if (st & ST_QUEUE) return fail(err, PIC_ERR_CAPACITY, "the work queue overflowed");
+    if (st & ST_NUMERIC)
+        return fail(err, PIC_ERR_NUMERIC, "non-finite particle state or a move of a cell or more");
     return fail(err, PIC_ERR_CUDA, "unknown device status");
 }
 
@@ -318,8 +329,9 @@ cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_pa
     if (le == cudaSuccess) le = cudaEventRecord(*o.ev_join, *o.cap1);
     if (le == cudaSuccess && window) le = launch_inject(db, nsims, max_column, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_exchange(db, nsims, max_patches, prec, *o.cap0);
+    if (le == cudaSuccess) le = launch_repack(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap0, *o.ev_join, 0);
-    if (le == cudaSuccess) le = launch_end_step(db, nsims, *o.cap0);
+    if (le == cudaSuccess) le = launch_end_step(db, nsims, max_patches, *o.cap0);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(*o.cap0, &g);
     if (le != cudaSuccess) {
@@ -502,7 +514,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         pcap[p] = (int)c;
         pbase[p] = (int)acc;
         acc += c;
-        mcap[p] = std::max(64, pcap[p] / 4);
+        mcap[p] = std::max(kMailboxMin, pcap[p] / 4);
         mbase[p] = (int)macc;
         macc += mcap[p];
     }
@@ -587,8 +599,6 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     CK(cudaMemcpyAsync(S.st, &st, sizeof(st), cudaMemcpyHostToDevice, s->stream), "copy state");
     CK(cudaMemsetAsync(S.status, 0, sizeof(int), s->stream), "zero status");
     CK(cudaStreamSynchronize(s->stream), "load particles");
-    s->h_pbase = pbase;
-    s->h_pcap = pcap;
     return PIC_OK;
 }
 
@@ -744,11 +754,12 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
             return PIC_OK;
         }
         case PIC_DIAG_STEP: {
-            if (!need(2 * sizeof(long long))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            if (!need(3 * sizeof(long long))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
             long long* o = static_cast<long long*>(out);
             o[0] = st.step;
             o[1] = st.nshift;
-            if (written) *written = 2 * sizeof(long long);
+            o[2] = st.nrepack;
+            if (written) *written = 3 * sizeof(long long);
             return PIC_OK;
         }
         case PIC_DIAG_PARTICLES: {
@@ -774,11 +785,14 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
                 hcell.resize(cap);
                 CK(cudaMemcpy(hcell.data(), S.cell, cap * sizeof(int), cudaMemcpyDeviceToHost), "read cell");
             }
+            std::vector<int> pbase(S.npatch);
+            CK(cudaMemcpy(pbase.data(), S.pbase, S.npatch * sizeof(int), cudaMemcpyDeviceToHost),
+               "read pbase");
             std::vector<std::pair<int, long long>> live;
             live.reserve(n);
             for (int p = 0; p < S.npatch; p++)
                 for (int c = 0; c < counts[p]; c++) {
-                    const long long sl = (long long)s->h_pbase[p] + c;
+                    const long long sl = (long long)pbase[p] + c;
                     live.emplace_back(hid[sl], sl);
                 }
             std::sort(live.begin(), live.end());
@@ -837,10 +851,11 @@ extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) 
         if (e == cudaSuccess && S.window) e = launch_inject(s->L.db, 1, s->column_pts, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], s->stream);
         if (e == cudaSuccess) e = launch_exchange(s->L.db, 1, S.npatch, S.prec, s->stream);
+        if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
         if (e == cudaSuccess) e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
-        if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, s->stream);
+        if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, S.npatch, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[6], s->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
         if (e != cudaSuccess) {

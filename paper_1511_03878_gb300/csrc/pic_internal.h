@@ -18,6 +18,7 @@ constexpr int kGuard = 1;        // guard cells below each axis in the padded fi
 constexpr int kThreads = 256;    // threads per CTA of the particle kernel
 constexpr int kQueueThreads = 1024;
 constexpr int kBuckets = 64;     // remainder buckets of the approximate LPT order
+constexpr int kMailboxMin = 1024; // exchange-buffer slots per patch at least (a step's arrivals)
 
 // status bits latched by device code
 enum : int {
@@ -34,7 +35,8 @@ struct StepState {
     long long next_id;  // next particle id handed to injected particles
     int shift;          // 1 if the current step ends with a window shift
     int gen;            // field buffer generation read by the current step (step & 1)
-    int pad[2];
+    int repack;         // set by the exchange when a patch nears or exceeds its capacity
+    int nrepack;        // repacks done
 };
 
 struct SimDev {
@@ -76,6 +78,15 @@ struct SimDev {
     void* mw;
     int* mid;
     long long capacity, mtotal;
+    // repack: scratch particle buffer (capacity slots) and the next layout
+    int* acell;
+    void* axi[3];
+    void* au[3];
+    void* aw;
+    int* aid;
+    int* pbase_new; int* pcap_new; int* mbase_new; int* mcap_new;
+    int* mpend;      // arrivals left in the exchange buffer for want of room (repack places them)
+    int* mpoff;      // offset of the first of them in the patch's exchange buffer
     // state and scratch
     StepState* st;
     int* status;
@@ -101,6 +112,9 @@ struct BatchDev {
 
 // ---- launchers (each enqueues on the given stream) ----
 cudaError_t launch_queue_build(const BatchDev* bd, cudaStream_t s);
+// capacity repack (no-op unless a sim's exchange flagged it)
+cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int prec,
+                          cudaStream_t s);
 cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping,
                         int P0, int P1, int P2, int grid, cudaStream_t s);
 int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes);
@@ -110,7 +124,7 @@ cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int 
                             cudaStream_t s);
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
                        cudaStream_t s);
-cudaError_t launch_end_step(const BatchDev* bd, int nsims, cudaStream_t s);
+cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cudaStream_t s);
 // 3D variants
 int push3d_smem(int prec, int P0, int P1, int P2);
 int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes);

@@ -209,16 +209,43 @@ def test_one_heavy_patch(binding):
         sim.close()
 
 
+def test_repack_under_uneven_load(binding):
+    """A dense blob next to empty patches with tight capacity: the device re-splits the
+    per-patch capacities (repack) instead of overflowing, and results stay exact."""
+    rng = np.random.default_rng(6)
+    N = 30000
+    x = rng.uniform(1.6, 3.2, N)
+    y = rng.uniform(1.6, 3.2, N)
+    p = dict(x=x, y=y, z=np.zeros(N), ux=rng.normal(0, 0.3, N), uy=rng.normal(0, 0.3, N),
+             uz=rng.normal(0, 0.1, N), w=np.full(N, 1e-3), id=np.arange(N, dtype=np.int32))
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, seed=2, patch=(16, 16))
+    w = dict(w, particles=p)
+    o = make_oracle(w)
+    o.step(15)
+    for prec in ("f64", "f32"):
+        sim = binding.Sim(w["params"], precision=binding.PIC_FP64 if prec == "f64" else binding.PIC_FP32,
+                          capacity=int(1.15 * N), chunk=700)
+        sim.load(w)
+        sim.step(15)
+        sim.sync()
+        assert sim.repacks() >= 1
+        if prec == "f64":
+            compare(sim, o, w["params"], 1e-9)
+        else:
+            q, qo = sim.particles(), o.get_particles()
+            assert np.array_equal(q["id"], qo["id"])
+            assert normwise(q["ux"], qo["ux"]) < 1e-4
+        sim.close()
+
+
 def test_capacity_overflow_is_reported(binding):
-    """A patch that cannot take its arrivals latches PIC_ERR_CAPACITY (no fault)."""
-    w = inputs.thermal2d(nx=32, ny=32, d=0.1, ppc_side=4, seed=1, patch=(16, 16))
-    # everything drifts to +x at high speed: the right patches overflow a tight capacity
-    p = dict(w["particles"])
-    n = len(p["x"])
-    p["ux"] = np.full(n, 5.0)
-    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=n + 8)
-    sim.load(dict(w, particles=p))
-    sim.step(40)
+    """More particles than the arena holds (window injection into a half-empty box):
+    the device latches PIC_ERR_CAPACITY; nothing faults."""
+    w = small_lwfa()
+    n = len(w["particles"]["x"])
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=n + 300)
+    sim.load(w)
+    sim.step(6)  # each shift injects 128 x 4 = 512 particles, few leave on the left
     with pytest.raises(binding.PicError) as e:
         sim.sync()
     assert e.value.code == binding.PIC_ERR_CAPACITY
