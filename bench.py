@@ -41,14 +41,17 @@ FLOPS_PER_PUSH_2D = 370
 FLOPS_PER_PUSH_3D = 660
 
 
+DTYPE = {"fp64": "f64", "fp32": "f32", "df64": "f32x2 (double-word, ~48-bit)"}
+
+
 def bytes_per_push(dt, w):
     """Algorithmic HBM bytes of the particle kernel per push: particle state read and
     written once, weight read once; E and B^n read once and J (FP64) written once per
-    cell, shared by the particles per cell."""
+    cell, shared by the particles per cell. dt: "fp64", "fp32" or "df64"."""
     p = w["params"]
     dims = p["dims"]
-    es = 8 if dt == "f64" else 4
-    pos = dims * es + (4 if dt == "f32" else 0)
+    es = 4 if dt == "fp32" else 8
+    pos = dims * es + (0 if dt == "fp64" else 4)
     ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
     return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
 KERNELS_PER_STEP = 7  # queue, push, inject, exchange, yee_e, yee_b, end_step
@@ -60,7 +63,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
+    ap.add_argument("--variants", default="fp32,df64",
+                    help="other precisions timed in the same run (comma list, or none)")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=0)
@@ -193,7 +198,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
 
     from paper_1511_03878_gb300 import binding
 
-    prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
+    prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
@@ -225,7 +230,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
     # per-kernel CUDA-event pass (same kernels, same launch shapes) for the roofline
     prof = sim.profile(K)
     push_ms = prof["push"] / K
-    dt = "f64" if precision == "fp64" else "f32"
+    dt = precision
     n_push = 0.5 * (n0 + n1)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -242,9 +247,13 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
     else:
         achieved = bytes_per_push(dt, w) * n_push / (push_ms * 1e-3) / 1e9
         peak = hbm if hbm else 6800.0
+        tname = "float" if precision == "fp32" else "df64"
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"push{dims}d_kernel<float>",
+                "frac": achieved / peak, "traffic": None, "kernel": f"push{dims}d_kernel<{tname}>",
                 "peak_source": "measured" if hbm else "fallback"}
+        if precision == "df64":
+            fl = FLOPS_PER_PUSH_2D if dims == 2 else FLOPS_PER_PUSH_3D
+            roof["fp64_equivalent_tflops"] = fl * n_push / (push_ms * 1e-3) / 1e12
     out = dict(ms=ms, pushes=pushes, n=n_push, profile={k: v / K for k, v in prof.items()},
                roofline=roof, push_ms=push_ms, repacks=repacks)
     sim.close()
@@ -260,7 +269,7 @@ def run_e2e(args, w, precision, K):
 
     from paper_1511_03878_gb300 import binding
 
-    prec = binding.PIC_FP64 if precision == "fp64" else binding.PIC_FP32
+    prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=args.chunk)
@@ -271,9 +280,9 @@ def run_e2e(args, w, precision, K):
     e = sim.energy()
     ax = sim.ex_axis()
     t1 = time.perf_counter()
-    es = 8 if precision == "fp64" else 4
+    es = 4 if precision == "fp32" else 8
     dims = w["params"]["dims"]
-    per_slot = es * (dims + 3 + 1) + 4 + (4 if precision == "fp32" else 0)
+    per_slot = es * (dims + 3 + 1) + 4 + (0 if precision == "fp64" else 4)
     cfg = sim.cfg
     fstride = (cfg.n[0] + 4) * (cfg.n[1] + 3) * ((cfg.n[2] + 3) if dims == 3 else 1)
     h2d = cap * per_slot + 9 * fstride * es + 5 * sim.npatch * 4
@@ -471,10 +480,9 @@ def main():
     w = workload(args.nx, args.ny, args.workload, args.total)
     clocks = ClockSampler(local)
     main_run = run_gpu(args, w, args.precision, args.steps, args.warmup, world, clocks)
-    other = "fp32" if args.precision == "fp64" else "fp64"
-    variant = None
-    if not args.no_variant:
-        variant = run_gpu(args, w, other, args.steps, args.warmup, world)
+    others = [] if args.no_variant or args.variants == "none" else [
+        v for v in args.variants.split(",") if v and v != args.precision]
+    variants = {v: run_gpu(args, w, v, args.steps, args.warmup, world) for v in others}
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, w, args.precision, args.steps)
@@ -492,7 +500,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "dtype": DTYPE[args.precision],
         "data": "synthetic (seeded LWFA-shaped initial condition, no dataset)",
         "config": config_dict(args, args.precision),
         "roofline": main_run["roofline"],
@@ -506,12 +514,11 @@ def main():
         "particles": main_run["n"],
         "capacity_repacks": main_run["repacks"],
     }
-    if variant:
-        line["variants"] = {other: {
-            "value": world * variant["pushes"] / (variant["ms"] * 1e-3),
-            "ms_per_step": variant["ms"] / args.steps, "roofline": variant["roofline"],
-            "kernel_ms_per_step": variant["profile"],
-            "dtype": "f64" if other == "fp64" else "f32"}}
+    if variants:
+        line["variants"] = {v: {
+            "value": world * r["pushes"] / (r["ms"] * 1e-3),
+            "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
+            "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v]} for v, r in variants.items()}
     print(json.dumps(line), flush=True)
 
 

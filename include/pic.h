@@ -56,7 +56,14 @@ typedef enum {
     PIC_ERR_TIMEOUT = -6   /* a bounded device-side wait expired */
 } pic_status;
 
-enum { PIC_FP64 = 0, PIC_FP32 = 1 };
+/* Precision of particles and fields (the global current is FP64 in all three):
+ *   PIC_FP64  IEEE binary64 throughout.
+ *   PIC_FP32  binary32 particles (cell index + offset) and fields.
+ *   PIC_DF64  double-word: every real held and computed as a pair of binary32 numbers
+ *             (hi + lo, about 48 significant bits), particles as cell index + pair
+ *             offset. FP64-class accuracy (relative errors of a few 2^-48) from FP32
+ *             arithmetic, for GPUs whose FP64 units are a small fraction of FP32. */
+enum { PIC_FP64 = 0, PIC_FP32 = 1, PIC_DF64 = 2 };
 
 /* Work distribution of the particle kernel. */
 enum {
@@ -70,8 +77,7 @@ typedef struct {
     double d[3];        /* cell sizes */
     double dt;          /* time step; must be below every d[a] */
     int patch[3];       /* cells per patch per axis: a multiple of 4, dividing n[a] */
-    int precision;      /* PIC_FP64: FP64 everywhere.  PIC_FP32: FP32 fields and
-                           particles (cell index + FP32 offset), FP64 global current */
+    int precision;      /* PIC_FP64, PIC_FP32 or PIC_DF64 (see above) */
     int window;         /* 0: all axes periodic.  1: x is a moving window at c
                            (fields zero outside, particles absorbed), y/z periodic */
     double n0;          /* window only: injected density n(x) = n0 *        */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpic.so")
 
 PIC_OK, PIC_ERR_INVALID, PIC_ERR_NOMEM, PIC_ERR_CAPACITY = 0, -1, -2, -3
 PIC_ERR_CUDA, PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT = -4, -5, -6
-PIC_FP64, PIC_FP32 = 0, 1
+PIC_FP64, PIC_FP32, PIC_DF64 = 0, 1, 2
 PIC_MAP_QUEUE, PIC_MAP_STATIC = 0, 1
 (PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_FIELDS, PIC_DIAG_PARTICLES,
  PIC_DIAG_NUM_PARTICLES, PIC_DIAG_PATCH_COUNTS, PIC_DIAG_STEP, PIC_DIAG_EX_AXIS) = range(8)

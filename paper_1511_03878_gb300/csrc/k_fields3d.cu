@@ -103,13 +103,7 @@ __global__ void __launch_bounds__(256) yee_b3d_kernel(const BatchDev* __restrict
 cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,
                          cudaStream_t s) {
     dim3 grid((unsigned)((max_ncell + 255) / 256), nsims);
-    if (prec == 0) {
-        yee_e3d_kernel<double><<<grid, 256, 0, s>>>(bd);
-        yee_b3d_kernel<double><<<grid, 256, 0, s>>>(bd);
-    } else {
-        yee_e3d_kernel<float><<<grid, 256, 0, s>>>(bd);
-        yee_b3d_kernel<float><<<grid, 256, 0, s>>>(bd);
-    }
+    PIC_DISPATCH(prec, (yee_e3d_kernel<T><<<grid, 256, 0, s>>>(bd), yee_b3d_kernel<T><<<grid, 256, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 
@@ -127,7 +121,7 @@ __global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double 
         const int t = b0 + k;
         int ic[3];
         double f[3];
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (is_f64<T>::value) {
             for (int a = 0; a < 3; a++) {
                 const double xi = reinterpret_cast<const double*>(S.xi[a])[t];
                 ic[a] = (int)floor(xi);
@@ -138,7 +132,7 @@ __global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double 
             ic[0] = c & 0x7FF;
             ic[1] = (c >> 11) & 0x7FF;
             ic[2] = (c >> 22) & 0x3FF;
-            for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const float*>(S.xi[a])[t];
+            for (int a = 0; a < 3; a++) f[a] = (double)reinterpret_cast<const T*>(S.xi[a])[t];
         }
         double Sw[3][3];
         int nd[3];
@@ -183,16 +177,10 @@ cudaError_t launch_gauss3d(const SimDev* sd, const SimDev& hs, int prec, int mod
     cudaError_t e = cudaMemsetAsync(target, 0, hs.ncell * sizeof(double), s);
     if (e != cudaSuccess) return e;
     const double sign = mode == 0 ? -1.0 : 1.0;
-    if (prec == 0)
-        rho3d_kernel<double><<<hs.npatch, 256, 0, s>>>(sd, target, sign);
-    else
-        rho3d_kernel<float><<<hs.npatch, 256, 0, s>>>(sd, target, sign);
+    PIC_DISPATCH(prec, (rho3d_kernel<T><<<hs.npatch, 256, 0, s>>>(sd, target, sign)));
     if (mode == 1) {
         const unsigned g2 = (unsigned)((hs.ncell + 255) / 256);
-        if (prec == 0)
-            gauss3d_kernel<double><<<g2, 256, 0, s>>>(sd);
-        else
-            gauss3d_kernel<float><<<g2, 256, 0, s>>>(sd);
+        PIC_DISPATCH(prec, (gauss3d_kernel<T><<<g2, 256, 0, s>>>(sd)));
     }
     return cudaGetLastError();
 }

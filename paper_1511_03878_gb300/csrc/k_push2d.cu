@@ -107,7 +107,7 @@ __device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 2)
     push2d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -175,12 +175,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 
         // per-sim constants in the working precision (precomputed on the host)
         T dtdx, dtdy, eps, cjx, cjy, cjz;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (is_f64<T>::value) {
             dtdx = S.c_dtd[0], dtdy = S.c_dtd[1], eps = S.c_eps;
             cjx = S.c_j[0], cjy = S.c_j[1], cjz = S.c_j[2];
-        } else {
+        } else if constexpr (std::is_same<T, float>::value) {
             dtdx = S.f_dtd[0], dtdy = S.f_dtd[1], eps = S.f_eps;
             cjx = S.f_j[0], cjy = S.f_j[1], cjz = S.f_j[2];
+        } else {
+            dtdx = T(S.c_dtd[0]), dtdy = T(S.c_dtd[1]), eps = T(S.c_eps);
+            cjx = T(S.c_j[0]), cjy = T(S.c_j[1]), cjz = T(S.c_j[2]);
         }
 
         const int base = S.pbase[patch] + item.z;
@@ -197,13 +200,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
         T nfx = T(0), nfy = T(0), nu0 = T(0), nu1 = T(0), nu2 = T(0), nw = T(0);
         auto fetch = [&](int kk) {
             const int sl = base + kk;
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (is_f64<T>::value) {
                 nx0 = reinterpret_cast<const double*>(S.xi[0])[sl];
                 ny0 = reinterpret_cast<const double*>(S.xi[1])[sl];
             } else {
                 nc = S.cell[sl];
-                nfx = reinterpret_cast<const float*>(S.xi[0])[sl];
-                nfy = reinterpret_cast<const float*>(S.xi[1])[sl];
+                nfx = reinterpret_cast<const T*>(S.xi[0])[sl];
+                nfy = reinterpret_cast<const T*>(S.xi[1])[sl];
             }
             nu0 = U0[sl];
             nu1 = U1[sl];
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
             T u[3] = {nu0, nu1, nu2};
             T w = nw;
             if (valid) {
-                if constexpr (sizeof(T) == 8) {
+                if constexpr (is_f64<T>::value) {
                     xi0 = nx0;
                     eta0 = ny0;
                     const double fxd = floor(xi0), fyd = floor(eta0);
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
                 const T vx = u[0] * ig, vy = u[1] * ig;
                 vz = u[2] * ig;
                 int nxp1, nyp1;
-                if constexpr (sizeof(T) == 8) {
+                if constexpr (is_f64<T>::value) {
                     xi1 = xi0 + dtdx * vx;
                     eta1 = eta0 + dtdy * vy;
                     const double nx1d = floor(xi1 + 0.5), ny1d = floor(eta1 + 0.5);
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 
                 // ---- D. boundaries and destination patch
                 bool del = false;
-                if constexpr (sizeof(T) == 8) {
+                if constexpr (is_f64<T>::value) {
                     double xs = xi1 - (double)shift;
                     if (window) {
                         del = xi1 < 0.0 || xi1 >= (double)nx || xs < 0.0;
@@ -361,13 +364,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
                     dest = ix1 / P0 + S.np[0] * (iy1 / P1);
                     leave = dest != patch;
                     if (!leave) {
-                        if constexpr (sizeof(T) == 8) {
+                        if constexpr (is_f64<T>::value) {
                             reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
                             reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
                         } else {
                             S.cell[slot] = ix1 | (iy1 << 16);
-                            reinterpret_cast<float*>(S.xi[0])[slot] = fx1;
-                            reinterpret_cast<float*>(S.xi[1])[slot] = fy1;
+                            reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
+                            reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
                         }
                         U0[slot] = u[0];
                         U1[slot] = u[1];
@@ -396,13 +399,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
                 if (send) {
                     if (mslot < S.mcap[dest]) {
                         const int m = S.mbase[dest] + mslot;
-                        if constexpr (sizeof(T) == 8) {
+                        if constexpr (is_f64<T>::value) {
                             reinterpret_cast<double*>(S.mxi[0])[m] = xi1;
                             reinterpret_cast<double*>(S.mxi[1])[m] = eta1;
                         } else {
                             S.mcell[m] = ix1 | (iy1 << 16);
-                            reinterpret_cast<float*>(S.mxi[0])[m] = fx1;
-                            reinterpret_cast<float*>(S.mxi[1])[m] = fy1;
+                            reinterpret_cast<T*>(S.mxi[0])[m] = fx1;
+                            reinterpret_cast<T*>(S.mxi[1])[m] = fy1;
                         }
                         reinterpret_cast<T*>(S.mu[0])[m] = u[0];
                         reinterpret_cast<T*>(S.mu[1])[m] = u[1];
@@ -446,33 +449,27 @@ static int smem_bytes_2d(int P0, int P1) {
     return ((fb + 127) & ~127) + jb;
 }
 
+template <typename T>
+static int occupancy_2d(int P0, int P1, int* smem_bytes) {
+    const int sb = smem_bytes_2d<T>(P0, P1);
+    *smem_bytes = sb;
+    int blocks = 0;
+    if (cudaFuncSetAttribute(push2d_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) !=
+        cudaSuccess)
+        return 0;
+    cudaFuncSetAttribute(push2d_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<T>, kThreads, sb) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
+}
+
 int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) {
     if (dims == 3) return push3d_occupancy(prec, P0, P1, P2, smem_bytes);
     if (dims != 2) return 0;
     int blocks = 0;
-    if (prec == 0) {
-        const int sb = smem_bytes_2d<double>(P0, P1);
-        *smem_bytes = sb;
-        if (cudaFuncSetAttribute(push2d_kernel<double>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
-            return 0;
-        cudaFuncSetAttribute(push2d_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<double>,
-                                                          kThreads, sb) != cudaSuccess)
-            return 0;
-    } else {
-        const int sb = smem_bytes_2d<float>(P0, P1);
-        *smem_bytes = sb;
-        if (cudaFuncSetAttribute(push2d_kernel<float>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sb) != cudaSuccess)
-            return 0;
-        cudaFuncSetAttribute(push2d_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<float>,
-                                                          kThreads, sb) != cudaSuccess)
-            return 0;
-    }
+    PIC_DISPATCH(prec, (blocks = occupancy_2d<T>(P0, P1, smem_bytes)));
     return blocks;
 }
 
@@ -481,13 +478,8 @@ cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping,
     if (dims == 3) return launch_push3d(bd_dev, prec, mapping, P0, P1, P2, grid, s);
     if (dims != 2) return cudaErrorInvalidValue;
     const int static_map = mapping == 1;
-    if (prec == 0) {
-        const int sb = smem_bytes_2d<double>(P0, P1);
-        push2d_kernel<double><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
-    } else {
-        const int sb = smem_bytes_2d<float>(P0, P1);
-        push2d_kernel<float><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
-    }
+    PIC_DISPATCH(prec, (push2d_kernel<T><<<grid, kThreads, smem_bytes_2d<T>(P0, P1), s>>>(
+                            bd_dev, static_map)));
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, 
 template <typename T>
 __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T f[3],
                                           double xi[3]) {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (is_f64<T>::value) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             xi[a] = reinterpret_cast<const double*>(S.xi[a])[slot];
@@ -44,7 +44,7 @@ __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T
         i[1] = (c >> 11) & 0x7FF;
         i[2] = (c >> 22) & 0x3FF;
 #pragma unroll
-        for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const float*>(S.xi[a])[slot];
+        for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const T*>(S.xi[a])[slot];
     }
 }
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 1)
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -150,12 +150,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         __syncthreads();
 
         T dtd[3], cj[3], eps;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (is_f64<T>::value) {
             for (int a = 0; a < 3; a++) dtd[a] = S.c_dtd[a], cj[a] = S.c_j[a];
             eps = S.c_eps;
-        } else {
+        } else if constexpr (std::is_same<T, float>::value) {
             for (int a = 0; a < 3; a++) dtd[a] = S.f_dtd[a], cj[a] = S.f_j[a];
             eps = S.f_eps;
+        } else {
+            for (int a = 0; a < 3; a++) dtd[a] = T(S.c_dtd[a]), cj[a] = T(S.c_j[a]);
+            eps = T(S.c_eps);
         }
         const int base = S.pbase[patch] + item.z;
         const int cnt = item.w;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                 T dp1[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    if constexpr (sizeof(T) == 8) {
+                    if constexpr (is_f64<T>::value) {
                         xin[a] = xi0[a] + dtd[a] * v[a];
                         const double nd = floor(xin[a] + 0.5);
                         np1[a] = (int)nd;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                     int dp_[3];
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
-                        if constexpr (sizeof(T) == 8) {
+                        if constexpr (is_f64<T>::value) {
                             if (xin[a] < 0.0) xin[a] += (double)n[a];
                             if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
                             icn[a] = (int)floor(xin[a]);
@@ -336,13 +339,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                     dest = dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
                     leave = dest != patch;
                     if (!leave) {
-                        if constexpr (sizeof(T) == 8) {
+                        if constexpr (is_f64<T>::value) {
                             for (int a = 0; a < 3; a++)
                                 reinterpret_cast<double*>(S.xi[a])[slot] = xin[a];
                         } else {
                             S.cell[slot] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
                             for (int a = 0; a < 3; a++)
-                                reinterpret_cast<float*>(S.xi[a])[slot] = fn[a];
+                                reinterpret_cast<T*>(S.xi[a])[slot] = fn[a];
                         }
                         U0[slot] = u[0];
                         U1[slot] = u[1];
@@ -364,13 +367,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                 if (send) {
                     if (mslot < S.mcap[dest]) {
                         const int m = S.mbase[dest] + mslot;
-                        if constexpr (sizeof(T) == 8) {
+                        if constexpr (is_f64<T>::value) {
                             for (int a = 0; a < 3; a++)
                                 reinterpret_cast<double*>(S.mxi[a])[m] = xin[a];
                         } else {
                             S.mcell[m] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
                             for (int a = 0; a < 3; a++)
-                                reinterpret_cast<float*>(S.mxi[a])[m] = fn[a];
+                                reinterpret_cast<T*>(S.mxi[a])[m] = fn[a];
                         }
                         reinterpret_cast<T*>(S.mu[0])[m] = u[0];
                         reinterpret_cast<T*>(S.mu[1])[m] = u[1];
@@ -415,32 +418,30 @@ int smem_bytes_3d(int P0, int P1, int P2) {
 }
 
 int push3d_smem(int prec, int P0, int P1, int P2) {
-    return prec == 0 ? smem_bytes_3d<double>(P0, P1, P2) : smem_bytes_3d<float>(P0, P1, P2);
+    int sb = 0;
+    PIC_DISPATCH(prec, (sb = smem_bytes_3d<T>(P0, P1, P2)));
+    return sb;
+}
+
+template <typename T>
+static int occupancy_3d(int sb) {
+    int blocks = 0;
+    if (cudaFuncSetAttribute(push3d_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) !=
+        cudaSuccess)
+        return 0;
+    cudaFuncSetAttribute(push3d_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<T>, kThreads, sb) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
 }
 
 int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes) {
-    int blocks = 0;
     const int sb = push3d_smem(prec, P0, P1, P2);
     *smem_bytes = sb;
-    if (prec == 0) {
-        if (cudaFuncSetAttribute(push3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 sb) != cudaSuccess)
-            return 0;
-        cudaFuncSetAttribute(push3d_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<double>, kThreads,
-                                                          sb) != cudaSuccess)
-            return 0;
-    } else {
-        if (cudaFuncSetAttribute(push3d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 sb) != cudaSuccess)
-            return 0;
-        cudaFuncSetAttribute(push3d_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<float>, kThreads,
-                                                          sb) != cudaSuccess)
-            return 0;
-    }
+    int blocks = 0;
+    PIC_DISPATCH(prec, (blocks = occupancy_3d<T>(sb)));
     return blocks;
 }
 
@@ -448,10 +449,7 @@ cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0,
                           int grid, cudaStream_t s) {
     const int sb = push3d_smem(prec, P0, P1, P2);
     const int static_map = mapping == 1;
-    if (prec == 0)
-        push3d_kernel<double><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
-    else
-        push3d_kernel<float><<<grid, kThreads, sb, s>>>(bd_dev, static_map);
+    PIC_DISPATCH(prec, (push3d_kernel<T><<<grid, kThreads, sb, s>>>(bd_dev, static_map)));
     return cudaGetLastError();
 }
 

@@ -137,7 +137,7 @@ template <typename T>
 __device__ __forceinline__ void copy_particle(const SimDev& S, int dims, int dst, int src,
                                               bool from_mailbox) {
     if (from_mailbox) {
-        if constexpr (sizeof(T) == 4) S.cell[dst] = S.mcell[src];
+        if constexpr (uses_cell<T>()) S.cell[dst] = S.mcell[src];
         for (int a = 0; a < dims; a++)
             reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.mxi[a])[src];
         for (int a = 0; a < 3; a++)
@@ -145,7 +145,7 @@ __device__ __forceinline__ void copy_particle(const SimDev& S, int dims, int dst
         reinterpret_cast<T*>(S.w)[dst] = reinterpret_cast<const T*>(S.mw)[src];
         S.id[dst] = S.mid[src];
     } else {
-        if constexpr (sizeof(T) == 4) S.cell[dst] = S.cell[src];
+        if constexpr (uses_cell<T>()) S.cell[dst] = S.cell[src];
         for (int a = 0; a < dims; a++)
             reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.xi[a])[src];
         for (int a = 0; a < 3; a++)
@@ -241,10 +241,7 @@ __global__ void __launch_bounds__(256) exchange_kernel(const BatchDev* __restric
 cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int prec,
                             cudaStream_t s) {
     dim3 grid(max_patches, nsims);
-    if (prec == 0)
-        exchange_kernel<double><<<grid, 256, 0, s>>>(bd);
-    else
-        exchange_kernel<float><<<grid, 256, 0, s>>>(bd);
+    PIC_DISPATCH(prec, (exchange_kernel<T><<<grid, 256, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 
@@ -285,13 +282,13 @@ __global__ void inject2d_kernel(const BatchDev* __restrict__ bd) {
     }
     const int m = S.mbase[dest] + slot;
     const double ox = ((double)a + 0.5) / px, oy = ((double)b + 0.5) / py;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (is_f64<T>::value) {
         reinterpret_cast<double*>(S.mxi[0])[m] = (double)(nx - 1) + ox;
         reinterpret_cast<double*>(S.mxi[1])[m] = (double)j + oy;
     } else {
         S.mcell[m] = (nx - 1) | (j << 16);
-        reinterpret_cast<float*>(S.mxi[0])[m] = (float)ox;
-        reinterpret_cast<float*>(S.mxi[1])[m] = (float)oy;
+        reinterpret_cast<T*>(S.mxi[0])[m] = T(ox);
+        reinterpret_cast<T*>(S.mxi[1])[m] = T(oy);
     }
     reinterpret_cast<T*>(S.mu[0])[m] = T(0);
     reinterpret_cast<T*>(S.mu[1])[m] = T(0);
@@ -304,10 +301,7 @@ cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int
                           cudaStream_t s) {
     if (max_column_pts <= 0) return cudaSuccess;
     dim3 grid((max_column_pts + 255) / 256, nsims);
-    if (prec == 0)
-        inject2d_kernel<double><<<grid, 256, 0, s>>>(bd);
-    else
-        inject2d_kernel<float><<<grid, 256, 0, s>>>(bd);
+    PIC_DISPATCH(prec, (inject2d_kernel<T><<<grid, 256, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 
@@ -435,13 +429,7 @@ cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, i
     if (dims == 3) return launch_yee3d(bd, nsims, max_ncell, prec, s);
     if (dims != 2) return cudaErrorInvalidValue;
     dim3 grid((max_ncell + 255) / 256, nsims);
-    if (prec == 0) {
-        yee_e2d_kernel<double><<<grid, 256, 0, s>>>(bd);
-        yee_b2d_kernel<double><<<grid, 256, 0, s>>>(bd);
-    } else {
-        yee_e2d_kernel<float><<<grid, 256, 0, s>>>(bd);
-        yee_b2d_kernel<float><<<grid, 256, 0, s>>>(bd);
-    }
+    PIC_DISPATCH(prec, (yee_e2d_kernel<T><<<grid, 256, 0, s>>>(bd), yee_b2d_kernel<T><<<grid, 256, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 
@@ -522,7 +510,7 @@ __global__ void __launch_bounds__(256) repack_copy_kernel(const BatchDev* __rest
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         const int a0 = from + k, b0 = to + k;
         if (back) {
-            if constexpr (sizeof(T) == 4) S.cell[b0] = S.acell[a0];
+            if constexpr (uses_cell<T>()) S.cell[b0] = S.acell[a0];
             for (int a = 0; a < dims; a++)
                 reinterpret_cast<T*>(S.xi[a])[b0] = reinterpret_cast<const T*>(S.axi[a])[a0];
             for (int a = 0; a < 3; a++)
@@ -530,7 +518,7 @@ __global__ void __launch_bounds__(256) repack_copy_kernel(const BatchDev* __rest
             reinterpret_cast<T*>(S.w)[b0] = reinterpret_cast<const T*>(S.aw)[a0];
             S.id[b0] = S.aid[a0];
         } else {
-            if constexpr (sizeof(T) == 4) S.acell[b0] = S.cell[a0];
+            if constexpr (uses_cell<T>()) S.acell[b0] = S.cell[a0];
             for (int a = 0; a < dims; a++)
                 reinterpret_cast<T*>(S.axi[a])[b0] = reinterpret_cast<const T*>(S.xi[a])[a0];
             for (int a = 0; a < 3; a++)
@@ -546,10 +534,7 @@ cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int pr
     repack_plan_kernel<<<nsims, 1024, 0, s>>>(bd);
     dim3 grid(max_patches, nsims);
     for (int back = 0; back < 2; back++) {
-        if (prec == 0)
-            repack_copy_kernel<double><<<grid, 256, 0, s>>>(bd, back);
-        else
-            repack_copy_kernel<float><<<grid, 256, 0, s>>>(bd, back);
+        PIC_DISPATCH(prec, (repack_copy_kernel<T><<<grid, 256, 0, s>>>(bd, back)));
     }
     return cudaGetLastError();
 }
@@ -632,7 +617,7 @@ __global__ void energy_kernel(const SimDev* __restrict__ sd, long long ncell, lo
         const int b0 = S.pbase[p], cnt = S.pcount[p];
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int sidx = b0 + k;
-            const double ux = U0[sidx], uy = U1[sidx], uz = U2[sidx];
+            const double ux = (double)U0[sidx], uy = (double)U1[sidx], uz = (double)U2[sidx];
             wk += (double)W[sidx] * S.m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
         }
     }
@@ -658,10 +643,7 @@ __global__ void energy_kernel(const SimDev* __restrict__ sd, long long ncell, lo
 cudaError_t launch_energy(const SimDev* sd, long long ncell, long long cap, int prec,
                           cudaStream_t s) {
     int grid = 152 * 4;
-    if (prec == 0)
-        energy_kernel<double><<<grid, 256, 0, s>>>(sd, ncell, cap);
-    else
-        energy_kernel<float><<<grid, 256, 0, s>>>(sd, ncell, cap);
+    PIC_DISPATCH(prec, (energy_kernel<T><<<grid, 256, 0, s>>>(sd, ncell, cap)));
     return cudaGetLastError();
 }
 
@@ -677,7 +659,7 @@ __global__ void rho2d_kernel(const SimDev* __restrict__ sd, double* rho, double 
     const int nx = S.n[0], ny = S.n[1];
     int ix, iy;
     double fx, fy;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (is_f64<T>::value) {
         const double xi = reinterpret_cast<const double*>(S.xi[0])[t];
         const double eta = reinterpret_cast<const double*>(S.xi[1])[t];
         ix = (int)floor(xi);
@@ -688,8 +670,8 @@ __global__ void rho2d_kernel(const SimDev* __restrict__ sd, double* rho, double 
         const int c = S.cell[t];
         ix = c & 0xFFFF;
         iy = (c >> 16) & 0xFFFF;
-        fx = reinterpret_cast<const float*>(S.xi[0])[t];
-        fy = reinterpret_cast<const float*>(S.xi[1])[t];
+        fx = (double)reinterpret_cast<const T*>(S.xi[0])[t];
+        fy = (double)reinterpret_cast<const T*>(S.xi[1])[t];
     }
     const int hx = fx >= 0.5, hy = fy >= 0.5;
     double Sx[3], Sy[3];
@@ -740,16 +722,10 @@ cudaError_t launch_gauss(const SimDev* sd, const SimDev& hs, int prec, int mode,
     const int g1 = hs.npatch;
     const double sign = mode == 0 ? -1.0 : 1.0;
     if (hs.dims != 2) return cudaErrorInvalidValue;
-    if (prec == 0)
-        rho2d_kernel<double><<<g1, 256, 0, s>>>(sd, target, sign);
-    else
-        rho2d_kernel<float><<<g1, 256, 0, s>>>(sd, target, sign);
+    PIC_DISPATCH(prec, (rho2d_kernel<T><<<g1, 256, 0, s>>>(sd, target, sign)));
     if (mode == 1) {
         const int g2 = (int)((nc + 255) / 256);
-        if (prec == 0)
-            gauss2d_kernel<double><<<g2, 256, 0, s>>>(sd);
-        else
-            gauss2d_kernel<float><<<g2, 256, 0, s>>>(sd);
+        PIC_DISPATCH(prec, (gauss2d_kernel<T><<<g2, 256, 0, s>>>(sd)));
     }
     return cudaGetLastError();
 }

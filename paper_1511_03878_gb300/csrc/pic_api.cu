@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "df64.cuh"
 #include "pic.h"
 #include "pic_internal.h"
 
@@ -82,7 +83,8 @@ namespace {
 const char* validate(const pic_config* c) {
     if (!c) return "null config";
     if (c->dims != 2 && c->dims != 3) return "dims must be 2 or 3";
-    if (c->precision != PIC_FP64 && c->precision != PIC_FP32) return "bad precision";
+    if (c->precision != PIC_FP64 && c->precision != PIC_FP32 && c->precision != PIC_DF64)
+        return "bad precision";
     if (c->window != 0 && c->window != 1) return "bad window flag";
     if (c->mapping != PIC_MAP_QUEUE && c->mapping != PIC_MAP_STATIC) return "bad mapping";
     for (int a = 0; a < c->dims; a++) {
@@ -160,7 +162,7 @@ Layout plan(const pic_config* c, char* base) {
         }
         S.f_eps = (float)S.c_eps;
     }
-    const long long es = c->precision == PIC_FP64 ? 8 : 4;
+    const long long es = c->precision == PIC_FP32 ? 4 : 8;
     const long long cap = c->capacity;
     S.capacity = cap;
 
@@ -176,7 +178,7 @@ Layout plan(const pic_config* c, char* base) {
     for (int g = 0; g < 2; g++) S.J[g] = cv.take<double>(3 * S.fstride);
     S.rho = cv.take<double>(S.ncell);
     S.rho_bg = cv.take<double>(S.ncell);
-    S.cell = c->precision == PIC_FP32 ? cv.take<int>(cap) : nullptr;
+    S.cell = c->precision != PIC_FP64 ? cv.take<int>(cap) : nullptr;
     for (int a = 0; a < 3; a++) S.xi[a] = a < c->dims ? cv.take<char>(cap * es) : nullptr;
     for (int a = 0; a < 3; a++) S.u[a] = cv.take<char>(cap * es);
     S.w = cv.take<char>(cap * es);
@@ -191,12 +193,12 @@ Layout plan(const pic_config* c, char* base) {
     S.mcap = cv.take<int>(S.npatch);
     S.mcount = cv.take<int>(S.npatch);
     S.mtotal = cap / 4 + (long long)kMailboxMin * S.npatch;
-    S.mcell = c->precision == PIC_FP32 ? cv.take<int>(S.mtotal) : nullptr;
+    S.mcell = c->precision != PIC_FP64 ? cv.take<int>(S.mtotal) : nullptr;
     for (int a = 0; a < 3; a++) S.mxi[a] = a < c->dims ? cv.take<char>(S.mtotal * es) : nullptr;
     for (int a = 0; a < 3; a++) S.mu[a] = cv.take<char>(S.mtotal * es);
     S.mw = cv.take<char>(S.mtotal * es);
     S.mid = cv.take<int>(S.mtotal);
-    S.acell = c->precision == PIC_FP32 ? cv.take<int>(cap) : nullptr;
+    S.acell = c->precision != PIC_FP64 ? cv.take<int>(cap) : nullptr;
     for (int a = 0; a < 3; a++) S.axi[a] = a < c->dims ? cv.take<char>(cap * es) : nullptr;
     for (int a = 0; a < 3; a++) S.au[a] = cv.take<char>(cap * es);
     S.aw = cv.take<char>(cap * es);
@@ -242,9 +244,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool encode_field_maps(const SimDev& S, CUtensorMap out[2]) {
     auto fn = encode_fn();
     if (!fn) return false;
-    const cuuint64_t es = S.prec == PIC_FP64 ? 8 : 4;
+    // 8-byte elements (FP64 or a double-word pair) move as FLOAT64; TMA copies bytes
+    const cuuint64_t es = S.prec == PIC_FP32 ? 4 : 8;
     const CUtensorMapDataType dt =
-        S.prec == PIC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        S.prec == PIC_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     for (int g = 0; g < 2; g++) {
         CUresult r;
         if (S.dims == 2) {
@@ -407,6 +410,36 @@ void unpad_field(const SimDev& S, const T* src, double* dst) {
             }
 }
 
+size_t elem_size(int prec) { return prec == PIC_FP32 ? 4 : 8; }
+
+// one real number of the sim's precision in a host buffer
+void store_real(int prec, void* a, long long i, double v) {
+    if (prec == PIC_FP64)
+        static_cast<double*>(a)[i] = v;
+    else if (prec == PIC_FP32)
+        static_cast<float*>(a)[i] = (float)v;
+    else
+        static_cast<df64*>(a)[i] = df64(v);
+}
+
+double load_real(int prec, const void* a, long long i) {
+    if (prec == PIC_FP64) return static_cast<const double*>(a)[i];
+    if (prec == PIC_FP32) return (double)static_cast<const float*>(a)[i];
+    return (double)static_cast<const df64*>(a)[i];
+}
+
+// offset in [0, 1) of a cell-based position, kept below 1 after rounding
+double cell_offset(int prec, double f) {
+    if (prec == PIC_FP32) {
+        float g = (float)f;
+        if (g >= 1.0f) g = std::nextafter(1.0f, 0.0f);
+        return g;
+    }
+    df64 g(f);
+    if (g.hi >= 1.0f || (g.hi == 1.0f && g.lo >= 0.0f)) return (double)std::nextafter(1.0f, 0.0f);
+    return f;
+}
+
 uint64_t mix64(uint64_t x) {
     x += 0x9E3779B97F4A7C15ULL;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -540,14 +573,14 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
             }
         }
     }
-    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const size_t es = elem_size(S.prec);
     const long long cap = S.capacity;
     std::vector<char> hx[3], hu[3], hw;
     std::vector<int> hid(cap, -1), hcell;
     for (int a = 0; a < dims; a++) hx[a].assign(cap * es, 0);
     for (int a = 0; a < 3; a++) hu[a].assign(cap * es, 0);
     hw.assign(cap * es, 0);
-    if (S.prec == PIC_FP32) hcell.assign(cap, 0);
+    if (S.prec != PIC_FP64) hcell.assign(cap, 0);
     {
         long long k = 0;
         for (int p = 0; p < S.npatch; p++) {
@@ -558,21 +591,18 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
                 if (S.prec == PIC_FP64) {
                     for (int a = 0; a < dims; a++)
                         reinterpret_cast<double*>(hx[a].data())[dst] = xi[src * 3 + a];
-                    for (int a = 0; a < 3; a++) reinterpret_cast<double*>(hu[a].data())[dst] = uu[a];
-                    reinterpret_cast<double*>(hw.data())[dst] = w[src];
                 } else {
                     int cellv = 0;
                     for (int a = 0; a < dims; a++) {
                         const int i = ip[src * 3 + a];
-                        float f = (float)(xi[src * 3 + a] - (double)i);
-                        if (f >= 1.0f) f = std::nextafter(1.0f, 0.0f);  // stay in the cell
-                        reinterpret_cast<float*>(hx[a].data())[dst] = f;
+                        const double f = cell_offset(S.prec, xi[src * 3 + a] - (double)i);
+                        store_real(S.prec, hx[a].data(), dst, f);
                         cellv |= i << (dims == 2 ? 16 * a : 11 * a);
                     }
                     hcell[dst] = cellv;
-                    for (int a = 0; a < 3; a++) reinterpret_cast<float*>(hu[a].data())[dst] = (float)uu[a];
-                    reinterpret_cast<float*>(hw.data())[dst] = (float)w[src];
                 }
+                for (int a = 0; a < 3; a++) store_real(S.prec, hu[a].data(), dst, uu[a]);
+                store_real(S.prec, hw.data(), dst, w[src]);
                 hid[dst] = id[src];
             }
         }
@@ -583,7 +613,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         CK(cudaMemcpyAsync(S.u[a], hu[a].data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy u");
     CK(cudaMemcpyAsync(S.w, hw.data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy w");
     CK(cudaMemcpyAsync(S.id, hid.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream), "copy id");
-    if (S.prec == PIC_FP32)
+    if (S.prec != PIC_FP64)
         CK(cudaMemcpyAsync(S.cell, hcell.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream),
            "copy cell");
     const size_t pb = S.npatch * sizeof(int);
@@ -609,20 +639,22 @@ extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], cons
         if (!E[a] || !B[a]) return fail(&s->err, PIC_ERR_INVALID, "null field array");
     const SimDev& S = s->L.S;
     CK(cudaStreamSynchronize(s->stream), "sync before fields");
-    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const size_t es = elem_size(S.prec);
     const long long fs = S.fstride;
     std::vector<char> hF(6 * fs * es, 0), hH(3 * fs * es, 0);
-    for (int a = 0; a < 3; a++) {
-        if (S.prec == PIC_FP64) {
-            pad_field(S, E[a], reinterpret_cast<double*>(hF.data()) + a * fs);
-            pad_field(S, B[a], reinterpret_cast<double*>(hF.data()) + (3 + a) * fs);
-            pad_field(S, B[a], reinterpret_cast<double*>(hH.data()) + a * fs);
-        } else {
-            pad_field(S, E[a], reinterpret_cast<float*>(hF.data()) + a * fs);
-            pad_field(S, B[a], reinterpret_cast<float*>(hF.data()) + (3 + a) * fs);
-            pad_field(S, B[a], reinterpret_cast<float*>(hH.data()) + a * fs);
+    auto pad_all = [&](auto* F, auto* H) {
+        for (int a = 0; a < 3; a++) {
+            pad_field(S, E[a], F + a * fs);
+            pad_field(S, B[a], F + (3 + a) * fs);
+            pad_field(S, B[a], H + a * fs);
         }
-    }
+    };
+    if (S.prec == PIC_FP64)
+        pad_all(reinterpret_cast<double*>(hF.data()), reinterpret_cast<double*>(hH.data()));
+    else if (S.prec == PIC_FP32)
+        pad_all(reinterpret_cast<float*>(hF.data()), reinterpret_cast<float*>(hH.data()));
+    else
+        pad_all(reinterpret_cast<df64*>(hF.data()), reinterpret_cast<df64*>(hH.data()));
     CK(cudaMemcpyAsync(S.F[0], hF.data(), hF.size(), cudaMemcpyHostToDevice, s->stream), "copy F");
     CK(cudaMemcpyAsync(S.H[0], hH.data(), hH.size(), cudaMemcpyHostToDevice, s->stream), "copy H");
     CK(cudaMemsetAsync(S.F[1], 0, hF.size(), s->stream), "zero F1");
@@ -669,7 +701,7 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
     pic_status rc = pic_sync(s);
     if (rc != PIC_OK) return rc;
     const SimDev& S = s->L.S;
-    const size_t es = S.prec == PIC_FP64 ? 8 : 4;
+    const size_t es = elem_size(S.prec);
     auto need = [&](size_t b) { return out && out_bytes >= b; };
     StepState st{};
     CK(cudaMemcpy(&st, S.st, sizeof(st), cudaMemcpyDeviceToHost), "read state");
@@ -715,18 +747,20 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
             CK(cudaMemcpy(hJ.data(), S.J[1 - g], hJ.size() * sizeof(double), cudaMemcpyDeviceToHost),
                "read J");
             std::vector<double> all(12 * nc);
-            for (int a = 0; a < 3; a++) {
-                if (S.prec == PIC_FP64) {
-                    unpad_field(S, reinterpret_cast<double*>(hF.data()) + a * fs, &all[(0 + a) * nc]);
-                    unpad_field(S, reinterpret_cast<double*>(hH.data()) + a * fs, &all[(3 + a) * nc]);
-                    unpad_field(S, reinterpret_cast<double*>(hF.data()) + (3 + a) * fs, &all[(6 + a) * nc]);
-                } else {
-                    unpad_field(S, reinterpret_cast<float*>(hF.data()) + a * fs, &all[(0 + a) * nc]);
-                    unpad_field(S, reinterpret_cast<float*>(hH.data()) + a * fs, &all[(3 + a) * nc]);
-                    unpad_field(S, reinterpret_cast<float*>(hF.data()) + (3 + a) * fs, &all[(6 + a) * nc]);
+            auto unpad_all = [&](const auto* F, const auto* H) {
+                for (int a = 0; a < 3; a++) {
+                    unpad_field(S, F + a * fs, &all[(0 + a) * nc]);
+                    unpad_field(S, H + a * fs, &all[(3 + a) * nc]);
+                    unpad_field(S, F + (3 + a) * fs, &all[(6 + a) * nc]);
                 }
-                unpad_field(S, hJ.data() + a * fs, &all[(9 + a) * nc]);
-            }
+            };
+            if (S.prec == PIC_FP64)
+                unpad_all(reinterpret_cast<double*>(hF.data()), reinterpret_cast<double*>(hH.data()));
+            else if (S.prec == PIC_FP32)
+                unpad_all(reinterpret_cast<float*>(hF.data()), reinterpret_cast<float*>(hH.data()));
+            else
+                unpad_all(reinterpret_cast<df64*>(hF.data()), reinterpret_cast<df64*>(hH.data()));
+            for (int a = 0; a < 3; a++) unpad_field(S, hJ.data() + a * fs, &all[(9 + a) * nc]);
             if (kind == PIC_DIAG_FIELDS) {
                 memcpy(out, all.data(), b);
             } else {
@@ -781,7 +815,7 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
             }
             CK(cudaMemcpy(hw.data(), S.w, cap * es, cudaMemcpyDeviceToHost), "read w");
             CK(cudaMemcpy(hid.data(), S.id, cap * sizeof(int), cudaMemcpyDeviceToHost), "read id");
-            if (S.prec == PIC_FP32) {
+            if (S.prec != PIC_FP64) {
                 hcell.resize(cap);
                 CK(cudaMemcpy(hcell.data(), S.cell, cap * sizeof(int), cudaMemcpyDeviceToHost), "read cell");
             }
@@ -808,14 +842,11 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
                         const int sh = S.dims == 2 ? 16 * a : 11 * a;
                         const int mask = S.dims == 2 ? 0xFFFF : (a < 2 ? 0x7FF : 0x3FF);
                         const int i = (hcell[sl] >> sh) & mask;
-                        pos[a] = ((double)i + (double)reinterpret_cast<float*>(hx[a].data())[sl]) * S.d[a];
+                        pos[a] = ((double)i + load_real(S.prec, hx[a].data(), sl)) * S.d[a];
                     }
                 }
-                for (int a = 0; a < 3; a++)
-                    uu[a] = S.prec == PIC_FP64 ? reinterpret_cast<double*>(hu[a].data())[sl]
-                                               : (double)reinterpret_cast<float*>(hu[a].data())[sl];
-                ww = S.prec == PIC_FP64 ? reinterpret_cast<double*>(hw.data())[sl]
-                                        : (double)reinterpret_cast<float*>(hw.data())[sl];
+                for (int a = 0; a < 3; a++) uu[a] = load_real(S.prec, hu[a].data(), sl);
+                ww = load_real(S.prec, hw.data(), sl);
                 o[0 * n + k] = pos[0];
                 o[1 * n + k] = pos[1];
                 o[2 * n + k] = pos[2];

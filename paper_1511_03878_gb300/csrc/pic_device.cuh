@@ -3,9 +3,26 @@
 #pragma once
 #include <stdint.h>
 
+#include "df64.cuh"
 #include "pic_internal.h"
 
 namespace pic {
+
+// Runs `body` with T bound to the storage/arithmetic type of a precision code:
+// 0 = FP64, 1 = FP32, 2 = double-word FP32 pairs.
+#define PIC_DISPATCH(prec, body)           \
+    do {                                   \
+        if ((prec) == 0) {                 \
+            using T = double;              \
+            body;                          \
+        } else if ((prec) == 1) {          \
+            using T = float;               \
+            body;                          \
+        } else {                           \
+            using T = ::pic::df64;         \
+            body;                          \
+        }                                  \
+    } while (0)
 
 // ---------------------------------------------------------------- PTX wrappers
 
@@ -120,6 +137,10 @@ struct JType<double> {
 template <>
 struct JType<float> {
     using type = float;
+};
+template <>
+struct JType<df64> {
+    using type = double;  // FP64 shared-memory current, FP64 global current
 };
 
 // Per-axis Esirkepov data on the five nodes node0-2 .. node0+2.

@@ -91,12 +91,16 @@ def small_lwfa(**kw):
 
 # ------------------------------------------------------------------ FP64 parity
 
+PREC64 = {"fp64": 0, "df64": 2}  # IEEE FP64 and double-word FP32 pairs: same tolerances
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (20, 1e-9)])
-def test_thermal_fp64_full_size(binding, steps, tol):
+def test_thermal_fp64_full_size(binding, steps, tol, prec):
     """configs[0]-sized thermal plasma: 128x128, 16 ppc (262 144 particles)."""
     w = inputs.thermal2d(seed=1511)
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim = binding.Sim(w["params"], precision=PREC64[prec], capacity=2 * n)
     sim.load(w)
     sim.step(steps)
     o = make_oracle(w)
@@ -105,12 +109,13 @@ def test_thermal_fp64_full_size(binding, steps, tol):
     assert sim.step_info() == (steps, 0)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (20, 1e-9)])
-def test_lwfa_small_fp64_window(binding, steps, tol):
+def test_lwfa_small_fp64_window(binding, steps, tol, prec):
     """Moving window + injection + laser: shrunk LWFA (256x128, same dx, dy, dt)."""
     w = small_lwfa()
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=8 * n + 100000)
+    sim = binding.Sim(w["params"], precision=PREC64[prec], capacity=8 * n + 100000)
     sim.load(w)
     sim.step(steps)
     o = make_oracle(w)
@@ -135,11 +140,12 @@ def test_patch_size_and_chunking_variants(binding):
         sim.close()
 
 
-def test_gauss_law_on_gpu(binding):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_gauss_law_on_gpu(binding, prec):
     """Esirkepov + Yee keep div E - rho at round-off on the GPU too (100 steps)."""
     w = inputs.thermal2d(nx=64, ny=64, d=0.1, uth=0.1, seed=8, patch=(16, 16))
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim = binding.Sim(w["params"], precision=PREC64[prec], capacity=2 * n)
     sim.load(w)
     g0 = sim.gauss()
     assert np.abs(g0).max() < 1e-12
@@ -328,11 +334,12 @@ def compare3d(sim, o, params, tol):
     return errs
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (10, 1e-9)])
-def test_stress3d_fp64(binding, steps, tol):
+def test_stress3d_fp64(binding, steps, tol, prec):
     w = stress3d_small()
     n = len(w["particles"]["x"])
-    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=2 * n)
+    sim = binding.Sim(w["params"], precision=PREC64[prec], capacity=2 * n)
     sim.load(w)
     sim.step(steps)
     o = make_oracle(w)
