@@ -111,15 +111,84 @@ __device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
 __device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
 
-// 1/sqrt(x): FP32 estimate, two Newton steps y <- y + y (1 - x y^2) / 2 in double-word
+// exact scaling by a power of two
+__device__ __forceinline__ df64 scale2(df64 x, float p2) {
+    return df64(__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2));
+}
+
+// 1/sqrt(x): FP32 estimate (within 2 ulp), one Newton step y <- y + y (1 - x y^2) / 2
+// in double-word: relative error about 2^-43
 __device__ __forceinline__ df64 rsqrt_t(df64 x) {
     df64 y(rsqrtf(x.hi));
-    for (int i = 0; i < 2; i++) {
-        const df64 e = df64(1.0f) - x * (y * y);
-        y = y + mul_f(y, 0.5f) * e;
-    }
-    return y;
+    const df64 e = df64(1.0f) - x * (y * y);
+    return y + scale2(y, 0.5f) * e;
 }
+
+// Compensated dot product accumulator (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), Dot2 extended to double-word inputs):
+// exact hi*hi products by TwoProd, cross terms by FMA, the running sum by TwoSum with
+// the errors gathered in FP32; absolute error about 2^-48 sum |a_i b_i|.
+struct Dot2 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(df64 a, df64 b) {
+        const float p = __fmul_rn(a.hi, b.hi);
+        float e = __fmaf_rn(a.hi, b.hi, -p);
+        e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+        const df64 t = two_sum(s, p);
+        s = t.hi;
+        c = __fadd_rn(c, __fadd_rn(t.lo, e));
+    }
+    __device__ __forceinline__ df64 result() const { return fast_two_sum(s, c); }
+};
+
+// Fixed-point conversions for an int64 current accumulator: v * 2^k rounded to an
+// integer with integer operations only (|v| 2^k < 2^62), and back.
+__device__ __forceinline__ long long f32_to_fixed(float x) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e == 0) return 0;  // zero or below the quantum
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150;
+    long long r;
+    if (sh >= 0)
+        r = m << sh;
+    else if (sh > -25)
+        r = (m + (1LL << (-sh - 1))) >> (-sh);
+    else
+        r = 0;
+    return (b >> 31) ? -r : r;
+}
+
+__device__ __forceinline__ long long to_fixed(df64 v, float scale) {
+    return f32_to_fixed(__fmul_rn(v.hi, scale)) + f32_to_fixed(__fmul_rn(v.lo, scale));
+}
+
+// int64 -> double times 2^-k built with integer operations (exact below 2^53,
+// rounded to nearest above)
+__device__ __forceinline__ double fixed_to_f64(long long q, int k) {
+    if (q == 0) return 0.0;
+    const unsigned long long sign = q < 0 ? 0x8000000000000000ULL : 0ULL;
+    const unsigned long long a = q < 0 ? (unsigned long long)(-q) : (unsigned long long)q;
+    int msb = 63 - __clzll((long long)a);
+    unsigned long long mant;
+    if (msb > 52) {
+        const int sh = msb - 52;
+        mant = (a + (1ULL << (sh - 1))) >> sh;
+        if (mant >> 53) {  // the rounding carried into a new leading bit
+            mant >>= 1;
+            msb += 1;
+        }
+    } else {
+        mant = a << (52 - msb);
+    }
+    const long long ex = (long long)msb - k + 1023;
+    if (ex <= 0) return 0.0;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+}
+
+// 2^e as an FP32 number (-126 <= e <= 127)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 #endif  // __CUDACC__
 

@@ -30,7 +30,8 @@ __device__ __forceinline__ T gather9(const T* __restrict__ f, int BX, const T Sx
 // sums have two non-zero entries, 6 + 6 + 9 shared-memory atomics.
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
-                                               const T S0y[3], T dx1, T dy1, T qx, T qy, T qz) {
+                                               const T S0y[3], T dx1, T dy1, T qx, T qy, T qz,
+                                               float jsc) {
     T S1x[3], S1y[3], a[3], b[3], wy[3], wz[3], wx[3];
     shape3(dx1, S1x);
     shape3(dy1, S1y);
@@ -47,23 +48,25 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
     // stencil nodes 1..3 start one tile cell in: pointers already at (1, 1)
 #pragma unroll
     for (int l = 0; l < 3; l++) {
-        atomicAdd(jx + l * JX + 0, JT(ax1 * wy[l]));
-        atomicAdd(jx + l * JX + 1, JT(ax2 * wy[l]));
+        jatomic(jx + l * JX + 0, jval<JT>(ax1 * wy[l], jsc));
+        jatomic(jx + l * JX + 1, jval<JT>(ax2 * wy[l], jsc));
 #pragma unroll
-        for (int k = 0; k < 3; k++) atomicAdd(jz + l * JX + k, JT(qz * (S0x[k] * wy[l] + a[k] * wz[l])));
+        for (int k = 0; k < 3; k++)
+            jatomic(jz + l * JX + k, jval<JT>(qz * (S0x[k] * wy[l] + a[k] * wz[l]), jsc));
     }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        atomicAdd(jy + 0 * JX + k, JT(by1 * wx[k]));
-        atomicAdd(jy + 1 * JX + k, JT(by2 * wx[k]));
+        jatomic(jy + 0 * JX + k, jval<JT>(by1 * wx[k], jsc));
+        jatomic(jy + 1 * JX + k, jval<JT>(by2 * wx[k], jsc));
     }
 }
 
-// General 2D Esirkepov deposition on the five-node stencil (any shift in {-1,0,1}).
+// General 2D Esirkepov deposition on the five-node stencil with per-node predicates
+// (used for FP64 and FP32, where it needs fewer registers than the four-node window).
 template <typename T, typename JT>
-__device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
-                                                  const T S0y[3], T dx1, T dy1, int sx, int sy,
-                                                  T qx, T qy, T qz) {
+__device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
+                                                   const T S0y[3], T dx1, T dy1, int sx, int sy,
+                                                   T qx, T qy, T qz, float jsc) {
     Axis5<T> ax, ay;
     esirkepov_axis(S0x, dx1, sx, ax);
     esirkepov_axis(S0y, dy1, sy, ay);
@@ -78,14 +81,14 @@ __device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX
             for (int kk = 0; kk < 4; kk++) {
                 if (kk >= ax.lo && kk < ax.hi) {
                     acc += ax.DS[kk] * wy;
-                    atomicAdd(jx + r + kk, JT(qx * acc));
+                    jatomic(jx + r + kk, jval<JT>(qx * acc, jsc));
                 }
             }
 #pragma unroll
             for (int kk = 0; kk < 5; kk++) {
                 if (kk >= ax.lo && kk <= ax.hi) {
                     const T wzk = ax.S0[kk] * wy + ax.DS[kk] * wz;
-                    atomicAdd(jz + r + kk, JT(qz * wzk));
+                    jatomic(jz + r + kk, jval<JT>(qz * wzk, jsc));
                 }
             }
         }
@@ -99,11 +102,70 @@ __device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX
             for (int l = 0; l < 4; l++) {
                 if (l >= ay.lo && l < ay.hi) {
                     acc += ay.DS[l] * wx;
-                    atomicAdd(jy + l * JX + kk, JT(qy * acc));
+                    jatomic(jy + l * JX + kk, jval<JT>(qy * acc, jsc));
                 }
             }
         }
     }
+}
+
+// General 2D Esirkepov deposition (any shift in {-1, 0, 1}) on a fixed four-node
+// window per axis: running sums of three entries along each axis, 12 + 12 + 16
+// atomics, no per-node predicates. `jx/jy/jz` point at stencil node (0, 0) of the
+// five-node numbering (old node - 2 on both axes).
+template <typename T, typename JT>
+__device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
+                                                  const T S0y[3], T dx1, T dy1, int sx, int sy,
+                                                  T qx, T qy, T qz, float jsc) {
+    Axis4<T> ax, ay;
+    esirkepov_axis4(S0x, dx1, sx, ax);
+    esirkepov_axis4(S0y, dy1, sy, ay);
+    const int o = ay.start * JX + ax.start;
+    T wy[4], wz[4], wx[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        wy[k] = ay.S0[k] + T(0.5) * ay.DS[k];
+        wz[k] = T(0.5) * ay.S0[k] + ay.DS[k] * T(1.0 / 3.0);
+        wx[k] = ax.S0[k] + T(0.5) * ax.DS[k];
+    }
+    const T cx1 = qx * ax.DS[0], cx2 = qx * (ax.DS[0] + ax.DS[1]),
+            cx3 = qx * (ax.DS[0] + ax.DS[1] + ax.DS[2]);
+    const T cy1 = qy * ay.DS[0], cy2 = qy * (ay.DS[0] + ay.DS[1]),
+            cy3 = qy * (ay.DS[0] + ay.DS[1] + ay.DS[2]);
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+        JT* rx = jx + o + l * JX;
+        jatomic(rx + 0, jval<JT>(cx1 * wy[l], jsc));
+        jatomic(rx + 1, jval<JT>(cx2 * wy[l], jsc));
+        jatomic(rx + 2, jval<JT>(cx3 * wy[l], jsc));
+        JT* rz = jz + o + l * JX;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            jatomic(rz + k, jval<JT>(qz * (ax.S0[k] * wy[l] + ax.DS[k] * wz[l]), jsc));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        JT* cy = jy + o + k;
+        jatomic(cy + 0 * JX, jval<JT>(cy1 * wx[k], jsc));
+        jatomic(cy + 1 * JX, jval<JT>(cy2 * wx[k], jsc));
+        jatomic(cy + 2 * JX, jval<JT>(cy3 * wx[k], jsc));
+    }
+}
+
+// double-word gather: compensated dot products (rows along x, then along y)
+__device__ __forceinline__ df64 gather9(const df64* __restrict__ f, int BX, const df64 Sx[3],
+                                       const df64 Sy[3]) {
+    Dot2 outer;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const df64* row = f + b * BX;
+        Dot2 inner;
+        inner.add(Sx[0], row[0]);
+        inner.add(Sx[1], row[1]);
+        inner.add(Sx[2], row[2]);
+        outer.add(Sy[b], inner.result());
+    }
+    return outer.result();
 }
 
 template <typename T>
@@ -188,6 +250,9 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 
 
         const int base = S.pbase[patch] + item.z;
         const int cnt = item.w;
+        // fixed-point exponent of the double-word current tile for this item
+        const int jk = item_fixed_exp(cnt, S.cmax_exp);
+        const float jsc = pow2f(jk);
         const T* W = reinterpret_cast<const T*>(S.w);
         T* U0 = reinterpret_cast<T*>(S.u[0]);
         T* U1 = reinterpret_cast<T*>(S.u[1]);
@@ -329,10 +394,14 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 
                 if (fast) {
                     const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
                     deposit2d_fast<T, JT>(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX, Sxp,
-                                          Syp, dxp1, dyp1, qx, qy, qz);
+                                          Syp, dxp1, dyp1, qx, qy, qz, jsc);
                 } else {
-                    deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0, JX,
-                                             Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
+                    if constexpr (std::is_same<T, df64>::value)
+                        deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
+                                                 JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz, jsc);
+                    else
+                        deposit2d_general5<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
+                                                  JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz, jsc);
                 }
 
                 // ---- D. boundaries and destination patch
@@ -436,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 
                 gi = wrapi(gi, nx);
             }
             gj = wrapi(gj, ny);
-            atomicAdd(Jg + comp * fs + (long long)(gj + kGuard) * NX + (gi + kGuard), widen_f32(v));
+            atomicAdd(Jg + comp * fs + (long long)(gj + kGuard) * NX + (gi + kGuard), jflush(v, jk));
         }
     }
 }

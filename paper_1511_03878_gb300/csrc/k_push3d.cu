@@ -27,6 +27,26 @@ __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, 
     return r;
 }
 
+__device__ __forceinline__ df64 gather27(const df64* __restrict__ f, int BX, int BXY,
+                                        const df64 Sx[3], const df64 Sy[3], const df64 Sz[3]) {
+    Dot2 outer;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        Dot2 plane;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const df64* row = f + c * BXY + b * BX;
+            Dot2 inner;
+            inner.add(Sx[0], row[0]);
+            inner.add(Sx[1], row[1]);
+            inner.add(Sx[2], row[2]);
+            plane.add(Sy[b], inner.result());
+        }
+        outer.add(Sz[c], plane.result());
+    }
+    return outer.result();
+}
+
 template <typename T>
 __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T f[3],
                                           double xi[3]) {
@@ -53,7 +73,7 @@ __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T
 // `jt[a]` point at stencil node (1, 1, 1) of component a.
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY, const T S0[3][3],
-                                               const T d1[3], const T q[3]) {
+                                               const T d1[3], const T q[3], float jsc) {
     T DS[3][3], wa[3][3], wb[3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -77,8 +97,8 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
             for (int kb = 0; kb < 3; kb++) {
                 const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
                 JT* p = jt[a] + kb * st[b] + kc * st[c];
-                atomicAdd(p, JT(c1 * A));
-                atomicAdd(p + st[a], JT(c2 * A));
+                jatomic(p, jval<JT>(c1 * A, jsc));
+                jatomic(p + st[a], jval<JT>(c2 * A, jsc));
             }
     }
 }
@@ -162,6 +182,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
         }
         const int base = S.pbase[patch] + item.z;
         const int cnt = item.w;
+        const int jk = item_fixed_exp(cnt, S.cmax_exp);
+        const float jsc = pow2f(jk);
         T* U0 = reinterpret_cast<T*>(S.u[0]);
         T* U1 = reinterpret_cast<T*>(S.u[1]);
         T* U2 = reinterpret_cast<T*>(S.u[2]);
@@ -280,46 +302,40 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         const T q3[3] = {cj[0] * w, cj[1] * w, cj[2] * w};
                         const int t111 = (tp[2] + 1) * JXY + (tp[1] + 1) * JX + (tp[0] + 1);
                         for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
-                        deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3);
+                        deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3, jsc);
                     } else {
-                    Axis5<T> ax[3];
+                    // four-node window per axis (any shift): 3 x 16 x 3 atomics
+                    Axis4<T> ax[3];
 #pragma unroll
-                    for (int a = 0; a < 3; a++) esirkepov_axis(Sp[a], dp1[a], sh[a], ax[a]);
-                    // (S0 + DS/2) and (S0/2 + DS/3) per axis
-                    T wa[3][5], wb[3][5];
+                    for (int a = 0; a < 3; a++) esirkepov_axis4(Sp[a], dp1[a], sh[a], ax[a]);
+                    T wa[3][4], wb[3][4];
 #pragma unroll
                     for (int a = 0; a < 3; a++)
 #pragma unroll
-                        for (int q = 0; q < 5; q++) {
+                        for (int q = 0; q < 4; q++) {
                             wa[a][q] = ax[a].S0[q] + T(0.5) * ax[a].DS[q];
                             wb[a][q] = T(0.5) * ax[a].S0[q] + ax[a].DS[q] * T(1.0 / 3.0);
                         }
-                    // tile origin p0 - 2: stencil index 0 at tile index tp[a]
+                    const int st3[3] = {1, JX, JXY};
+                    const int o3 = (tp[2] + ax[2].start) * JXY + (tp[1] + ax[1].start) * JX +
+                                   (tp[0] + ax[0].start);
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const int b = (a + 1) % 3, c = (a + 2) % 3;
                         const T qa = cj[a] * w;
-                        JT* jt = Jt + a * jvol;
+                        const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
+                                c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
+                        JT* jt = Jt + a * jvol + o3;
 #pragma unroll
-                        for (int kc = 0; kc < 5; kc++) {
-                            if (kc < ax[c].lo || kc > ax[c].hi) continue;
+                        for (int kc = 0; kc < 4; kc++)
 #pragma unroll
-                            for (int kb = 0; kb < 5; kb++) {
-                                if (kb < ax[b].lo || kb > ax[b].hi) continue;
+                            for (int kb = 0; kb < 4; kb++) {
                                 const T A = wa[b][kb] * ax[c].S0[kc] + wb[b][kb] * ax[c].DS[kc];
-                                T acc = T(0);
-#pragma unroll
-                                for (int ka = 0; ka < 4; ka++) {
-                                    if (ka < ax[a].lo || ka >= ax[a].hi) continue;
-                                    acc += ax[a].DS[ka] * A;
-                                    int t[3];
-                                    t[a] = tp[a] + ka;
-                                    t[b] = tp[b] + kb;
-                                    t[c] = tp[c] + kc;
-                                    atomicAdd(jt + t[2] * JXY + t[1] * JX + t[0], JT(qa * acc));
-                                }
+                                JT* p = jt + kb * st3[b] + kc * st3[c];
+                                jatomic(p, jval<JT>(c1 * A, jsc));
+                                jatomic(p + st3[a], jval<JT>(c2 * A, jsc));
+                                jatomic(p + 2 * st3[a], jval<JT>(c3 * A, jsc));
                             }
-                        }
                     }
                     }
                 }
@@ -404,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
             const int gk = wrapi(p0[2] - 2 + tz, n[2]);
             atomicAdd(Jg + comp * fs + ((long long)(gk + kGuard) * S.NY + (gj + kGuard)) * S.NX +
                           (gi + kGuard),
-                      widen_f32(v));
+                      jflush(v, jk));
         }
     }
 }

@@ -624,6 +624,25 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     CK(cudaMemcpyAsync(S.mcap, mcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mcap");
     CK(cudaMemsetAsync(S.hcount, 0, pb, s->stream), "zero hcount");
     CK(cudaMemsetAsync(S.mcount, 0, pb, s->stream), "zero mcount");
+    // bound of one particle's current contribution (|cumulative DS| <= 1, |v| < 1):
+    // sets the double-word fixed-point current scale
+    {
+        double wmax = 0.0;
+        for (long long p = 0; p < n; p++) wmax = std::max(wmax, std::fabs(w[p]));
+        if (S.window) {
+            const double dV = S.d[0] * S.d[1] * (S.dims == 3 ? S.d[2] : 1.0);
+            wmax = std::max(wmax, std::fabs(S.n0) * dV /
+                                      ((double)S.ippc[0] * S.ippc[1] * (S.dims == 3 ? S.ippc[2] : 1)));
+        }
+        double cj = 0.0;
+        for (int a = 0; a < 3; a++) cj = std::max(cj, std::fabs(S.c_j[a]));
+        const double cmax = cj * wmax;
+        int e = -100;
+        if (cmax > 0) std::frexp(cmax, &e);  // cmax < 2^e
+        s->L.S.cmax_exp = e;
+        CK(cudaMemcpyAsync(s->L.ds, &s->L.S, sizeof(SimDev), cudaMemcpyHostToDevice, s->stream),
+           "copy descriptor");
+    }
     StepState st{};
     st.next_id = (long long)maxid + 1;
     CK(cudaMemcpyAsync(S.st, &st, sizeof(st), cudaMemcpyHostToDevice, s->stream), "copy state");

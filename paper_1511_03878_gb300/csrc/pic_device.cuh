@@ -104,6 +104,14 @@ __device__ __forceinline__ void shape3(T delta, T S[3]) {
     S[2] = T(0.5) * b * b;
 }
 
+// double-word shapes with exact halving
+__device__ __forceinline__ void shape3(df64 delta, df64 S[3]) {
+    const df64 a = df64(0.5f) - delta, b = df64(0.5f) + delta;
+    S[0] = scale2(a * a, 0.5f);
+    S[1] = df64(0.75f) - delta * delta;
+    S[2] = scale2(b * b, 0.5f);
+}
+
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 
@@ -140,8 +148,16 @@ struct JType<float> {
 };
 template <>
 struct JType<df64> {
-    using type = double;  // FP64 shared-memory current, FP64 global current
+    using type = long long;  // int64 fixed-point shared-memory current (see jval)
 };
+
+// fixed-point exponent of an item of `count` particles: a tile entry sums at most
+// `count` contributions, each below 2^cmax_exp, and must stay below 2^62
+__device__ __forceinline__ int item_fixed_exp(int count, int cmax_exp) {
+    const int lg = 32 - __clz(count > 1 ? count - 1 : 1);  // ceil(log2(count))
+    int k = 61 - cmax_exp - lg;
+    return k < -120 ? -120 : (k > 120 ? 120 : k);
+}
 
 // Per-axis Esirkepov data on the five nodes node0-2 .. node0+2.
 template <typename T>
@@ -184,6 +200,59 @@ __device__ __forceinline__ double widen_f32(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen_f32(double d) { return d; }
+
+// current-tile value and atomic for each accumulator type; `scale` = 2^k of the
+// fixed-point tile (unused for the floating-point tiles)
+template <typename JT, typename T>
+__device__ __forceinline__ JT jval(T v, float scale) {
+    (void)scale;
+    return JT(v);
+}
+template <>
+__device__ __forceinline__ long long jval<long long, df64>(df64 v, float scale) {
+    return to_fixed(v, scale);
+}
+__device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void jatomic(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void jatomic(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+// tile entry -> FP64 for the global current (k: the fixed-point exponent)
+__device__ __forceinline__ double jflush(float v, int) { return widen_f32(v); }
+__device__ __forceinline__ double jflush(double v, int) { return v; }
+__device__ __forceinline__ double jflush(long long v, int k) { return fixed_to_f64(v, k); }
+
+
+// Esirkepov data of one axis on a four-node window that always holds both the old
+// and the new support: the window starts one node before min(old node, new node).
+// S0/DS on the window nodes 0..3 (DS sums to zero); `start` = window start minus
+// (old node - 2), i.e. 0 or 1 in the five-node numbering.
+template <typename T>
+struct Axis4 {
+    T S0[4], DS[4];
+    int start;
+};
+
+template <typename T>
+__device__ __forceinline__ void esirkepov_axis4(const T s0[3], T delta1, int shift, Axis4<T>& a) {
+    T s1[3];
+    shape3(delta1, s1);
+    const bool m = shift < 0, p = shift > 0;
+    // old support at window nodes (m ? 1..3 : 0..2), new at (p ? 1..3 : 0..2)
+    a.S0[0] = m ? T(0) : s0[0];
+    a.S0[1] = m ? s0[0] : s0[1];
+    a.S0[2] = m ? s0[1] : s0[2];
+    a.S0[3] = m ? s0[2] : T(0);
+    const T n0 = p ? T(0) : s1[0];
+    const T n1 = p ? s1[0] : s1[1];
+    const T n2 = p ? s1[1] : s1[2];
+    const T n3 = p ? s1[2] : T(0);
+    a.DS[0] = n0 - a.S0[0];
+    a.DS[1] = n1 - a.S0[1];
+    a.DS[2] = n2 - a.S0[2];
+    a.DS[3] = n3 - a.S0[3];
+    a.start = m ? 0 : 1;
+}
 
 // ---------------------------------------------------------------- scans
 
