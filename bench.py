@@ -68,7 +68,9 @@ def parse():
                     help="other precisions timed in the same run (comma list, or none)")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=512)
-    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0, help="queue chunk when not autotuned")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="measure patch and chunk candidates before the timed run")
     ap.add_argument("--workload", default="lwfa", choices=["lwfa", "stress3d", "thermal", "serve"])
     ap.add_argument("--requests", type=int, default=256, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
@@ -192,7 +194,7 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def run_gpu(args, w, precision, K, W, world, clocks=None):
+def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
     """Returns timing + roofline of one precision on this rank's GPU."""
     import torch
 
@@ -202,7 +204,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
-    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=args.chunk, mapping=mapping)
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping)
     sim.load(w)
     stream = sim.stream
     sim.step(W)
@@ -262,7 +264,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None):
     return out
 
 
-def run_e2e(args, w, precision, K):
+def run_e2e(args, w, precision, K, chunk=0):
     """Same metric through the public C ABI with host buffers: load (H2D), K steps,
     read back the energy and the axis wake field (D2H), all inside the timed region."""
     import torch
@@ -272,7 +274,7 @@ def run_e2e(args, w, precision, K):
     prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
-    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=args.chunk)
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.load(w)
@@ -385,22 +387,43 @@ def reference_arm(args):
 
 
 def config_dict(args, precision):
+    """The workload (the same for both arms); the launch layout is reported apart."""
     if args.workload == "stress3d":
         base = {"workload": "stress3d-256x128x128-lognormal1.5", "grid": [256, 128, 128],
-                "dx": 0.1, "particles": args.total, "patch": [8, 8, 8]}
+                "dx": 0.1, "particles": args.total}
     elif args.workload == "thermal":
         base = {"workload": "thermal2d-128x128-ppc16", "grid": [128, 128], "dx": 0.1,
-                "particles_per_cell": 16, "patch": [32, 32]}
+                "particles_per_cell": 16}
     else:
         base = {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
                 "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
-                "patch": [32, 32], "laser_a0": 4.0}
+                "laser_a0": 4.0}
     return {**base, "precision": precision,
-            "mapping": ("persistent work queue (largest chunk first)" if args.mapping == "queue"
-                        else "static: one CTA per patch"),
-            "chunk": args.chunk or 2048,
             "l2": "inputs larger than L2 (particles + fields > 129 MB), no flush",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def launch_layout(args, w, precision):
+    """Patch and chunk for one precision: measured by the autotuner, or the workload's
+    patch and --chunk. Returns the workload with that patch, the chunk and a record."""
+    from paper_1511_03878_gb300 import autotune, binding
+
+    prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
+    mapping = ("persistent work queue (largest chunk first)" if args.mapping == "queue"
+               else "static: one CTA per patch")
+    if args.autotune == "off" or args.mapping == "static":
+        chunk = args.chunk
+        rec = {"patch": list(w["params"]["patch"]), "chunk": chunk or autotune.DEFAULT_CHUNK,
+               "mapping": mapping, "autotuned": False}
+        return w, chunk, rec
+    n = len(w["particles"]["x"])
+    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
+    c = autotune.tune(w, prec, capacity=cap, warmup=3, steps=20)
+    rec = {"patch": list(c.patch), "chunk": c.chunk, "mapping": mapping, "autotuned": True,
+           "autotune": {"candidates": len(c.table), "seconds": round(c.seconds, 1),
+                        "ns_per_push": {f"{'x'.join(map(str, p))}/{k}": round(v, 4)
+                                        for p, k, v in c.table}}}
+    return dict(w, params=dict(w["params"], patch=c.patch)), c.chunk, rec
 
 
 def serve_arm(args):
@@ -479,13 +502,16 @@ def main():
 
     w = workload(args.nx, args.ny, args.workload, args.total)
     clocks = ClockSampler(local)
-    main_run = run_gpu(args, w, args.precision, args.steps, args.warmup, world, clocks)
     others = [] if args.no_variant or args.variants == "none" else [
         v for v in args.variants.split(",") if v and v != args.precision]
-    variants = {v: run_gpu(args, w, v, args.steps, args.warmup, world) for v in others}
+    layouts = {v: launch_layout(args, w, v) for v in [args.precision] + others}
+    wm, chunk_m, _ = layouts[args.precision]
+    main_run = run_gpu(args, wm, args.precision, args.steps, args.warmup, world, clocks, chunk_m)
+    variants = {v: run_gpu(args, layouts[v][0], v, args.steps, args.warmup, world,
+                           chunk=layouts[v][1]) for v in others}
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, w, args.precision, args.steps)
+        e2e = run_e2e(args, wm, args.precision, args.steps, chunk_m)
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         rate, steps, n = oracle_rate(w, args.cpu_seconds)
@@ -503,6 +529,7 @@ def main():
         "dtype": DTYPE[args.precision],
         "data": "synthetic (seeded LWFA-shaped initial condition, no dataset)",
         "config": config_dict(args, args.precision),
+        "launch": layouts[args.precision][2],
         "roofline": main_run["roofline"],
         "cpu_baseline": cpu,
         "e2e": ({"value": world * e2e["value"], "unit": UNIT,
@@ -518,7 +545,8 @@ def main():
         line["variants"] = {v: {
             "value": world * r["pushes"] / (r["ms"] * 1e-3),
             "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
-            "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v]} for v, r in variants.items()}
+            "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v],
+            "launch": layouts[v][2]} for v, r in variants.items()}
     print(json.dumps(line), flush=True)
 
 

@@ -76,7 +76,10 @@ typedef struct {
     int n[3];           /* cells per axis; n[2] = 1 in 2D */
     double d[3];        /* cell sizes */
     double dt;          /* time step; must be below every d[a] */
-    int patch[3];       /* cells per patch per axis: a multiple of 4, dividing n[a] */
+    int patch[3];       /* cells per patch per axis: a multiple of 4 in [4, 64], dividing
+                           n[a]; the patch's field and current tiles must fit in the 227 KB
+                           of shared memory of one CTA (pic_required_bytes returns 0 when
+                           they do not) */
     int precision;      /* PIC_FP64, PIC_FP32 or PIC_DF64 (see above) */
     int window;         /* 0: all axes periodic.  1: x is a moving window at c
                            (fields zero outside, particles absorbed), y/z periodic */
@@ -86,7 +89,8 @@ typedef struct {
     int inject_ppc[3];  /* window only: injected lattice per cell per axis */
     double q, m;        /* species charge and mass (electrons: -1, 1) */
     long long capacity; /* particle slots in the arena (>= the largest count held) */
-    int chunk;          /* work-queue chunk size in particles (0 = 2048) */
+    int chunk;          /* work-queue chunk size in particles (0 = 2048); the Python
+                           autotuner measures patch and chunk candidates on a workload */
     int mapping;        /* PIC_MAP_QUEUE or PIC_MAP_STATIC */
 } pic_config;
 

@@ -534,6 +534,12 @@ static int occupancy_2d(int P0, int P1, int* smem_bytes) {
     return blocks;
 }
 
+int push2d_smem(int prec, int P0, int P1) {
+    int sb = 0;
+    PIC_DISPATCH(prec, (sb = smem_bytes_2d<T>(P0, P1)));
+    return sb;
+}
+
 int push_occupancy(int dims, int prec, int P0, int P1, int P2, int* smem_bytes) {
     if (dims == 3) return push3d_occupancy(prec, P0, P1, P2, smem_bytes);
     if (dims != 2) return 0;

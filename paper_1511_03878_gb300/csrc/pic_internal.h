@@ -127,6 +127,7 @@ cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, i
                        cudaStream_t s);
 cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cudaStream_t s);
 // 3D variants
+int push2d_smem(int prec, int P0, int P1);
 int push3d_smem(int prec, int P0, int P1, int P2);
 int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes);
 cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0, int P1, int P2,

@@ -1,0 +1,62 @@
+"""The autotuner on the GPU: it measures every candidate it is given, returns one of
+them, and its choice gives the same simulation as the default layout."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1511_03878_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1511_03878_gb300 import binding as b, build
+
+    build.build()
+    return b
+
+
+def normwise(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_tune_and_parity_of_choice(binding):
+    from paper_1511_03878_gb300 import autotune
+
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, ppc_side=4, uth=0.1, seed=41, patch=(32, 32))
+    n = len(w["particles"]["x"])
+    patches = [(8, 8), (16, 16), (32, 32)]
+    chunks = (256, 1024, 2048)
+    c = autotune.tune(w, binding.PIC_FP64, capacity=2 * n, patches=patches, chunks=chunks,
+                      warmup=2, steps=4)
+    assert len(c.table) == len(patches) + len(chunks) - 1
+    assert c.patch in patches and c.chunk in chunks
+    assert all(math.isfinite(r[2]) and r[2] > 0 for r in c.table)
+    assert (c.patch, c.chunk, c.ns_per_push) in c.table
+    assert c.table[0][0] == (32, 32)  # the workload's own patch is the first incumbent
+    # the winner is within the replacement margin of the fastest candidate
+    assert c.ns_per_push * (1 - 0.02) <= min(r[2] for r in c.table)
+    # cached: the same call returns the same object without measuring
+    assert autotune.tune(w, binding.PIC_FP64, capacity=2 * n, patches=patches,
+                         chunks=chunks) is c
+
+    out = []
+    for patch, chunk in ((c.patch, c.chunk), ((32, 32), 0)):
+        s = binding.Sim(dict(w["params"], patch=patch), precision=binding.PIC_FP64,
+                        capacity=2 * n, chunk=chunk)
+        s.load(w)
+        s.step(5)
+        out.append((s.fields(), s.particles()))
+        s.close()
+    (f1, q1), (f2, q2) = out
+    assert np.array_equal(q1["id"], q2["id"])
+    for k in ("Ex", "Ey", "Bz", "Jx", "Jy", "Jz"):
+        assert normwise(f1[k], f2[k]) < 1e-11, k
+    for k in ("x", "y", "ux", "uy", "uz"):
+        assert normwise(q1[k], q2[k]) < 1e-11, k
