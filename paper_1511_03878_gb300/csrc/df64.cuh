@@ -72,6 +72,12 @@ __device__ __forceinline__ df64 operator+(df64 x, df64 y) {
     return fast_two_sum(v.hi, w);
 }
 __device__ __forceinline__ df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
+
+// DWPlusFP: x + b for an FP32 number b (relative error below 2u^2)
+__device__ __forceinline__ df64 add_f(df64 x, float b) {
+    const df64 s = two_sum(x.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(x.lo, s.lo));
+}
 __device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
 
 // DWTimesDW with FMA (relative error below 4u^2)
@@ -120,7 +126,7 @@ __device__ __forceinline__ df64 scale2(df64 x, float p2) {
 // in double-word: relative error about 2^-43
 __device__ __forceinline__ df64 rsqrt_t(df64 x) {
     df64 y(rsqrtf(x.hi));
-    const df64 e = df64(1.0f) - x * (y * y);
+    const df64 e = add_f(-(x * (y * y)), 1.0f);
     return y + scale2(y, 0.5f) * e;
 }
 
@@ -130,6 +136,14 @@ __device__ __forceinline__ df64 rsqrt_t(df64 x) {
 // the errors gathered in FP32; absolute error about 2^-48 sum |a_i b_i|.
 struct Dot2 {
     float s = 0.0f, c = 0.0f;
+    Dot2() = default;
+    __device__ __forceinline__ explicit Dot2(float s0) : s(s0), c(0.0f) {}
+    // a plain double-word term
+    __device__ __forceinline__ void add(df64 v) {
+        const df64 t = two_sum(s, v.hi);
+        s = t.hi;
+        c = __fadd_rn(c, __fadd_rn(t.lo, v.lo));
+    }
     __device__ __forceinline__ void add(df64 a, df64 b) {
         const float p = __fmul_rn(a.hi, b.hi);
         float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -161,6 +175,16 @@ __device__ __forceinline__ long long f32_to_fixed(float x) {
 
 __device__ __forceinline__ long long to_fixed(df64 v, float scale) {
     return f32_to_fixed(__fmul_rn(v.hi, scale)) + f32_to_fixed(__fmul_rn(v.lo, scale));
+}
+
+// fixed-point value of a product a*b, a already carrying the fixed-point factor 2^k:
+// the rounded product of the high parts and its exact error (FMA) plus the cross terms,
+// each FP32 part converted on its own (no renormalisation needed before an integer sum)
+__device__ __forceinline__ long long fixed_prod(df64 a, df64 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float t = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.lo)));
+    const float e = __fadd_rn(__fmaf_rn(a.hi, b.hi, -p), t);
+    return f32_to_fixed(p) + f32_to_fixed(e);
 }
 
 // int64 -> double times 2^-k built with integer operations (exact below 2^53,

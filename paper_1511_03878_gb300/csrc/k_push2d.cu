@@ -30,8 +30,7 @@ __device__ __forceinline__ T gather9(const T* __restrict__ f, int BX, const T Sx
 // sums have two non-zero entries, 6 + 6 + 9 shared-memory atomics.
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
-                                               const T S0y[3], T dx1, T dy1, T qx, T qy, T qz,
-                                               float jsc) {
+                                               const T S0y[3], T dx1, T dy1, T qx, T qy, T qz) {
     T S1x[3], S1y[3], a[3], b[3], wy[3], wz[3], wx[3];
     shape3(dx1, S1x);
     shape3(dy1, S1y);
@@ -46,18 +45,42 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
     const T ax1 = qx * a[0], ax2 = qx * (a[0] + a[1]);
     const T by1 = qy * b[0], by2 = qy * (b[0] + b[1]);
     // stencil nodes 1..3 start one tile cell in: pointers already at (1, 1)
+    if constexpr (std::is_same<T, df64>::value) {
+        // double-word: rolled loops (the unrolled body overflows the instruction
+        // cache); per-row weights rotate through registers instead of being indexed
+        T wy0 = wy[0], wy1 = wy[1], wy2 = wy[2], wz0 = wz[0], wz1 = wz[1], wz2 = wz[2];
+#pragma unroll 1
+        for (int l = 0; l < 3; l++) {
+            JT* r = jx + l * JX;
+            jatomic(r + 0, jprod<JT>(ax1, wy0));
+            jatomic(r + 1, jprod<JT>(ax2, wy0));
+            JT* rz = jz + l * JX;
 #pragma unroll
-    for (int l = 0; l < 3; l++) {
-        jatomic(jx + l * JX + 0, jval<JT>(ax1 * wy[l], jsc));
-        jatomic(jx + l * JX + 1, jval<JT>(ax2 * wy[l], jsc));
+            for (int k = 0; k < 3; k++)
+                jatomic(rz + k, jprod<JT>(qz, S0x[k] * wy0 + a[k] * wz0));
+            wy0 = wy1, wy1 = wy2, wz0 = wz1, wz1 = wz2;
+        }
+        T wx0 = wx[0], wx1 = wx[1], wx2 = wx[2];
+#pragma unroll 1
+        for (int k = 0; k < 3; k++) {
+            jatomic(jy + k, jprod<JT>(by1, wx0));
+            jatomic(jy + JX + k, jprod<JT>(by2, wx0));
+            wx0 = wx1, wx1 = wx2;
+        }
+    } else {
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-            jatomic(jz + l * JX + k, jval<JT>(qz * (S0x[k] * wy[l] + a[k] * wz[l]), jsc));
-    }
+        for (int l = 0; l < 3; l++) {
+            jatomic(jx + l * JX + 0, jprod<JT>(ax1, wy[l]));
+            jatomic(jx + l * JX + 1, jprod<JT>(ax2, wy[l]));
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        jatomic(jy + 0 * JX + k, jval<JT>(by1 * wx[k], jsc));
-        jatomic(jy + 1 * JX + k, jval<JT>(by2 * wx[k], jsc));
+            for (int k = 0; k < 3; k++)
+                jatomic(jz + l * JX + k, jprod<JT>(qz, S0x[k] * wy[l] + a[k] * wz[l]));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            jatomic(jy + 0 * JX + k, jprod<JT>(by1, wx[k]));
+            jatomic(jy + 1 * JX + k, jprod<JT>(by2, wx[k]));
+        }
     }
 }
 
@@ -66,7 +89,7 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
                                                    const T S0y[3], T dx1, T dy1, int sx, int sy,
-                                                   T qx, T qy, T qz, float jsc) {
+                                                   T qx, T qy, T qz) {
     Axis5<T> ax, ay;
     esirkepov_axis(S0x, dx1, sx, ax);
     esirkepov_axis(S0y, dy1, sy, ay);
@@ -81,14 +104,14 @@ __device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int J
             for (int kk = 0; kk < 4; kk++) {
                 if (kk >= ax.lo && kk < ax.hi) {
                     acc += ax.DS[kk] * wy;
-                    jatomic(jx + r + kk, jval<JT>(qx * acc, jsc));
+                    jatomic(jx + r + kk, jprod<JT>(qx, acc));
                 }
             }
 #pragma unroll
             for (int kk = 0; kk < 5; kk++) {
                 if (kk >= ax.lo && kk <= ax.hi) {
                     const T wzk = ax.S0[kk] * wy + ax.DS[kk] * wz;
-                    jatomic(jz + r + kk, jval<JT>(qz * wzk, jsc));
+                    jatomic(jz + r + kk, jprod<JT>(qz, wzk));
                 }
             }
         }
@@ -102,7 +125,7 @@ __device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int J
             for (int l = 0; l < 4; l++) {
                 if (l >= ay.lo && l < ay.hi) {
                     acc += ay.DS[l] * wx;
-                    jatomic(jy + l * JX + kk, jval<JT>(qy * acc, jsc));
+                    jatomic(jy + l * JX + kk, jprod<JT>(qy, acc));
                 }
             }
         }
@@ -116,7 +139,7 @@ __device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int J
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
                                                   const T S0y[3], T dx1, T dy1, int sx, int sy,
-                                                  T qx, T qy, T qz, float jsc) {
+                                                  T qx, T qy, T qz) {
     Axis4<T> ax, ay;
     esirkepov_axis4(S0x, dx1, sx, ax);
     esirkepov_axis4(S0y, dy1, sy, ay);
@@ -132,23 +155,29 @@ __device__ __forceinline__ void deposit2d_general(JT* jx, JT* jy, JT* jz, int JX
             cx3 = qx * (ax.DS[0] + ax.DS[1] + ax.DS[2]);
     const T cy1 = qy * ay.DS[0], cy2 = qy * (ay.DS[0] + ay.DS[1]),
             cy3 = qy * (ay.DS[0] + ay.DS[1] + ay.DS[2]);
-#pragma unroll
+    // rolled loops, the per-row (per-column) weights rotating through registers
+    T wy0 = wy[0], wy1 = wy[1], wy2 = wy[2], wy3 = wy[3];
+    T wz0 = wz[0], wz1 = wz[1], wz2 = wz[2], wz3 = wz[3];
+#pragma unroll 1
     for (int l = 0; l < 4; l++) {
         JT* rx = jx + o + l * JX;
-        jatomic(rx + 0, jval<JT>(cx1 * wy[l], jsc));
-        jatomic(rx + 1, jval<JT>(cx2 * wy[l], jsc));
-        jatomic(rx + 2, jval<JT>(cx3 * wy[l], jsc));
+        jatomic(rx + 0, jprod<JT>(cx1, wy0));
+        jatomic(rx + 1, jprod<JT>(cx2, wy0));
+        jatomic(rx + 2, jprod<JT>(cx3, wy0));
         JT* rz = jz + o + l * JX;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            jatomic(rz + k, jval<JT>(qz * (ax.S0[k] * wy[l] + ax.DS[k] * wz[l]), jsc));
+            jatomic(rz + k, jprod<JT>(qz, ax.S0[k] * wy0 + ax.DS[k] * wz0));
+        wy0 = wy1, wy1 = wy2, wy2 = wy3, wz0 = wz1, wz1 = wz2, wz2 = wz3;
     }
-#pragma unroll
+    T wx0 = wx[0], wx1 = wx[1], wx2 = wx[2], wx3 = wx[3];
+#pragma unroll 1
     for (int k = 0; k < 4; k++) {
         JT* cy = jy + o + k;
-        jatomic(cy + 0 * JX, jval<JT>(cy1 * wx[k], jsc));
-        jatomic(cy + 1 * JX, jval<JT>(cy2 * wx[k], jsc));
-        jatomic(cy + 2 * JX, jval<JT>(cy3 * wx[k], jsc));
+        jatomic(cy + 0 * JX, jprod<JT>(cy1, wx0));
+        jatomic(cy + 1 * JX, jprod<JT>(cy2, wx0));
+        jatomic(cy + 2 * JX, jprod<JT>(cy3, wx0));
+        wx0 = wx1, wx1 = wx2, wx2 = wx3;
     }
 }
 
@@ -168,8 +197,29 @@ __device__ __forceinline__ df64 gather9(const df64* __restrict__ f, int BX, cons
     return outer.result();
 }
 
+// CTA shape of the particle kernel per precision: threads per CTA and the CTAs per SM
+// the register budget is sized for
+#ifndef PIC_DF64_THREADS
+#define PIC_DF64_THREADS 256
+#endif
+#ifndef PIC_DF64_MINB
+#define PIC_DF64_MINB 2
+#endif
 template <typename T>
-__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 2)
+struct Push2DShape {
+    static constexpr int threads = kThreads, min_blocks = 2;
+};
+template <>
+struct Push2DShape<float> {
+    static constexpr int threads = kThreads, min_blocks = 3;
+};
+template <>
+struct Push2DShape<df64> {
+    static constexpr int threads = PIC_DF64_THREADS, min_blocks = PIC_DF64_MINB;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_blocks)
     push2d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -332,12 +382,32 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 
                 shape3(dyd, Syd);
                 const int pl = BX * BY;
                 T E[3], B[3];
-                E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
-                E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
-                B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
-                B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+                if constexpr (std::is_same<T, df64>::value) {
+                    // one rolled loop over Ex Ey Ez Bx By Bz: x primal for Ey Ez Bx,
+                    // y primal for Ex Ez By; results rotate through six registers
+                    T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
+#pragma unroll 1
+                    for (int c = 0; c < 6; c++) {
+                        const bool xp = c >= 1 && c <= 3, yp = (c & 1) == 0;
+                        T sx[3], sy[3];
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            sx[k] = xp ? Sxp[k] : Sxd[k];
+                            sy[k] = yp ? Syp[k] : Syd[k];
+                        }
+                        const T g = gather9(Ft + c * pl + (yp ? typ : tyd) * BX + (xp ? txp : txd),
+                                            BX, sx, sy);
+                        r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5, r5 = g;
+                    }
+                    E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
+                } else {
+                    E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
+                    E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                    E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
+                    B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                    B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
+                    B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+                }
 
                 const T ig = boris(eps, E, B, u);
                 const T vx = u[0] * ig, vy = u[1] * ig;
@@ -389,19 +459,20 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 3 : 
             bool leave = false;
             int dest = patch;
             if (ok) {
-                const T qx = cjx * w, qy = cjy * w, qz = cjz * w * vz;
+                const T qx = jscale(cjx * w, jsc), qy = jscale(cjy * w, jsc),
+                        qz = jscale(cjz * w * vz, jsc);
                 const int t0 = typ * JX + txp;  // stencil node 0 of both axes
                 if (fast) {
                     const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
                     deposit2d_fast<T, JT>(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX, Sxp,
-                                          Syp, dxp1, dyp1, qx, qy, qz, jsc);
+                                          Syp, dxp1, dyp1, qx, qy, qz);
                 } else {
                     if constexpr (std::is_same<T, df64>::value)
                         deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
-                                                 JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz, jsc);
+                                                 JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
                     else
                         deposit2d_general5<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
-                                                  JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz, jsc);
+                                                  JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
                 }
 
                 // ---- D. boundaries and destination patch
@@ -528,7 +599,8 @@ static int occupancy_2d(int P0, int P1, int* smem_bytes) {
         return 0;
     cudaFuncSetAttribute(push2d_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<T>, kThreads, sb) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push2d_kernel<T>,
+                                                      Push2DShape<T>::threads, sb) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -553,7 +625,7 @@ cudaError_t launch_push(const BatchDev* bd_dev, int dims, int prec, int mapping,
     if (dims == 3) return launch_push3d(bd_dev, prec, mapping, P0, P1, P2, grid, s);
     if (dims != 2) return cudaErrorInvalidValue;
     const int static_map = mapping == 1;
-    PIC_DISPATCH(prec, (push2d_kernel<T><<<grid, kThreads, smem_bytes_2d<T>(P0, P1), s>>>(
+    PIC_DISPATCH(prec, (push2d_kernel<T><<<grid, Push2DShape<T>::threads, smem_bytes_2d<T>(P0, P1), s>>>(
                             bd_dev, static_map)));
     return cudaGetLastError();
 }

@@ -73,7 +73,7 @@ __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T
 // `jt[a]` point at stencil node (1, 1, 1) of component a.
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY, const T S0[3][3],
-                                               const T d1[3], const T q[3], float jsc) {
+                                               const T d1[3], const T q[3]) {
     T DS[3][3], wa[3][3], wb[3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -97,8 +97,8 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
             for (int kb = 0; kb < 3; kb++) {
                 const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
                 JT* p = jt[a] + kb * st[b] + kc * st[c];
-                jatomic(p, jval<JT>(c1 * A, jsc));
-                jatomic(p + st[a], jval<JT>(c2 * A, jsc));
+                jatomic(p, jprod<JT>(c1, A));
+                jatomic(p + st[a], jprod<JT>(c2, A));
             }
     }
 }
@@ -299,10 +299,11 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         for (int q = 0; q < 3; q++) Sp[a][q] = S0keep[a][q];
                     if (fast) {
                         JT* jt3[3];
-                        const T q3[3] = {cj[0] * w, cj[1] * w, cj[2] * w};
+                        const T q3[3] = {jscale(cj[0] * w, jsc), jscale(cj[1] * w, jsc),
+                                         jscale(cj[2] * w, jsc)};
                         const int t111 = (tp[2] + 1) * JXY + (tp[1] + 1) * JX + (tp[0] + 1);
                         for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
-                        deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3, jsc);
+                        deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3);
                     } else {
                     // four-node window per axis (any shift): 3 x 16 x 3 atomics
                     Axis4<T> ax[3];
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const int b = (a + 1) % 3, c = (a + 2) % 3;
-                        const T qa = cj[a] * w;
+                        const T qa = jscale(cj[a] * w, jsc);
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;
@@ -332,9 +333,9 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                             for (int kb = 0; kb < 4; kb++) {
                                 const T A = wa[b][kb] * ax[c].S0[kc] + wb[b][kb] * ax[c].DS[kc];
                                 JT* p = jt + kb * st3[b] + kc * st3[c];
-                                jatomic(p, jval<JT>(c1 * A, jsc));
-                                jatomic(p + st3[a], jval<JT>(c2 * A, jsc));
-                                jatomic(p + 2 * st3[a], jval<JT>(c3 * A, jsc));
+                                jatomic(p, jprod<JT>(c1, A));
+                                jatomic(p + st3[a], jprod<JT>(c2, A));
+                                jatomic(p + 2 * st3[a], jprod<JT>(c3, A));
                             }
                     }
                     }

@@ -104,11 +104,11 @@ __device__ __forceinline__ void shape3(T delta, T S[3]) {
     S[2] = T(0.5) * b * b;
 }
 
-// double-word shapes with exact halving
+// double-word shapes: FP32 constants added with DWPlusFP, exact halving
 __device__ __forceinline__ void shape3(df64 delta, df64 S[3]) {
-    const df64 a = df64(0.5f) - delta, b = df64(0.5f) + delta;
+    const df64 a = add_f(-delta, 0.5f), b = add_f(delta, 0.5f);
     S[0] = scale2(a * a, 0.5f);
-    S[1] = df64(0.75f) - delta * delta;
+    S[1] = add_f(-(delta * delta), 0.75f);
     S[2] = scale2(b * b, 0.5f);
 }
 
@@ -134,6 +134,36 @@ __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     u[1] = um1 + eps * E[1];
     u[2] = um2 + eps * E[2];
     return rsqrt_t(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// Double-word Boris: the same steps, with every sum of products (|u|^2, |t|^2 and the
+// two cross-product updates) as one compensated dot product.
+__device__ __forceinline__ df64 boris(df64 eps, const df64 E[3], const df64 B[3], df64 u[3]) {
+    const df64 h0 = eps * E[0], h1 = eps * E[1], h2 = eps * E[2];
+    const df64 um0 = u[0] + h0, um1 = u[1] + h1, um2 = u[2] + h2;
+    Dot2 g(1.0f);
+    g.add(um0, um0), g.add(um1, um1), g.add(um2, um2);
+    const df64 ei = eps * rsqrt_t(g.result());
+    const df64 t0 = ei * B[0], t1 = ei * B[1], t2 = ei * B[2];
+    Dot2 n(1.0f);
+    n.add(t0, t0), n.add(t1, t1), n.add(t2, t2);
+    const df64 f = df64(2.0f) / n.result();
+    const df64 s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    Dot2 a0, a1, a2;
+    a0.add(um0), a0.add(um1, t2), a0.add(-um2, t1);
+    a1.add(um1), a1.add(um2, t0), a1.add(-um0, t2);
+    a2.add(um2), a2.add(um0, t1), a2.add(-um1, t0);
+    const df64 up0 = a0.result(), up1 = a1.result(), up2 = a2.result();
+    Dot2 b0, b1, b2;
+    b0.add(um0), b0.add(up1, s2), b0.add(-up2, s1);
+    b1.add(um1), b1.add(up2, s0), b1.add(-up0, s2);
+    b2.add(um2), b2.add(up0, s1), b2.add(-up1, s0);
+    u[0] = b0.result() + h0;
+    u[1] = b1.result() + h1;
+    u[2] = b2.result() + h2;
+    Dot2 k(1.0f);
+    k.add(u[0], u[0]), k.add(u[1], u[1]), k.add(u[2], u[2]);
+    return rsqrt_t(k.result());
 }
 
 template <typename T>
@@ -211,6 +241,25 @@ __device__ __forceinline__ JT jval(T v, float scale) {
 template <>
 __device__ __forceinline__ long long jval<long long, df64>(df64 v, float scale) {
     return to_fixed(v, scale);
+}
+// tile value of the product a*b; for the fixed-point tile `a` already carries the factor
+// 2^k (see jscale)
+template <typename JT, typename T>
+__device__ __forceinline__ JT jprod(T a, T b) {
+    return JT(a * b);
+}
+template <>
+__device__ __forceinline__ long long jprod<long long, df64>(df64 a, df64 b) {
+    return fixed_prod(a, b);
+}
+// charge factor scaled for the tile: exact power-of-two scaling for the fixed-point tile
+template <typename T>
+__device__ __forceinline__ T jscale(T q, float) {
+    return q;
+}
+template <>
+__device__ __forceinline__ df64 jscale<df64>(df64 q, float scale) {
+    return scale2(q, scale);
 }
 __device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(double* p, double v) { atomicAdd(p, v); }
