@@ -165,14 +165,23 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus):
+    """One process per GPU (replicas of the whole simulation, no data-path collective):
+    NCCL between GPUs, gloo when there is no GPU (host-side tests of this logic)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if n_gpus > 1 else "gloo")
+        dist.init_process_group("nccl" if n_gpus > 1 and torch.cuda.is_available() else "gloo")
     return rank, world, local
+
+
+def _on_gpu_backend():
+    import torch.distributed as dist
+
+    return dist.get_backend() == "nccl"
 
 
 def barrier(world):
@@ -180,18 +189,38 @@ def barrier(world):
         import torch
         import torch.distributed as dist
 
-        dist.barrier(device_ids=[torch.cuda.current_device()])
+        if _on_gpu_backend():
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _on_gpu_backend() else "cpu")
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+
+    return _reduce(x, world, dist.ReduceOp.MAX if world > 1 else None)
+
+
+def sum_over_ranks(x, world):
+    import torch.distributed as dist
+
+    return _reduce(x, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def job_value(pushes_all_ranks, ms_slowest):
+    """Whole-job throughput: the pushes of all ranks over the slowest rank's time."""
+    return pushes_all_ranks / (ms_slowest * 1e-3)
 
 
 def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
@@ -229,6 +258,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
     repacks = sim.repacks()
     ms = max_over_ranks(ms, world)
     pushes = K * 0.5 * (n0 + n1)
+    pushes_all = sum_over_ranks(pushes, world)
     # per-kernel CUDA-event pass (same kernels, same launch shapes) for the roofline
     prof = sim.profile(K)
     push_ms = prof["push"] / K
@@ -256,7 +286,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
         if precision == "df64":
             fl = FLOPS_PER_PUSH_2D if dims == 2 else FLOPS_PER_PUSH_3D
             roof["fp64_equivalent_tflops"] = fl * n_push / (push_ms * 1e-3) / 1e12
-    out = dict(ms=ms, pushes=pushes, n=n_push, profile={k: v / K for k, v in prof.items()},
+    out = dict(ms=ms, pushes=pushes, pushes_all=pushes_all, n=n_push, profile={k: v / K for k, v in prof.items()},
                roofline=roof, push_ms=push_ms, repacks=repacks)
     sim.close()
     del sim
@@ -264,7 +294,7 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
     return out
 
 
-def run_e2e(args, w, precision, K, chunk=0):
+def run_e2e(args, w, precision, K, chunk=0, world=1):
     """Same metric through the public C ABI with host buffers: load (H2D), K steps,
     read back the energy and the axis wake field (D2H), all inside the timed region."""
     import torch
@@ -276,6 +306,7 @@ def run_e2e(args, w, precision, K, chunk=0):
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk)
     torch.cuda.synchronize()
+    barrier(world)
     t0 = time.perf_counter()
     sim.load(w)
     sim.step(K)
@@ -290,7 +321,9 @@ def run_e2e(args, w, precision, K, chunk=0):
     h2d = cap * per_slot + 9 * fstride * es + 5 * sim.npatch * 4
     d2h = e.nbytes + ax.nbytes
     sim.close()
-    return dict(value=n * K / (t1 - t0), h2d=h2d / K, d2h=d2h / K, seconds=t1 - t0)
+    seconds = max_over_ranks(t1 - t0, world)
+    return dict(value=job_value(sum_over_ranks(n * K, world), 1e3 * seconds), h2d=h2d / K,
+                d2h=d2h / K, seconds=seconds)
 
 
 def oracle_rate(w, seconds_budget, max_steps=50):
@@ -511,7 +544,7 @@ def main():
                            chunk=layouts[v][1]) for v in others}
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, wm, args.precision, args.steps, chunk_m)
+        e2e = run_e2e(args, wm, args.precision, args.steps, chunk_m, world)
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         rate, steps, n = oracle_rate(w, args.cpu_seconds)
@@ -520,7 +553,7 @@ def main():
                          f"LWFA window ({n} particles)"}
     if rank != 0:
         return
-    value = world * main_run["pushes"] / (main_run["ms"] * 1e-3)
+    value = job_value(main_run["pushes_all"], main_run["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -532,7 +565,7 @@ def main():
         "launch": layouts[args.precision][2],
         "roofline": main_run["roofline"],
         "cpu_baseline": cpu,
-        "e2e": ({"value": world * e2e["value"], "unit": UNIT,
+        "e2e": ({"value": e2e["value"], "unit": UNIT,
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
                 if e2e else None),
         "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -543,7 +576,7 @@ def main():
     }
     if variants:
         line["variants"] = {v: {
-            "value": world * r["pushes"] / (r["ms"] * 1e-3),
+            "value": job_value(r["pushes_all"], r["ms"]),
             "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
             "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v],
             "launch": layouts[v][2]} for v, r in variants.items()}
