@@ -69,8 +69,9 @@ def parse():
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=0, help="queue chunk when not autotuned")
-    ap.add_argument("--autotune", default="on", choices=["on", "off"],
-                    help="measure patch and chunk candidates before the timed run")
+    ap.add_argument("--autotune", default="cached", choices=["cached", "on", "off"],
+                    help="cached: the layouts recorded in the package's tuning table (measured "
+                         "there when missing); on: measure again; off: workload patch, --chunk")
     ap.add_argument("--workload", default="lwfa", choices=["lwfa", "stress3d", "thermal", "serve"])
     ap.add_argument("--requests", type=int, default=256, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
@@ -451,9 +452,11 @@ def launch_layout(args, w, precision):
         return w, chunk, rec
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
-    c = autotune.tune(w, prec, capacity=cap, warmup=3, steps=20)
+    cache = autotune.TUNING_TABLE if args.autotune == "cached" else None
+    c = autotune.tune(w, prec, capacity=cap, warmup=3, steps=20, cache_file=cache)
     rec = {"patch": list(c.patch), "chunk": c.chunk, "mapping": mapping, "autotuned": True,
-           "autotune": {"candidates": len(c.table), "seconds": round(c.seconds, 1),
+           "autotune": {"source": "tuning table" if cache else "measured in this run",
+                        "candidates": len(c.table), "seconds": round(c.seconds, 1),
                         "ns_per_push": {f"{'x'.join(map(str, p))}/{k}": round(v, 4)
                                         for p, k, v in c.table}}}
     return dict(w, params=dict(w["params"], patch=c.patch)), c.chunk, rec

@@ -31,6 +31,8 @@ import time
 from . import binding
 
 PATCH_SIDES = (8, 16, 32, 64)
+# layouts measured on a GB300 for the standard workloads, keyed like the in-process cache
+TUNING_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_layouts.json")
 CHUNKS = (512, 1024, 2048, 4096, 8192, 16384)
 DEFAULT_CHUNK = 2048
 
