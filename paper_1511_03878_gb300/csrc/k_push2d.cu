@@ -298,7 +298,8 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             cjx = T(S.c_j[0]), cjy = T(S.c_j[1]), cjz = T(S.c_j[2]);
         }
 
-        const int base = S.pbase[patch] + item.z;
+        const int pb = S.pbase[patch];
+        const int base = pb + item.z;
         const int cnt = item.w;
         // fixed-point exponent of the double-word current tile for this item
         const int jk = item_fixed_exp(cnt, S.cmax_exp);
@@ -528,17 +529,25 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 dest = -1;
             }
 
-            // ---- E. exchange hand-off (warp-aggregated counters)
-            const int hslot = warp_claim(S.hcount, patch, valid && leave, 0xffffffffu);
-            const bool send = valid && leave && dest >= 0;
-            const int mslot = warp_claim(S.mcount, send ? dest : 0, send, 0xffffffffu);
-            if (valid && leave) {
-                S.holes[S.pbase[patch] + hslot] = slot;
-                const int pid = S.id[slot];
+            // ---- E. exchange hand-off (warp-aggregated counters); the loads it needs are
+            // issued before the two claims so that all their latencies overlap
+            const bool lv = valid && leave;
+            const bool send = lv && dest >= 0;
+            if (__any_sync(0xffffffffu, lv)) {
+                int pid = 0, mcap = 0, mb = 0;
+                if (lv) pid = S.id[slot];
+                if (send) {
+                    mcap = S.mcap[dest];
+                    mb = S.mbase[dest];
+                }
+                const int2 cl = warp_claim2(S.hcount, patch, lv, S.mcount, send ? dest : 0, send);
+                const int hslot = cl.x, mslot = cl.y;
+              if (lv) {
+                S.holes[pb + hslot] = slot;
                 S.id[slot] = -1;
                 if (send) {
-                    if (mslot < S.mcap[dest]) {
-                        const int m = S.mbase[dest] + mslot;
+                    if (mslot < mcap) {
+                        const int m = mb + mslot;
                         if constexpr (is_f64<T>::value) {
                             reinterpret_cast<double*>(S.mxi[0])[m] = xi1;
                             reinterpret_cast<double*>(S.mxi[1])[m] = eta1;
@@ -556,6 +565,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                         atomicOr(S.status, ST_MAILBOX);
                     }
                 }
+              }
             }
         }
         __syncthreads();

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
             for (int a = 0; a < 3; a++) dtd[a] = T(S.c_dtd[a]), cj[a] = T(S.c_j[a]);
             eps = T(S.c_eps);
         }
-        const int base = S.pbase[patch] + item.z;
+        const int pb = S.pbase[patch];
+        const int base = pb + item.z;
         const int cnt = item.w;
         const int jk = item_fixed_exp(cnt, S.cmax_exp);
         const float jsc = pow2f(jk);
@@ -374,16 +375,24 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                 leave = true;
                 dest = -1;
             }
-            const int hslot = warp_claim(S.hcount, patch, valid && leave, 0xffffffffu);
-            const bool send = valid && leave && dest >= 0;
-            const int mslot = warp_claim(S.mcount, send ? dest : 0, send, 0xffffffffu);
-            if (valid && leave) {
-                S.holes[S.pbase[patch] + hslot] = slot;
-                const int pid = S.id[slot];
+            // loads first, then both claims, so that all their latencies overlap
+            const bool lv = valid && leave;
+            const bool send = lv && dest >= 0;
+            if (__any_sync(0xffffffffu, lv)) {
+                int pid = 0, mcap = 0, mb = 0;
+                if (lv) pid = S.id[slot];
+                if (send) {
+                    mcap = S.mcap[dest];
+                    mb = S.mbase[dest];
+                }
+                const int2 cl = warp_claim2(S.hcount, patch, lv, S.mcount, send ? dest : 0, send);
+                const int hslot = cl.x, mslot = cl.y;
+              if (lv) {
+                S.holes[pb + hslot] = slot;
                 S.id[slot] = -1;
                 if (send) {
-                    if (mslot < S.mcap[dest]) {
-                        const int m = S.mbase[dest] + mslot;
+                    if (mslot < mcap) {
+                        const int m = mb + mslot;
                         if constexpr (is_f64<T>::value) {
                             for (int a = 0; a < 3; a++)
                                 reinterpret_cast<double*>(S.mxi[a])[m] = xin[a];
@@ -401,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         atomicOr(S.status, ST_MAILBOX);
                     }
                 }
+              }
             }
         }
         __syncthreads();

@@ -567,6 +567,40 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         }
         std::vector<long long> start(cursor);
         for (long long p = 0; p < n; p++) order[cursor[patch[p]]++] = p;
+#ifdef PIC_ORDER_ROUNDS
+        // cell rounds: the r-th particle of every cell, cells x fastest, then r + 1, ...
+        const int pcells = S.P[0] * S.P[1] * S.P[2];
+        std::vector<int> ccount(pcells), cstart(pcells);
+        std::vector<long long> tmp;
+        for (int p = 0; p < S.npatch; p++) {
+            const long long b0 = start[p], c = counts[p];
+            if (c == 0) continue;
+            const int px0 = (p % S.np[0]) * S.P[0], py0 = ((p / S.np[0]) % S.np[1]) * S.P[1],
+                      pz0 = (p / (S.np[0] * S.np[1])) * S.P[2];
+            auto lcell = [&](long long q) {
+                const int i = ip[q * 3] - px0, j = ip[q * 3 + 1] - py0,
+                          k = dims == 3 ? ip[q * 3 + 2] - pz0 : 0;
+                return (k * S.P[1] + j) * S.P[0] + i;
+            };
+            std::fill(ccount.begin(), ccount.end(), 0);
+            for (long long k = 0; k < c; k++) ccount[lcell(order[b0 + k])]++;
+            int acc2 = 0, maxc = 0;
+            for (int q = 0; q < pcells; q++) {
+                cstart[q] = acc2;
+                acc2 += ccount[q];
+                maxc = std::max(maxc, ccount[q]);
+            }
+            tmp.assign(c, 0);
+            {
+                std::vector<int> cur(cstart);
+                for (long long k = 0; k < c; k++) tmp[cur[lcell(order[b0 + k])]++] = order[b0 + k];
+            }
+            long long o = b0;
+            for (int r = 0; r < maxc; r++)
+                for (int q = 0; q < pcells; q++)
+                    if (ccount[q] > r) order[o++] = tmp[cstart[q] + r];
+        }
+#else
         for (int p = 0; p < S.npatch; p++) {
             const long long b0 = start[p], c = counts[p];
             for (long long k = c - 1; k > 0; k--) {
@@ -574,6 +608,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
                 std::swap(order[b0 + k], order[b0 + r]);
             }
         }
+#endif
     }
     const size_t es = elem_size(S.prec);
     const long long cap = S.capacity;

@@ -341,22 +341,24 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Warp-aggregated atomicAdd of 1 on counter[key] for every active lane of `mask`
-// that holds `active`; returns this lane's slot. All lanes of `mask` must call it.
-__device__ __forceinline__ int warp_claim(int* counter_base, int key, bool active,
-                                          unsigned mask) {
-    const unsigned act = __ballot_sync(mask, active);
-    int slot = 0;
-    if (active) {
-        const unsigned peers = __match_any_sync(act, key);
-        const int leader = __ffs(peers) - 1;
-        const int rank = __popc(peers & lanemask_lt());
-        int base = 0;
-        if ((threadIdx.x & 31) == leader) base = atomicAdd(counter_base + key, __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        slot = base + rank;
-    }
-    return slot;
+// Two warp-aggregated claims at once, both atomics in flight together: one slot on
+// c1[k1] for every lane holding a1 (k1 is the same for all lanes) and one on c2[k2[lane]]
+// for every lane holding a2. All 32 lanes must call it.
+__device__ __forceinline__ int2 warp_claim2(int* c1, int k1, bool a1, int* c2, int k2, bool a2) {
+    const int lane = threadIdx.x & 31;
+    const unsigned act1 = __ballot_sync(0xffffffffu, a1);
+    const unsigned act2 = __ballot_sync(0xffffffffu, a2);
+    const int lead1 = act1 ? __ffs(act1) - 1 : 0;
+    unsigned peers2 = 0;
+    if (a2) peers2 = __match_any_sync(act2, k2);
+    const int lead2 = a2 ? __ffs(peers2) - 1 : lane;
+    int b1 = 0, b2 = 0;
+    if (act1 && lane == lead1) b1 = atomicAdd(c1 + k1, __popc(act1));
+    if (a2 && lane == lead2) b2 = atomicAdd(c2 + k2, __popc(peers2));
+    b1 = __shfl_sync(0xffffffffu, b1, lead1);
+    b2 = __shfl_sync(0xffffffffu, b2, lead2);
+    const unsigned lt = lanemask_lt();
+    return make_int2(b1 + __popc(act1 & lt), b2 + __popc(peers2 & lt));
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
