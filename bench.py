@@ -54,7 +54,10 @@ def bytes_per_push(dt, w):
     pos = dims * es + (0 if dt == "fp64" else 4)
     ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
     return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
-KERNELS_PER_STEP = 7  # queue, push, inject, exchange, yee_e, yee_b, end_step
+# kernels per step: queue build, push, [window injection], exchange, repack plan and its
+# two copy kernels (which return at once unless a patch needs room), Yee E, Yee B, end
+def kernels_per_step(window: bool) -> int:
+    return 10 if window else 9
 
 
 def parse():
@@ -571,7 +574,7 @@ def main():
         "e2e": ({"value": e2e["value"], "unit": UNIT,
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
                 if e2e else None),
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": kernels_per_step(bool(w["params"].get("window"))) * args.steps,
         "clocks": clocks.summary(),
         "kernel_ms_per_step": main_run["profile"],
         "particles": main_run["n"],

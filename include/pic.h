@@ -88,7 +88,9 @@ typedef struct {
     double ramp_len;    /*                                                    */
     int inject_ppc[3];  /* window only: injected lattice per cell per axis */
     double q, m;        /* species charge and mass (electrons: -1, 1) */
-    long long capacity; /* particle slots in the arena (>= the largest count held) */
+    long long capacity; /* particles the sim may hold (>= the largest count held); the
+                           arena adds 32 slots per patch so that per-patch bases stay
+                           aligned */
     int chunk;          /* work-queue chunk size in particles (0 = 2048); the Python
                            autotuner measures patch and chunk candidates on a workload */
     int mapping;        /* PIC_MAP_QUEUE or PIC_MAP_STATIC */
@@ -146,10 +148,11 @@ pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t*
 
 /* Instrumentation (per-kernel timing): runs nsteps steps with one plain launch per
  * kernel (no graph) and CUDA events around each kernel on the sim's stream, then
- * synchronises. ms[0..6] receive the summed times in milliseconds of: work-queue
- * build, particle push/deposit, window injection, particle exchange, Yee E+B, end of
- * step, and the whole steps. n_ms must be >= 7. Same kernels and launch shapes as
- * pic_step; the state advances by nsteps. */
+ * synchronises. ms[0..7] receive the summed times in milliseconds of: work-queue
+ * build, particle push/deposit, window injection, particle exchange, capacity repack
+ * (kernels that return at once unless a patch needs room), Yee E+B, end of step, and
+ * the whole steps. n_ms must be >= 8. Same kernels and launch shapes as pic_step; the
+ * state advances by nsteps. */
 pic_status pic_profile(pic_sim* sim, int nsteps, double* ms, int n_ms);
 
 /* Destroy the host-side state (synchronises; does not free the arena). */

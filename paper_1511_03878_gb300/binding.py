@@ -195,12 +195,13 @@ def pic_diag(h, kind: int, nbytes: int) -> bytes:
     return buf.raw[: written.value]
 
 
-PROFILE_KERNELS = ("queue_build", "push", "inject", "exchange", "yee", "end_step", "step")
+PROFILE_KERNELS = ("queue_build", "push", "inject", "exchange", "repack", "yee", "end_step",
+                   "step")
 
 
 def pic_profile(h, nsteps: int) -> dict:
-    ms = np.zeros(7)
-    _check(lib().pic_profile(h, int(nsteps), _dp(ms), 7), h)
+    ms = np.zeros(len(PROFILE_KERNELS))
+    _check(lib().pic_profile(h, int(nsteps), _dp(ms), len(PROFILE_KERNELS)), h)
     return dict(zip(PROFILE_KERNELS, ms.tolist()))
 
 

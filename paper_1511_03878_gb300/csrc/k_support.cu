@@ -436,7 +436,8 @@ cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, i
 // ================================================================ capacity repack
 
 // New per-patch capacities from the current counts (free slots shared half by count,
-// half evenly, as at load) and their prefix bases. One CTA per sim.
+// half evenly, each rounded up to kSlotAlign, as at load) and their prefix bases. One
+// CTA per sim.
 __global__ void __launch_bounds__(1024) repack_plan_kernel(const BatchDev* __restrict__ bd) {
     __shared__ int warp_sums[32];
     __shared__ long long s_total;
@@ -450,14 +451,14 @@ __global__ void __launch_bounds__(1024) repack_plan_kernel(const BatchDev* __res
     atomicAdd((unsigned long long*)&s_total, (unsigned long long)part);
     __syncthreads();
     const long long N = s_total;
-    if (N > S.capacity) {  // more particles (with pending arrivals) than slots
+    if (N > S.ucap) {  // more particles (with pending arrivals) than the capacity
         if (tid == 0) {
             atomicOr(S.status, ST_CAPACITY);
             S.st->repack = 2;
         }
         return;
     }
-    const double spare = (double)(S.capacity - N);
+    const double spare = (double)(S.ucap - N);
     int carry = 0, mcarry = 0;
     for (int p0 = 0; p0 < S.npatch; p0 += blockDim.x) {
         const int p = p0 + tid;
@@ -465,8 +466,8 @@ __global__ void __launch_bounds__(1024) repack_plan_kernel(const BatchDev* __res
         if (p < S.npatch) {
             const int c = S.pcount[p] + S.mpend[p];
             const double share = N > 0 ? 0.5 * (double)c / (double)N + 0.5 / S.npatch : 1.0 / S.npatch;
-            cap = c + (int)floor(spare * share);
-            mc = cap / 4 > kMailboxMin ? cap / 4 : kMailboxMin;
+            cap = (int)align_slots(c + (long long)floor(spare * share));
+            mc = (int)align_slots(cap / 4 > kMailboxMin ? cap / 4 : kMailboxMin);
         }
         int tot, mtot;
         const int ex = block_exclusive_scan(cap, warp_sums, &tot);

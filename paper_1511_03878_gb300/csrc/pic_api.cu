@@ -165,8 +165,11 @@ Layout plan(const pic_config* c, char* base) {
         S.f_eps = (float)S.c_eps;
     }
     const long long es = c->precision == PIC_FP32 ? 4 : 8;
-    const long long cap = c->capacity;
-    S.capacity = cap;
+    // slots: the configured capacity plus one alignment's slack per patch, so that every
+    // per-patch base can be a multiple of kSlotAlign
+    S.ucap = c->capacity;
+    S.capacity = align_slots(c->capacity) + (long long)kSlotAlign * S.npatch;
+    const long long cap = S.capacity;
 
     L.ds = cv.take<SimDev>(1);
     L.db = cv.take<BatchDev>(1);
@@ -194,7 +197,7 @@ Layout plan(const pic_config* c, char* base) {
     S.mbase = cv.take<int>(S.npatch);
     S.mcap = cv.take<int>(S.npatch);
     S.mcount = cv.take<int>(S.npatch);
-    S.mtotal = cap / 4 + (long long)kMailboxMin * S.npatch;
+    S.mtotal = cap / 4 + (long long)(kMailboxMin + kSlotAlign) * S.npatch;
     S.mcell = c->precision != PIC_FP64 ? cv.take<int>(S.mtotal) : nullptr;
     for (int a = 0; a < 3; a++) S.mxi[a] = a < c->dims ? cv.take<char>(S.mtotal * es) : nullptr;
     for (int a = 0; a < 3; a++) S.mu[a] = cv.take<char>(S.mtotal * es);
@@ -506,7 +509,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     if (!s) return PIC_ERR_INVALID;
     const SimDev& S = s->L.S;
     if (n < 0) return fail(&s->err, PIC_ERR_INVALID, "negative particle count");
-    if (n > S.capacity) return fail(&s->err, PIC_ERR_CAPACITY, "more particles than capacity");
+    if (n > S.ucap) return fail(&s->err, PIC_ERR_CAPACITY, "more particles than capacity");
     if (n > 0 && (!x || !y || !ux || !uy || !uz || !w || !id || (S.dims == 3 && !z)))
         return fail(&s->err, PIC_ERR_INVALID, "null particle array");
     CK(cudaStreamSynchronize(s->stream), "sync before load");
@@ -539,17 +542,18 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         patch[p] = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
         counts[patch[p]]++;
     }
-    // per-patch capacity: the free slots are shared half by count, half evenly
-    const long long spare = S.capacity - n;
+    // per-patch capacity: the free slots are shared half by count, half evenly; every
+    // capacity is rounded up to kSlotAlign so that all bases stay aligned
+    const long long spare = S.ucap - n;
     std::vector<int> pcap(S.npatch), pbase(S.npatch), mcap(S.npatch), mbase(S.npatch);
     long long acc = 0, macc = 0;
     for (int p = 0; p < S.npatch; p++) {
         double share = n > 0 ? 0.5 * (double)counts[p] / (double)n + 0.5 / S.npatch : 1.0 / S.npatch;
-        long long c = counts[p] + (long long)std::floor((double)spare * share);
+        long long c = align_slots(counts[p] + (long long)std::floor((double)spare * share));
         pcap[p] = (int)c;
         pbase[p] = (int)acc;
         acc += c;
-        mcap[p] = std::max(kMailboxMin, pcap[p] / 4);
+        mcap[p] = (int)align_slots(std::max(kMailboxMin, pcap[p] / 4));
         mbase[p] = (int)macc;
         macc += mcap[p];
     }
@@ -921,11 +925,11 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
 }
 
 extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) {
-    if (!s || nsteps < 0 || !ms || n_ms < 7) return PIC_ERR_INVALID;
+    if (!s || nsteps < 0 || !ms || n_ms < 8) return PIC_ERR_INVALID;
     const SimDev& S = s->L.S;
-    cudaEvent_t ev[7];
-    for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ev[i]), "event create");
-    for (int i = 0; i < 7; i++) ms[i] = 0.0;
+    cudaEvent_t ev[8];
+    for (int i = 0; i < 8; i++) CK(cudaEventCreate(&ev[i]), "event create");
+    for (int i = 0; i < 8; i++) ms[i] = 0.0;
     pic_status rc = PIC_OK;
     for (int it = 0; it < nsteps && rc == PIC_OK; it++) {
         cudaError_t e = cudaEventRecord(ev[0], s->stream);
@@ -938,27 +942,28 @@ extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) 
         if (e == cudaSuccess && S.window) e = launch_inject(s->L.db, 1, s->column_pts, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], s->stream);
         if (e == cudaSuccess) e = launch_exchange(s->L.db, 1, S.npatch, S.prec, s->stream);
-        if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
-        if (e == cudaSuccess) e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, s->stream);
+        if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
-        if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, S.npatch, s->stream);
+        if (e == cudaSuccess) e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[6], s->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, S.npatch, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[7], s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
         if (e != cudaSuccess) {
             rc = cuda_fail(&s->err, e, "profile");
             break;
         }
-        for (int k = 0; k < 6; k++) {
+        for (int k = 0; k < 7; k++) {
             float t = 0.f;
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             ms[k] += t;
         }
         float tt = 0.f;
-        cudaEventElapsedTime(&tt, ev[0], ev[6]);
-        ms[6] += tt;
+        cudaEventElapsedTime(&tt, ev[0], ev[7]);
+        ms[7] += tt;
     }
-    for (int i = 0; i < 7; i++) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 8; i++) cudaEventDestroy(ev[i]);
     return rc;
 }
 

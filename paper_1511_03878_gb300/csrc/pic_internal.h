@@ -19,6 +19,12 @@ constexpr int kThreads = 256;    // threads per CTA of the particle kernel
 constexpr int kQueueThreads = 1024;
 constexpr int kBuckets = 64;     // remainder buckets of the approximate LPT order
 constexpr int kMailboxMin = 1024; // exchange-buffer slots per patch at least (a step's arrivals)
+constexpr int kSlotAlign = 32;    // per-patch particle and exchange-buffer bases are multiples
+                                  // of this, so that a warp's particle loads start a line
+
+__host__ __device__ inline long long align_slots(long long v) {
+    return (v + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+}
 
 // status bits latched by device code
 enum : int {
@@ -78,7 +84,9 @@ struct SimDev {
     void* mu[3];
     void* mw;
     int* mid;
-    long long capacity, mtotal;
+    long long capacity;  // particle slots in the arrays (ucap + alignment slack)
+    long long mtotal;    // exchange-buffer slots
+    long long ucap;      // particles the sim may hold (the configured capacity)
     // repack: scratch particle buffer (capacity slots) and the next layout
     int* acell;
     void* axi[3];
