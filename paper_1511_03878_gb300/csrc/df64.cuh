@@ -173,10 +173,6 @@ __device__ __forceinline__ long long f32_to_fixed(float x) {
     return (b >> 31) ? -r : r;
 }
 
-__device__ __forceinline__ long long to_fixed(df64 v, float scale) {
-    return f32_to_fixed(__fmul_rn(v.hi, scale)) + f32_to_fixed(__fmul_rn(v.lo, scale));
-}
-
 // fixed-point value of a product a*b, a already carrying the fixed-point factor 2^k:
 // the rounded product of the high parts and its exact error (FMA) plus the cross terms,
 // each FP32 part converted on its own (no renormalisation needed before an integer sum)

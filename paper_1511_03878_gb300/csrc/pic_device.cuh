@@ -170,7 +170,7 @@ template <typename T>
 struct JType;
 template <>
 struct JType<double> {
-    using type = double;
+    using type = long long;  // int64 fixed point: FP64 shared atomics run on the FP64 pipe
 };
 template <>
 struct JType<float> {
@@ -178,7 +178,7 @@ struct JType<float> {
 };
 template <>
 struct JType<df64> {
-    using type = long long;  // int64 fixed-point shared-memory current (see jval)
+    using type = long long;  // int64 fixed-point shared-memory current (see jprod)
 };
 
 // fixed-point exponent of an item of `count` particles: a tile entry sums at most
@@ -231,16 +231,22 @@ __device__ __forceinline__ double widen_f32(float f) {
 }
 __device__ __forceinline__ double widen_f32(double d) { return d; }
 
-// current-tile value and atomic for each accumulator type; `scale` = 2^k of the
-// fixed-point tile (unused for the floating-point tiles)
-template <typename JT, typename T>
-__device__ __forceinline__ JT jval(T v, float scale) {
-    (void)scale;
-    return JT(v);
-}
-template <>
-__device__ __forceinline__ long long jval<long long, df64>(df64 v, float scale) {
-    return to_fixed(v, scale);
+// round(x) as int64 with integer operations only, for |x| < 2^62 (the fixed-point
+// exponent guarantees it); keeps the conversion off the FP64 pipe
+__device__ __forceinline__ long long f64_to_fixed(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    if (e == 0) return 0;  // zero or far below the quantum
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+    const int sh = e - 1075;  // |x| = m 2^sh
+    long long r;
+    if (sh >= 0)
+        r = m << sh;
+    else if (sh > -54)
+        r = (m + (1LL << (-sh - 1))) >> (-sh);
+    else
+        r = 0;
+    return (b >> 63) ? -r : r;
 }
 // tile value of the product a*b; for the fixed-point tile `a` already carries the factor
 // 2^k (see jscale)
@@ -252,6 +258,10 @@ template <>
 __device__ __forceinline__ long long jprod<long long, df64>(df64 a, df64 b) {
     return fixed_prod(a, b);
 }
+template <>
+__device__ __forceinline__ long long jprod<long long, double>(double a, double b) {
+    return f64_to_fixed(a * b);
+}
 // charge factor scaled for the tile: exact power-of-two scaling for the fixed-point tile
 template <typename T>
 __device__ __forceinline__ T jscale(T q, float) {
@@ -261,6 +271,10 @@ template <>
 __device__ __forceinline__ df64 jscale<df64>(df64 q, float scale) {
     return scale2(q, scale);
 }
+template <>
+__device__ __forceinline__ double jscale<double>(double q, float scale) {
+    return q * (double)scale;
+}
 __device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(long long* p, long long v) {
@@ -268,7 +282,6 @@ __device__ __forceinline__ void jatomic(long long* p, long long v) {
 }
 // tile entry -> FP64 for the global current (k: the fixed-point exponent)
 __device__ __forceinline__ double jflush(float v, int) { return widen_f32(v); }
-__device__ __forceinline__ double jflush(double v, int) { return v; }
 __device__ __forceinline__ double jflush(long long v, int k) { return fixed_to_f64(v, k); }
 
 
