@@ -53,14 +53,16 @@ __global__ void __launch_bounds__(256) yee_e3d_kernel(const BatchDev* __restrict
     Jnext[fs + p] = 0.0;
     Jnext[2 * fs + p] = 0.0;
     const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
-    const T dt = T(S.dt), ix = T(1.0 / S.d[0]), iy = T(1.0 / S.d[1]), iz = T(1.0 / S.d[2]);
+    using C = FieldConst<T>;
+    const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
     const T bx = H[p], by = H[fs + p], bz = H[2 * fs + p];
     const T bx_jm = H[pidx3(S, i, jm, k)], bx_km = H[pidx3(S, i, j, km)];
     const T by_im = H[fs + pidx3(S, im, j, k)], by_km = H[fs + pidx3(S, i, j, km)];
     const T bz_im = H[2 * fs + pidx3(S, im, j, k)], bz_jm = H[2 * fs + pidx3(S, i, jm, k)];
-    const T ex = Ein[p] + dt * ((bz - bz_jm) * iy - (by - by_km) * iz - T(Jin[p]));
-    const T ey = Ein[fs + p] + dt * ((bx - bx_km) * iz - (bz - bz_im) * ix - T(Jin[fs + p]));
-    const T ez = Ein[2 * fs + p] + dt * ((by - by_im) * ix - (bx - bx_jm) * iy - T(Jin[2 * fs + p]));
+    const T ex = Ein[p] + dt * ((bz - bz_jm) * iy - (by - by_km) * iz - C::cur(Jin[p]));
+    const T ey = Ein[fs + p] + dt * ((bx - bx_km) * iz - (bz - bz_im) * ix - C::cur(Jin[fs + p]));
+    const T ez = Ein[2 * fs + p] +
+                 dt * ((by - by_im) * ix - (bx - bx_jm) * iy - C::cur(Jin[2 * fs + p]));
     put3d(S, Eout, i, j, k, ex);
     put3d(S, Eout + fs, i, j, k, ey);
     put3d(S, Eout + 2 * fs, i, j, k, ez);
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(256) yee_b3d_kernel(const BatchDev* __restrict
     T* Hout = reinterpret_cast<T*>(S.H[1 - g]);
     const long long p = pidx3(S, i, j, k);
     const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1, kp = k == nz - 1 ? 0 : k + 1;
-    const T dt = T(S.dt), ix = T(1.0 / S.d[0]), iy = T(1.0 / S.d[1]), iz = T(1.0 / S.d[2]);
+    using C = FieldConst<T>;
+    const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
     const T ex = E[p], ey = E[fs + p], ez = E[2 * fs + p];
     const T ex_jp = E[pidx3(S, i, jp, k)], ex_kp = E[pidx3(S, i, j, kp)];
     const T ey_ip = E[fs + pidx3(S, ip, j, k)], ey_kp = E[fs + pidx3(S, i, j, kp)];

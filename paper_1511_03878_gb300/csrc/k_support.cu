@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(256) yee_e2d_kernel(const BatchDev* __restrict
     const int i = ox + s, j = oy;
     T ex = T(0), ey = T(0), ez = T(0);
     if (i < nx) {
-        const T dt = T(S.dt), idx_ = T(1.0 / S.d[0]), idy = T(1.0 / S.d[1]);
+        using C = FieldConst<T>;
+        const T dt = C::dt(S), idx_ = C::id(S, 0), idy = C::id(S, 1);
         const int jm = j == 0 ? ny - 1 : j - 1;
         const bool has_im = !(win && i == 0);
         const int im = i == 0 ? nx - 1 : i - 1;
@@ -366,9 +367,10 @@ __global__ void __launch_bounds__(256) yee_e2d_kernel(const BatchDev* __restrict
         const T bzim = has_im ? at(Hin, 2, im, j) : T(0);
         const T by = at(Hin, 1, i, j), byim = has_im ? at(Hin, 1, im, j) : T(0);
         const T bx = at(Hin, 0, i, j), bxjm = at(Hin, 0, i, jm);
-        ex = Ein[pi] + dt * ((bz - bzjm) * idy - T(Jin[pi]));
-        ey = Ein[fs + pi] + dt * (-(bz - bzim) * idx_ - T(Jin[fs + pi]));
-        ez = Ein[2 * fs + pi] + dt * ((by - byim) * idx_ - (bx - bxjm) * idy - T(Jin[2 * fs + pi]));
+        ex = Ein[pi] + dt * ((bz - bzjm) * idy - C::cur(Jin[pi]));
+        ey = Ein[fs + pi] + dt * (-(bz - bzim) * idx_ - C::cur(Jin[fs + pi]));
+        ez = Ein[2 * fs + pi] +
+             dt * ((by - byim) * idx_ - (bx - bxjm) * idy - C::cur(Jin[2 * fs + pi]));
     }
     put2d(Eout, NX, ox, oy, nx, ny, !win, ex);
     put2d(Eout + fs, NX, ox, oy, nx, ny, !win, ey);
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(256) yee_b2d_kernel(const BatchDev* __restrict
     const int i = ox + s, j = oy;
     T hx = T(0), hy = T(0), hz = T(0), nbx = T(0), nby = T(0), nbz = T(0);
     if (i < nx) {
-        const T dt = T(S.dt), idx_ = T(1.0 / S.d[0]), idy = T(1.0 / S.d[1]);
+        using C = FieldConst<T>;
+        const T dt = C::dt(S), idx_ = C::id(S, 0), idy = C::id(S, 1);
         auto at = [&](const T* a, int c, int ii, int jj) {
             return a[c * fs + (long long)(jj + kGuard) * NX + (ii + kGuard)];
         };

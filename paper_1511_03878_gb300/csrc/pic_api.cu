@@ -163,6 +163,13 @@ Layout plan(const pic_config* c, char* base) {
             S.f_j[a] = (float)S.c_j[a];
         }
         S.f_eps = (float)S.c_eps;
+        S.f_dt = (float)S.dt;
+        S.f_dt_lo = (float)(S.dt - (double)S.f_dt);
+        for (int a = 0; a < 3; a++) {
+            S.c_id[a] = 1.0 / S.d[a];
+            S.f_id[a] = (float)S.c_id[a];
+            S.f_id_lo[a] = (float)(S.c_id[a] - (double)S.f_id[a]);
+        }
     }
     const long long es = c->precision == PIC_FP32 ? 4 : 8;
     // slots: the configured capacity plus one alignment's slack per patch, so that every

@@ -231,6 +231,52 @@ __device__ __forceinline__ double widen_f32(float f) {
 }
 __device__ __forceinline__ double widen_f32(double d) { return d; }
 
+// double -> float rounded to nearest even with integer operations only when the result
+// is a normal float or zero (the conversion instruction runs on the FP64 pipe); other
+// values take the conversion instruction
+__device__ __forceinline__ float narrow_f64(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if ((b & 0x7FFFFFFFFFFFFFFFULL) == 0) return __uint_as_float(sign);
+    const int e = (int)((b >> 52) & 0x7FFu) - 1023 + 127;  // biased FP32 exponent
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    unsigned r = (unsigned)(m >> 29);
+    const unsigned long long rem = m & 0x1FFFFFFFULL;
+    if (rem > 0x10000000ULL || (rem == 0x10000000ULL && (r & 1u))) r += 1u;
+    const unsigned f = ((unsigned)e << 23) + r;  // a mantissa carry bumps the exponent
+    if (f >= 0x7F800000u) return __double2float_rn(d);
+    return __uint_as_float(f | sign);
+}
+
+// field-solver constants and FP64 current values in the working precision
+template <typename T>
+struct FieldConst;
+template <>
+struct FieldConst<double> {
+    static __device__ __forceinline__ double dt(const SimDev& S) { return S.dt; }
+    static __device__ __forceinline__ double id(const SimDev& S, int a) { return S.c_id[a]; }
+    static __device__ __forceinline__ double cur(double j) { return j; }
+};
+template <>
+struct FieldConst<float> {
+    static __device__ __forceinline__ float dt(const SimDev& S) { return S.f_dt; }
+    static __device__ __forceinline__ float id(const SimDev& S, int a) { return S.f_id[a]; }
+    static __device__ __forceinline__ float cur(double j) { return narrow_f64(j); }
+};
+template <>
+struct FieldConst<df64> {
+    static __device__ __forceinline__ df64 dt(const SimDev& S) { return df64(S.f_dt, S.f_dt_lo); }
+    static __device__ __forceinline__ df64 id(const SimDev& S, int a) {
+        return df64(S.f_id[a], S.f_id_lo[a]);
+    }
+    // hi = nearest float, lo = the rounded remainder (one FP64 subtraction)
+    static __device__ __forceinline__ df64 cur(double j) {
+        const float hi = narrow_f64(j);
+        return df64(hi, narrow_f64(j - widen_f32(hi)));
+    }
+};
+
 // round(x) as int64 with integer operations only, for |x| < 2^62 (the fixed-point
 // exponent guarantees it); keeps the conversion off the FP64 pipe
 __device__ __forceinline__ long long f64_to_fixed(double x) {

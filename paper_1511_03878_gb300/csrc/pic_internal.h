@@ -63,6 +63,9 @@ struct SimDev {
     double c_eps;      // q dt / (2 m)
     double c_j[3];     // 2D: -q/dV d[a]/dt for Jx, Jy and q/dV for Jz (times v_z)
     float f_dtd[3], f_eps, f_j[3];
+    // field-solver constants: dt and 1/d[a] in FP64, and as FP32 (hi) + FP32 (lo) pairs
+    double c_id[3];
+    float f_dt, f_dt_lo, f_id[3], f_id_lo[3];
     int cmax_exp;      // one particle's current contribution stays below 2^cmax_exp
     // fields
     void* F[2];      // [6][NZ][NY][NX]: Ex Ey Ez Bnx Bny Bnz (B^n for the push)
