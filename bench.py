@@ -456,7 +456,7 @@ def launch_layout(args, w, precision):
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     cache = autotune.TUNING_TABLE if args.autotune == "cached" else None
-    c = autotune.tune(w, prec, capacity=cap, warmup=3, steps=20, cache_file=cache)
+    c = autotune.tune(w, prec, capacity=cap, warmup=10, steps=100, margin=0.03, cache_file=cache)
     rec = {"patch": list(c.patch), "chunk": c.chunk, "mapping": mapping, "autotuned": True,
            "autotune": {"source": "tuning table" if cache else "measured in this run",
                         "candidates": len(c.table), "seconds": round(c.seconds, 1),
@@ -585,6 +585,7 @@ def main():
             "value": job_value(r["pushes_all"], r["ms"]),
             "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
             "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v],
+            "capacity_repacks": r["repacks"],
             "launch": layouts[v][2]} for v, r in variants.items()}
     print(json.dumps(line), flush=True)
 

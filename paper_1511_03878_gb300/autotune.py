@@ -16,7 +16,9 @@ precision, so it is measured, not modelled. Every candidate is built with the li
 ``steps`` times timed with CUDA events on its stream; the cost is the time per particle
 push. The search is coordinate descent: all patch candidates at the default chunk, then
 all chunk candidates at the best patch; a candidate must beat the incumbent by more than
-a margin (2 %) to replace it, starting from the workload's own patch. Candidates that the library rejects
+a margin (3 %) to replace it, starting from the workload's own patch. The timed window
+(100 steps after 10 warm-up steps by default) has to be long enough to include the
+capacity repacks that small patches trigger as the plasma is compressed. Candidates that the library rejects
 (``pic_required_bytes`` returns 0: a side that does not divide the grid, or tiles that
 do not fit in shared memory) are skipped without touching the GPU.
 """
@@ -117,7 +119,7 @@ def _better(r, best, margin):
 
 
 def tune(workload: dict, precision: int, capacity: int, patches=None, chunks=CHUNKS,
-         warmup: int = 3, steps: int = 10, margin: float = 0.02,
+         warmup: int = 10, steps: int = 100, margin: float = 0.03,
          cache_file: str | None = None) -> Choice:
     """Pick (patch, chunk) for `workload` at `precision` by measurement.
 

@@ -205,13 +205,16 @@ __device__ __forceinline__ df64 gather9(const df64* __restrict__ f, int BX, cons
 #ifndef PIC_DF64_MINB
 #define PIC_DF64_MINB 2
 #endif
+#ifndef PIC_F32_MINB
+#define PIC_F32_MINB 3
+#endif
 template <typename T>
 struct Push2DShape {
     static constexpr int threads = kThreads, min_blocks = 2;
 };
 template <>
 struct Push2DShape<float> {
-    static constexpr int threads = kThreads, min_blocks = 3;
+    static constexpr int threads = kThreads, min_blocks = PIC_F32_MINB;
 };
 template <>
 struct Push2DShape<df64> {
@@ -460,8 +463,8 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             bool leave = false;
             int dest = patch;
             if (ok) {
-                const T qx = jscale(cjx * w, jsc), qy = jscale(cjy * w, jsc),
-                        qz = jscale(cjz * w * vz, jsc);
+                const T qx = jscale<JT>(cjx * w, jsc), qy = jscale<JT>(cjy * w, jsc),
+                        qz = jscale<JT>(cjz * w * vz, jsc);
                 const int t0 = typ * JX + txp;  // stencil node 0 of both axes
                 if (fast) {
                     const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)

@@ -106,7 +106,7 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
 template <typename T>
 __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 1)
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
-    using JT = typename JType<T>::type;
+    using JT = typename JType3D<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int s_item;
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         for (int q = 0; q < 3; q++) Sp[a][q] = S0keep[a][q];
                     if (fast) {
                         JT* jt3[3];
-                        const T q3[3] = {jscale(cj[0] * w, jsc), jscale(cj[1] * w, jsc),
-                                         jscale(cj[2] * w, jsc)};
+                        const T q3[3] = {jscale<JT>(cj[0] * w, jsc), jscale<JT>(cj[1] * w, jsc),
+                                         jscale<JT>(cj[2] * w, jsc)};
                         const int t111 = (tp[2] + 1) * JXY + (tp[1] + 1) * JX + (tp[0] + 1);
                         for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
                         deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3);
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const int b = (a + 1) % 3, c = (a + 2) % 3;
-                        const T qa = jscale(cj[a] * w, jsc);
+                        const T qa = jscale<JT>(cj[a] * w, jsc);
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;
@@ -440,7 +440,7 @@ template <typename T>
 int smem_bytes_3d(int P0, int P1, int P2) {
     const int BX = P0 + 4, BY = P1 + 3, BZ = P2 + 3;
     const int fb = 6 * BX * BY * BZ * (int)sizeof(T);
-    const int jb = 3 * (P0 + 5) * (P1 + 5) * (P2 + 5) * (int)sizeof(typename JType<T>::type);
+    const int jb = 3 * (P0 + 5) * (P1 + 5) * (P2 + 5) * (int)sizeof(typename JType3D<T>::type);
     return ((fb + 127) & ~127) + jb;
 }
 

@@ -497,14 +497,13 @@ __global__ void __launch_bounds__(256) repack_copy_kernel(const BatchDev* __rest
     const int sim = blockIdx.y;
     if (sim >= bd->nsims) return;
     const SimDev& S = bd->sims[sim];
-    if (S.st->repack != 1) return;
-    const int p = blockIdx.x;
-    if (p >= S.npatch) return;
+    if (S.st->repack != 1) return;  // the usual case: a small grid that exits at once
+    for (int p = blockIdx.x; p < S.npatch; p += gridDim.x) {
     const int cnt = S.pcount[p];
     const int from = back ? S.pbase_new[p] : S.pbase[p];
     const int to = S.pbase_new[p];
     const int pend = S.mpend[p];
-    if ((long long)to + cnt + pend > S.capacity || (long long)from + cnt > S.capacity) return;
+    if ((long long)to + cnt + pend > S.capacity || (long long)from + cnt > S.capacity) continue;
     if (back && pend > 0) {  // arrivals that did not fit before: append after the live ones
         const int m0 = S.mbase[p] + S.mpoff[p];
         for (int k = threadIdx.x; k < pend; k += blockDim.x)
@@ -531,12 +530,22 @@ __global__ void __launch_bounds__(256) repack_copy_kernel(const BatchDev* __rest
             S.aid[b0] = S.id[a0];
         }
     }
+    }
 }
 
 cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int prec,
                           cudaStream_t s) {
     repack_plan_kernel<<<nsims, 1024, 0, s>>>(bd);
-    dim3 grid(max_patches, nsims);
+    // CTAs loop over patches: eight per SM keep enough loads in flight to copy at full
+    // bandwidth, and an idle step (no repack) launches only those
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    dim3 grid(max_patches < 8 * nsm ? max_patches : 8 * nsm, nsims);
     for (int back = 0; back < 2; back++) {
         PIC_DISPATCH(prec, (repack_copy_kernel<T><<<grid, 256, 0, s>>>(bd, back)));
     }

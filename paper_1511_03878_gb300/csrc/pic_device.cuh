@@ -181,6 +181,21 @@ struct JType<df64> {
     using type = long long;  // int64 fixed-point shared-memory current (see jprod)
 };
 
+// 3D tile type: the 3D FP64 kernel keeps FP64 shared atomics unless built with
+// PIC_3D_F64_FIXED (its occupancy is register-bound, one CTA per SM, and the integer
+// conversion of 54 to 144 contributions per particle costs more issue slots than the
+// FP64 pipe time it frees)
+template <typename T>
+struct JType3D {
+    using type = typename JType<T>::type;
+};
+#ifndef PIC_3D_F64_FIXED
+template <>
+struct JType3D<double> {
+    using type = double;
+};
+#endif
+
 // fixed-point exponent of an item of `count` particles: a tile entry sums at most
 // `count` contributions, each below 2^cmax_exp, and must stay below 2^62
 __device__ __forceinline__ int item_fixed_exp(int count, int cmax_exp) {
@@ -308,17 +323,18 @@ template <>
 __device__ __forceinline__ long long jprod<long long, double>(double a, double b) {
     return f64_to_fixed(a * b);
 }
-// charge factor scaled for the tile: exact power-of-two scaling for the fixed-point tile
-template <typename T>
+// charge factor scaled for the tile: exact power-of-two scaling for a fixed-point tile,
+// unchanged for a floating-point one
+template <typename JT, typename T>
 __device__ __forceinline__ T jscale(T q, float) {
     return q;
 }
 template <>
-__device__ __forceinline__ df64 jscale<df64>(df64 q, float scale) {
+__device__ __forceinline__ df64 jscale<long long, df64>(df64 q, float scale) {
     return scale2(q, scale);
 }
 template <>
-__device__ __forceinline__ double jscale<double>(double q, float scale) {
+__device__ __forceinline__ double jscale<long long, double>(double q, float scale) {
     return q * (double)scale;
 }
 __device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
@@ -328,6 +344,7 @@ __device__ __forceinline__ void jatomic(long long* p, long long v) {
 }
 // tile entry -> FP64 for the global current (k: the fixed-point exponent)
 __device__ __forceinline__ double jflush(float v, int) { return widen_f32(v); }
+__device__ __forceinline__ double jflush(double v, int) { return v; }
 __device__ __forceinline__ double jflush(long long v, int k) { return fixed_to_f64(v, k); }
 
 

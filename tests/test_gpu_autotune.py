@@ -41,7 +41,7 @@ def test_tune_and_parity_of_choice(binding):
     assert (c.patch, c.chunk, c.ns_per_push) in c.table
     assert c.table[0][0] == (32, 32)  # the workload's own patch is the first incumbent
     # the winner is within the replacement margin of the fastest candidate
-    assert c.ns_per_push * (1 - 0.02) <= min(r[2] for r in c.table)
+    assert c.ns_per_push * (1 - 0.03) <= min(r[2] for r in c.table)
     # cached: the same call returns the same object without measuring
     assert autotune.tune(w, binding.PIC_FP64, capacity=2 * n, patches=patches,
                          chunks=chunks) is c
