@@ -14,6 +14,7 @@ working set (particles + fields) is larger than the 129 MB L2.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -72,6 +73,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=0, help="queue chunk when not autotuned")
+    ap.add_argument("--patch", default="", help="patch sides when not autotuned, e.g. 16,8,8")
     ap.add_argument("--autotune", default="cached", choices=["cached", "on", "off"],
                     help="cached: the layouts recorded in the package's tuning table (measured "
                          "there when missing); on: measure again; off: workload patch, --chunk")
@@ -100,6 +102,41 @@ def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20):
         return inputs.thermal2d(seed=1511)
     # the window full of plasma: density ramp placed before x = 0
     return inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
+
+
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic.md")
+# the sources a particle kernel is built from (the digest in the traffic table)
+KERNEL_SOURCES = {2: ("k_push2d.cu", "pic_device.cuh", "df64.cuh", "pic_internal.h"),
+                  3: ("k_push3d.cu", "pic_device.cuh", "df64.cuh", "pic_internal.h")}
+
+
+def source_digest(dims):
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[dims]:
+        with open(os.path.join(ROOT, "paper_1511_03878_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload_name, patch, chunk, dims):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary table, or None
+    when no capture matches this workload and layout or the kernel sources changed
+    since the capture (their digest differs)."""
+    try:
+        with open(TRAFFIC_TABLE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    digest = source_digest(dims)
+    lay = "x".join(str(v) for v in patch)
+    for ln in lines:
+        cols = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
+        if len(cols) < 6 or not cols[4].isdigit():
+            continue
+        if (cols[0] == kernel and cols[1] == workload_name and cols[2] == lay
+                and cols[3] == str(chunk) and cols[5] == digest):
+            return int(cols[4])
+    return None
 
 
 def measured_peaks():
@@ -290,6 +327,12 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
         if precision == "df64":
             fl = FLOPS_PER_PUSH_2D if dims == 2 else FLOPS_PER_PUSH_3D
             roof["fp64_equivalent_tflops"] = fl * n_push / (push_ms * 1e-3) / 1e12
+    # DRAM bytes per launch from the committed ncu capture of this kernel and layout
+    roof["traffic"] = measured_traffic(roof["kernel"], config_dict(args, precision)["workload"],
+                                       w["params"]["patch"], chunk or 2048, dims)
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                              "(profiles/traffic.md)" if roof["traffic"] is not None else
+                              "no capture of the current kernel sources in this layout")
     out = dict(ms=ms, pushes=pushes, pushes_all=pushes_all, n=n_push, profile={k: v / K for k, v in prof.items()},
                roofline=roof, push_ms=push_ms, repacks=repacks)
     sim.close()
@@ -450,6 +493,8 @@ def launch_layout(args, w, precision):
                else "static: one CTA per patch")
     if args.autotune == "off" or args.mapping == "static":
         chunk = args.chunk
+        if args.patch:
+            w = dict(w, params=dict(w["params"], patch=tuple(int(v) for v in args.patch.split(","))))
         rec = {"patch": list(w["params"]["patch"]), "chunk": chunk or autotune.DEFAULT_CHUNK,
                "mapping": mapping, "autotuned": False}
         return w, chunk, rec
