@@ -92,6 +92,11 @@ def lib():
         L.orc_shifts_done.argtypes = [ctypes.c_void_p]
         L.orc_energy.argtypes = [ctypes.c_void_p, _dp]
         L.orc_gauss.argtypes = [ctypes.c_void_p, _dp]
+        L.orc_merge_group.restype = ctypes.c_int
+        L.orc_merge_group.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, _dp, _ip, _dp, _dp,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_merge.restype = ctypes.c_longlong
+        L.orc_merge.argtypes = [ctypes.c_void_p, _ip, ctypes.c_longlong, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -189,6 +194,22 @@ def div_e(c: OrcConfig, E):
     return out
 
 
+def merge_group(ux, uy, uz, w, ids):
+    """Two-particle replacement of one merge group (None when fewer than 3 members):
+    returns (u_a, u_b, common weight, (index of a, index of b))."""
+    n = len(ux)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ux, uy, uz, w)]
+    ida = np.ascontiguousarray(ids, dtype=np.int32)
+    out = np.zeros(6)
+    ow = ctypes.c_double()
+    keep = (ctypes.c_longlong * 2)()
+    r = lib().orc_merge_group(n, *[_ptr(a) for a in arrs], ida.ctypes.data_as(_ip), _ptr(out),
+                              ctypes.byref(ow), keep)
+    if r == 0:
+        return None
+    return out[:3].copy(), out[3:].copy(), ow.value, (int(keep[0]), int(keep[1]))
+
+
 def shift_count(c: OrcConfig, step: int) -> int:
     return int(lib().orc_shift_count(ctypes.byref(c), int(step)))
 
@@ -268,6 +289,15 @@ class OracleSim:
     @property
     def shifts(self) -> int:
         return int(lib().orc_shifts_done(self._h))
+
+    def merge(self, patch, above: int, dp: float) -> int:
+        """Merge groups (same cell and momentum bin of width dp, >= 3 members) in every
+        patch holding more than `above` particles; returns the number removed."""
+        pt = np.ascontiguousarray(list(patch) + [1] * (3 - len(patch)), dtype=np.int32)
+        r = lib().orc_merge(self._h, pt.ctypes.data_as(_ip), int(above), float(dp))
+        if r < 0:
+            raise MemoryError("oracle merge")
+        return int(r)
 
     def energy(self):
         out = np.zeros(3)

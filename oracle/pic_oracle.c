@@ -603,3 +603,175 @@ void orc_gauss(const orc_sim* s, double* out) {
     for (long long t = 0; t < s->ncell; t++) out[t] -= rho[t] + s->rho_bg[t];
     free(rho);
 }
+
+/* ------------------------------------------------------------------ merging */
+
+int orc_merge_group(long long n, const double* ux, const double* uy, const double* uz,
+                    const double* w, const int* id, double out_u[6], double* out_w,
+                    long long keep[2]) {
+    if (n < 3) return 0;
+    /* the two smallest ids */
+    long long a = -1, b = -1;
+    for (long long k = 0; k < n; k++) {
+        if (a < 0 || id[k] < id[a]) {
+            b = a;
+            a = k;
+        } else if (b < 0 || id[k] < id[b]) {
+            b = k;
+        }
+    }
+    keep[0] = a;
+    keep[1] = b;
+    /* totals, members in increasing id */
+    double W = 0.0, P[3] = {0.0, 0.0, 0.0}, E = 0.0;
+    int last = -2147483647 - 1;
+    for (long long done = 0; done < n; done++) {
+        long long k = -1;
+        for (long long j = 0; j < n; j++)
+            if (id[j] > last && (k < 0 || id[j] < id[k])) k = j;
+        if (k < 0) break; /* ids repeat: not a valid group */
+        last = id[k];
+        const double g = sqrt(1.0 + ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
+        W += w[k];
+        P[0] += w[k] * ux[k];
+        P[1] += w[k] * uy[k];
+        P[2] += w[k] * uz[k];
+        E += w[k] * g;
+    }
+    *out_w = 0.5 * W;
+    const double gn = E / W;
+    const double un = sqrt(gn * gn - 1.0 > 0.0 ? gn * gn - 1.0 : 0.0);
+    const double pm = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    double e1[3], e2[3];
+    const double r[3] = {ux[a], uy[a], uz[a]};
+    const double rm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (pm > 0.0) {
+        for (int i = 0; i < 3; i++) e1[i] = P[i] / pm;
+    } else if (rm > 0.0) {
+        for (int i = 0; i < 3; i++) e1[i] = r[i] / rm;
+    } else {
+        e1[0] = 1.0, e1[1] = 0.0, e1[2] = 0.0;
+    }
+    /* e2: the reference momentum's part normal to e1, else an axis's */
+    double v[3] = {r[0], r[1], r[2]};
+    double dot = v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2];
+    double t[3] = {v[0] - dot * e1[0], v[1] - dot * e1[1], v[2] - dot * e1[2]};
+    double tm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    if (!(tm > 1e-12 * (rm > 0.0 ? rm : 1.0))) {
+        int ax = 0;
+        for (int i = 1; i < 3; i++)
+            if (fabs(e1[i]) < fabs(e1[ax])) ax = i;
+        v[0] = v[1] = v[2] = 0.0;
+        v[ax] = 1.0;
+        dot = e1[ax];
+        t[0] = v[0] - dot * e1[0];
+        t[1] = v[1] - dot * e1[1];
+        t[2] = v[2] - dot * e1[2];
+        tm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    }
+    for (int i = 0; i < 3; i++) e2[i] = t[i] / tm;
+    double ct = (un > 0.0) ? pm / (W * un) : 0.0;
+    if (ct > 1.0) ct = 1.0;
+    const double st = sqrt(1.0 - ct * ct);
+    for (int i = 0; i < 3; i++) {
+        out_u[i] = un * (ct * e1[i] + st * e2[i]);
+        out_u[3 + i] = un * (ct * e1[i] - st * e2[i]);
+    }
+    return 1;
+}
+
+/* cell and patch of particle p (window or periodic, positions in [0, L)) */
+static void cell_of(const orc_sim* s, long long p, long ic[3]) {
+    const orc_config* c = &s->c;
+    const double pos[3] = {s->x[p], s->y[p], s->z[p]};
+    for (int a = 0; a < 3; a++) {
+        if (a >= c->dims) {
+            ic[a] = 0;
+            continue;
+        }
+        long i = (long)floor(pos[a] / c->d[a]);
+        if (i < 0) i = 0;
+        if (i >= c->n[a]) i = c->n[a] - 1;
+        ic[a] = i;
+    }
+}
+
+long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) {
+    const orc_config* c = &s->c;
+    long np_[3];
+    for (int a = 0; a < 3; a++) np_[a] = a < c->dims ? c->n[a] / patch[a] : 1;
+    const long long npatch = (long long)np_[0] * np_[1] * np_[2];
+    long long* count = (long long*)calloc((size_t)npatch, sizeof(long long));
+    long long* pidx = (long long*)malloc((size_t)(s->np > 0 ? s->np : 1) * sizeof(long long));
+    long long* key = (long long*)malloc((size_t)(s->np > 0 ? s->np : 1) * 4 * sizeof(long long));
+    unsigned char* keep = (unsigned char*)malloc((size_t)(s->np > 0 ? s->np : 1));
+    if (!count || !pidx || !key || !keep) {
+        free(count), free(pidx), free(key), free(keep);
+        return -1;
+    }
+    for (long long p = 0; p < s->np; p++) {
+        long ic[3];
+        cell_of(s, p, ic);
+        const long pc = ic[0] / (c->dims > 0 ? patch[0] : 1);
+        const long pcy = ic[1] / patch[1];
+        const long pcz = c->dims == 3 ? ic[2] / patch[2] : 0;
+        pidx[p] = (long long)pc + np_[0] * ((long long)pcy + np_[1] * pcz);
+        count[pidx[p]]++;
+        key[4 * p + 0] = ((long long)ic[2] * c->n[1] + ic[1]) * c->n[0] + ic[0];
+        key[4 * p + 1] = (long long)floor(s->ux[p] / dp);
+        key[4 * p + 2] = (long long)floor(s->uy[p] / dp);
+        key[4 * p + 3] = (long long)floor(s->uz[p] / dp);
+        keep[p] = 1;
+    }
+    /* plain grouping: for each unvisited particle of an overloaded patch, collect the
+     * members sharing its cell and bin (quadratic, fine for an oracle) */
+    unsigned char* seen = (unsigned char*)calloc((size_t)(s->np > 0 ? s->np : 1), 1);
+    long long* mem = (long long*)malloc((size_t)(s->np > 0 ? s->np : 1) * sizeof(long long));
+    double *gx = (double*)malloc((size_t)(s->np > 0 ? s->np : 1) * 4 * sizeof(double));
+    int* gid = (int*)malloc((size_t)(s->np > 0 ? s->np : 1) * sizeof(int));
+    long long removed = 0;
+    if (seen && mem && gx && gid) {
+        for (long long p = 0; p < s->np; p++) {
+            if (seen[p] || count[pidx[p]] <= above) continue;
+            long long m = 0;
+            for (long long q = p; q < s->np; q++) {
+                if (seen[q] || pidx[q] != pidx[p]) continue;
+                if (key[4 * q] != key[4 * p] || key[4 * q + 1] != key[4 * p + 1] ||
+                    key[4 * q + 2] != key[4 * p + 2] || key[4 * q + 3] != key[4 * p + 3])
+                    continue;
+                seen[q] = 1;
+                mem[m++] = q;
+            }
+            if (m < 3) continue;
+            double* gux = gx;
+            double* guy = gx + m;
+            double* guz = gx + 2 * m;
+            double* gw = gx + 3 * m;
+            for (long long k = 0; k < m; k++) {
+                gux[k] = s->ux[mem[k]];
+                guy[k] = s->uy[mem[k]];
+                guz[k] = s->uz[mem[k]];
+                gw[k] = s->w[mem[k]];
+                gid[k] = s->id[mem[k]];
+            }
+            double nu[6], nw;
+            long long kp[2];
+            orc_merge_group(m, gux, guy, guz, gw, gid, nu, &nw, kp);
+            for (long long k = 0; k < m; k++) keep[mem[k]] = 0;
+            for (int j = 0; j < 2; j++) {
+                const long long q = mem[kp[j]];
+                keep[q] = 1;
+                s->ux[q] = nu[3 * j + 0];
+                s->uy[q] = nu[3 * j + 1];
+                s->uz[q] = nu[3 * j + 2];
+                s->w[q] = nw;
+            }
+            removed += m - 2;
+        }
+        compact(s, keep);
+    } else {
+        removed = -1;
+    }
+    free(count), free(pidx), free(key), free(keep), free(seen), free(mem), free(gx), free(gid);
+    return removed;
+}

@@ -111,6 +111,35 @@ void orc_energy(const orc_sim* s, double out[3]);
 /* div E - rho_e - rho_bg on nodes (ncell values). */
 void orc_gauss(const orc_sim* s, double* out);
 
+/* ---- load limiting by particle merging ----
+ * The paper bounds the SP count of overloaded regions by merging SP (Sec. 3.2, and
+ * Sec. 3, where regions holding up to 40x the initial count are the load problem). It
+ * prints no merge algorithm; this follows the published energy- and momentum-conserving
+ * merge of Vranic et al., Comput. Phys. Commun. 191 (2015) 65:
+ *   a group of N >= 3 particles sharing one cell and one momentum bin becomes two
+ *   particles a, b with w_a = w_b = W/2 (W = sum w), gamma_a = gamma_b = E/W
+ *   (E = sum w gamma), and momenta symmetric about P = sum w u, at the half angle
+ *   theta with cos(theta) = |P| / (W |u_ab|), so that W, P and E are kept exactly.
+ * Choices of this implementation (the published method leaves them free):
+ *   - members are taken in increasing id; a and b keep the ids and positions of the two
+ *     smallest ids;
+ *   - the plane of u_a, u_b is spanned by P and the momentum of the smallest-id member
+ *     (when that is parallel to P, by P and the coordinate axis least aligned with P);
+ *     when P = 0, u_a = -u_b lies along that member's momentum (else the x axis);
+ *   - the momentum bin of a particle is floor(u_a / dp) on each axis. */
+
+/* Two-particle replacement of one group of n members. Returns 0 (nothing to do) when
+ * n < 3; else 1 with the new momenta out_u[0..2] (a) and out_u[3..5] (b), the common
+ * weight *out_w, and the member indices of a and b in keep[0], keep[1]. */
+int orc_merge_group(long long n, const double* ux, const double* uy, const double* uz,
+                    const double* w, const int* id, double out_u[6], double* out_w,
+                    long long keep[2]);
+
+/* Merge every group (same cell, same momentum bin of width dp, N >= 3) inside each
+ * patch (patch[a] cells per axis) holding more than `above` particles. Removed
+ * particles are compacted away, order otherwise kept. Returns the number removed. */
+long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp);
+
 #ifdef __cplusplus
 }
 #endif
