@@ -94,6 +94,14 @@ typedef struct {
     int chunk;          /* work-queue chunk size in particles (0 = 2048); the Python
                            autotuner measures patch and chunk candidates on a workload */
     int mapping;        /* PIC_MAP_QUEUE or PIC_MAP_STATIC */
+    int merge_above;    /* load limiting (Sec. 3.2): at the end of every step, each patch
+                           holding more than this many particles has every group of >= 3
+                           particles sharing a cell and a momentum bin replaced by two
+                           particles with the group's total weight, momentum and energy
+                           (Vranic et al. 2015); 0 = off. Needs patches of at most 4096
+                           cells. */
+    double merge_dp;    /* momentum-bin width (units of m c) of the merge; > 0 when
+                           merge_above > 0 */
 } pic_config;
 
 /* Device bytes one arena needs for this configuration (0 if the config is invalid). */
@@ -141,7 +149,9 @@ enum {
     PIC_DIAG_PATCH_COUNTS = 5,  /* npatch int32 (x fastest)                        */
     PIC_DIAG_STEP = 6,          /* 3 int64: steps taken, window shifts, capacity
                                    repacks (per-patch capacities re-split on the
-                                   device when a patch nears its capacity)        */
+                                   device when a patch nears its capacity); a 4th,
+                                   particles removed by merging, when out_bytes
+                                   allows                                         */
     PIC_DIAG_EX_AXIS = 7        /* nx float64: Ex on the row (and plane) ny/2      */
 };
 pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);

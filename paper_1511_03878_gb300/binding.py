@@ -57,6 +57,8 @@ class PicConfig(ctypes.Structure):
         ("capacity", ctypes.c_longlong),
         ("chunk", ctypes.c_int),
         ("mapping", ctypes.c_int),
+        ("merge_above", ctypes.c_int),
+        ("merge_dp", ctypes.c_double),
     ]
 
 
@@ -126,7 +128,8 @@ def _check(rc, handle=None):
 # ------------------------------------------------------------------ same-name wrappers
 
 def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chunk: int = 0,
-                mapping: int = PIC_MAP_QUEUE) -> PicConfig:
+                mapping: int = PIC_MAP_QUEUE, merge_above: int = 0,
+                merge_dp: float = 0.0) -> PicConfig:
     c = PicConfig()
     c.dims = int(params["dims"])
     for a in range(3):
@@ -149,6 +152,8 @@ def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chun
     c.capacity = int(capacity)
     c.chunk = int(chunk)
     c.mapping = int(mapping)
+    c.merge_above = int(merge_above)
+    c.merge_dp = float(merge_dp)
     return c
 
 
@@ -251,13 +256,14 @@ class Sim:
     """One simulation resident on the GPU: arena from torch, work on a torch stream."""
 
     def __init__(self, params: dict, precision: int = PIC_FP64, capacity: int = 0,
-                 chunk: int = 0, mapping: int = PIC_MAP_QUEUE, stream=None, device="cuda"):
+                 chunk: int = 0, mapping: int = PIC_MAP_QUEUE, stream=None, device="cuda",
+                 merge_above: int = 0, merge_dp: float = 0.0):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA GPU is required (the library has no CPU path)")
         self.params = params
-        self.cfg = make_config(params, precision, capacity, chunk, mapping)
+        self.cfg = make_config(params, precision, capacity, chunk, mapping, merge_above, merge_dp)
         self.nbytes = pic_required_bytes(self.cfg)
         if self.nbytes == 0:
             raise PicError(PIC_ERR_INVALID, "invalid configuration")
@@ -326,6 +332,10 @@ class Sim:
     def step_info(self):
         s, k, _ = np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)
         return int(s), int(k)
+
+    def merged(self) -> int:
+        """Particles removed by merging so far."""
+        return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 32), dtype=np.int64)[3])
 
     def repacks(self) -> int:
         return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)[2])

@@ -109,6 +109,13 @@ const char* validate(const pic_config* c) {
     if (!(c->m > 0)) return "mass must be positive";
     if (c->capacity < 0 || c->capacity > (1LL << 31) - (1LL << 24)) return "bad capacity";
     if (c->chunk < 0) return "bad chunk";
+    if (c->merge_above < 0) return "bad merge_above";
+    if (c->merge_above > 0) {
+        if (!(c->merge_dp > 0) || !std::isfinite(c->merge_dp)) return "merge_dp must be positive";
+        long long cells = 1;
+        for (int a = 0; a < c->dims; a++) cells *= c->patch[a];
+        if (cells > kMergeCells) return "merging needs patches of at most 4096 cells";
+    }
     if (c->window) {
         if (!(c->ramp_len > 0)) return "ramp_len must be positive";
         for (int a = 0; a < c->dims; a++)
@@ -126,6 +133,8 @@ Layout plan(const pic_config* c, char* base) {
     S.prec = c->precision;
     S.window = c->window;
     S.mapping = c->mapping;
+    S.merge_above = c->merge_above;
+    S.merge_dp = c->merge_dp;
     for (int a = 0; a < 3; a++) {
         S.n[a] = a < c->dims ? c->n[a] : 1;
         S.P[a] = a < c->dims ? c->patch[a] : 1;
@@ -326,7 +335,7 @@ struct GraphOwner {
 // second branch) | (injection -> exchange) -> end of step.
 cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_patches,
                          int max_ncell, int max_column, int dims, int prec, int mapping,
-                         const int P[3], int grid, bool window) {
+                         const int P[3], int grid, bool window, bool merge) {
     cudaError_t e;
     if (!*o.cap0) {
         if ((e = cudaStreamCreateWithFlags(o.cap0, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -344,6 +353,7 @@ cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_pa
     if (le == cudaSuccess) le = cudaEventRecord(*o.ev_join, *o.cap1);
     if (le == cudaSuccess && window) le = launch_inject(db, nsims, max_column, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_exchange(db, nsims, max_patches, prec, *o.cap0);
+    if (le == cudaSuccess && merge) le = launch_merge(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_repack(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap0, *o.ev_join, 0);
     if (le == cudaSuccess) le = launch_end_step(db, nsims, max_patches, *o.cap0);
@@ -503,7 +513,7 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
     s->push_grid = push_grid_size(S.dims, S.prec, S.P, cfg->mapping == PIC_MAP_STATIC, S.npatch);
     GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
     if (capture_step(o, s->L.db, 1, S.npatch, (int)S.ncell, s->column_pts, S.dims, S.prec,
-                     S.mapping, S.P, s->push_grid, S.window != 0) != cudaSuccess)
+                     S.mapping, S.P, s->push_grid, S.window != 0, S.merge_above > 0) != cudaSuccess)
         return bail(PIC_ERR_CUDA);
     *out = s;
     return PIC_OK;
@@ -860,7 +870,12 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
             o[0] = st.step;
             o[1] = st.nshift;
             o[2] = st.nrepack;
-            if (written) *written = 3 * sizeof(long long);
+            size_t wb = 3 * sizeof(long long);
+            if (out_bytes >= 4 * sizeof(long long)) {
+                o[3] = st.nmerged;
+                wb = 4 * sizeof(long long);
+            }
+            if (written) *written = wb;
             return PIC_OK;
         }
         case PIC_DIAG_PARTICLES: {
@@ -949,6 +964,8 @@ extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) 
         if (e == cudaSuccess && S.window) e = launch_inject(s->L.db, 1, s->column_pts, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], s->stream);
         if (e == cudaSuccess) e = launch_exchange(s->L.db, 1, S.npatch, S.prec, s->stream);
+        if (e == cudaSuccess && S.merge_above > 0)
+            e = launch_merge(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
         if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
@@ -1092,9 +1109,11 @@ extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* de
     const int grid = push_grid_size(S0.dims, S0.prec, S0.P, sims[0]->cfg.mapping == PIC_MAP_STATIC,
                                     prefix[nsims]);
     GraphOwner o{&b->cap0, &b->cap1, &b->ev_fork, &b->ev_join, &b->graph, &b->gexec};
+    bool any_merge = false;
+    for (int i = 0; i < nsims; i++) any_merge = any_merge || hsims[i].merge_above > 0;
     if (e == cudaSuccess)
         e = capture_step(o, bl.db, nsims, max_patches, max_ncell, max_column, S0.dims, S0.prec,
-                         sims[0]->cfg.mapping, S0.P, grid, any_window);
+                         sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge);
     if (e != cudaSuccess) {
         destroy_graph_owner(o);
         delete b;

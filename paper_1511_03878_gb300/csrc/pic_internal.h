@@ -19,6 +19,7 @@ constexpr int kThreads = 256;    // threads per CTA of the particle kernel
 constexpr int kQueueThreads = 1024;
 constexpr int kBuckets = 64;     // remainder buckets of the approximate LPT order
 constexpr int kMailboxMin = 1024; // exchange-buffer slots per patch at least (a step's arrivals)
+constexpr int kMergeCells = 4096;  // largest patch (in cells) the merge kernel sorts
 constexpr int kSlotAlign = 32;    // per-patch particle and exchange-buffer bases are multiples
                                   // of this, so that a warp's particle loads start a line
 
@@ -43,6 +44,7 @@ struct StepState {
     int gen;            // field buffer generation read by the current step (step & 1)
     int repack;         // set by the exchange when a patch nears or exceeds its capacity
     int nrepack;        // repacks done
+    long long nmerged;  // particles removed by merging
 };
 
 struct SimDev {
@@ -67,6 +69,8 @@ struct SimDev {
     double c_id[3];
     float f_dt, f_dt_lo, f_id[3], f_id_lo[3];
     int cmax_exp;      // one particle's current contribution stays below 2^cmax_exp
+    int merge_above;   // load limiting: patches above this count are merged (0: off)
+    double merge_dp;   // momentum-bin width of the merge
     // fields
     void* F[2];      // [6][NZ][NY][NX]: Ex Ey Ez Bnx Bny Bnz (B^n for the push)
     void* H[2];      // [3][...]: B^{n+1/2}
@@ -137,6 +141,9 @@ cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int 
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
                        cudaStream_t s);
 cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cudaStream_t s);
+// load limiting by merging (no-op for sims with merge_above = 0)
+cudaError_t launch_merge(const BatchDev* bd, int nsims, int max_patches, int prec,
+                         cudaStream_t s);
 // 3D variants
 int push2d_smem(int prec, int P0, int P1);
 int push3d_smem(int prec, int P0, int P1, int P2);
