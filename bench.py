@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--chunk", type=int, default=0, help="queue chunk when not autotuned")
     ap.add_argument("--patch", default="", help="patch sides when not autotuned, e.g. 16,8,8")
+    ap.add_argument("--merge-above", type=int, default=0,
+                    help="load limiting: merge particle groups in patches above this count")
+    ap.add_argument("--merge-dp", type=float, default=0.05, help="merge momentum-bin width")
     ap.add_argument("--autotune", default="cached", choices=["cached", "on", "off"],
                     help="cached: the layouts recorded in the package's tuning table (measured "
                          "there when missing); on: measure again; off: workload patch, --chunk")
@@ -274,8 +277,10 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
     n = len(w["particles"]["x"])
     cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
-    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping)
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping,
+                      merge_above=args.merge_above, merge_dp=args.merge_dp)
     sim.load(w)
+    counts0 = sim.patch_counts()
     stream = sim.stream
     sim.step(W)
     sim.sync()
@@ -335,6 +340,14 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
                               "no capture of the current kernel sources in this layout")
     out = dict(ms=ms, pushes=pushes, pushes_all=pushes_all, n=n_push, profile={k: v / K for k, v in prof.items()},
                roofline=roof, push_ms=push_ms, repacks=repacks)
+    if args.merge_above > 0:
+        counts1 = sim.patch_counts()
+        out["merge"] = {"above": args.merge_above, "dp": args.merge_dp,
+                        "removed": sim.merged(),
+                        "particles_at_load": int(counts0.sum()), "particles_end": int(counts1.sum()),
+                        "max_over_mean_at_load": float(counts0.max() / counts0.mean()),
+                        "max_over_mean_end": float(counts1.max() / counts1.mean()),
+                        "max_patch_at_load": int(counts0.max()), "max_patch_end": int(counts1.max())}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -625,6 +638,8 @@ def main():
         "particles": main_run["n"],
         "capacity_repacks": main_run["repacks"],
     }
+    if "merge" in main_run:
+        line["merge"] = main_run["merge"]
     if variants:
         line["variants"] = {v: {
             "value": job_value(r["pushes_all"], r["ms"]),

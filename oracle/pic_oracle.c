@@ -40,6 +40,8 @@ struct orc_sim {
     double *x, *y, *z, *ux, *uy, *uz, *w;
     int* id;
     long long step, nshift, next_id;
+    long long* mlast;  /* per patch: count after its last merge pass (0 = none yet) */
+    long long mlast_n;
 };
 
 /* ------------------------------------------------------------------ helpers */
@@ -353,6 +355,7 @@ void orc_destroy(orc_sim* s) {
         free(s->J[a]);
     }
     free(s->rho_bg);
+    free(s->mlast);
     free(s->x);
     free(s->y);
     free(s->z);
@@ -369,6 +372,8 @@ int orc_set_particles(orc_sim* s, long long n, const double* x, const double* y,
                       const double* uz, const double* w, const int* id) {
     if (n < 0 || n > s->cap) return -1;
     s->np = n;
+    if (s->mlast)  /* a new particle set: no patch has been merged yet */
+        for (long long q = 0; q < s->mlast_n; q++) s->mlast[q] = 0;
     int maxid = -1;
     for (long long p = 0; p < n; p++) {
         s->x[p] = x[p];
@@ -701,12 +706,19 @@ long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) 
     long np_[3];
     for (int a = 0; a < 3; a++) np_[a] = a < c->dims ? c->n[a] / patch[a] : 1;
     const long long npatch = (long long)np_[0] * np_[1] * np_[2];
+    if (s->mlast_n != npatch) {
+        free(s->mlast);
+        s->mlast = (long long*)calloc((size_t)npatch, sizeof(long long));
+        s->mlast_n = s->mlast ? npatch : 0;
+        if (!s->mlast) return -1;
+    }
     long long* count = (long long*)calloc((size_t)npatch, sizeof(long long));
+    long long* prem = (long long*)calloc((size_t)npatch, sizeof(long long));
     long long* pidx = (long long*)malloc((size_t)(s->np > 0 ? s->np : 1) * sizeof(long long));
     long long* key = (long long*)malloc((size_t)(s->np > 0 ? s->np : 1) * 4 * sizeof(long long));
     unsigned char* keep = (unsigned char*)malloc((size_t)(s->np > 0 ? s->np : 1));
-    if (!count || !pidx || !key || !keep) {
-        free(count), free(pidx), free(key), free(keep);
+    if (!count || !prem || !pidx || !key || !keep) {
+        free(count), free(prem), free(pidx), free(key), free(keep);
         return -1;
     }
     for (long long p = 0; p < s->np; p++) {
@@ -723,6 +735,12 @@ long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) 
         key[4 * p + 3] = (long long)floor(s->uz[p] / dp);
         keep[p] = 1;
     }
+    /* a patch is merged when it holds more than `above` particles and more than 5/4 of
+     * its count after its previous merge pass (so a patch that merging cannot bring
+     * below the threshold is not reprocessed every step) */
+    unsigned char* hot = (unsigned char*)calloc((size_t)npatch, 1);
+    for (long long q = 0; q < npatch && hot; q++)
+        hot[q] = count[q] > above && count[q] > s->mlast[q] + s->mlast[q] / 4;
     /* plain grouping: for each unvisited particle of an overloaded patch, collect the
      * members sharing its cell and bin (quadratic, fine for an oracle) */
     unsigned char* seen = (unsigned char*)calloc((size_t)(s->np > 0 ? s->np : 1), 1);
@@ -730,9 +748,9 @@ long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) 
     double *gx = (double*)malloc((size_t)(s->np > 0 ? s->np : 1) * 4 * sizeof(double));
     int* gid = (int*)malloc((size_t)(s->np > 0 ? s->np : 1) * sizeof(int));
     long long removed = 0;
-    if (seen && mem && gx && gid) {
+    if (seen && mem && gx && gid && hot) {
         for (long long p = 0; p < s->np; p++) {
-            if (seen[p] || count[pidx[p]] <= above) continue;
+            if (seen[p] || !hot[pidx[p]]) continue;
             long long m = 0;
             for (long long q = p; q < s->np; q++) {
                 if (seen[q] || pidx[q] != pidx[p]) continue;
@@ -767,11 +785,15 @@ long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) 
                 s->w[q] = nw;
             }
             removed += m - 2;
+            prem[pidx[p]] += m - 2;
         }
         compact(s, keep);
+        for (long long q = 0; q < npatch; q++)
+            if (hot[q]) s->mlast[q] = count[q] - prem[q];
     } else {
         removed = -1;
     }
-    free(count), free(pidx), free(key), free(keep), free(seen), free(mem), free(gx), free(gid);
+    free(count), free(prem), free(pidx), free(key), free(keep), free(seen), free(mem), free(gx),
+        free(gid), free(hot);
     return removed;
 }

@@ -136,8 +136,11 @@ int orc_merge_group(long long n, const double* ux, const double* uy, const doubl
                     long long keep[2]);
 
 /* Merge every group (same cell, same momentum bin of width dp, N >= 3) inside each
- * patch (patch[a] cells per axis) holding more than `above` particles. Removed
- * particles are compacted away, order otherwise kept. Returns the number removed. */
+ * patch (patch[a] cells per axis) holding more than `above` particles and more than
+ * 5/4 of its count after its previous merge pass (the sim remembers that count per
+ * patch; an implementation choice, so that patches merging cannot bring below the
+ * threshold are not reprocessed every step). Removed particles are compacted away,
+ * order otherwise kept. Returns the number removed. */
 long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp);
 
 #ifdef __cplusplus

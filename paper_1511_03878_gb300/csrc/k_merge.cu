@@ -11,6 +11,9 @@
 // smallest-id member's momentum (a coordinate axis when those are parallel, that
 // momentum or the x axis when P = 0).
 //
+// A patch is merged when it holds more than merge_above particles and more than 5/4 of its
+// count after its previous merge pass (the oracle's rule), so that patches merging cannot
+// bring below the threshold are not reprocessed every step.
 // One CTA per overloaded patch (grid-stride over patches), at the end of the step after
 // the exchange: counting sort of the patch's slots by cell in shared memory, one thread
 // per cell sorts its slots by (momentum bin, id) and merges the groups, then the holes
@@ -129,7 +132,7 @@ __device__ void merge_one_group(const SimDev& S, const int* ord, int m) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) merge_kernel(const BatchDev* __restrict__ bd) {
+__global__ void __launch_bounds__(512) merge_kernel(const BatchDev* __restrict__ bd) {
     __shared__ int start[kMergeCells];
     __shared__ int cursor[kMergeCells];
     __shared__ int warp_sums[32];
@@ -148,7 +151,9 @@ __global__ void __launch_bounds__(256) merge_kernel(const BatchDev* __restrict__
     for (int p = blockIdx.x; p < S.npatch; p += gridDim.x) {
         __syncthreads();  // the previous patch's shared state is no longer read
         const int n = S.pcount[p];
-        if (n <= S.merge_above) continue;  // uniform over the CTA
+        // above the threshold and grown by a quarter since the patch's last merge pass
+        const int last = S.mlast[p];
+        if (n <= S.merge_above || n <= last + last / 4) continue;  // uniform over the CTA
         const int base = S.pbase[p];
         const int o[3] = {(p % S.np[0]) * S.P[0], ((p / S.np[0]) % S.np[1]) * S.P[1],
                           (p / (S.np[0] * S.np[1])) * S.P[2]};
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(256) merge_kernel(const BatchDev* __restrict__
         }
         __syncthreads();
         const int removed = s_removed;
+        if (tid == 0) S.mlast[p] = n - removed;
         if (removed == 0) continue;  // uniform
         // fill the holes below the new count with the live particles above it
         const int nn = n - removed;
@@ -261,7 +267,7 @@ cudaError_t launch_merge(const BatchDev* bd, int nsims, int max_patches, int pre
         if (nsm <= 0) nsm = 1;
     }
     dim3 grid(max_patches < 2 * nsm ? max_patches : 2 * nsm, nsims);
-    PIC_DISPATCH(prec, (merge_kernel<T><<<grid, 256, 0, s>>>(bd)));
+    PIC_DISPATCH(prec, (merge_kernel<T><<<grid, 512, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 

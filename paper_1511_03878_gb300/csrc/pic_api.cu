@@ -230,6 +230,7 @@ Layout plan(const pic_config* c, char* base) {
     S.mcap_new = cv.take<int>(S.npatch);
     S.mpend = cv.take<int>(S.npatch);
     S.mpoff = cv.take<int>(S.npatch);
+    S.mlast = cv.take<int>(S.npatch);
 
     BatchDev& B = L.B;
     B.nsims = 1;
@@ -682,6 +683,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     CK(cudaMemcpyAsync(S.mcap, mcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mcap");
     CK(cudaMemsetAsync(S.hcount, 0, pb, s->stream), "zero hcount");
     CK(cudaMemsetAsync(S.mcount, 0, pb, s->stream), "zero mcount");
+    CK(cudaMemsetAsync(S.mlast, 0, pb, s->stream), "zero mlast");
     // bound of one particle's current contribution (|cumulative DS| <= 1, |v| < 1):
     // sets the double-word fixed-point current scale
     {

@@ -103,6 +103,7 @@ struct SimDev {
     int* pbase_new; int* pcap_new; int* mbase_new; int* mcap_new;
     int* mpend;      // arrivals left in the exchange buffer for want of room (repack places them)
     int* mpoff;      // offset of the first of them in the patch's exchange buffer
+    int* mlast;      // per patch: count after its last merge pass (0 = none yet)
     // state and scratch
     StepState* st;
     int* status;

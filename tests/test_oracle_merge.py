@@ -151,3 +151,17 @@ def test_sim_merge_below_threshold_changes_nothing():
     i0 = np.argsort(p0["id"])
     for key in ("x", "y", "ux", "uy", "uz", "w"):
         assert np.array_equal(p1[key], p0[key][i0])
+
+
+def test_sim_merge_hysteresis():
+    """A patch merged once is not merged again until it grows past 5/4 of its count
+    after that pass, even while it stays above the threshold."""
+    c, o, p0 = _sim_with_hot_patch(seed=7)
+    first = o.merge((8, 8), above=200, dp=0.1)
+    n1 = o.num_particles()
+    hot = (o.get_particles()["x"] < 0.8) & (o.get_particles()["y"] < 0.8)
+    assert first > 0 and hot.sum() > 200  # still above the threshold
+    assert o.merge((8, 8), above=200, dp=0.1) == 0 and o.num_particles() == n1
+    # a fresh particle set clears the memory: the same merge happens again
+    o.set_particles(p0)
+    assert o.merge((8, 8), above=200, dp=0.1) == first
