@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--autotune", default="cached", choices=["cached", "on", "off"],
                     help="cached: the layouts recorded in the package's tuning table (measured "
                          "there when missing); on: measure again; off: workload patch, --chunk")
-    ap.add_argument("--workload", default="lwfa", choices=["lwfa", "stress3d", "thermal", "serve"])
+    ap.add_argument("--workload", default="lwfa",
+                    choices=["lwfa", "lwfa3d", "stress3d", "thermal", "serve"])
     ap.add_argument("--requests", type=int, default=256, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget")
@@ -103,6 +104,9 @@ def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20):
         return w
     if kind == "thermal":
         return inputs.thermal2d(seed=1511)
+    if kind == "lwfa3d":
+        # 512x128x128 window full of plasma, 2 particles per cell (16 777 216)
+        return inputs.lwfa3d(ramp_x0=-8.0, ppc=(2, 1, 1))
     # the window full of plasma: density ramp placed before x = 0
     return inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
 
@@ -484,6 +488,9 @@ def config_dict(args, precision):
     if args.workload == "stress3d":
         base = {"workload": "stress3d-256x128x128-lognormal1.5", "grid": [256, 128, 128],
                 "dx": 0.1, "particles": args.total}
+    elif args.workload == "lwfa3d":
+        base = {"workload": "lwfa3d-512x128x128-ppc2-fullwindow", "grid": [512, 128, 128],
+                "dx": 0.125, "dy": 0.5, "dz": 0.5, "particles_per_cell": 2, "laser_a0": 4.0}
     elif args.workload == "thermal":
         base = {"workload": "thermal2d-128x128-ppc16", "grid": [128, 128], "dx": 0.1,
                 "particles_per_cell": 16}

@@ -14,12 +14,15 @@ __device__ __forceinline__ long long pidx3(const SimDev& S, int i, int j, int k)
     return ((long long)(k + kGuard) * S.NY + (j + kGuard)) * S.NX + (i + kGuard);
 }
 
-// value at interior (i, j, k) and its periodic images in the guard cells
+// value at interior (i, j, k) and its periodic images in the guard cells (no x images
+// along a moving-window x axis, whose guards stay zero)
 template <typename T>
 __device__ __forceinline__ void put3d(const SimDev& S, T* a, int i, int j, int k, T v) {
     int xs[2] = {i + kGuard, -1}, ys[2] = {j + kGuard, -1}, zs[2] = {k + kGuard, -1};
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-    if (i == nx - 1) xs[1] = 0; else if (i == 0) xs[1] = nx + kGuard; else if (i == 1) xs[1] = nx + 1 + kGuard;
+    if (!S.window) {
+        if (i == nx - 1) xs[1] = 0; else if (i == 0) xs[1] = nx + kGuard; else if (i == 1) xs[1] = nx + 1 + kGuard;
+    }
     if (j == ny - 1) ys[1] = 0; else if (j == 0) ys[1] = ny + kGuard; else if (j == 1) ys[1] = ny + 1 + kGuard;
     if (k == nz - 1) zs[1] = 0; else if (k == 0) zs[1] = nz + kGuard; else if (k == 1) zs[1] = nz + 1 + kGuard;
 #pragma unroll
@@ -40,32 +43,43 @@ __global__ void __launch_bounds__(256) yee_e3d_kernel(const BatchDev* __restrict
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= S.ncell) return;
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    // output cell (ox, j, k) of the new frame; input cell i = ox + shift of the old one
+    const int ox = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
     const int g = S.st->gen;
+    const int i = ox + S.st->shift;
+    const bool win = S.window != 0;
     const long long fs = S.fstride;
     const T* Ein = reinterpret_cast<const T*>(S.F[g]);
     T* Eout = reinterpret_cast<T*>(S.F[1 - g]);
     const T* H = reinterpret_cast<const T*>(S.H[g]);
     const double* Jin = S.J[g];
     double* Jnext = S.J[1 - g];
-    const long long p = pidx3(S, i, j, k);
-    Jnext[p] = 0.0;
-    Jnext[fs + p] = 0.0;
-    Jnext[2 * fs + p] = 0.0;
-    const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
-    using C = FieldConst<T>;
-    const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
-    const T bx = H[p], by = H[fs + p], bz = H[2 * fs + p];
-    const T bx_jm = H[pidx3(S, i, jm, k)], bx_km = H[pidx3(S, i, j, km)];
-    const T by_im = H[fs + pidx3(S, im, j, k)], by_km = H[fs + pidx3(S, i, j, km)];
-    const T bz_im = H[2 * fs + pidx3(S, im, j, k)], bz_jm = H[2 * fs + pidx3(S, i, jm, k)];
-    const T ex = Ein[p] + dt * ((bz - bz_jm) * iy - (by - by_km) * iz - C::cur(Jin[p]));
-    const T ey = Ein[fs + p] + dt * ((bx - bx_km) * iz - (bz - bz_im) * ix - C::cur(Jin[fs + p]));
-    const T ez = Ein[2 * fs + p] +
-                 dt * ((by - by_im) * ix - (bx - bx_jm) * iy - C::cur(Jin[2 * fs + p]));
-    put3d(S, Eout, i, j, k, ex);
-    put3d(S, Eout + fs, i, j, k, ey);
-    put3d(S, Eout + 2 * fs, i, j, k, ez);
+    const long long po = pidx3(S, ox, j, k);
+    Jnext[po] = 0.0;
+    Jnext[fs + po] = 0.0;
+    Jnext[2 * fs + po] = 0.0;
+    T ex = T(0), ey = T(0), ez = T(0);
+    if (i < nx) {
+        const bool has_im = !(win && i == 0);
+        const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1,
+                  km = k == 0 ? nz - 1 : k - 1;
+        using C = FieldConst<T>;
+        const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
+        const long long p = pidx3(S, i, j, k);
+        const T bx = H[p], by = H[fs + p], bz = H[2 * fs + p];
+        const T bx_jm = H[pidx3(S, i, jm, k)], bx_km = H[pidx3(S, i, j, km)];
+        const T by_im = has_im ? H[fs + pidx3(S, im, j, k)] : T(0);
+        const T by_km = H[fs + pidx3(S, i, j, km)];
+        const T bz_im = has_im ? H[2 * fs + pidx3(S, im, j, k)] : T(0);
+        const T bz_jm = H[2 * fs + pidx3(S, i, jm, k)];
+        ex = Ein[p] + dt * ((bz - bz_jm) * iy - (by - by_km) * iz - C::cur(Jin[p]));
+        ey = Ein[fs + p] + dt * ((bx - bx_km) * iz - (bz - bz_im) * ix - C::cur(Jin[fs + p]));
+        ez = Ein[2 * fs + p] +
+             dt * ((by - by_im) * ix - (bx - bx_jm) * iy - C::cur(Jin[2 * fs + p]));
+    }
+    put3d(S, Eout, ox, j, k, ex);
+    put3d(S, Eout + fs, ox, j, k, ey);
+    put3d(S, Eout + 2 * fs, ox, j, k, ez);
 }
 
 template <typename T>
@@ -76,31 +90,46 @@ __global__ void __launch_bounds__(256) yee_b3d_kernel(const BatchDev* __restrict
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= S.ncell) return;
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    // output cell (ox, j, k): E^{n+1} is already in the new frame, B^{n+1/2} is read at
+    // i = ox + shift of the old one
+    const int ox = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
     const int g = S.st->gen;
+    const int i = ox + S.st->shift;
+    const bool win = S.window != 0;
     const long long fs = S.fstride;
     const T* E = reinterpret_cast<const T*>(S.F[1 - g]);
     T* Bn = reinterpret_cast<T*>(S.F[1 - g]) + 3 * fs;
     const T* H = reinterpret_cast<const T*>(S.H[g]);
     T* Hout = reinterpret_cast<T*>(S.H[1 - g]);
-    const long long p = pidx3(S, i, j, k);
-    const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1, kp = k == nz - 1 ? 0 : k + 1;
-    using C = FieldConst<T>;
-    const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
-    const T ex = E[p], ey = E[fs + p], ez = E[2 * fs + p];
-    const T ex_jp = E[pidx3(S, i, jp, k)], ex_kp = E[pidx3(S, i, j, kp)];
-    const T ey_ip = E[fs + pidx3(S, ip, j, k)], ey_kp = E[fs + pidx3(S, i, j, kp)];
-    const T ez_ip = E[2 * fs + pidx3(S, ip, j, k)], ez_jp = E[2 * fs + pidx3(S, i, jp, k)];
-    const T h0x = H[p], h0y = H[fs + p], h0z = H[2 * fs + p];
-    const T hx = h0x - dt * ((ez_jp - ez) * iy - (ey_kp - ey) * iz);
-    const T hy = h0y - dt * ((ex_kp - ex) * iz - (ez_ip - ez) * ix);
-    const T hz = h0z - dt * ((ey_ip - ey) * ix - (ex_jp - ex) * iy);
-    Hout[p] = hx;
-    Hout[fs + p] = hy;
-    Hout[2 * fs + p] = hz;
-    put3d(S, Bn, i, j, k, T(0.5) * (h0x + hx));
-    put3d(S, Bn + fs, i, j, k, T(0.5) * (h0y + hy));
-    put3d(S, Bn + 2 * fs, i, j, k, T(0.5) * (h0z + hz));
+    const long long po = pidx3(S, ox, j, k);
+    T hx = T(0), hy = T(0), hz = T(0), nbx = T(0), nby = T(0), nbz = T(0);
+    if (i < nx) {
+        const bool has_ip = !(win && ox + 1 >= nx);
+        const int ip = ox == nx - 1 ? 0 : ox + 1, jp = j == ny - 1 ? 0 : j + 1,
+                  kp = k == nz - 1 ? 0 : k + 1;
+        using C = FieldConst<T>;
+        const T dt = C::dt(S), ix = C::id(S, 0), iy = C::id(S, 1), iz = C::id(S, 2);
+        const T ex = E[po], ey = E[fs + po], ez = E[2 * fs + po];
+        const T ex_jp = E[pidx3(S, ox, jp, k)], ex_kp = E[pidx3(S, ox, j, kp)];
+        const T ey_ip = has_ip ? E[fs + pidx3(S, ip, j, k)] : T(0);
+        const T ey_kp = E[fs + pidx3(S, ox, j, kp)];
+        const T ez_ip = has_ip ? E[2 * fs + pidx3(S, ip, j, k)] : T(0);
+        const T ez_jp = E[2 * fs + pidx3(S, ox, jp, k)];
+        const long long p = pidx3(S, i, j, k);
+        const T h0x = H[p], h0y = H[fs + p], h0z = H[2 * fs + p];
+        hx = h0x - dt * ((ez_jp - ez) * iy - (ey_kp - ey) * iz);
+        hy = h0y - dt * ((ex_kp - ex) * iz - (ez_ip - ez) * ix);
+        hz = h0z - dt * ((ey_ip - ey) * ix - (ex_jp - ex) * iy);
+        nbx = T(0.5) * (h0x + hx);
+        nby = T(0.5) * (h0y + hy);
+        nbz = T(0.5) * (h0z + hz);
+    }
+    Hout[po] = hx;
+    Hout[fs + po] = hy;
+    Hout[2 * fs + po] = hz;
+    put3d(S, Bn, ox, j, k, nbx);
+    put3d(S, Bn + fs, ox, j, k, nby);
+    put3d(S, Bn + 2 * fs, ox, j, k, nbz);
 }
 
 cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,
@@ -150,7 +179,12 @@ __global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double 
             for (int b = 0; b < 3; b++) {
                 const int jj = wrapi(nd[1] + b - 1, n[1]);
                 for (int a = 0; a < 3; a++) {
-                    const int ii = wrapi(nd[0] + a - 1, n[0]);
+                    int ii = nd[0] + a - 1;
+                    if (S.window) {
+                        if (ii < 0 || ii >= n[0]) continue;  // outside the window
+                    } else {
+                        ii = wrapi(ii, n[0]);
+                    }
                     atomicAdd(rho + ((long long)kk * n[1] + jj) * n[0] + ii,
                               qw * Sw[0][a] * Sw[1][b] * Sw[2][c3]);
                 }
@@ -169,7 +203,8 @@ __global__ void gauss3d_kernel(const SimDev* __restrict__ sd) {
     const T* E = reinterpret_cast<const T*>(S.F[S.st->step & 1]);  // current time level
     const long long fs = S.fstride;
     const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
-    const double div = ((double)E[pidx3(S, i, j, k)] - (double)E[pidx3(S, im, j, k)]) / S.d[0] +
+    const double exm = (S.window && i == 0) ? 0.0 : (double)E[pidx3(S, im, j, k)];
+    const double div = ((double)E[pidx3(S, i, j, k)] - exm) / S.d[0] +
                        ((double)E[fs + pidx3(S, i, j, k)] - (double)E[fs + pidx3(S, i, jm, k)]) / S.d[1] +
                        ((double)E[2 * fs + pidx3(S, i, j, k)] - (double)E[2 * fs + pidx3(S, i, j, km)]) / S.d[2];
     S.rho[c] = div - S.rho[c] - S.rho_bg[c];

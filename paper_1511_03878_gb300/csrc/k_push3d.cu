@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
         const int p0[3] = {(patch % S.np[0]) * P[0], ((patch / S.np[0]) % S.np[1]) * P[1],
                            (patch / (S.np[0] * S.np[1])) * P[2]};
         const int gen = S.st->gen;
+        const int shift = S.st->shift;
+        const bool window = S.window != 0;
 
         T* Ft = reinterpret_cast<T*>(smem);
         const int fbytes = 6 * BXY * BZ * (int)sizeof(T);
@@ -341,21 +343,36 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                     }
                     }
                 }
-                    // periodic wrap and destination patch
+                    // boundaries and destination patch: periodic, except a moving-window x
+                    // axis (this step's shift applied, particles leaving [0, nx) absorbed)
+                    bool del = false;
+                    if (window) {
+                        if constexpr (is_f64<T>::value) {
+                            del = xin[0] < 0.0 || xin[0] >= (double)n[0];
+                            xin[0] -= (double)shift;
+                            del = del || xin[0] < 0.0;
+                        } else {
+                            del = icn[0] < 0 || icn[0] >= n[0];
+                            icn[0] -= shift;
+                            del = del || icn[0] < 0;
+                        }
+                    }
                     int dp_[3];
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         if constexpr (is_f64<T>::value) {
-                            if (xin[a] < 0.0) xin[a] += (double)n[a];
-                            if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
+                            if (!(window && a == 0)) {
+                                if (xin[a] < 0.0) xin[a] += (double)n[a];
+                                if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
+                            }
                             icn[a] = (int)floor(xin[a]);
-                        } else {
+                        } else if (!(window && a == 0)) {
                             icn[a] = wrapi(icn[a], n[a]);
                         }
                         dp_[a] = icn[a] / P[a];
                     }
-                    dest = dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
-                    leave = dest != patch;
+                    dest = del ? -1 : dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
+                    leave = del || dest != patch;
                     if (!leave) {
                         if constexpr (is_f64<T>::value) {
                             for (int a = 0; a < 3; a++)
@@ -426,7 +443,12 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
             const int tz = r / JXY;
             const int r2 = r - tz * JXY;
             const int ty = r2 / JX, tx = r2 - ty * JX;
-            const int gi = wrapi(p0[0] - 2 + tx, n[0]);
+            int gi = p0[0] - 2 + tx;
+            if (window) {
+                if (gi < 0 || gi >= n[0]) continue;  // outside the window: dropped
+            } else {
+                gi = wrapi(gi, n[0]);
+            }
             const int gj = wrapi(p0[1] - 2 + ty, n[1]);
             const int gk = wrapi(p0[2] - 2 + tz, n[2]);
             atomicAdd(Jg + comp * fs + ((long long)(gk + kGuard) * S.NY + (gj + kGuard)) * S.NX +

@@ -247,48 +247,58 @@ cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int 
 
 // ================================================================ moving-window injection
 
-// Lattice point t of the uncovered column (2D): row j varies fastest so that the
-// lanes of a warp sit in different cells (no shared-memory atomic collisions in the
-// next push). Lattice index (id offset) = (j * py + b) * px + a.
+// Lattice point t of the uncovered column (2D: ny cells, 3D: ny x nz cells): row j
+// varies fastest so that the lanes of a warp sit in different cells (no shared-memory
+// atomic collisions in the next push). Lattice index (id offset) =
+// (((k ny + j) pz + c) py + b) px + a, the oracle's order.
 template <typename T>
-__global__ void inject2d_kernel(const BatchDev* __restrict__ bd) {
+__global__ void inject_kernel(const BatchDev* __restrict__ bd) {
     const int sim = blockIdx.y;
     if (sim >= bd->nsims) return;
     const SimDev& S = bd->sims[sim];
     if (!S.window || !S.st->shift) return;
-    const int ny = S.n[1], nx = S.n[0];
-    const int px = S.ippc[0], py = S.ippc[1];
-    const int npts = ny * px * py;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool d3 = S.dims == 3;
+    const int nx = S.n[0], ny = S.n[1], nz = d3 ? S.n[2] : 1;
+    const int px = S.ippc[0], py = S.ippc[1], pz = d3 ? S.ippc[2] : 1;
+    const long long npts = (long long)ny * nz * px * py * pz;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= npts) return;
-    const int j = t % ny;
-    const int r = t / ny;
-    const int b = r % py;
-    const int a = r / py;
-    const double dx = S.d[0], dy = S.d[1];
+    const int j = (int)(t % ny);
+    long long r = t / ny;
+    const int k = (int)(r % nz);
+    r /= nz;
+    const int cz = (int)(r % pz);
+    r /= pz;
+    const int b = (int)(r % py);
+    const int a = (int)(r / py);
+    const double dx = S.d[0];
     const double xw = ((double)(nx - 1) + ((double)a + 0.5) / px) * dx;
     const double xl = xw + (double)(S.st->nshift + 1) * dx;
     double f = (xl - S.ramp_x0) / S.ramp_len;
     f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
     const double dens = S.n0 * f;
     if (!(dens > 0.0)) return;
-    const double wgt = dens * (dx * dy) / ((double)px * py * 1.0);
-    const long long lat = ((long long)j * py + b) * px + a;
-    const int dest = ((nx - 1) / S.P[0]) + S.np[0] * (j / S.P[1]);
+    const double dV = dx * S.d[1] * (d3 ? S.d[2] : 1.0);
+    const double wgt = dens * dV / ((double)px * py * pz);
+    const long long lat = ((((long long)k * ny + j) * pz + cz) * py + b) * px + a;
+    const int dest = ((nx - 1) / S.P[0]) + S.np[0] * (j / S.P[1] + S.np[1] * (k / S.P[2]));
     const int slot = atomicAdd(S.mcount + dest, 1);
     if (slot >= S.mcap[dest]) {
         atomicOr(S.status, ST_MAILBOX);
         return;
     }
     const int m = S.mbase[dest] + slot;
-    const double ox = ((double)a + 0.5) / px, oy = ((double)b + 0.5) / py;
+    const double ox = ((double)a + 0.5) / px, oy = ((double)b + 0.5) / py,
+                 oz = ((double)cz + 0.5) / pz;
     if constexpr (is_f64<T>::value) {
         reinterpret_cast<double*>(S.mxi[0])[m] = (double)(nx - 1) + ox;
         reinterpret_cast<double*>(S.mxi[1])[m] = (double)j + oy;
+        if (d3) reinterpret_cast<double*>(S.mxi[2])[m] = (double)k + oz;
     } else {
-        S.mcell[m] = (nx - 1) | (j << 16);
+        S.mcell[m] = d3 ? ((nx - 1) | (j << 11) | (k << 22)) : ((nx - 1) | (j << 16));
         reinterpret_cast<T*>(S.mxi[0])[m] = T(ox);
         reinterpret_cast<T*>(S.mxi[1])[m] = T(oy);
+        if (d3) reinterpret_cast<T*>(S.mxi[2])[m] = T(oz);
     }
     reinterpret_cast<T*>(S.mu[0])[m] = T(0);
     reinterpret_cast<T*>(S.mu[1])[m] = T(0);
@@ -301,7 +311,7 @@ cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int
                           cudaStream_t s) {
     if (max_column_pts <= 0) return cudaSuccess;
     dim3 grid((max_column_pts + 255) / 256, nsims);
-    PIC_DISPATCH(prec, (inject2d_kernel<T><<<grid, 256, 0, s>>>(bd)));
+    PIC_DISPATCH(prec, (inject_kernel<T><<<grid, 256, 0, s>>>(bd)));
     return cudaGetLastError();
 }
 

@@ -101,7 +101,6 @@ const char* validate(const pic_config* c) {
         return "2D patch tile does not fit in shared memory";
     if (c->dims == 3) {
         if (c->n[0] > 2048 || c->n[1] > 2048 || c->n[2] > 1024) return "3D grid too large";
-        if (c->window) return "the moving window is 2D only";
         if (push3d_smem(c->precision, c->patch[0], c->patch[1], c->patch[2]) > 227 * 1024)
             return "3D patch tile does not fit in shared memory";
     }
@@ -493,7 +492,9 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     s->L = plan(cfg, s->arena);
     const SimDev& S = s->L.S;
-    s->column_pts = cfg->window ? S.n[1] * S.ippc[0] * S.ippc[1] : 0;
+    s->column_pts = cfg->window ? S.n[1] * S.ippc[0] * S.ippc[1] *
+                                      (S.dims == 3 ? S.n[2] * S.ippc[2] : 1)
+                                : 0;
     auto bail = [&](pic_status st) {
         GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
         destroy_graph_owner(o);

@@ -113,6 +113,66 @@ def lwfa2d(nx: int = 2048, ny: int = 512, dx: float = 0.125, dy: float = 0.5,
     return dict(params=params, particles=parts, E=E, B=B)
 
 
+def _lattice_3d(nx, ny, nz, d, ppc):
+    """Positions of a ppc lattice in every cell of an nx x ny x nz grid at offsets
+    (a + 1/2)/ppc; ordered (k, j, c, b, i, a) as ids."""
+    px, py, pz = ppc
+    offs = [(np.arange(p) + 0.5) / p for p in ppc]
+    k, j, c, b, i, a = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(pz), np.arange(py),
+                                   np.arange(nx), np.arange(px), indexing="ij")
+    x = (i + offs[0][a]) * d[0]
+    y = (j + offs[1][b]) * d[1]
+    z = (k + offs[2][c]) * d[2]
+    return x.ravel(), y.ravel(), z.ravel()
+
+
+def laser_profile3d(x, y, z, a0, w0, tau, xc, yc, zc):
+    """The pulse of laser_profile with a round transverse Gaussian in (y, z)."""
+    r2 = (y - yc) ** 2 + (z - zc) ** 2
+    return (a0 * np.exp(-r2 / w0 ** 2) * np.exp(-2.0 * math.log(2.0) * (x - xc) ** 2 / tau ** 2)
+            * np.cos(x - xc))
+
+
+def lwfa3d(nx: int = 512, ny: int = 128, nz: int = 128, dx: float = 0.125,
+           dy: float = 0.5, ppc=(1, 1, 1), n0: float = 0.01, ramp_cells: int = 32,
+           a0: float = 4.0, w0: float = 15.0, tau: float = 10.0, laser_back: float = 24.0,
+           ramp_x0: float | None = None, seed: int = 1514, cfl: float = 0.95,
+           patch=(16, 8, 8)) -> dict:
+    """3D LWFA in a moving window (the 3D counterpart of lwfa2d): cold electrons on a
+    ppc lattice with the density ramp, a round Gaussian pulse polarised along y
+    (E_y at t = 0 on (i, j+1/2, k), B_z at t = +dt/2 on (i+1/2, j+1/2, k))."""
+    dz = dy
+    d = (dx, dy, dz)
+    dt = cfl_dt(d, cfl)
+    Lx, Ly, Lz = nx * dx, ny * dy, nz * dz
+    xc, yc, zc = Lx - laser_back, Ly / 2.0, Lz / 2.0
+    if ramp_x0 is None:
+        ramp_x0 = xc
+    ramp_len = ramp_cells * dx
+    x, y, z = _lattice_3d(nx, ny, nz, d, ppc)
+    dens = n0 * np.clip((x - ramp_x0) / ramp_len, 0.0, 1.0)
+    keep = dens > 0.0
+    x, y, z, dens = x[keep], y[keep], z[keep], dens[keep]
+    n = x.size
+    w = dens * dx * dy * dz / (ppc[0] * ppc[1] * ppc[2])
+    kk = np.arange(nz, dtype=np.float64)[:, None, None]
+    jj = np.arange(ny, dtype=np.float64)[None, :, None]
+    ii = np.arange(nx, dtype=np.float64)[None, None, :]
+    Ey = laser_profile3d(ii * dx, (jj + 0.5) * dy, kk * dz, a0, w0, tau, xc, yc, zc)
+    Bz = laser_profile3d((ii + 0.5) * dx - 0.5 * dt, (jj + 0.5) * dy, kk * dz, a0, w0, tau,
+                         xc, yc, zc)
+    shp = (nz, ny, nx)
+    E = [np.zeros(shp), np.ascontiguousarray(np.broadcast_to(Ey, shp)), np.zeros(shp)]
+    B = [np.zeros(shp), np.zeros(shp), np.ascontiguousarray(np.broadcast_to(Bz, shp))]
+    params = dict(dims=3, n=(nx, ny, nz), d=d, dt=dt, window=True, q=-1.0, m=1.0, n0=n0,
+                  ramp_x0=float(ramp_x0), ramp_len=ramp_len, inject_ppc=tuple(ppc),
+                  patch=tuple(patch), seed=seed, a0=a0, w0=w0, tau=tau, xc=xc,
+                  name=f"lwfa3d-{nx}x{ny}x{nz}-ppc{ppc[0] * ppc[1] * ppc[2]}")
+    parts = dict(x=x, y=y, z=z, ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n), w=w,
+                 id=np.arange(n, dtype=np.int32))
+    return dict(params=params, particles=parts, E=E, B=B)
+
+
 def lognormal_counts(n_patch: int, total: int, sigma: float, rng) -> np.ndarray:
     """Per-patch counts ~ LogNormal(0, sigma) scaled to `total` by largest remainder."""
     L = rng.lognormal(0.0, sigma, size=n_patch)

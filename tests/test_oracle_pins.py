@@ -461,3 +461,50 @@ def test_window_drops_particles_leaving_left_edge():
     assert s.num_particles() == n0
     assert q["x"].min() >= 0.0
     assert q["id"].max() == n0 + 16 * 4 - 1
+
+
+def test_window_3d_translation_injection_and_ids():
+    """3D moving window: fields after a shifting step are a field-only Yee step then a
+    pure translation; the uncovered x column (ny x nz cells) gets the injected lattice
+    with the lab-frame weight; particles leaving x < 0 drop; ids continue from the
+    largest one."""
+    w = inputs.lwfa3d(nx=32, ny=8, nz=8, ppc=(2, 1, 2), laser_back=6.0, w0=3.0, tau=3.0,
+                      ramp_cells=4, ramp_x0=-100.0, patch=(8, 8, 8))
+    p = w["params"]
+    c = orc.make_config(3, p["n"], p["d"], p["dt"], window=True, n0=p["n0"],
+                        ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"], inject_ppc=p["inject_ppc"])
+    dx = p["d"][0]
+    steps = next(n for n in range(1, 10) if orc.shift_count(c, n) == 1)
+    assert orc.shift_count(c, steps - 1) == 0 and steps == math.floor(dx / p["dt"]) + 1
+    # fields: no particles
+    s = orc.OracleSim(c, 100000)
+    s.set_particles({k: np.zeros(0) for k in orc.PARTICLE_KEYS} | {"id": np.zeros(0, np.int32)})
+    s.set_fields(w["E"], w["B"])
+    E = [e.copy() for e in w["E"]]
+    B = [b.copy() for b in w["B"]]
+    for _ in range(steps):
+        orc.yee_e(c, E, B, [np.zeros_like(E[0])] * 3)
+        orc.yee_b(c, E, B)
+    s.step(steps)
+    assert s.shifts == 1
+    f = s.get_fields()
+    for a, k in enumerate(("Ex", "Ey", "Ez")):
+        assert np.array_equal(f[k][:, :, :-1], E[a][:, :, 1:]) and np.all(f[k][:, :, -1] == 0)
+    for a, k in enumerate(("Bx", "By", "Bz")):
+        assert np.array_equal(f[k][:, :, :-1], B[a][:, :, 1:])
+    q = s.get_particles()
+    assert len(q["x"]) == 8 * 8 * 4  # ny * nz * (2 * 1 * 2)
+    assert np.allclose(np.sort(np.unique(q["x"])), (31 + np.array([0.25, 0.75])) * dx)
+    assert np.allclose(np.sort(np.unique(q["z"])), (np.arange(8)[:, None] + np.array([0.25, 0.75])).ravel() * p["d"][2])
+    assert np.allclose(q["w"], p["n0"] * dx * p["d"][1] * p["d"][2] / 4)
+    assert np.array_equal(np.sort(q["id"]), np.arange(len(q["x"])))
+    # with plasma: the left column leaves, a new one enters, ids continue
+    s2 = orc.OracleSim(c, 200000)
+    s2.set_particles(w["particles"])
+    s2.set_fields([np.zeros_like(e) for e in w["E"]], [np.zeros_like(b) for b in w["B"]])
+    n0 = s2.num_particles()
+    assert n0 == 32 * 8 * 8 * 4
+    s2.step(steps)
+    q2 = s2.get_particles()
+    assert s2.num_particles() == n0 and q2["x"].min() >= 0.0
+    assert q2["id"].max() == n0 + 8 * 8 * 4 - 1
