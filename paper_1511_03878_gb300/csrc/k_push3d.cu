@@ -27,10 +27,14 @@ __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, 
     return r;
 }
 
+// double-word: compensated dot products, the three z planes in a rolled loop (the plane
+// weight rotating through registers) to keep the kernel's code within the
+// instruction cache
 __device__ __forceinline__ df64 gather27(const df64* __restrict__ f, int BX, int BXY,
                                         const df64 Sx[3], const df64 Sy[3], const df64 Sz[3]) {
     Dot2 outer;
-#pragma unroll
+    df64 z0 = Sz[0], z1 = Sz[1], z2 = Sz[2];
+#pragma unroll 1
     for (int c = 0; c < 3; c++) {
         Dot2 plane;
 #pragma unroll
@@ -42,7 +46,8 @@ __device__ __forceinline__ df64 gather27(const df64* __restrict__ f, int BX, int
             inner.add(Sx[2], row[2]);
             plane.add(Sy[b], inner.result());
         }
-        outer.add(Sz[c], plane.result());
+        outer.add(z0, plane.result());
+        z0 = z1, z1 = z2;
     }
     return outer.result();
 }
@@ -91,20 +96,42 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
     for (int a = 0; a < 3; a++) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
         const T c1 = q[a] * DS[a][0], c2 = q[a] * (DS[a][0] + DS[a][1]);
+        if constexpr (std::is_same<T, df64>::value) {
+            // rolled over kc, the c-axis weights rotating through registers
+            T s0 = S0[c][0], s1 = S0[c][1], s2 = S0[c][2];
+            T d0 = DS[c][0], d1_ = DS[c][1], d2 = DS[c][2];
+#pragma unroll 1
+            for (int kc = 0; kc < 3; kc++) {
 #pragma unroll
-        for (int kc = 0; kc < 3; kc++)
-#pragma unroll
-            for (int kb = 0; kb < 3; kb++) {
-                const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
-                JT* p = jt[a] + kb * st[b] + kc * st[c];
-                jatomic(p, jprod<JT>(c1, A));
-                jatomic(p + st[a], jprod<JT>(c2, A));
+                for (int kb = 0; kb < 3; kb++) {
+                    const T A = wa[b][kb] * s0 + wb[b][kb] * d0;
+                    JT* p = jt[a] + kb * st[b] + kc * st[c];
+                    jatomic(p, jprod<JT>(c1, A));
+                    jatomic(p + st[a], jprod<JT>(c2, A));
+                }
+                s0 = s1, s1 = s2, d0 = d1_, d1_ = d2;
             }
+        } else {
+#pragma unroll
+            for (int kc = 0; kc < 3; kc++)
+#pragma unroll
+                for (int kb = 0; kb < 3; kb++) {
+                    const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
+                    JT* p = jt[a] + kb * st[b] + kc * st[c];
+                    jatomic(p, jprod<JT>(c1, A));
+                    jatomic(p + st[a], jprod<JT>(c2, A));
+                }
+        }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 1)
+#ifndef PIC_DF64_3D_MINB
+#define PIC_DF64_3D_MINB 1
+#endif
+__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
+                                                ? 2
+                                                : (std::is_same<T, df64>::value ? PIC_DF64_3D_MINB : 1))
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType3D<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -247,12 +274,35 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                 }
                 T E[3], B[3];
                 // Ex (d,p,p) Ey (p,d,p) Ez (p,p,d) Bx (p,d,d) By (d,p,d) Bz (d,d,p)
+                if constexpr (std::is_same<T, df64>::value) {
+                    // one rolled loop over the six components; results rotate
+                    T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
+#pragma unroll 1
+                    for (int c = 0; c < 6; c++) {
+                        const bool xd = c == 0 || c == 4 || c == 5;
+                        const bool yd = c == 1 || c == 3 || c == 5;
+                        const bool zd = c == 2 || c == 3 || c == 4;
+                        T sx[3], sy[3], sz[3];
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            sx[k] = xd ? Sd[0][k] : Sp[0][k];
+                            sy[k] = yd ? Sd[1][k] : Sp[1][k];
+                            sz[k] = zd ? Sd[2][k] : Sp[2][k];
+                        }
+                        const T g = gather27(Ft + c * BXY * BZ + (zd ? td[2] : tp[2]) * BXY +
+                                                 (yd ? td[1] : tp[1]) * BX + (xd ? td[0] : tp[0]),
+                                             BX, BXY, sx, sy, sz);
+                        r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5, r5 = g;
+                    }
+                    E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
+                } else {
                 E[0] = gather27(Ft + 0 * BXY * BZ + tp[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sp[2]);
                 E[1] = gather27(Ft + 1 * BXY * BZ + tp[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sp[2]);
                 E[2] = gather27(Ft + 2 * BXY * BZ + td[2] * BXY + tp[1] * BX + tp[0], BX, BXY, Sp[0], Sp[1], Sd[2]);
                 B[0] = gather27(Ft + 3 * BXY * BZ + td[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sd[2]);
                 B[1] = gather27(Ft + 4 * BXY * BZ + td[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sd[2]);
                 B[2] = gather27(Ft + 5 * BXY * BZ + tp[2] * BXY + td[1] * BX + td[0], BX, BXY, Sd[0], Sd[1], Sp[2]);
+                }
                 const T ig = boris(eps, E, B, u);
                 const T v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
                 int np1[3], sh[3];
@@ -330,6 +380,22 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;
+                        if constexpr (std::is_same<T, df64>::value) {
+                            T s0 = ax[c].S0[0], s1 = ax[c].S0[1], s2 = ax[c].S0[2], s3 = ax[c].S0[3];
+                            T d0 = ax[c].DS[0], d1 = ax[c].DS[1], d2 = ax[c].DS[2], d3 = ax[c].DS[3];
+#pragma unroll 1
+                            for (int kc = 0; kc < 4; kc++) {
+#pragma unroll
+                                for (int kb = 0; kb < 4; kb++) {
+                                    const T A = wa[b][kb] * s0 + wb[b][kb] * d0;
+                                    JT* p = jt + kb * st3[b] + kc * st3[c];
+                                    jatomic(p, jprod<JT>(c1, A));
+                                    jatomic(p + st3[a], jprod<JT>(c2, A));
+                                    jatomic(p + 2 * st3[a], jprod<JT>(c3, A));
+                                }
+                                s0 = s1, s1 = s2, s2 = s3, d0 = d1, d1 = d2, d2 = d3;
+                            }
+                        } else {
 #pragma unroll
                         for (int kc = 0; kc < 4; kc++)
 #pragma unroll
@@ -340,6 +406,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                                 jatomic(p + st3[a], jprod<JT>(c2, A));
                                 jatomic(p + 2 * st3[a], jprod<JT>(c3, A));
                             }
+                        }
                     }
                     }
                 }

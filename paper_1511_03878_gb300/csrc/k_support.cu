@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) exchange_kernel(const BatchDev* __restric
         S.mpoff[p] = nm;
         const int nn = n - nh + nm;
         // ask for a repack before a patch or its exchange buffer runs out
-        if (pend > 0 || nn > cap - cap / 8 - 16 || S.mcount[p] > mc / 2) atomicOr(&S.st->repack, 1);
+        if (pend > 0 || nn > cap - cap / 8 - 16 || S.mcount[p] > mc / 4) atomicOr(&S.st->repack, 1);
         s_n = n;
         s_nh = nh;
         s_nm = nm;
@@ -480,7 +480,13 @@ __global__ void __launch_bounds__(1024) repack_plan_kernel(const BatchDev* __res
             const int c = S.pcount[p] + S.mpend[p];
             const double share = N > 0 ? 0.5 * (double)c / (double)N + 0.5 / S.npatch : 1.0 / S.npatch;
             cap = (int)align_slots(c + (long long)floor(spare * share));
-            mc = (int)align_slots(cap / 4 > kMailboxMin ? cap / 4 : kMailboxMin);
+            // exchange buffer: half the capacity, at least kMailboxMin, and at least four
+            // times the arrivals of this step (placed + pending): a patch flooded from
+            // denser neighbours gets room even while its own count is still small, and the
+            // arrivals may grow fourfold before the next repack (triggered at a quarter)
+            const int arr = S.mpoff[p] + S.mpend[p];
+            mc = cap / kMailboxDiv > kMailboxMin ? cap / kMailboxDiv : kMailboxMin;
+            mc = (int)align_slots(mc > 4 * arr ? mc : 4 * arr);
         }
         int tot, mtot;
         const int ex = block_exclusive_scan(cap, warp_sums, &tot);

@@ -212,7 +212,9 @@ Layout plan(const pic_config* c, char* base) {
     S.mbase = cv.take<int>(S.npatch);
     S.mcap = cv.take<int>(S.npatch);
     S.mcount = cv.take<int>(S.npatch);
-    S.mtotal = cap / 4 + (long long)(kMailboxMin + kSlotAlign) * S.npatch;
+    // exchange-buffer slots: room for the per-patch minimum, half of every capacity and
+    // for the arrival-driven enlargements a repack may grant
+    S.mtotal = cap + (long long)(kMailboxMin + kSlotAlign) * S.npatch;
     S.mcell = c->precision != PIC_FP64 ? cv.take<int>(S.mtotal) : nullptr;
     for (int a = 0; a < 3; a++) S.mxi[a] = a < c->dims ? cv.take<char>(S.mtotal * es) : nullptr;
     for (int a = 0; a < 3; a++) S.mu[a] = cv.take<char>(S.mtotal * es);
@@ -572,7 +574,7 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         pcap[p] = (int)c;
         pbase[p] = (int)acc;
         acc += c;
-        mcap[p] = (int)align_slots(std::max(kMailboxMin, pcap[p] / 4));
+        mcap[p] = (int)align_slots(std::max(kMailboxMin, pcap[p] / kMailboxDiv));
         mbase[p] = (int)macc;
         macc += mcap[p];
     }

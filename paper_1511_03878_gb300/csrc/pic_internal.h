@@ -19,6 +19,9 @@ constexpr int kThreads = 256;    // threads per CTA of the particle kernel
 constexpr int kQueueThreads = 1024;
 constexpr int kBuckets = 64;     // remainder buckets of the approximate LPT order
 constexpr int kMailboxMin = 1024; // exchange-buffer slots per patch at least (a step's arrivals)
+constexpr int kMailboxDiv = 2;    // exchange-buffer slots per patch: capacity / kMailboxDiv
+                                  // (a compressed 3D LWFA patch took in more than 1/4 of its
+                                  // capacity in one step)
 constexpr int kMergeCells = 4096;  // largest patch (in cells) the merge kernel sorts
 constexpr int kSlotAlign = 32;    // per-patch particle and exchange-buffer bases are multiples
                                   // of this, so that a warp's particle loads start a line
