@@ -350,8 +350,8 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     xi0 = nx0;
                     eta0 = ny0;
                     const double fxd = floor(xi0), fyd = floor(eta0);
-                    ix = (int)fxd;
-                    iy = (int)fyd;
+                    ix = floor_to_int(xi0);
+                    iy = floor_to_int(eta0);
                     fx = xi0 - fxd;
                     fy = eta0 - fyd;
                 } else {
@@ -363,7 +363,12 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             }
             if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
             // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
-            const bool hx = fx >= T(0.5), hy = fy >= T(0.5);
+            bool hx, hy;
+            if constexpr (is_f64<T>::value) {
+                hx = ge_half(fx), hy = ge_half(fy);  // 0 <= f < 1
+            } else {
+                hx = fx >= T(0.5), hy = fy >= T(0.5);
+            }
             const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
             const T dxp = hx ? fx - T(1) : fx, dyp = hy ? fy - T(1) : fy;
             const T dxd = fx - T(0.5), dyd = fy - T(0.5);
@@ -420,9 +425,10 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 if constexpr (is_f64<T>::value) {
                     xi1 = xi0 + dtdx * vx;
                     eta1 = eta0 + dtdy * vy;
-                    const double nx1d = floor(xi1 + 0.5), ny1d = floor(eta1 + 0.5);
-                    nxp1 = (int)nx1d;
-                    nyp1 = (int)ny1d;
+                    const double hx1 = xi1 + 0.5, hy1 = eta1 + 0.5;
+                    const double nx1d = floor(hx1), ny1d = floor(hy1);
+                    nxp1 = floor_to_int(hx1);
+                    nyp1 = floor_to_int(hy1);
                     dxp1 = xi1 - nx1d;
                     dyp1 = eta1 - ny1d;
                 } else {
@@ -482,18 +488,21 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 // ---- D. boundaries and destination patch
                 bool del = false;
                 if constexpr (is_f64<T>::value) {
+                    // the comparisons with 0 and n are taken on integer floors (the
+                    // same decisions as comparing the doubles, off the FP64 pipe)
+                    const int fxi = floor_to_int(xi1);
                     double xs = xi1 - (double)shift;
                     if (window) {
-                        del = xi1 < 0.0 || xi1 >= (double)nx || xs < 0.0;
+                        del = fxi < 0 || fxi >= nx || fxi - shift < 0;
                     } else {
-                        if (xs < 0.0) xs += (double)nx;
-                        if (xs >= (double)nx) xs -= (double)nx;
+                        if (fxi - shift < 0) xs += (double)nx;
+                        if (floor_to_int(xs) >= nx) xs -= (double)nx;
                     }
-                    if (eta1 < 0.0) eta1 += (double)ny;
-                    if (eta1 >= (double)ny) eta1 -= (double)ny;
+                    if (floor_to_int(eta1) < 0) eta1 += (double)ny;
+                    if (floor_to_int(eta1) >= ny) eta1 -= (double)ny;
                     xi1 = xs;
-                    ix1 = (int)floor(xi1);
-                    iy1 = (int)floor(eta1);
+                    ix1 = floor_to_int(xi1);
+                    iy1 = floor_to_int(eta1);
                 } else {
                     if (window) {
                         del = ix1 < 0 || ix1 >= nx;

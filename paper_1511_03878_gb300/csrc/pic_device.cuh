@@ -246,6 +246,23 @@ __device__ __forceinline__ double widen_f32(float f) {
 }
 __device__ __forceinline__ double widen_f32(double d) { return d; }
 
+// floor(x) as an int with integer operations only (|x| < 2^30): keeps the rounding and
+// the conversion off the FP64 pipe, which the FP64 particle kernel is bound by
+__device__ __forceinline__ int floor_to_int(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;  // unbiased exponent
+    const bool neg = b < 0;
+    if (e < 0) return (neg && (b & 0x7FFFFFFFFFFFFFFFLL) != 0) ? -1 : 0;  // |x| < 1
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = 52 - e;
+    long long ip = m >> sh;  // integer part of |x|
+    if (neg) ip = ((ip << sh) != m) ? -(ip + 1) : -ip;
+    return (int)ip;
+}
+// x >= 1/2 for x >= 0, from the high word (0.5 = 0x3FE00000 00000000)
+__device__ __forceinline__ bool ge_half(double x) { return __double2hiint(x) >= 0x3FE00000; }
+__device__ __forceinline__ bool ge_half(float x) { return x >= 0.5f; }
+
 // double -> float rounded to nearest even with integer operations only when the result
 // is a normal float or zero (the conversion instruction runs on the FP64 pipe); other
 // values take the conversion instruction
