@@ -18,7 +18,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
                      "-I", INCLUDE, "-I", CSRC]
 
 
@@ -56,7 +56,7 @@ def build(force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + ".tmp"
-    subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)
+    subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + objs)
     os.replace(tmp, LIB)
     return LIB
 

@@ -11,7 +11,9 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "df64.cuh"
@@ -523,6 +525,31 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
     return PIC_OK;
 }
 
+// Host threads of the particle load: binning and laying out millions of particles is
+// the bulk of loading a sim, and it splits into independent ranges.
+static int load_threads(long long n) {
+    if (n < (1LL << 16)) return 1;
+    const unsigned hc = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hc == 0 ? 4u : hc, 32u));
+}
+
+// f(begin, end, t) on nt contiguous ranges of [0, n), in parallel
+template <typename F>
+static void parallel_ranges(long long n, int nt, F&& f) {
+    if (nt <= 1) {
+        f(0LL, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    const long long chunk = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; t++) {
+        const long long b = std::min(n, (long long)t * chunk), e = std::min(n, b + chunk);
+        th.emplace_back([&f, b, e, t] { f(b, e, t); });
+    }
+    for (auto& x : th) x.join();
+}
+
 extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* x,
                                          const double* y, const double* z, const double* ux,
                                          const double* uy, const double* uz, const double* w,
@@ -536,32 +563,61 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     CK(cudaStreamSynchronize(s->stream), "sync before load");
     const int dims = S.dims;
     const double* pos[3] = {x, y, z};
+    const int nt = load_threads(n);
     std::vector<int> ip(n * 3);
     std::vector<double> xi(n * 3);
     std::vector<int> patch(n);
+    // per-thread patch counts, largest id and first invalid particle (index, code)
+    std::vector<std::vector<int>> tcount(nt, std::vector<int>(S.npatch, 0));
+    std::vector<int> tmaxid(nt, -1);
+    std::vector<long long> tbad(nt, -1);
+    std::vector<int> tcode(nt, 0);
+    parallel_ranges(n, nt, [&](long long b, long long e, int t) {
+        std::vector<int>& cnt = tcount[t];
+        int mid = -1;
+        for (long long p = b; p < e; p++) {
+            int pc[3] = {0, 0, 0};
+            int code = 0;
+            for (int a = 0; a < dims && !code; a++) {
+                const double v = pos[a][p];
+                const double L = S.n[a] * S.d[a];
+                if (!std::isfinite(v) || v < 0.0 || v >= L) {
+                    code = 1;
+                    break;
+                }
+                double c = v / S.d[a];
+                if (c >= (double)S.n[a]) c = std::nextafter((double)S.n[a], 0.0);
+                const int i = (int)std::floor(c);
+                xi[p * 3 + a] = c;
+                ip[p * 3 + a] = i;
+                pc[a] = i / S.P[a];
+            }
+            if (!code && (!std::isfinite(ux[p]) || !std::isfinite(uy[p]) ||
+                          !std::isfinite(uz[p]) || !std::isfinite(w[p])))
+                code = 2;
+            if (!code && id[p] < 0) code = 3;
+            if (code) {
+                tbad[t] = p;
+                tcode[t] = code;
+                return;  // the first invalid particle of this range
+            }
+            mid = std::max(mid, id[p]);
+            patch[p] = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
+            cnt[patch[p]]++;
+        }
+        tmaxid[t] = mid;
+    });
+    for (int t = 0; t < nt; t++) {  // the first invalid particle overall
+        if (tbad[t] < 0) continue;
+        if (tcode[t] == 1) return fail(&s->err, PIC_ERR_INVALID, "particle position outside the grid");
+        if (tcode[t] == 2) return fail(&s->err, PIC_ERR_NUMERIC, "non-finite particle momentum or weight");
+        return fail(&s->err, PIC_ERR_INVALID, "negative particle id");
+    }
     std::vector<int> counts(S.npatch, 0);
     int maxid = -1;
-    for (long long p = 0; p < n; p++) {
-        int pc[3] = {0, 0, 0};
-        for (int a = 0; a < dims; a++) {
-            const double v = pos[a][p];
-            const double L = S.n[a] * S.d[a];
-            if (!std::isfinite(v) || v < 0.0 || v >= L)
-                return fail(&s->err, PIC_ERR_INVALID, "particle position outside the grid");
-            double c = v / S.d[a];
-            if (c >= (double)S.n[a]) c = std::nextafter((double)S.n[a], 0.0);
-            const int i = (int)std::floor(c);
-            xi[p * 3 + a] = c;
-            ip[p * 3 + a] = i;
-            pc[a] = i / S.P[a];
-        }
-        if (!std::isfinite(ux[p]) || !std::isfinite(uy[p]) || !std::isfinite(uz[p]) ||
-            !std::isfinite(w[p]))
-            return fail(&s->err, PIC_ERR_NUMERIC, "non-finite particle momentum or weight");
-        if (id[p] < 0) return fail(&s->err, PIC_ERR_INVALID, "negative particle id");
-        maxid = std::max(maxid, id[p]);
-        patch[p] = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
-        counts[patch[p]]++;
+    for (int t = 0; t < nt; t++) {
+        maxid = std::max(maxid, tmaxid[t]);
+        for (int p = 0; p < S.npatch; p++) counts[p] += tcount[t][p];
     }
     // per-patch capacity: the free slots are shared half by count, half evenly; every
     // capacity is rounded up to kSlotAlign so that all bases stay aligned
@@ -580,103 +636,89 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     }
     if (acc > S.capacity || macc > S.mtotal)
         return fail(&s->err, PIC_ERR_CAPACITY, "capacity split failed");
-    // stable binning, then a fixed pseudo-random order inside each patch so that the
-    // lanes of a warp rarely share a cell (spreads shared-memory atomics)
-    std::vector<long long> order(n);
+    // stable binning (thread t's particles of patch p follow those of threads < t), then
+    // a fixed pseudo-random order inside each patch so that the lanes of a warp rarely
+    // share a cell (spreads shared-memory atomics)
+    std::vector<long long> order(n), start(S.npatch);
     {
-        std::vector<long long> cursor(S.npatch);
         long long a = 0;
         for (int p = 0; p < S.npatch; p++) {
-            cursor[p] = a;
+            start[p] = a;
             a += counts[p];
         }
-        std::vector<long long> start(cursor);
-        for (long long p = 0; p < n; p++) order[cursor[patch[p]]++] = p;
-#ifdef PIC_ORDER_ROUNDS
-        // cell rounds: the r-th particle of every cell, cells x fastest, then r + 1, ...
-        const int pcells = S.P[0] * S.P[1] * S.P[2];
-        std::vector<int> ccount(pcells), cstart(pcells);
-        std::vector<long long> tmp;
+        std::vector<std::vector<long long>> cursor(nt, std::vector<long long>(S.npatch));
         for (int p = 0; p < S.npatch; p++) {
-            const long long b0 = start[p], c = counts[p];
-            if (c == 0) continue;
-            const int px0 = (p % S.np[0]) * S.P[0], py0 = ((p / S.np[0]) % S.np[1]) * S.P[1],
-                      pz0 = (p / (S.np[0] * S.np[1])) * S.P[2];
-            auto lcell = [&](long long q) {
-                const int i = ip[q * 3] - px0, j = ip[q * 3 + 1] - py0,
-                          k = dims == 3 ? ip[q * 3 + 2] - pz0 : 0;
-                return (k * S.P[1] + j) * S.P[0] + i;
-            };
-            std::fill(ccount.begin(), ccount.end(), 0);
-            for (long long k = 0; k < c; k++) ccount[lcell(order[b0 + k])]++;
-            int acc2 = 0, maxc = 0;
-            for (int q = 0; q < pcells; q++) {
-                cstart[q] = acc2;
-                acc2 += ccount[q];
-                maxc = std::max(maxc, ccount[q]);
-            }
-            tmp.assign(c, 0);
-            {
-                std::vector<int> cur(cstart);
-                for (long long k = 0; k < c; k++) tmp[cur[lcell(order[b0 + k])]++] = order[b0 + k];
-            }
-            long long o = b0;
-            for (int r = 0; r < maxc; r++)
-                for (int q = 0; q < pcells; q++)
-                    if (ccount[q] > r) order[o++] = tmp[cstart[q] + r];
-        }
-#else
-        for (int p = 0; p < S.npatch; p++) {
-            const long long b0 = start[p], c = counts[p];
-            for (long long k = c - 1; k > 0; k--) {
-                const long long r = (long long)(mix64(((uint64_t)p << 32) ^ (uint64_t)k) % (uint64_t)(k + 1));
-                std::swap(order[b0 + k], order[b0 + r]);
+            long long c = start[p];
+            for (int t = 0; t < nt; t++) {
+                cursor[t][p] = c;
+                c += tcount[t][p];
             }
         }
-#endif
+        parallel_ranges(n, nt, [&](long long b, long long e, int t) {
+            std::vector<long long>& cur = cursor[t];
+            for (long long p = b; p < e; p++) order[cur[patch[p]]++] = p;
+        });
+        parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
+            for (long long p = pb0; p < pb1; p++) {
+                const long long b0 = start[p], c = counts[p];
+                for (long long k = c - 1; k > 0; k--) {
+                    const long long r =
+                        (long long)(mix64(((uint64_t)p << 32) ^ (uint64_t)k) % (uint64_t)(k + 1));
+                    std::swap(order[b0 + k], order[b0 + r]);
+                }
+            }
+        });
     }
+    // device-layout host arrays (capacity slots; empty slots id -1), filled per patch
     const size_t es = elem_size(S.prec);
     const long long cap = S.capacity;
-    std::vector<char> hx[3], hu[3], hw;
-    std::vector<int> hid(cap, -1), hcell;
-    for (int a = 0; a < dims; a++) hx[a].assign(cap * es, 0);
-    for (int a = 0; a < 3; a++) hu[a].assign(cap * es, 0);
-    hw.assign(cap * es, 0);
-    if (S.prec != PIC_FP64) hcell.assign(cap, 0);
-    {
-        long long k = 0;
-        for (int p = 0; p < S.npatch; p++) {
-            for (int c = 0; c < counts[p]; c++, k++) {
-                const long long src = order[k];
-                const long long dst = pbase[p] + c;
-                const double uu[3] = {ux[src], uy[src], uz[src]};
+    std::unique_ptr<char[]> hx[3], hu[3], hw(new char[cap * es]);
+    std::unique_ptr<int[]> hid(new int[cap]), hcell;
+    for (int a = 0; a < dims; a++) hx[a].reset(new char[cap * es]);
+    for (int a = 0; a < 3; a++) hu[a].reset(new char[cap * es]);
+    if (S.prec != PIC_FP64) hcell.reset(new int[cap]);
+    parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
+        for (long long p = pb0; p < pb1; p++) {
+            const long long lo = pbase[p], hi = p + 1 < S.npatch ? pbase[p + 1] : cap;
+            for (long long c = 0; c < counts[p]; c++) {
+                const long long src = order[start[p] + c];
+                const long long dst = lo + c;
                 if (S.prec == PIC_FP64) {
                     for (int a = 0; a < dims; a++)
-                        reinterpret_cast<double*>(hx[a].data())[dst] = xi[src * 3 + a];
+                        reinterpret_cast<double*>(hx[a].get())[dst] = xi[src * 3 + a];
                 } else {
                     int cellv = 0;
                     for (int a = 0; a < dims; a++) {
                         const int i = ip[src * 3 + a];
                         const double f = cell_offset(S.prec, xi[src * 3 + a] - (double)i);
-                        store_real(S.prec, hx[a].data(), dst, f);
+                        store_real(S.prec, hx[a].get(), dst, f);
                         cellv |= i << (dims == 2 ? 16 * a : 11 * a);
                     }
                     hcell[dst] = cellv;
                 }
-                for (int a = 0; a < 3; a++) store_real(S.prec, hu[a].data(), dst, uu[a]);
-                store_real(S.prec, hw.data(), dst, w[src]);
+                store_real(S.prec, hu[0].get(), dst, ux[src]);
+                store_real(S.prec, hu[1].get(), dst, uy[src]);
+                store_real(S.prec, hu[2].get(), dst, uz[src]);
+                store_real(S.prec, hw.get(), dst, w[src]);
                 hid[dst] = id[src];
             }
+            // the patch's free slots (and the tail after the last patch)
+            const long long f0 = lo + counts[p];
+            for (int a = 0; a < dims; a++) std::memset(hx[a].get() + f0 * es, 0, (hi - f0) * es);
+            for (int a = 0; a < 3; a++) std::memset(hu[a].get() + f0 * es, 0, (hi - f0) * es);
+            std::memset(hw.get() + f0 * es, 0, (hi - f0) * es);
+            std::memset(hid.get() + f0, 0xFF, (hi - f0) * sizeof(int));  // id -1
+            if (hcell) std::memset(hcell.get() + f0, 0, (hi - f0) * sizeof(int));
         }
-    }
+    });
     for (int a = 0; a < dims; a++)
-        CK(cudaMemcpyAsync(S.xi[a], hx[a].data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy x");
+        CK(cudaMemcpyAsync(S.xi[a], hx[a].get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy x");
     for (int a = 0; a < 3; a++)
-        CK(cudaMemcpyAsync(S.u[a], hu[a].data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy u");
-    CK(cudaMemcpyAsync(S.w, hw.data(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy w");
-    CK(cudaMemcpyAsync(S.id, hid.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream), "copy id");
+        CK(cudaMemcpyAsync(S.u[a], hu[a].get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy u");
+    CK(cudaMemcpyAsync(S.w, hw.get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy w");
+    CK(cudaMemcpyAsync(S.id, hid.get(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream), "copy id");
     if (S.prec != PIC_FP64)
-        CK(cudaMemcpyAsync(S.cell, hcell.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream),
+        CK(cudaMemcpyAsync(S.cell, hcell.get(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream),
            "copy cell");
     const size_t pb = S.npatch * sizeof(int);
     CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
