@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         const int base = pb + item.z;
         const int cnt = item.w;
         // fixed-point exponent of the double-word current tile for this item
-        const int jk = item_fixed_exp(cnt, S.cmax_exp);
+        const int jk = item_fixed_exp<JT>(cnt, S.cmax_exp);
         const float jsc = pow2f(jk);
         const T* W = reinterpret_cast<const T*>(S.w);
         T* U0 = reinterpret_cast<T*>(S.u[0]);

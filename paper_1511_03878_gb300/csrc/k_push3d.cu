@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
         const int pb = S.pbase[patch];
         const int base = pb + item.z;
         const int cnt = item.w;
-        const int jk = item_fixed_exp(cnt, S.cmax_exp);
+        const int jk = item_fixed_exp<JT>(cnt, S.cmax_exp);
         const float jsc = pow2f(jk);
         T* U0 = reinterpret_cast<T*>(S.u[0]);
         T* U1 = reinterpret_cast<T*>(S.u[1]);

@@ -172,9 +172,18 @@ template <>
 struct JType<double> {
     using type = long long;  // int64 fixed point: FP64 shared atomics run on the FP64 pipe
 };
+#ifndef PIC_F32_FIXED_TILE
+#define PIC_F32_FIXED_TILE 1
+#endif
 template <>
 struct JType<float> {
+#if PIC_F32_FIXED_TILE
+    // int32 fixed point: shared-memory int32 atomics run at 3.4x the rate of FP32 ones on
+    // this GPU (measured: 3.1e12 vs 0.91e12 random-address adds per second)
+    using type = int;
+#else
     using type = float;
+#endif
 };
 template <>
 struct JType<df64> {
@@ -197,10 +206,12 @@ struct JType3D<double> {
 #endif
 
 // fixed-point exponent of an item of `count` particles: a tile entry sums at most
-// `count` contributions, each below 2^cmax_exp, and must stay below 2^62
+// `count` contributions, each below 2^cmax_exp, and must stay below 2^62 (int64 tile)
+// or 2^30 (int32 tile)
+template <typename JT>
 __device__ __forceinline__ int item_fixed_exp(int count, int cmax_exp) {
     const int lg = 32 - __clz(count > 1 ? count - 1 : 1);  // ceil(log2(count))
-    int k = 61 - cmax_exp - lg;
+    int k = (sizeof(JT) == 4 ? 30 : 61) - cmax_exp - lg;
     return k < -120 ? -120 : (k > 120 ? 120 : k);
 }
 
@@ -340,6 +351,10 @@ template <>
 __device__ __forceinline__ long long jprod<long long, double>(double a, double b) {
     return f64_to_fixed(a * b);
 }
+template <>
+__device__ __forceinline__ int jprod<int, float>(float a, float b) {
+    return __float2int_rn(a * b);
+}
 // charge factor scaled for the tile: exact power-of-two scaling for a fixed-point tile,
 // unchanged for a floating-point one
 template <typename JT, typename T>
@@ -354,8 +369,13 @@ template <>
 __device__ __forceinline__ double jscale<long long, double>(double q, float scale) {
     return q * (double)scale;
 }
+template <>
+__device__ __forceinline__ float jscale<int, float>(float q, float scale) {
+    return q * scale;
+}
 __device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void jatomic(int* p, int v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(long long* p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
@@ -363,6 +383,7 @@ __device__ __forceinline__ void jatomic(long long* p, long long v) {
 __device__ __forceinline__ double jflush(float v, int) { return widen_f32(v); }
 __device__ __forceinline__ double jflush(double v, int) { return v; }
 __device__ __forceinline__ double jflush(long long v, int k) { return fixed_to_f64(v, k); }
+__device__ __forceinline__ double jflush(int v, int k) { return fixed_to_f64((long long)v, k); }
 
 
 // Esirkepov data of one axis on a four-node window that always holds both the old

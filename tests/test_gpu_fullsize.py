@@ -123,7 +123,11 @@ def stress_full():
     return w, expect, scale, rho_max
 
 
-@pytest.mark.parametrize("prec,tol_j,tol_g", [("fp64", 1e-12, 1e-12), ("fp32", 1e-7, 1e-6)])
+# FP32 accumulates each work item's current in an int32 fixed-point tile whose quantum is
+# 2^(lg(items) - 30) of the bound on one contribution (items of 8192 particles here):
+# the current sum stays at ~4e-8 and the Gauss-law drift at ~1.3e-6 of max rho (it was
+# 6e-9 with an FP32 float tile, 2.1x slower)
+@pytest.mark.parametrize("prec,tol_j,tol_g", [("fp64", 1e-12, 1e-12), ("fp32", 1e-7, 5e-6)])
 def test_stress3d_full_size_invariants(binding, stress_full, prec, tol_j, tol_g):
     w, expect, scale, rho_max = stress_full
     P = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32}[prec]
