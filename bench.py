@@ -57,8 +57,10 @@ def bytes_per_push(dt, w):
     return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
 # kernels per step: queue build, push, [window injection], exchange, repack plan and its
 # two copy kernels (which return at once unless a patch needs room), Yee E, Yee B, end
-def kernels_per_step(window: bool) -> int:
-    return 10 if window else 9
+def kernels_per_step(window: bool, merge: bool = False) -> int:
+    """Kernels in one captured step: queue build, push, 2 Yee, exchange, repack plan + 2
+    copies, end step; injection with the window; the merge kernel with load limiting."""
+    return (10 if window else 9) + (1 if merge else 0)
 
 
 def parse():
@@ -91,6 +93,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--trace-steps", type=int, default=0,
+                    help="after the timed runs, step one more sim this many steps and record "
+                         "the time per step and the patch-load spread along the run")
+    ap.add_argument("--trace-every", type=int, default=100, help="trace window in steps")
     return ap.parse_args()
 
 
@@ -271,6 +277,46 @@ def job_value(pushes_all_ranks, ms_slowest):
     return pushes_all_ranks / (ms_slowest * 1e-3)
 
 
+def trace_run(args, w, precision, chunk):
+    """Time per step and patch-load spread along one long run (ablation of the mapping).
+
+    Every `trace_every` steps: the mean ms per step of that window (CUDA events on the
+    sim's stream), max/mean particles per patch at its end, and the particle count. The
+    patch-count read syncs between windows, so these rows are not the bench's value."""
+    import torch
+
+    from paper_1511_03878_gb300 import binding
+
+    prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
+    n = len(w["particles"]["x"])
+    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
+    mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
+    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping,
+                      merge_above=args.merge_above, merge_dp=args.merge_dp)
+    rows = []
+    try:
+        sim.load(w)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        done = 0
+        while done < args.trace_steps:
+            k = min(args.trace_every, args.trace_steps - done)
+            ev0.record(sim.stream)
+            sim.step(k)
+            ev1.record(sim.stream)
+            ev1.synchronize()
+            done += k
+            c = sim.patch_counts().astype(np.float64)
+            rows.append([done, round(ev0.elapsed_time(ev1) / k, 4),
+                         round(float(c.max() / max(c.mean(), 1e-30)), 3), int(c.sum())])
+        sim.sync()
+    finally:
+        sim.close()
+    return {"precision": precision, "mapping": args.mapping, "every": args.trace_every,
+            "columns": ["step", "ms_per_step", "max_over_mean_patch", "particles"],
+            "rows": rows}
+
+
 def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
     """Returns timing + roofline of one precision on this rank's GPU."""
     import torch
@@ -390,24 +436,52 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
                 d2h=d2h / K, seconds=seconds)
 
 
-def oracle_rate(w, seconds_budget, max_steps=50):
-    """Pushes/s of the FP64 CPU oracle (single thread, as it stands) on a bounded
-    number of steps of the same workload."""
+def oracle_sim(w, steps):
+    """The FP64 CPU oracle loaded with workload `w`, with particle room for `steps`
+    steps of window injection (at most one column of cells per step)."""
     import oracle as orc
 
     p = w["params"]
-    n_all = len(w["particles"]["x"])
-    if n_all > 5_000_000:  # bounded sample: every k-th particle of the same grid
-        k = -(-n_all // 5_000_000)
-        w = dict(w, particles={key: v[::k].copy() for key, v in w["particles"].items()})
     dims = p["dims"]
-    c = orc.make_config(dims, p["n"][:dims], p["d"][:dims], p["dt"], window=p["window"], q=p["q"],
-                        m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
-                        inject_ppc=p["inject_ppc"])
-    n = len(w["particles"]["x"])
-    o = orc.OracleSim(c, n + 2 * (max_steps + 2) * p["n"][1] * 4)
+    c = orc.make_config(dims, p["n"][:dims], p["d"][:dims], p["dt"], window=p["window"],
+                        q=p["q"], m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"],
+                        ramp_len=p["ramp_len"], inject_ppc=p["inject_ppc"])
+    col = (int(np.prod(p["n"][1:dims])) * int(np.prod(p["inject_ppc"][:dims]))
+           if p["window"] else 0)
+    o = orc.OracleSim(c, len(w["particles"]["x"]) + (steps + 2) * col)
     o.set_particles(w["particles"])
     o.set_fields(w["E"], w["B"])
+    return o
+
+
+def oracle_sample(args, frac):
+    """The bench's workload cut to about `frac` of its particles, for a bounded CPU
+    timing sample: fewer transverse rows of the window (LWFA, so that the injected
+    columns shrink with it), or every k-th particle of the same grid (thermal, 3D
+    stress). Returns the workload and a description of the cut."""
+    w = workload(args.nx, args.ny, args.workload, args.total)
+    if frac >= 1.0:
+        return w, "the full workload"
+    if args.workload == "lwfa":
+        ny = max(32, int(args.ny * frac) // 32 * 32)
+        return workload(args.nx, ny, "lwfa"), f"{args.nx}x{ny} rows of the window"
+    if args.workload == "lwfa3d":
+        from paper_1511_03878_gb300 import inputs
+
+        side = max(16, int(128 * math.sqrt(frac)) // 8 * 8)
+        return (inputs.lwfa3d(ny=side, nz=side, ramp_x0=-8.0, ppc=(2, 1, 1)),
+                f"512x{side}x{side} cells of the window")
+    k = max(1, int(round(1.0 / frac)))
+    w = dict(w, particles={key: v[::k].copy() for key, v in w["particles"].items()})
+    return w, f"one particle in {k} on the same grid"
+
+
+def oracle_rate(args, n_full, seconds_budget, max_steps=50):
+    """Pushes/s of the FP64 CPU oracle (single thread, as it stands) on a bounded
+    number of steps of the same workload (at most 5M particles of it)."""
+    w, what = oracle_sample(args, min(1.0, 5e6 / n_full))
+    n = len(w["particles"]["x"])
+    o = oracle_sim(w, max_steps)
     t0 = time.perf_counter()
     o.step(1)
     t1 = time.perf_counter()
@@ -422,62 +496,50 @@ def oracle_rate(w, seconds_budget, max_steps=50):
         steps += budget_steps
         pushes += n1 * budget_steps
         t1 = t1 + (t3 - t2)
-    return pushes / (t1 - t0), steps, n
+    return pushes / (t1 - t0), steps, n, what
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.nx, args.ny, args.workload, args.total)
     import oracle as orc
 
     orc.build()
-    p = w["params"]
-    n = len(w["particles"]["x"])
-    c = orc.make_config(p["dims"], p["n"][:p["dims"]], p["d"][:p["dims"]], p["dt"],
-                        window=p["window"], q=p["q"],
-                        m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
-                        inject_ppc=p["inject_ppc"])
+    n_full = len(workload(args.nx, args.ny, args.workload, args.total)["particles"]["x"])
     total = args.steps + args.warmup
-    o = orc.OracleSim(c, n + 4 * (total + 2) * p["n"][1] * 4)
-    o.set_particles(w["particles"])
-    o.set_fields(w["E"], w["B"])
+    # each step is a bounded sample: a cut of the same workload (at most 5M particles,
+    # fewer if K+W steps would exceed about three minutes), timed after one probe step
+    frac = min(1.0, 5e6 / n_full)
+    w, what = oracle_sample(args, frac)
+    o = oracle_sim(w, total)
     t0 = time.perf_counter()
     o.step(1)
     t_step = time.perf_counter() - t0
-    # each step is a bounded sample: fewer rows of the same window if K+W full steps
-    # would exceed about three minutes
-    frac = min(1.0, 180.0 / max(total * t_step, 1e-9))
-    sample = "full window"
-    if frac < 1.0:
-        ny = max(32, int(p["n"][1] * frac) // 32 * 32)
-        w = workload(args.nx, ny, args.workload, args.total)
-        p = w["params"]
-        n = len(w["particles"]["x"])
-        c = orc.make_config(p["dims"], p["n"][:p["dims"]], p["d"][:p["dims"]], p["dt"],
-                        window=p["window"], q=p["q"],
-                            m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"], ramp_len=p["ramp_len"],
-                            inject_ppc=p["inject_ppc"])
-        o = orc.OracleSim(c, n + 4 * (total + 2) * p["n"][1] * 4)
-        o.set_particles(w["particles"])
-        o.set_fields(w["E"], w["B"])
-        sample = f"{args.nx}x{ny} rows of the window ({n} particles)"
-    o.step(max(0, args.warmup - 1))
+    done = 1
+    need = min(1.0, 180.0 / max(total * t_step, 1e-9))
+    if need < 1.0:
+        w, what = oracle_sample(args, frac * need)
+        o = oracle_sim(w, total)
+        done = 0
+    n = len(w["particles"]["x"])
+    o.step(max(0, args.warmup - done))
     n0 = o.num_particles()
     t0 = time.perf_counter()
     o.step(args.steps)
     el = time.perf_counter() - t0
     n1 = o.num_particles()
     value = args.steps * 0.5 * (n0 + n1) / el
+    name = config_dict(args, "fp64")["workload"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded LWFA-shaped initial condition)",
+        "data": "synthetic (seeded, shaped like the paper's runs)",
         "config": config_dict(args, "fp64"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 C oracle, single thread, {sample}, {args.steps} steps"},
+                         "sample": f"FP64 C oracle, single thread, {what} of {name} "
+                                   f"({n} particles), {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -486,7 +548,7 @@ def reference_arm(args):
 def config_dict(args, precision):
     """The workload (the same for both arms); the launch layout is reported apart."""
     if args.workload == "stress3d":
-        base = {"workload": "stress3d-256x128x128-lognormal1.5", "grid": [256, 128, 128],
+        base = {"workload": f"stress3d-256x128x128-lognormal1.5-n{args.total}", "grid": [256, 128, 128],
                 "dx": 0.1, "particles": args.total}
     elif args.workload == "lwfa3d":
         base = {"workload": "lwfa3d-512x128x128-ppc2-fullwindow", "grid": [512, 128, 128],
@@ -616,12 +678,15 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, wm, args.precision, args.steps, chunk_m, world)
+    trace = None
+    if rank == 0 and args.trace_steps > 0:
+        trace = trace_run(args, wm, args.precision, chunk_m)
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        rate, steps, n = oracle_rate(w, args.cpu_seconds)
+        rate, steps, n, what = oracle_rate(args, len(w["particles"]["x"]), args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, single thread, {steps} steps of the same "
-                         f"LWFA window ({n} particles)"}
+               "sample": f"FP64 C oracle, single thread, {steps} steps of {what} of "
+                         f"{config_dict(args, 'fp64')['workload']} ({n} particles)"}
     if rank != 0:
         return
     value = job_value(main_run["pushes_all"], main_run["ms"])
@@ -639,7 +704,8 @@ def main():
         "e2e": ({"value": e2e["value"], "unit": UNIT,
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
                 if e2e else None),
-        "gpu_launches": kernels_per_step(bool(w["params"].get("window"))) * args.steps,
+        "gpu_launches": kernels_per_step(bool(w["params"].get("window")),
+                                         args.merge_above > 0) * args.steps,
         "clocks": clocks.summary(),
         "kernel_ms_per_step": main_run["profile"],
         "particles": main_run["n"],
@@ -647,6 +713,8 @@ def main():
     }
     if "merge" in main_run:
         line["merge"] = main_run["merge"]
+    if trace is not None:
+        line["trace"] = trace
     if variants:
         line["variants"] = {v: {
             "value": job_value(r["pushes_all"], r["ms"]),

@@ -1,0 +1,45 @@
+"""Host logic of bench.py that needs no GPU: launch counts and the CPU timing samples."""
+import types
+
+import bench
+
+
+def test_kernels_per_step_counts_injection_and_merge():
+    assert bench.kernels_per_step(False) == 9
+    assert bench.kernels_per_step(True) == 10
+    assert bench.kernels_per_step(False, True) == 10
+    assert bench.kernels_per_step(True, True) == 11
+
+
+def _args(**kw):
+    a = dict(nx=2048, ny=512, workload="lwfa", total=64 * 2 ** 20)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+def test_oracle_sample_cuts_rows_of_the_window():
+    w, what = bench.oracle_sample(_args(nx=64, ny=256), 0.25)
+    assert list(w["params"]["n"][:2]) == [64, 64]
+    assert "64x64 rows" in what
+
+
+def test_oracle_sample_thins_particles_on_the_same_grid():
+    full, _ = bench.oracle_sample(_args(workload="thermal"), 1.0)
+    w, what = bench.oracle_sample(_args(workload="thermal"), 0.25)
+    assert list(w["params"]["n"]) == list(full["params"]["n"])
+    assert len(w["particles"]["x"]) == len(full["particles"]["x"]) // 4
+    assert "one particle in 4" in what
+
+
+def test_oracle_sim_has_room_for_the_injected_columns():
+    import oracle as orc
+
+    orc.build()
+    from paper_1511_03878_gb300 import inputs
+
+    w = inputs.lwfa2d(nx=64, ny=32, ramp_x0=-8.0, patch=(16, 16))
+    o = bench.oracle_sim(w, 12)
+    n0 = o.num_particles()
+    o.step(12)  # the window shifts about 11 times, dropping and injecting a column each time
+    assert o.shifts >= 10
+    assert abs(o.num_particles() - n0) <= 32 * 4
