@@ -52,6 +52,7 @@ class OrcConfig(ctypes.Structure):
         ("ramp_x0", ctypes.c_double),
         ("ramp_len", ctypes.c_double),
         ("inject_ppc", ctypes.c_int * 3),
+        ("order", ctypes.c_int),
     ]
 
 
@@ -115,8 +116,10 @@ def _arr_ptrs(arrs):
 
 
 def make_config(dims, n, d, dt, window=False, q=-1.0, m=1.0, n0=0.0, ramp_x0=0.0,
-                ramp_len=1.0, inject_ppc=(1, 1, 1)) -> OrcConfig:
+                ramp_len=1.0, inject_ppc=(1, 1, 1), order=2) -> OrcConfig:
+    """`order`: 2 for Yee's solver, 6 for sixth-order staggered space derivatives."""
     c = OrcConfig()
+    c.order = int(order)
     c.dims = dims
     n = list(n) + [1] * (3 - len(n))
     d = list(d) + [1.0] * (3 - len(d))

@@ -251,22 +251,70 @@ void orc_rho(const orc_config* c, long long n, const double* x, const double* y,
 
 /* ------------------------------------------------------------------ Yee */
 
+/* Coefficients c_l of the staggered first difference of the configured order.
+ * Order 2: c_1 = 1 (Yee 1966). Order 6: the c_l solving
+ *   sum_l c_l (2l - 1)^(2m+1) = [m == 0],  m = 0, 1, 2,
+ * i.e. the Taylor conditions that make the difference exact up to degree 6:
+ * 75/64, -25/384, 3/640. Returns the number of terms. */
+static int stag_coef(const orc_config* c, const double** coef) {
+    static const double C2[1] = {1.0};
+    static const double C6[3] = {75.0 / 64.0, -25.0 / 384.0, 3.0 / 640.0};
+    if (c->order == 6) {
+        *coef = C6;
+        return 3;
+    }
+    *coef = C2;
+    return 1;
+}
+
+/* d/dx_a of F at the integer position (i, j, k) from values at the half-integer
+ * positions below it: F stored at index m sits at m + 1/2 along axis a, so the
+ * difference pairs are F(m = i + l - 1) and F(m = i - l). */
+static double dminus(const orc_config* c, const double* F, int a, long i, long j, long k) {
+    const double* cf;
+    int R = stag_coef(c, &cf);
+    double s = 0.0;
+    for (int l = 1; l <= R; l++) {
+        long p[3] = {i, j, k}, m[3] = {i, j, k};
+        p[a] += l - 1;
+        m[a] -= l;
+        s += cf[l - 1] * (at(c, F, p[0], p[1], p[2]) - at(c, F, m[0], m[1], m[2]));
+    }
+    return s / c->d[a];
+}
+
+/* d/dx_a of F at the half-integer position (i + 1/2) along axis a from values at the
+ * integer positions: pairs F(i + l) and F(i - l + 1). */
+static double dplus(const orc_config* c, const double* F, int a, long i, long j, long k) {
+    const double* cf;
+    int R = stag_coef(c, &cf);
+    double s = 0.0;
+    for (int l = 1; l <= R; l++) {
+        long p[3] = {i, j, k}, m[3] = {i, j, k};
+        p[a] += l;
+        m[a] -= l - 1;
+        s += cf[l - 1] * (at(c, F, p[0], p[1], p[2]) - at(c, F, m[0], m[1], m[2]));
+    }
+    return s / c->d[a];
+}
+
 void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
                const double* const J[3]) {
-    double dt = c->dt, dx = c->d[0], dy = c->d[1], dz = c->d[2];
+    double dt = c->dt;
     int d3 = c->dims == 3;
     for (long k = 0; k < c->n[2]; k++)
         for (long j = 0; j < c->n[1]; j++)
             for (long i = 0; i < c->n[0]; i++) {
                 long long t = flat(c, i, j, k);
                 const double *Bx = B[0], *By = B[1], *Bz = B[2];
-                double cx = (at(c, Bz, i, j, k) - at(c, Bz, i, j - 1, k)) / dy;
-                double cy = -(at(c, Bz, i, j, k) - at(c, Bz, i - 1, j, k)) / dx;
-                double cz = (at(c, By, i, j, k) - at(c, By, i - 1, j, k)) / dx -
-                            (at(c, Bx, i, j, k) - at(c, Bx, i, j - 1, k)) / dy;
+                /* curl B at the E positions: each derivative crosses the stagger of
+                   the B component along its own axis */
+                double cx = dminus(c, Bz, 1, i, j, k);
+                double cy = -dminus(c, Bz, 0, i, j, k);
+                double cz = dminus(c, By, 0, i, j, k) - dminus(c, Bx, 1, i, j, k);
                 if (d3) {
-                    cx -= (at(c, By, i, j, k) - at(c, By, i, j, k - 1)) / dz;
-                    cy += (at(c, Bx, i, j, k) - at(c, Bx, i, j, k - 1)) / dz;
+                    cx -= dminus(c, By, 2, i, j, k);
+                    cy += dminus(c, Bx, 2, i, j, k);
                 }
                 E[0][t] += dt * (cx - J[0][t]);
                 E[1][t] += dt * (cy - J[1][t]);
@@ -275,20 +323,19 @@ void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3]
 }
 
 void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]) {
-    double dt = c->dt, dx = c->d[0], dy = c->d[1], dz = c->d[2];
+    double dt = c->dt;
     int d3 = c->dims == 3;
     for (long k = 0; k < c->n[2]; k++)
         for (long j = 0; j < c->n[1]; j++)
             for (long i = 0; i < c->n[0]; i++) {
                 long long t = flat(c, i, j, k);
                 const double *Ex = E[0], *Ey = E[1], *Ez = E[2];
-                double cx = (at(c, Ez, i, j + 1, k) - at(c, Ez, i, j, k)) / dy;
-                double cy = -(at(c, Ez, i + 1, j, k) - at(c, Ez, i, j, k)) / dx;
-                double cz = (at(c, Ey, i + 1, j, k) - at(c, Ey, i, j, k)) / dx -
-                            (at(c, Ex, i, j + 1, k) - at(c, Ex, i, j, k)) / dy;
+                double cx = dplus(c, Ez, 1, i, j, k);
+                double cy = -dplus(c, Ez, 0, i, j, k);
+                double cz = dplus(c, Ey, 0, i, j, k) - dplus(c, Ex, 1, i, j, k);
                 if (d3) {
-                    cx -= (at(c, Ey, i, j, k + 1) - at(c, Ey, i, j, k)) / dz;
-                    cy += (at(c, Ex, i, j, k + 1) - at(c, Ex, i, j, k)) / dz;
+                    cx -= dplus(c, Ey, 2, i, j, k);
+                    cy += dplus(c, Ex, 2, i, j, k);
                 }
                 B[0][t] -= dt * cx;
                 B[1][t] -= dt * cy;
@@ -318,6 +365,7 @@ static int valid_config(const orc_config* c) {
     if (!(c->dt > 0) || !(c->m > 0)) return 0;
     for (int a = 0; a < c->dims; a++)
         if (c->dt >= c->d[a]) return 0; /* displacement must stay below one cell */
+    if (c->order != 0 && c->order != 2 && c->order != 6) return 0;
     return 1;
 }
 

@@ -43,6 +43,8 @@ typedef struct orc_config {
     double ramp_x0;     /* lab-frame x where the linear density ramp starts */
     double ramp_len;    /* ramp length; n(x) = n0 * clamp((x - ramp_x0)/ramp_len, 0, 1) */
     int inject_ppc[3];  /* injected lattice per cell (window only) */
+    int order;          /* Maxwell solver: 2 (or 0) = Yee; 6 = sixth-order staggered space
+                           derivatives, leapfrog (second order) in time */
 } orc_config;
 
 typedef struct orc_sim orc_sim;
@@ -73,12 +75,18 @@ void orc_deposit(const orc_config* c, const double pos0[3], const double pos1[3]
 void orc_rho(const orc_config* c, long long n, const double* x, const double* y,
              const double* z, const double* w, double q, double* rho);
 
-/* Yee half-updates: E += dt (curl B - J); B -= dt curl E. In place. */
+/* Yee half-updates: E += dt (curl B - J); B -= dt curl E. In place. The curl takes
+ * staggered differences of the configured order: order 2 is Yee's two-point difference;
+ * order 6 is the centred staggered difference over six points,
+ *   D f(x) = sum_{l=1..3} c_l [f(x + (l - 1/2) h) - f(x - (l - 1/2) h)] / h,
+ * with c_l the unique coefficients exact for polynomials up to degree 6 (the
+ * higher-order scheme of the paper's Photon-Plasma runs, Sec. 2.1). */
 void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
                const double* const J[3]);
 void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]);
 
-/* div E on nodes (backward differences of the staggered E). */
+/* div E on nodes (two-point backward differences of the staggered E, whatever the
+ * solver order: the difference under which Esirkepov's current conserves charge). */
 void orc_div_e(const orc_config* c, const double* const E[3], double* out);
 
 /* Number of window shifts after `step` steps: floor(step * dt / dx[0]). */

@@ -1,0 +1,253 @@
+"""Pins of the oracle's sixth-order Maxwell solver (the higher-order scheme of the
+paper's Photon-Plasma runs, Sec. 2.1), against what the mathematics fixes:
+
+* the staggered difference is exact on polynomials up to degree 6 and not on degree 7:
+  this fixes its three coefficients without restating them;
+* vacuum modes follow the discrete dispersion relation of leapfrog in time with the
+  sixth-order space symbol, in 2D (both polarisations, oblique k) and 3D;
+* the sixth-order divergence of E and B is conserved in vacuum (div curl = 0 for the
+  matching stencil), while the two-point divergence is not;
+* the scheme is stable below dt = 1 / (kappa sqrt(sum 1/d^2)), kappa = c1 - c2 + c3 =
+  149/120 (the symbol's maximum, at the grid Nyquist wave), and blows up above it;
+* Sec. 2.1's qualitative claim: at the same dt the second-order scheme under-estimates
+  the group velocity of light, the sixth-order one over-estimates it;
+* along a moving-window x axis the stencil reads zero beyond the window.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+C6 = (75 / 64, -25 / 384, 3 / 640)  # used only where a closed form needs the symbol
+KAPPA6 = 149 / 120
+
+
+def setup_module(_):
+    orc.build()
+
+
+def _zeros(c):
+    return [np.zeros(orc.field_shape(c)) for _ in range(3)]
+
+
+# ------------------------------------------------------------------ the difference
+
+@pytest.mark.parametrize("p", range(0, 8))
+def test_staggered_difference_exact_to_degree_six(p):
+    nx, ny, dx = 40, 4, 0.5
+    c = orc.make_config(2, (nx, ny), (dx, 0.5), 1.0, window=True, order=6)
+    x0 = 10.0
+    xi = np.arange(nx) * dx - x0             # node positions
+    xh = xi + dx / 2                         # half-node positions
+    inner = slice(4, nx - 4)                 # away from the window edges
+    # D+ : Ez on nodes -> By at half nodes; B -= dt curl E with cy = -D+ Ez
+    E, B = _zeros(c), _zeros(c)
+    E[2][...] = (xi ** p)[None, :]
+    orc.yee_b(c, E, B)
+    want = p * xh ** (p - 1) if p > 0 else np.zeros(nx)
+    got = B[1][0]
+    scale = np.abs(xh[inner]).max() ** max(p - 1, 0) * max(p, 1)
+    dev_plus = got[inner] - want[inner]
+    err_plus = np.abs(dev_plus).max() / scale
+    # D- : Bz at half nodes -> Ey at nodes; E += dt (curl B - J) with cy = -D- Bz
+    E, B = _zeros(c), _zeros(c)
+    B[2][...] = (xh ** p)[None, :]
+    orc.yee_e(c, E, B, _zeros(c))
+    want = -(p * xi ** (p - 1)) if p > 0 else np.zeros(nx)
+    got = E[1][0]
+    dev_minus = got[inner] - want[inner]
+    err_minus = np.abs(dev_minus).max() / scale
+    if p <= 6:
+        assert err_plus < 1e-12 and err_minus < 1e-12, (err_plus, err_minus)
+    else:
+        # the leading error term e h^6 f^(7) appears; f^(8) = 0, so it is the same
+        # nonzero constant at every point (D+ and D- alike, up to the sign of E's update)
+        for dev in (dev_plus, -dev_minus):
+            assert abs(dev.mean()) > 1e-3, dev.mean()
+            assert np.abs(dev - dev.mean()).max() < 1e-9 * scale
+
+
+def test_window_axis_reads_zero_beyond_the_window():
+    nx, ny, pad = 24, 8, 3
+    d, dt = (0.1, 0.15), 0.03
+    cw = orc.make_config(2, (nx, ny), d, dt, window=True, order=6)
+    cp = orc.make_config(2, (nx + 2 * pad, ny), d, dt, order=6)
+    rng = np.random.default_rng(5)
+    for half in ("e", "b"):
+        E = [rng.standard_normal((ny, nx)) for _ in range(3)]
+        B = [rng.standard_normal((ny, nx)) for _ in range(3)]
+        J = [rng.standard_normal((ny, nx)) for _ in range(3)]
+
+        def padded(a):
+            out = np.zeros((ny, nx + 2 * pad))
+            out[:, pad:pad + nx] = a
+            return out
+
+        Ep, Bp, Jp = [padded(a) for a in E], [padded(a) for a in B], [padded(a) for a in J]
+        if half == "e":
+            orc.yee_e(cw, E, B, J)
+            orc.yee_e(cp, Ep, Bp, Jp)
+            got, ref = E, Ep
+        else:
+            orc.yee_b(cw, E, B)
+            orc.yee_b(cp, Ep, Bp)
+            got, ref = B, Bp
+        for a, r in zip(got, ref):
+            assert np.array_equal(a, r[:, pad:pad + nx])
+
+
+# ------------------------------------------------------------------ dispersion
+
+def _run(c, E, B, nsteps):
+    J = _zeros(c)
+    hist = []
+    for _ in range(nsteps):
+        orc.yee_e(c, E, B, J)
+        orc.yee_b(c, E, B)
+        hist.append([e.copy() for e in E] + [b.copy() for b in B])
+    return hist
+
+
+def _symbol(k, h):
+    """K with D e^{ikx} = i K e^{ikx} for the sixth-order staggered difference."""
+    return 2 / h * sum(cl * math.sin((2 * l + 1) * k * h / 2) for l, cl in enumerate(C6))
+
+
+def _cos_wdt(c, k):
+    K2 = sum(_symbol(k[a], c.d[a]) ** 2 for a in range(c.dims))
+    return 1 - c.dt ** 2 * K2 / 2
+
+
+@pytest.mark.parametrize("mode", ["TM", "TE"])
+def test_dispersion_2d(mode):
+    n, d = (32, 24), (0.1, 0.15)
+    dt = 0.9 / (KAPPA6 * math.sqrt(1 / d[0] ** 2 + 1 / d[1] ** 2))
+    c = orc.make_config(2, n, d, dt, order=6)
+    k = (2 * math.pi * 5 / (n[0] * d[0]), 2 * math.pi * 3 / (n[1] * d[1]))
+    E, B = _zeros(c), _zeros(c)
+    X = np.arange(n[0])[None, :] * d[0]
+    Y = np.arange(n[1])[:, None] * d[1]
+    if mode == "TM":
+        E[2][...] = np.cos(k[0] * X + k[1] * Y)
+        comp = 2
+    else:
+        B[2][...] = np.cos(k[0] * (X + d[0] / 2) + k[1] * (Y + d[1] / 2))
+        comp = 5
+    s = np.array([h[comp] for h in _run(c, E, B, 40)])
+    cw = _cos_wdt(c, k)
+    assert np.abs(s[2:] + s[:-2] - 2 * cw * s[1:-1]).max() < 1e-12
+    # the Yee relation would predict a different frequency for this mode
+    K2y = sum((2 * math.sin(k[a] * d[a] / 2) / d[a]) ** 2 for a in range(2))
+    assert abs((1 - dt ** 2 * K2y / 2) - cw) > 1e-4
+
+
+def test_dispersion_3d():
+    n, d = (12, 10, 8), (0.1, 0.12, 0.14)
+    dt = 0.9 / (KAPPA6 * math.sqrt(sum(1 / x ** 2 for x in d)))
+    c = orc.make_config(3, n, d, dt, order=6)
+    k = [2 * math.pi * m / (n[a] * d[a]) for a, m in enumerate((2, 1, 1))]
+    Z, Y, X = np.meshgrid(np.arange(n[2]) * d[2], np.arange(n[1]) * d[1],
+                          np.arange(n[0]) * d[0], indexing="ij")
+    # B = sixth-order staggered curl of A = (0, 0, Az): free of divergence for the
+    # matching stencil, so the field is one transverse mode with no static part
+    Az = np.cos(k[0] * X + k[1] * Y + k[2] * (Z + d[2] / 2))
+
+    def dplus(f, axis, h):
+        return sum(cl * (np.roll(f, -(l + 1), axis=axis) - np.roll(f, l, axis=axis))
+                   for l, cl in enumerate(C6)) / h
+
+    E, B = _zeros(c), _zeros(c)
+    B[0][...] = dplus(Az, 1, d[1])
+    B[1][...] = -dplus(Az, 2, d[0])
+    hist = _run(c, E, B, 30)
+    cw = _cos_wdt(c, k)
+    for comp in (0, 1, 3, 4, 5):
+        s = np.array([h[comp] for h in hist])
+        assert np.abs(s[2:] + s[:-2] - 2 * cw * s[1:-1]).max() < 1e-12
+
+
+# ------------------------------------------------------------------ divergence
+
+def _div(fields, dims, d, plus, coef):
+    """Staggered divergence with the given coefficients: backward differences for E
+    (nodes), forward for B (cell centres)."""
+    out = 0.0
+    for a in range(dims):
+        axis = dims - 1 - a
+        f = fields[a]
+        s = 0.0
+        for l, cl in enumerate(coef):
+            if plus:
+                s = s + cl * (np.roll(f, -(l + 1), axis=axis) - np.roll(f, l, axis=axis))
+            else:
+                s = s + cl * (np.roll(f, -l, axis=axis) - np.roll(f, l + 1, axis=axis))
+        out = out + s / d[a]
+    return out
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_sixth_order_divergence_conserved_in_vacuum(dims):
+    n = (16, 12) if dims == 2 else (8, 6, 6)
+    d = (0.1, 0.13, 0.17)[:dims]
+    dt = 0.8 / (KAPPA6 * math.sqrt(sum(1 / x ** 2 for x in d)))
+    c = orc.make_config(dims, n, d, dt, order=6)
+    rng = np.random.default_rng(2)
+    E = [rng.standard_normal(orc.field_shape(c)) for _ in range(3)]
+    B = [rng.standard_normal(orc.field_shape(c)) for _ in range(3)]
+    e6 = _div(E, dims, d, False, C6)
+    b6 = _div(B, dims, d, True, C6)
+    e2 = _div(E, dims, d, False, (1.0,))
+    _run(c, E, B, 20)
+    scale = np.abs(e6).max()
+    assert np.abs(_div(E, dims, d, False, C6) - e6).max() < 1e-12 * scale
+    assert np.abs(_div(B, dims, d, True, C6) - b6).max() < 1e-12 * np.abs(b6).max()
+    # the two-point divergence is not an invariant of the sixth-order curl
+    assert np.abs(_div(E, dims, d, False, (1.0,)) - e2).max() > 1e-3 * scale
+
+
+# ------------------------------------------------------------------ stability
+
+@pytest.mark.parametrize("order,kappa", [(6, KAPPA6), (2, 1.0)])
+def test_stability_limit(order, kappa):
+    n, d = (32, 24), (0.1, 0.15)
+    lim = 1 / (kappa * math.sqrt(1 / d[0] ** 2 + 1 / d[1] ** 2))
+    growth = {}
+    for f in (0.98, 1.05):
+        c = orc.make_config(2, n, d, f * lim, order=order)
+        rng = np.random.default_rng(3)
+        E = [rng.standard_normal((n[1], n[0])) for _ in range(3)]
+        B = [rng.standard_normal((n[1], n[0])) for _ in range(3)]
+        a0 = max(np.abs(x).max() for x in E + B)
+        J = _zeros(c)
+        for _ in range(300):
+            orc.yee_e(c, E, B, J)
+            orc.yee_b(c, E, B)
+        growth[f] = max(np.abs(x).max() for x in E + B) / a0
+    assert growth[0.98] < 100, growth
+    assert growth[1.05] > 1e6, growth
+
+
+# ------------------------------------------------------------------ Sec. 2.1's claim
+
+def _omega(order, m, nx=64, dx=0.1, dt=0.05, steps=40):
+    ny = 4
+    c = orc.make_config(2, (nx, ny), (dx, 0.1), dt, order=order)
+    k = 2 * math.pi * m / (nx * dx)
+    E, B = _zeros(c), _zeros(c)
+    E[2][...] = np.cos(k * np.arange(nx) * dx)[None, :]
+    s = np.array([h[2][0] for h in _run(c, E, B, steps)])
+    mask = np.abs(s[1:-1]) > 0.3
+    cw = np.median(((s[2:] + s[:-2]) / (2 * s[1:-1]))[mask])
+    return math.acos(cw) / dt, k
+
+
+@pytest.mark.parametrize("m", [4, 8, 12])
+def test_group_velocity_under_for_yee_over_for_sixth_order(m):
+    v = {}
+    for order in (2, 6):
+        w1, k1 = _omega(order, m)
+        w2, k2 = _omega(order, m + 1)
+        v[order] = (w2 - w1) / (k2 - k1)
+    assert v[2] < 1.0 < v[6], v
