@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget")
     ap.add_argument("--mapping", default="queue", choices=["queue", "static"])
     ap.add_argument("--total", type=int, default=64 * 2 ** 20, help="stress3d particles")
+    ap.add_argument("--maxwell-order", type=int, default=2, choices=[2, 6],
+                    help="field solver: 2 = Yee, 6 = sixth-order staggered differences "
+                         "(time step 0.76 of Yee's limit instead of 0.95)")
     ap.add_argument("--no-variant", action="store_true", help="skip the other precision")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -100,21 +103,27 @@ def parse():
     return ap.parse_args()
 
 
-def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20):
+def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20, order=2):
+    """The synthetic workload; with the sixth-order solver the time step is 0.76 of
+    Yee's limit (the sixth-order scheme is stable below 120/149 = 0.805 of it)."""
     from paper_1511_03878_gb300 import inputs
 
+    cfl = 0.76 if order == 6 else 0.95
     if kind == "stress3d":
         # 256x128x128 cells, log-normal counts per 16^3 block, 8^3 patches
-        w = inputs.stress3d(total=total)
+        w = inputs.stress3d(total=total, cfl=cfl)
         w["params"] = dict(w["params"], patch=(8, 8, 8))
-        return w
-    if kind == "thermal":
-        return inputs.thermal2d(seed=1511)
-    if kind == "lwfa3d":
+    elif kind == "thermal":
+        w = inputs.thermal2d(seed=1511, cfl=cfl)
+    elif kind == "lwfa3d":
         # 512x128x128 window full of plasma, 2 particles per cell (16 777 216)
-        return inputs.lwfa3d(ramp_x0=-8.0, ppc=(2, 1, 1))
-    # the window full of plasma: density ramp placed before x = 0
-    return inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0)
+        w = inputs.lwfa3d(ramp_x0=-8.0, ppc=(2, 1, 1), cfl=cfl)
+    else:
+        # the window full of plasma: density ramp placed before x = 0
+        w = inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0, cfl=cfl)
+    if order != 2:
+        w["params"] = dict(w["params"], maxwell_order=order)
+    return w
 
 
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic.md")
@@ -445,7 +454,8 @@ def oracle_sim(w, steps):
     dims = p["dims"]
     c = orc.make_config(dims, p["n"][:dims], p["d"][:dims], p["dt"], window=p["window"],
                         q=p["q"], m=p["m"], n0=p["n0"], ramp_x0=p["ramp_x0"],
-                        ramp_len=p["ramp_len"], inject_ppc=p["inject_ppc"])
+                        ramp_len=p["ramp_len"], inject_ppc=p["inject_ppc"],
+                        order=p.get("maxwell_order", 2))
     col = (int(np.prod(p["n"][1:dims])) * int(np.prod(p["inject_ppc"][:dims]))
            if p["window"] else 0)
     o = orc.OracleSim(c, len(w["particles"]["x"]) + (steps + 2) * col)
@@ -459,18 +469,22 @@ def oracle_sample(args, frac):
     timing sample: fewer transverse rows of the window (LWFA, so that the injected
     columns shrink with it), or every k-th particle of the same grid (thermal, 3D
     stress). Returns the workload and a description of the cut."""
-    w = workload(args.nx, args.ny, args.workload, args.total)
+    order = args.maxwell_order
+    w = workload(args.nx, args.ny, args.workload, args.total, order)
     if frac >= 1.0:
         return w, "the full workload"
     if args.workload == "lwfa":
         ny = max(32, int(args.ny * frac) // 32 * 32)
-        return workload(args.nx, ny, "lwfa"), f"{args.nx}x{ny} rows of the window"
+        return workload(args.nx, ny, "lwfa", order=order), f"{args.nx}x{ny} rows of the window"
     if args.workload == "lwfa3d":
         from paper_1511_03878_gb300 import inputs
 
         side = max(16, int(128 * math.sqrt(frac)) // 8 * 8)
-        return (inputs.lwfa3d(ny=side, nz=side, ramp_x0=-8.0, ppc=(2, 1, 1)),
-                f"512x{side}x{side} cells of the window")
+        w3 = inputs.lwfa3d(ny=side, nz=side, ramp_x0=-8.0, ppc=(2, 1, 1),
+                           cfl=0.76 if order == 6 else 0.95)
+        if order != 2:
+            w3["params"] = dict(w3["params"], maxwell_order=order)
+        return w3, f"512x{side}x{side} cells of the window"
     k = max(1, int(round(1.0 / frac)))
     w = dict(w, particles={key: v[::k].copy() for key, v in w["particles"].items()})
     return w, f"one particle in {k} on the same grid"
@@ -506,7 +520,8 @@ def reference_arm(args):
     import oracle as orc
 
     orc.build()
-    n_full = len(workload(args.nx, args.ny, args.workload, args.total)["particles"]["x"])
+    n_full = len(workload(args.nx, args.ny, args.workload, args.total,
+                          args.maxwell_order)["particles"]["x"])
     total = args.steps + args.warmup
     # each step is a bounded sample: a cut of the same workload (at most 5M particles,
     # fewer if K+W steps would exceed about three minutes), timed after one probe step
@@ -560,6 +575,9 @@ def config_dict(args, precision):
         base = {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
                 "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
                 "laser_a0": 4.0}
+    if args.maxwell_order != 2:
+        base = dict(base, workload=base["workload"] + f"-maxwell{args.maxwell_order}",
+                    maxwell_order=args.maxwell_order, cfl=0.76)
     return {**base, "precision": precision,
             "l2": "inputs larger than L2 (particles + fields > 129 MB), no flush",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
@@ -666,7 +684,7 @@ def main():
     if rank != 0:
         __graft_entry__.build()
 
-    w = workload(args.nx, args.ny, args.workload, args.total)
+    w = workload(args.nx, args.ny, args.workload, args.total, args.maxwell_order)
     clocks = ClockSampler(local)
     others = [] if args.no_variant or args.variants == "none" else [
         v for v in args.variants.split(",") if v and v != args.precision]

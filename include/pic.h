@@ -75,7 +75,8 @@ typedef struct {
     int dims;           /* 2 (2D3V) or 3 (3D3V) */
     int n[3];           /* cells per axis; n[2] = 1 in 2D */
     double d[3];        /* cell sizes */
-    double dt;          /* time step; must be below every d[a] */
+    double dt;          /* time step; below every d[a] and within the stability limit
+                           of the field solver (maxwell_order) */
     int patch[3];       /* cells per patch per axis: a multiple of 4 in [4, 64], dividing
                            n[a]; the patch's field and current tiles must fit in the 227 KB
                            of shared memory of one CTA (pic_required_bytes returns 0 when
@@ -102,7 +103,20 @@ typedef struct {
                            cells. */
     double merge_dp;    /* momentum-bin width (units of m c) of the merge; > 0 when
                            merge_above > 0 */
+    int maxwell_order;  /* field solver (Sec. 2.1): 0 or 2 = Yee's two-point staggered
+                           differences; 6 = sixth-order staggered space differences
+                           sum_{l=1..3} c_l [f(x + (l-1/2)h) - f(x - (l-1/2)h)] / h with
+                           c = (75/64, -25/384, 3/640), leapfrog in time. The time step
+                           must satisfy dt * kappa * sqrt(sum_a 1/d[a]^2) < 1 with kappa = 1
+                           (order 2) or 149/120 (order 6), else the config is invalid.
+                           Esirkepov's current conserves charge for the two-point
+                           divergence, so with order 6 the GAUSS diagnostic is no longer
+                           preserved to round-off. */
 } pic_config;
+
+/* sizeof(pic_config) as this library was built: a binding compares it with its own
+ * layout of the struct before passing one. */
+size_t pic_config_bytes(void);
 
 /* Device bytes one arena needs for this configuration (0 if the config is invalid). */
 size_t pic_required_bytes(const pic_config* cfg);

@@ -67,7 +67,10 @@ def patch_candidates(params: dict, precision: int, sides=PATCH_SIDES, max_aspect
 def _key(workload: dict, precision: int, patches, chunks) -> str:
     p = workload["params"]
     dims = int(p["dims"])
-    return json.dumps({"dims": dims, "n": list(p["n"][:dims]), "d": list(p["d"][:dims]),
+    extra = {}
+    if int(p.get("maxwell_order", 2)) != 2:  # keys of the Yee solver stay as they were
+        extra = {"maxwell_order": int(p["maxwell_order"]), "dt": float(p["dt"])}
+    return json.dumps({**extra, "dims": dims, "n": list(p["n"][:dims]), "d": list(p["d"][:dims]),
                        "precision": int(precision), "window": bool(p.get("window")),
                        "particles": int(len(workload["particles"]["x"])),
                        "patches": None if patches is None else [list(q) for q in patches],

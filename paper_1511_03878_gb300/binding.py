@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
                 -6: "PIC_ERR_TIMEOUT"}
 
 # every symbol include/pic.h declares
-EXPORTS = ("pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
+EXPORTS = ("pic_config_bytes", "pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
            "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
            "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
            "pic_batch_destroy", "pic_gauss_residual_2d_static")
@@ -59,6 +59,7 @@ class PicConfig(ctypes.Structure):
         ("mapping", ctypes.c_int),
         ("merge_above", ctypes.c_int),
         ("merge_dp", ctypes.c_double),
+        ("maxwell_order", ctypes.c_int),
     ]
 
 
@@ -74,6 +75,11 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
         cfgp = ctypes.POINTER(PicConfig)
+        L.pic_config_bytes.restype = ctypes.c_size_t
+        L.pic_config_bytes.argtypes = []
+        if L.pic_config_bytes() != ctypes.sizeof(PicConfig):
+            raise RuntimeError(f"{LIB_PATH} was built with a different pic_config layout "
+                               f"({L.pic_config_bytes()} bytes, binding {ctypes.sizeof(PicConfig)})")
         L.pic_required_bytes.restype = ctypes.c_size_t
         L.pic_required_bytes.argtypes = [cfgp]
         L.pic_create.restype = ctypes.c_int
@@ -154,7 +160,12 @@ def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chun
     c.mapping = int(mapping)
     c.merge_above = int(merge_above)
     c.merge_dp = float(merge_dp)
+    c.maxwell_order = int(params.get("maxwell_order", 2))
     return c
+
+
+def pic_config_bytes() -> int:
+    return int(lib().pic_config_bytes())
 
 
 def pic_required_bytes(cfg: PicConfig) -> int:

@@ -7,33 +7,9 @@
 
 #include "pic_device.cuh"
 #include "pic_internal.h"
+#include "fields.cuh"
 
 namespace pic {
-
-__device__ __forceinline__ long long pidx3(const SimDev& S, int i, int j, int k) {
-    return ((long long)(k + kGuard) * S.NY + (j + kGuard)) * S.NX + (i + kGuard);
-}
-
-// value at interior (i, j, k) and its periodic images in the guard cells (no x images
-// along a moving-window x axis, whose guards stay zero)
-template <typename T>
-__device__ __forceinline__ void put3d(const SimDev& S, T* a, int i, int j, int k, T v) {
-    int xs[2] = {i + kGuard, -1}, ys[2] = {j + kGuard, -1}, zs[2] = {k + kGuard, -1};
-    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-    if (!S.window) {
-        if (i == nx - 1) xs[1] = 0; else if (i == 0) xs[1] = nx + kGuard; else if (i == 1) xs[1] = nx + 1 + kGuard;
-    }
-    if (j == ny - 1) ys[1] = 0; else if (j == 0) ys[1] = ny + kGuard; else if (j == 1) ys[1] = ny + 1 + kGuard;
-    if (k == nz - 1) zs[1] = 0; else if (k == 0) zs[1] = nz + kGuard; else if (k == 1) zs[1] = nz + 1 + kGuard;
-#pragma unroll
-    for (int c = 0; c < 2; c++)
-#pragma unroll
-        for (int b = 0; b < 2; b++)
-#pragma unroll
-            for (int a2 = 0; a2 < 2; a2++)
-                if (xs[a2] >= 0 && ys[b] >= 0 && zs[c] >= 0)
-                    a[((long long)zs[c] * S.NY + ys[b]) * S.NX + xs[a2]] = v;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) yee_e3d_kernel(const BatchDev* __restrict__ bd) {

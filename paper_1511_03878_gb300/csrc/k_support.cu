@@ -15,6 +15,7 @@
 
 #include "pic_device.cuh"
 #include "pic_internal.h"
+#include "fields.cuh"
 
 namespace pic {
 
@@ -317,26 +318,6 @@ cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int
 
 // ================================================================ Yee (2D)
 
-// Writes v at interior (i, j) of a padded component and at its periodic images in
-// the guard cells (x images only when x is periodic).
-template <typename T>
-__device__ __forceinline__ void put2d(T* a, int NX, int i, int j, int nx, int ny, bool px, T v) {
-    int xs[2] = {i + kGuard, -1}, ys[2] = {j + kGuard, -1};
-    if (px) {
-        if (i == nx - 1) xs[1] = 0;
-        else if (i == 0) xs[1] = nx + kGuard;
-        else if (i == 1) xs[1] = nx + 1 + kGuard;
-    }
-    if (j == ny - 1) ys[1] = 0;
-    else if (j == 0) ys[1] = ny + kGuard;
-    else if (j == 1) ys[1] = ny + 1 + kGuard;
-#pragma unroll
-    for (int a2 = 0; a2 < 2; a2++)
-#pragma unroll
-        for (int b2 = 0; b2 < 2; b2++)
-            if (xs[a2] >= 0 && ys[b2] >= 0) a[(long long)ys[b2] * NX + xs[a2]] = v;
-}
-
 // E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2}); output written shifted by the
 // window shift of this step; the next step's current buffer is zeroed.
 template <typename T>
@@ -438,7 +419,8 @@ __global__ void __launch_bounds__(256) yee_b2d_kernel(const BatchDev* __restrict
 }
 
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
-                       cudaStream_t s) {
+                       int order, cudaStream_t s) {
+    if (order == 6) return launch_maxwell6(bd, nsims, max_ncell, dims, prec, s);
     if (dims == 3) return launch_yee3d(bd, nsims, max_ncell, prec, s);
     if (dims != 2) return cudaErrorInvalidValue;
     dim3 grid((max_ncell + 255) / 256, nsims);

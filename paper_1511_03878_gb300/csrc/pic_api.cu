@@ -107,6 +107,18 @@ const char* validate(const pic_config* c) {
             return "3D patch tile does not fit in shared memory";
     }
     if (!(c->dt > 0) || !std::isfinite(c->dt)) return "dt must be positive";
+    if (c->maxwell_order != 0 && c->maxwell_order != 2 && c->maxwell_order != 6)
+        return "maxwell_order must be 0, 2 or 6";
+    {
+        // leapfrog is stable while (dt/2) max|K| < 1 over the grid's waves; the symbol of
+        // the staggered difference peaks at the Nyquist wave at (2/d) sum_l |c_l|, i.e.
+        // 2/d (Yee) and (2/d) 149/120 (sixth order)
+        double s2 = 0.0;
+        for (int a = 0; a < c->dims; a++) s2 += 1.0 / (c->d[a] * c->d[a]);
+        const double kappa = c->maxwell_order == 6 ? 149.0 / 120.0 : 1.0;
+        if (!(c->dt * kappa * std::sqrt(s2) < 1.0))
+            return "dt above the stability limit of the field solver";
+    }
     if (!(c->m > 0)) return "mass must be positive";
     if (c->capacity < 0 || c->capacity > (1LL << 31) - (1LL << 24)) return "bad capacity";
     if (c->chunk < 0) return "bad chunk";
@@ -136,6 +148,7 @@ Layout plan(const pic_config* c, char* base) {
     S.mapping = c->mapping;
     S.merge_above = c->merge_above;
     S.merge_dp = c->merge_dp;
+    S.order = c->maxwell_order == 6 ? 6 : 2;
     for (int a = 0; a < 3; a++) {
         S.n[a] = a < c->dims ? c->n[a] : 1;
         S.P[a] = a < c->dims ? c->patch[a] : 1;
@@ -180,6 +193,15 @@ Layout plan(const pic_config* c, char* base) {
             S.f_id[a] = (float)S.c_id[a];
             S.f_id_lo[a] = (float)(S.c_id[a] - (double)S.f_id[a]);
         }
+        // sixth-order staggered difference: the coefficients fixed by exactness up to
+        // degree 6, pre-divided by the cell size
+        const double c6[3] = {75.0 / 64.0, -25.0 / 384.0, 3.0 / 640.0};
+        for (int a = 0; a < 3; a++)
+            for (int l = 0; l < 3; l++) {
+                S.c_k[a][l] = c6[l] / S.d[a];
+                S.f_k[a][l] = (float)S.c_k[a][l];
+                S.f_k_lo[a][l] = (float)(S.c_k[a][l] - (double)S.f_k[a][l]);
+            }
     }
     const long long es = c->precision == PIC_FP32 ? 4 : 8;
     // slots: the configured capacity plus one alignment's slack per patch, so that every
@@ -234,6 +256,10 @@ Layout plan(const pic_config* c, char* base) {
     S.mpend = cv.take<int>(S.npatch);
     S.mpoff = cv.take<int>(S.npatch);
     S.mlast = cv.take<int>(S.npatch);
+    // sixth order in a moving window: E^{n+1} of the column the shift drops, which the
+    // B update of the new frame's first columns still reads
+    S.ecol = S.order == 6 && c->window ? cv.take<char>(3 * (long long)S.n[1] * S.n[2] * es)
+                                       : nullptr;
 
     BatchDev& B = L.B;
     B.nsims = 1;
@@ -338,8 +364,8 @@ struct GraphOwner {
 // Captures one step into a graph: queue build -> particle kernel -> (Yee on a
 // second branch) | (injection -> exchange) -> end of step.
 cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_patches,
-                         int max_ncell, int max_column, int dims, int prec, int mapping,
-                         const int P[3], int grid, bool window, bool merge) {
+                         int max_ncell, int max_column, int dims, int prec, int order,
+                         int mapping, const int P[3], int grid, bool window, bool merge) {
     cudaError_t e;
     if (!*o.cap0) {
         if ((e = cudaStreamCreateWithFlags(o.cap0, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -353,7 +379,7 @@ cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_pa
     if (le == cudaSuccess) le = launch_push(db, dims, prec, mapping, P[0], P[1], P[2], grid, *o.cap0);
     if (le == cudaSuccess) le = cudaEventRecord(*o.ev_fork, *o.cap0);
     if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap1, *o.ev_fork, 0);
-    if (le == cudaSuccess) le = launch_yee(db, nsims, max_ncell, dims, prec, *o.cap1);
+    if (le == cudaSuccess) le = launch_yee(db, nsims, max_ncell, dims, prec, order, *o.cap1);
     if (le == cudaSuccess) le = cudaEventRecord(*o.ev_join, *o.cap1);
     if (le == cudaSuccess && window) le = launch_inject(db, nsims, max_column, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_exchange(db, nsims, max_patches, prec, *o.cap0);
@@ -477,6 +503,8 @@ uint64_t mix64(uint64_t x) {
 
 // ===================================================================== C ABI
 
+extern "C" size_t pic_config_bytes(void) { return sizeof(pic_config); }
+
 extern "C" size_t pic_required_bytes(const pic_config* cfg) {
     if (validate(cfg)) return 0;
     return plan(cfg, nullptr).bytes;
@@ -519,7 +547,8 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
     s->push_grid = push_grid_size(S.dims, S.prec, S.P, cfg->mapping == PIC_MAP_STATIC, S.npatch);
     GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
     if (capture_step(o, s->L.db, 1, S.npatch, (int)S.ncell, s->column_pts, S.dims, S.prec,
-                     S.mapping, S.P, s->push_grid, S.window != 0, S.merge_above > 0) != cudaSuccess)
+                     S.order, S.mapping, S.P, s->push_grid, S.window != 0,
+                     S.merge_above > 0) != cudaSuccess)
         return bail(PIC_ERR_CUDA);
     *out = s;
     return PIC_OK;
@@ -1016,7 +1045,8 @@ extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) 
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
         if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
-        if (e == cudaSuccess) e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, s->stream);
+        if (e == cudaSuccess)
+            e = launch_yee(s->L.db, 1, (int)S.ncell, S.dims, S.prec, S.order, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[6], s->stream);
         if (e == cudaSuccess) e = launch_end_step(s->L.db, 1, S.npatch, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[7], s->stream);
@@ -1095,6 +1125,8 @@ const char* batch_check(pic_sim* const* sims, int nsims) {
             sims[i]->L.S.P[2] != sims[0]->L.S.P[2])
             return "sims of a batch must share the patch size";
         if (sims[i]->cfg.mapping != sims[0]->cfg.mapping) return "sims must share the mapping";
+        if (sims[i]->L.S.order != sims[0]->L.S.order)
+            return "sims of a batch must share the field solver order";
     }
     return nullptr;
 }
@@ -1160,7 +1192,7 @@ extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* de
     for (int i = 0; i < nsims; i++) any_merge = any_merge || hsims[i].merge_above > 0;
     if (e == cudaSuccess)
         e = capture_step(o, bl.db, nsims, max_patches, max_ncell, max_column, S0.dims, S0.prec,
-                         sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge);
+                         S0.order, sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge);
     if (e != cudaSuccess) {
         destroy_graph_owner(o);
         delete b;

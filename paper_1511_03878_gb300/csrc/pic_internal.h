@@ -71,6 +71,10 @@ struct SimDev {
     // field-solver constants: dt and 1/d[a] in FP64, and as FP32 (hi) + FP32 (lo) pairs
     double c_id[3];
     float f_dt, f_dt_lo, f_id[3], f_id_lo[3];
+    int order;         // field solver: 2 (Yee) or 6 (sixth-order staggered differences)
+    // sixth order: c_l / d[a] for l = 1..3 in FP64 and as FP32 hi + lo pairs
+    double c_k[3][3];
+    float f_k[3][3], f_k_lo[3][3];
     int cmax_exp;      // one particle's current contribution stays below 2^cmax_exp
     int merge_above;   // load limiting: patches above this count are merged (0: off)
     double merge_dp;   // momentum-bin width of the merge
@@ -107,6 +111,8 @@ struct SimDev {
     int* mpend;      // arrivals left in the exchange buffer for want of room (repack places them)
     int* mpoff;      // offset of the first of them in the patch's exchange buffer
     int* mlast;      // per patch: count after its last merge pass (0 = none yet)
+    void* ecol;      // sixth order with the window: [3][nz][ny] E^{n+1} of the column a
+                     // shift drops (old-frame x = 0), read by the B update
     // state and scratch
     StepState* st;
     int* status;
@@ -143,7 +149,7 @@ cudaError_t launch_inject(const BatchDev* bd, int nsims, int max_column_pts, int
 cudaError_t launch_exchange(const BatchDev* bd, int nsims, int max_patches, int prec,
                             cudaStream_t s);
 cudaError_t launch_yee(const BatchDev* bd, int nsims, int max_ncell, int dims, int prec,
-                       cudaStream_t s);
+                       int order, cudaStream_t s);
 cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cudaStream_t s);
 // load limiting by merging (no-op for sims with merge_above = 0)
 cudaError_t launch_merge(const BatchDev* bd, int nsims, int max_patches, int prec,
@@ -154,6 +160,8 @@ int push3d_smem(int prec, int P0, int P1, int P2);
 int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes);
 cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0, int P1, int P2,
                           int grid, cudaStream_t s);
+cudaError_t launch_maxwell6(const BatchDev* bd, int nsims, long long max_ncell, int dims,
+                           int prec, cudaStream_t s);
 cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,
                          cudaStream_t s);
 cudaError_t launch_gauss3d(const SimDev* sd, const SimDev& hs, int prec, int mode, cudaStream_t s);

@@ -12,7 +12,7 @@ def test_kernels_per_step_counts_injection_and_merge():
 
 
 def _args(**kw):
-    a = dict(nx=2048, ny=512, workload="lwfa", total=64 * 2 ** 20)
+    a = dict(nx=2048, ny=512, workload="lwfa", total=64 * 2 ** 20, maxwell_order=2)
     a.update(kw)
     return types.SimpleNamespace(**a)
 

@@ -50,3 +50,25 @@ def test_create_rejects_bad_arguments(lib):
     # too small an arena
     assert lib.pic_create(ctypes.byref(cfg), ctypes.c_void_p(4096), 16, None,
                           ctypes.byref(h)) == binding.PIC_ERR_NOMEM
+
+
+def test_config_layout_matches_the_library(lib):
+    import ctypes
+    assert binding.pic_config_bytes() == ctypes.sizeof(binding.PicConfig)
+
+
+def test_field_solver_order_and_stability_limit(lib):
+    import math
+    p = inputs.thermal2d(nx=64, ny=64, patch=(16, 16))["params"]
+    lim2 = 1 / math.sqrt(sum(1 / x ** 2 for x in p["d"][:2]))
+    lim6 = lim2 * 120 / 149
+    ok = lambda **kw: binding.pic_required_bytes(binding.make_config(dict(p, **kw), capacity=10)) > 0
+    assert ok(maxwell_order=2, dt=0.99 * lim2) and not ok(maxwell_order=2, dt=1.01 * lim2)
+    assert ok(maxwell_order=6, dt=0.99 * lim6) and not ok(maxwell_order=6, dt=1.01 * lim6)
+    assert not ok(maxwell_order=6, dt=0.9 * lim2)  # stable for Yee, not for order 6
+    assert not ok(maxwell_order=4, dt=0.5 * lim6)
+    # the moving window with order 6 keeps one extra column of E (3 x ny values)
+    w = inputs.lwfa2d(nx=128, ny=64, patch=(16, 16), cfl=0.76)["params"]
+    b2 = binding.pic_required_bytes(binding.make_config(w, capacity=1000))
+    b6 = binding.pic_required_bytes(binding.make_config(dict(w, maxwell_order=6), capacity=1000))
+    assert 3 * 64 * 8 <= b6 - b2 <= 3 * 64 * 8 + 512
