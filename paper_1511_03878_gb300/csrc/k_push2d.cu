@@ -72,9 +72,11 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
         for (int l = 0; l < 3; l++) {
             jatomic(jx + l * JX + 0, jprod<JT>(ax1, wy[l]));
             jatomic(jx + l * JX + 1, jprod<JT>(ax2, wy[l]));
+            // qz folded into the row weights: one multiply and one FMA per node
+            const T qwy = qz * wy[l], qwz = qz * wz[l];
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                jatomic(jz + l * JX + k, jprod<JT>(qz, S0x[k] * wy[l] + a[k] * wz[l]));
+                jatomic(jz + l * JX + k, jval<JT>(S0x[k] * qwy + a[k] * qwz));
         }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -307,6 +309,10 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         // fixed-point exponent of the double-word current tile for this item
         const int jk = item_fixed_exp<JT>(cnt, S.cmax_exp);
         const float jsc = pow2f(jk);
+        // charge factors carrying the tile's power-of-two scale (exact: the same values as
+        // scaling each particle's product)
+        const T cjxs = jscale<JT>(cjx, jsc), cjys = jscale<JT>(cjy, jsc),
+                cjzs = jscale<JT>(cjz, jsc);
         const T* W = reinterpret_cast<const T*>(S.w);
         T* U0 = reinterpret_cast<T*>(S.u[0]);
         T* U1 = reinterpret_cast<T*>(S.u[1]);
@@ -469,8 +475,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             bool leave = false;
             int dest = patch;
             if (ok) {
-                const T qx = jscale<JT>(cjx * w, jsc), qy = jscale<JT>(cjy * w, jsc),
-                        qz = jscale<JT>(cjz * w * vz, jsc);
+                const T qx = cjxs * w, qy = cjys * w, qz = cjzs * w * vz;
                 const int t0 = typ * JX + txp;  // stencil node 0 of both axes
                 if (fast) {
                     const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)

@@ -214,6 +214,11 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
         const int cnt = item.w;
         const int jk = item_fixed_exp<JT>(cnt, S.cmax_exp);
         const float jsc = pow2f(jk);
+        // charge factors carrying the tile's power-of-two scale (exact: the same values as
+        // scaling each particle's product)
+        T cjs[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) cjs[a] = jscale<JT>(cj[a], jsc);
         T* U0 = reinterpret_cast<T*>(S.u[0]);
         T* U1 = reinterpret_cast<T*>(S.u[1]);
         T* U2 = reinterpret_cast<T*>(S.u[2]);
@@ -352,8 +357,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                         for (int q = 0; q < 3; q++) Sp[a][q] = S0keep[a][q];
                     if (fast) {
                         JT* jt3[3];
-                        const T q3[3] = {jscale<JT>(cj[0] * w, jsc), jscale<JT>(cj[1] * w, jsc),
-                                         jscale<JT>(cj[2] * w, jsc)};
+                        const T q3[3] = {cjs[0] * w, cjs[1] * w, cjs[2] * w};
                         const int t111 = (tp[2] + 1) * JXY + (tp[1] + 1) * JX + (tp[0] + 1);
                         for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
                         deposit3d_fast<T, JT>(jt3, JX, JXY, Sp, dp1, q3);
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
                         const int b = (a + 1) % 3, c = (a + 2) % 3;
-                        const T qa = jscale<JT>(cj[a] * w, jsc);
+                        const T qa = cjs[a] * w;
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;

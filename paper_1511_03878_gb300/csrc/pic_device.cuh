@@ -104,6 +104,17 @@ __device__ __forceinline__ void shape3(T delta, T S[3]) {
     S[2] = T(0.5) * b * b;
 }
 
+// FP64 shapes in five FP64-pipe operations instead of seven: with h = delta/2 (exact)
+// and q = delta^2/2 + 1/8, the outer weights are q -/+ h (their sum is 1/4 + delta^2 and
+// their difference delta), the middle one 3/4 - delta^2
+__device__ __forceinline__ void shape3(double delta, double S[3]) {
+    const double h = 0.5 * delta;
+    const double q = fma(h, delta, 0.125);
+    S[0] = q - h;
+    S[1] = fma(-delta, delta, 0.75);
+    S[2] = q + h;
+}
+
 // double-word shapes: FP32 constants added with DWPlusFP, exact halving
 __device__ __forceinline__ void shape3(df64 delta, df64 S[3]) {
     const df64 a = add_f(-delta, 0.5f), b = add_f(delta, 0.5f);
@@ -121,7 +132,8 @@ template <typename T>
 __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     T um0 = u[0] + eps * E[0], um1 = u[1] + eps * E[1], um2 = u[2] + eps * E[2];
     const T ig = rsqrt_t(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
-    const T t0 = eps * B[0] * ig, t1 = eps * B[1] * ig, t2 = eps * B[2] * ig;
+    const T ei = eps * ig;
+    const T t0 = ei * B[0], t1 = ei * B[1], t2 = ei * B[2];
     const T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
     const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
     const T up0 = um0 + (um1 * t2 - um2 * t1);
@@ -354,6 +366,19 @@ __device__ __forceinline__ long long jprod<long long, double>(double a, double b
 template <>
 __device__ __forceinline__ int jprod<int, float>(float a, float b) {
     return __float2int_rn(a * b);
+}
+// tile value of a contribution already formed (and already carrying 2^k)
+template <typename JT, typename T>
+__device__ __forceinline__ JT jval(T v) {
+    return JT(v);
+}
+template <>
+__device__ __forceinline__ long long jval<long long, double>(double v) {
+    return f64_to_fixed(v);
+}
+template <>
+__device__ __forceinline__ int jval<int, float>(float v) {
+    return __float2int_rn(v);
 }
 // charge factor scaled for the tile: exact power-of-two scaling for a fixed-point tile,
 // unchanged for a floating-point one
