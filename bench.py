@@ -34,12 +34,16 @@ METRIC = "particle pushes/s (interp+push+deposit) vs HBM roofline; served p50/p9
 UNIT = "pushes/s"
 # FP64 dense rate of GB300 from the unit counts and clock (nominal 1.25 TFLOP/s)
 FP64_NOMINAL_TFLOPS = 1.25
-# Algorithmic FP64 flops of one 2D push (FMA = 2 flops), counted from the kernel:
-# shapes 40, interpolation 126, Boris 70, move 7, new shapes + DS 30, deposit 97.
-FLOPS_PER_PUSH_2D = 370
-# 3D: shapes 60, interpolation 6 x 57, Boris 70, move 10, new shapes + DS 45,
-# deposition (no crossing) 3 x 9 x 7 + 12
-FLOPS_PER_PUSH_3D = 660
+# Algorithmic FP64 flops of one push (FMA = 2, rsqrt and division 1 each), counted from
+# the kernels' no-crossing path.
+# 2D: positions 6, shapes 4 x 7, interpolation 6 x 20, Boris 64, move 11, deposition 96
+# (new shapes 14, weights and running sums 33, charge factors 4, 21 taps 45). ncu counts
+# 371 executed FP64 flops per push: the rsqrt and division iterations and the deposits of
+# cell-crossing particles add the rest.
+FLOPS_PER_PUSH_2D = 325
+# 3D: positions 9, shapes 6 x 7, interpolation 6 x 65, Boris 64, move 15, deposition 222
+# (new shapes 21, weights 54, running sums 9, charge factors 3, 54 taps 135).
+FLOPS_PER_PUSH_3D = 742
 
 
 DTYPE = {"fp64": "f64", "fp32": "f32", "df64": "f32x2 (double-word, ~48-bit)"}
