@@ -418,8 +418,10 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
 
 
 def run_e2e(args, w, precision, K, chunk=0, world=1):
-    """Same metric through the public C ABI with host buffers: load (H2D), K steps,
-    read back the energy and the axis wake field (D2H), all inside the timed region."""
+    """Same metric through the public C ABI with host buffers, all inside the timed
+    region: load the particles and fields from host arrays (H2D), then K steps, each
+    followed by a read of its step record (step count and window shifts, 24 bytes D2H,
+    which waits for the step), and at the end the energy and the axis wake field."""
     import torch
 
     from paper_1511_03878_gb300 import binding
@@ -432,7 +434,9 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     barrier(world)
     t0 = time.perf_counter()
     sim.load(w)
-    sim.step(K)
+    for _ in range(K):
+        sim.step(1)
+        sim.step_info()
     e = sim.energy()
     ax = sim.ex_axis()
     t1 = time.perf_counter()
@@ -441,8 +445,10 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     per_slot = es * (dims + 3 + 1) + 4 + (0 if precision == "fp64" else 4)
     cfg = sim.cfg
     fstride = (cfg.n[0] + 4) * (cfg.n[1] + 3) * ((cfg.n[2] + 3) if dims == 3 else 1)
-    h2d = cap * per_slot + 9 * fstride * es + 5 * sim.npatch * 4
-    d2h = e.nbytes + ax.nbytes
+    # the loader copies the n live particles packed (free slots are cleared on the device),
+    # six per-patch int arrays and the fields (E, B and the background charge)
+    h2d = n * per_slot + 9 * fstride * es + 6 * sim.npatch * 4
+    d2h = 24 * K + e.nbytes + ax.nbytes
     sim.close()
     seconds = max_over_ranks(t1 - t0, world)
     return dict(value=job_value(sum_over_ranks(n * K, world), 1e3 * seconds), h2d=h2d / K,

@@ -67,6 +67,37 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
             jatomic(jy + JX + k, jprod<JT>(by2, wx0));
             wx0 = wx1, wx1 = wx2;
         }
+    } else if constexpr (std::is_same<T, double>::value && std::is_same<JT, long long>::value) {
+        // FP64 with the int64 tile: the 21 tap products in integer arithmetic, with the
+        // weights (all in [-1, 1]) in 2^62 fixed point and the charge factors already
+        // carrying the tile's 2^k; the FP64 pipe, which bounds this kernel, only forms the
+        // weights
+        long long WY[3], WX[3], WZ[3], SX[3], AX[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            WY[k] = f64_to_fixed_shift(wy[k], 62);
+            WX[k] = f64_to_fixed_shift(wx[k], 62);
+            WZ[k] = f64_to_fixed_shift(wz[k], 62);
+            SX[k] = f64_to_fixed_shift(S0x[k], 62);
+            AX[k] = f64_to_fixed_shift(a[k], 62);
+        }
+        const long long CX1 = f64_to_fixed(ax1), CX2 = f64_to_fixed(ax2);
+        const long long CY1 = f64_to_fixed(by1), CY2 = f64_to_fixed(by2);
+        const long long CZ = f64_to_fixed(qz);
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            jatomic(jx + l * JX + 0, fixmul62(CX1, WY[l]));
+            jatomic(jx + l * JX + 1, fixmul62(CX2, WY[l]));
+            const long long QWY = fixmul62(CZ, WY[l]), QWZ = fixmul62(CZ, WZ[l]);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                jatomic(jz + l * JX + k, fixmul62(QWY, SX[k]) + fixmul62(QWZ, AX[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            jatomic(jy + 0 * JX + k, fixmul62(CY1, WX[k]));
+            jatomic(jy + 1 * JX + k, fixmul62(CY2, WX[k]));
+        }
     } else {
 #pragma unroll
         for (int l = 0; l < 3; l++) {

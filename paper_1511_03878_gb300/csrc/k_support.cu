@@ -550,6 +550,51 @@ cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int pr
     return cudaGetLastError();
 }
 
+// ================================================================ particle load
+
+// Places the particles a load staged, packed in patch order, in the repack scratch
+// arrays (a*): the k-th staged particle belongs to the patch p with
+// start[p] <= k < start[p+1] (start, one entry per patch, is in S.aux) and goes to slot
+// pbase[p] + k - start[p]. Free slots were cleared beforehand (id -1).
+template <typename T>
+__global__ void __launch_bounds__(256) load_scatter_kernel(const BatchDev* __restrict__ bd,
+                                                           long long n) {
+    const SimDev& S = bd->sims[0];
+    const int* start = S.aux;
+    const int np = S.npatch, dims = S.dims;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        // largest p with start[p] <= k (empty patches share the next one's start)
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const long long dst = S.pbase[lo] + (k - start[lo]);
+        if constexpr (uses_cell<T>()) S.cell[dst] = S.acell[k];
+        for (int a = 0; a < dims; a++)
+            reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.axi[a])[k];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            reinterpret_cast<T*>(S.u[a])[dst] = reinterpret_cast<const T*>(S.au[a])[k];
+        reinterpret_cast<T*>(S.w)[dst] = reinterpret_cast<const T*>(S.aw)[k];
+        S.id[dst] = S.aid[k];
+    }
+}
+
+cudaError_t launch_load_scatter(const BatchDev* bd, long long n, int prec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    const long long want = (n + 255) / 256;
+    const int grid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
+    PIC_DISPATCH(prec, (load_scatter_kernel<T><<<grid, 256, 0, s>>>(bd, n)));
+    return cudaGetLastError();
+}
+
 // ================================================================ end of step
 
 // End of step, one CTA per sim: install the layout of a repack done in this step

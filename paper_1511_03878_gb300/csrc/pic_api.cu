@@ -698,61 +698,67 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
             }
         });
     }
-    // device-layout host arrays (capacity slots; empty slots id -1), filled per patch
+    // the live particles packed in patch order (start[p] + c for the c-th of patch p) in
+    // host staging arrays; the device scatters them to their slots. Only n particles
+    // cross the link, and the free slots are cleared on the device.
     const size_t es = elem_size(S.prec);
     const long long cap = S.capacity;
-    std::unique_ptr<char[]> hx[3], hu[3], hw(new char[cap * es]);
-    std::unique_ptr<int[]> hid(new int[cap]), hcell;
-    for (int a = 0; a < dims; a++) hx[a].reset(new char[cap * es]);
-    for (int a = 0; a < 3; a++) hu[a].reset(new char[cap * es]);
-    if (S.prec != PIC_FP64) hcell.reset(new int[cap]);
-    parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
-        for (long long p = pb0; p < pb1; p++) {
-            const long long lo = pbase[p], hi = p + 1 < S.npatch ? pbase[p + 1] : cap;
-            for (long long c = 0; c < counts[p]; c++) {
-                const long long src = order[start[p] + c];
-                const long long dst = lo + c;
-                if (S.prec == PIC_FP64) {
-                    for (int a = 0; a < dims; a++)
-                        reinterpret_cast<double*>(hx[a].get())[dst] = xi[src * 3 + a];
-                } else {
-                    int cellv = 0;
-                    for (int a = 0; a < dims; a++) {
-                        const int i = ip[src * 3 + a];
-                        const double f = cell_offset(S.prec, xi[src * 3 + a] - (double)i);
-                        store_real(S.prec, hx[a].get(), dst, f);
-                        cellv |= i << (dims == 2 ? 16 * a : 11 * a);
-                    }
-                    hcell[dst] = cellv;
+    std::unique_ptr<char[]> hx[3], hu[3], hw(new char[std::max(n, 1LL) * es]);
+    std::unique_ptr<int[]> hid(new int[std::max(n, 1LL)]), hcell;
+    for (int a = 0; a < dims; a++) hx[a].reset(new char[std::max(n, 1LL) * es]);
+    for (int a = 0; a < 3; a++) hu[a].reset(new char[std::max(n, 1LL) * es]);
+    if (S.prec != PIC_FP64) hcell.reset(new int[std::max(n, 1LL)]);
+    parallel_ranges(n, nt, [&](long long k0, long long k1, int) {
+        for (long long k = k0; k < k1; k++) {
+            const long long src = order[k];
+            if (S.prec == PIC_FP64) {
+                for (int a = 0; a < dims; a++)
+                    reinterpret_cast<double*>(hx[a].get())[k] = xi[src * 3 + a];
+            } else {
+                int cellv = 0;
+                for (int a = 0; a < dims; a++) {
+                    const int i = ip[src * 3 + a];
+                    const double f = cell_offset(S.prec, xi[src * 3 + a] - (double)i);
+                    store_real(S.prec, hx[a].get(), k, f);
+                    cellv |= i << (dims == 2 ? 16 * a : 11 * a);
                 }
-                store_real(S.prec, hu[0].get(), dst, ux[src]);
-                store_real(S.prec, hu[1].get(), dst, uy[src]);
-                store_real(S.prec, hu[2].get(), dst, uz[src]);
-                store_real(S.prec, hw.get(), dst, w[src]);
-                hid[dst] = id[src];
+                hcell[k] = cellv;
             }
-            // the patch's free slots (and the tail after the last patch)
-            const long long f0 = lo + counts[p];
-            for (int a = 0; a < dims; a++) std::memset(hx[a].get() + f0 * es, 0, (hi - f0) * es);
-            for (int a = 0; a < 3; a++) std::memset(hu[a].get() + f0 * es, 0, (hi - f0) * es);
-            std::memset(hw.get() + f0 * es, 0, (hi - f0) * es);
-            std::memset(hid.get() + f0, 0xFF, (hi - f0) * sizeof(int));  // id -1
-            if (hcell) std::memset(hcell.get() + f0, 0, (hi - f0) * sizeof(int));
+            store_real(S.prec, hu[0].get(), k, ux[src]);
+            store_real(S.prec, hu[1].get(), k, uy[src]);
+            store_real(S.prec, hu[2].get(), k, uz[src]);
+            store_real(S.prec, hw.get(), k, w[src]);
+            hid[k] = id[src];
         }
     });
-    for (int a = 0; a < dims; a++)
-        CK(cudaMemcpyAsync(S.xi[a], hx[a].get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy x");
-    for (int a = 0; a < 3; a++)
-        CK(cudaMemcpyAsync(S.u[a], hu[a].get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy u");
-    CK(cudaMemcpyAsync(S.w, hw.get(), cap * es, cudaMemcpyHostToDevice, s->stream), "copy w");
-    CK(cudaMemcpyAsync(S.id, hid.get(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream), "copy id");
-    if (S.prec != PIC_FP64)
-        CK(cudaMemcpyAsync(S.cell, hcell.get(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream),
-           "copy cell");
+    std::vector<int> hstart(S.npatch);
+    for (int p = 0; p < S.npatch; p++) hstart[p] = (int)start[p];
+    // free slots: zero state, id -1
+    for (int a = 0; a < dims; a++) CK(cudaMemsetAsync(S.xi[a], 0, cap * es, s->stream), "clear x");
+    for (int a = 0; a < 3; a++) CK(cudaMemsetAsync(S.u[a], 0, cap * es, s->stream), "clear u");
+    CK(cudaMemsetAsync(S.w, 0, cap * es, s->stream), "clear w");
+    CK(cudaMemsetAsync(S.id, 0xFF, cap * sizeof(int), s->stream), "clear id");
+    if (S.prec != PIC_FP64) CK(cudaMemsetAsync(S.cell, 0, cap * sizeof(int), s->stream), "clear cell");
+    if (n > 0) {
+        for (int a = 0; a < dims; a++)
+            CK(cudaMemcpyAsync(S.axi[a], hx[a].get(), n * es, cudaMemcpyHostToDevice, s->stream),
+               "copy x");
+        for (int a = 0; a < 3; a++)
+            CK(cudaMemcpyAsync(S.au[a], hu[a].get(), n * es, cudaMemcpyHostToDevice, s->stream),
+               "copy u");
+        CK(cudaMemcpyAsync(S.aw, hw.get(), n * es, cudaMemcpyHostToDevice, s->stream), "copy w");
+        CK(cudaMemcpyAsync(S.aid, hid.get(), n * sizeof(int), cudaMemcpyHostToDevice, s->stream),
+           "copy id");
+        if (S.prec != PIC_FP64)
+            CK(cudaMemcpyAsync(S.acell, hcell.get(), n * sizeof(int), cudaMemcpyHostToDevice,
+                               s->stream), "copy cell");
+    }
     const size_t pb = S.npatch * sizeof(int);
     CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
     CK(cudaMemcpyAsync(S.pcap, pcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcap");
     CK(cudaMemcpyAsync(S.pcount, counts.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcount");
+    CK(cudaMemcpyAsync(S.aux, hstart.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy start");
+    CK(launch_load_scatter(s->L.db, n, S.prec, s->stream), "scatter particles");
     CK(cudaMemcpyAsync(S.mbase, mbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mbase");
     CK(cudaMemcpyAsync(S.mcap, mcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mcap");
     CK(cudaMemsetAsync(S.hcount, 0, pb, s->stream), "zero hcount");

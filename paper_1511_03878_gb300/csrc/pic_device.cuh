@@ -332,14 +332,14 @@ struct FieldConst<df64> {
     }
 };
 
-// round(x) as int64 with integer operations only, for |x| < 2^62 (the fixed-point
-// exponent guarantees it); keeps the conversion off the FP64 pipe
-__device__ __forceinline__ long long f64_to_fixed(double x) {
+// round(x 2^s) as int64 with integer operations only, for |x| 2^s < 2^62 (the fixed-point
+// exponents guarantee it); keeps the conversion off the FP64 pipe
+__device__ __forceinline__ long long f64_to_fixed_shift(double x, int s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7FFu);
     if (e == 0) return 0;  // zero or far below the quantum
     const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
-    const int sh = e - 1075;  // |x| = m 2^sh
+    const int sh = e - 1075 + s;  // |x| 2^s = m 2^sh
     long long r;
     if (sh >= 0)
         r = m << sh;
@@ -348,6 +348,15 @@ __device__ __forceinline__ long long f64_to_fixed(double x) {
     else
         r = 0;
     return (b >> 63) ? -r : r;
+}
+// round(x) as int64 (see above)
+__device__ __forceinline__ long long f64_to_fixed(double x) { return f64_to_fixed_shift(x, 0); }
+// round(a w / 2^62) for a weight w held in 2^62 fixed point (|w| <= 2^62, |a| < 2^62),
+// from the 128-bit product: integer multiplies instead of an FP64 one
+__device__ __forceinline__ long long fixmul62(long long a, long long w) {
+    const long long hi = __mul64hi(a, w);
+    const unsigned long long lo = (unsigned long long)a * (unsigned long long)w;
+    return hi * 4 + (long long)(lo >> 62) + (long long)((lo >> 61) & 1ULL);
 }
 // tile value of the product a*b; for the fixed-point tile `a` already carries the factor
 // 2^k (see jscale)
