@@ -386,11 +386,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 if constexpr (is_f64<T>::value) {
                     xi0 = nx0;
                     eta0 = ny0;
-                    const double fxd = floor(xi0), fyd = floor(eta0);
                     ix = floor_to_int(xi0);
                     iy = floor_to_int(eta0);
-                    fx = xi0 - fxd;
-                    fy = eta0 - fyd;
+                    // floors widened back with integer operations (exact)
+                    fx = xi0 - fixed_to_f64(ix, 0);
+                    fy = eta0 - fixed_to_f64(iy, 0);
                 } else {
                     ix = nc & 0xFFFF;
                     iy = (nc >> 16) & 0xFFFF;
@@ -463,11 +463,10 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     xi1 = xi0 + dtdx * vx;
                     eta1 = eta0 + dtdy * vy;
                     const double hx1 = xi1 + 0.5, hy1 = eta1 + 0.5;
-                    const double nx1d = floor(hx1), ny1d = floor(hy1);
                     nxp1 = floor_to_int(hx1);
                     nyp1 = floor_to_int(hy1);
-                    dxp1 = xi1 - nx1d;
-                    dyp1 = eta1 - ny1d;
+                    dxp1 = xi1 - fixed_to_f64(nxp1, 0);
+                    dyp1 = eta1 - fixed_to_f64(nyp1, 0);
                 } else {
                     fx1 = fx + dtdx * vx;
                     fy1 = fy + dtdy * vy;

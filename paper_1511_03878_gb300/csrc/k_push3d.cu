@@ -59,9 +59,8 @@ __device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             xi[a] = reinterpret_cast<const double*>(S.xi[a])[slot];
-            const double fl = floor(xi[a]);
-            i[a] = (int)fl;
-            f[a] = xi[a] - fl;
+            i[a] = floor_to_int(xi[a]);  // integer floor, widened back exactly
+            f[a] = xi[a] - fixed_to_f64(i[a], 0);
         }
     } else {
         const int c = S.cell[slot];
@@ -316,9 +315,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                 for (int a = 0; a < 3; a++) {
                     if constexpr (is_f64<T>::value) {
                         xin[a] = xi0[a] + dtd[a] * v[a];
-                        const double nd = floor(xin[a] + 0.5);
-                        np1[a] = (int)nd;
-                        dp1[a] = xin[a] - nd;
+                        np1[a] = floor_to_int(xin[a] + 0.5);
+                        dp1[a] = xin[a] - fixed_to_f64(np1[a], 0);
                     } else {
                         T g = f[a] + dtd[a] * v[a];
                         int i1 = ic[a];
@@ -436,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                                 if (xin[a] < 0.0) xin[a] += (double)n[a];
                                 if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
                             }
-                            icn[a] = (int)floor(xin[a]);
+                            icn[a] = floor_to_int(xin[a]);
                         } else if (!(window && a == 0)) {
                             icn[a] = wrapi(icn[a], n[a]);
                         }
