@@ -128,9 +128,15 @@ template <typename T>
 #ifndef PIC_DF64_3D_MINB
 #define PIC_DF64_3D_MINB 1
 #endif
+// FP64: one CTA per SM (210 registers). Two (128 registers, 564 bytes of spills) measured
+// 1 % slower on the 3D stress case.
+#ifndef PIC_F64_3D_MINB
+#define PIC_F64_3D_MINB 1
+#endif
 __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                                                 ? 2
-                                                : (std::is_same<T, df64>::value ? PIC_DF64_3D_MINB : 1))
+                                                : (std::is_same<T, df64>::value ? PIC_DF64_3D_MINB
+                                                                               : PIC_F64_3D_MINB))
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType3D<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
