@@ -11,6 +11,15 @@
 
 namespace pic {
 
+// Row stride of the 2D current tile, whose rows hold P0 + 5 nodes. The 4-byte (FP32) tile
+// is padded to the field tile's stride P0 + 4 modulo the 32 shared-memory banks: a
+// particle's field taps and current taps then sit in the same bank classes, so the bank
+// interleaving of the particle order spreads the loads and the atomics of a warp alike.
+template <typename T>
+__host__ __device__ constexpr int jrow2d(int P0) {
+    return sizeof(typename JType<T>::type) == 4 ? P0 + 4 + 32 : P0 + 5;
+}
+
 // Gather of one staggered component: Sx/Sy are the three weights, (tx, ty) the tile
 // index of the first tap.
 template <typename T>
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
 
         const int P0 = S.P[0], P1 = S.P[1];
         const int BX = S.BX, BY = S.BY;
-        const int JX = P0 + 5, JY = P1 + 5;
+        const int JX = jrow2d<T>(P0), JY = P1 + 5, JW = P0 + 5;  // stride, rows, row width
         const int nx = S.n[0], ny = S.n[1];
         const int NX = S.NX;
         const int px0 = (patch % S.np[0]) * P0;
@@ -300,7 +309,10 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         JT* Jt = reinterpret_cast<JT*>(smem + ((fbytes + 127) & ~127));
         const int jplane = JX * JY;
 
-        for (int e = tid; e < 3 * jplane; e += blockDim.x) Jt[e] = JT(0);
+        for (int e = tid; e < 3 * JY * JW; e += blockDim.x) {
+            const int r = e / JW;  // component * JY + row
+            Jt[r * JX + (e - r * JW)] = JT(0);
+        }
 
         if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
             if (tid == 0) {
@@ -620,12 +632,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         // ---- flush the current tile (origin px0-2, py0-2) into the global FP64 J
         double* Jg = S.J[gen];
         const long long fs = S.fstride;
-        for (int e = tid; e < 3 * jplane; e += blockDim.x) {
-            const JT v = Jt[e];
+        for (int e = tid; e < 3 * JY * JW; e += blockDim.x) {
+            const int rr = e / JW, tx = e - rr * JW;  // rr = component * JY + row
+            const int comp = rr / JY, ty = rr - comp * JY;
+            const JT v = Jt[rr * JX + tx];
             if (v == JT(0)) continue;
-            const int comp = e / jplane;
-            const int r = e - comp * jplane;
-            const int ty = r / JX, tx = r - ty * JX;
             int gi = px0 - 2 + tx, gj = py0 - 2 + ty;
             if (window) {
                 if (gi < 0 || gi >= nx) continue;
@@ -642,7 +653,7 @@ template <typename T>
 static int smem_bytes_2d(int P0, int P1) {
     const int BX = ((P0 + 3) + 3) & ~3, BY = P1 + 3;
     const int fb = 6 * BX * BY * (int)sizeof(T);
-    const int jb = 3 * (P0 + 5) * (P1 + 5) * (int)sizeof(typename JType<T>::type);
+    const int jb = 3 * jrow2d<T>(P0) * (P1 + 5) * (int)sizeof(typename JType<T>::type);
     return ((fb + 127) & ~127) + jb;
 }
 

@@ -697,6 +697,41 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
                 }
             }
         });
+        // then interleave the 32 shared-memory bank classes of the particles' cells (the
+        // cell's field-tile address modulo 32): run j of 32 consecutive particles takes the
+        // j-th particle of every class that has one, so the lanes of a warp read and add
+        // into different banks and never share a cell
+        parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
+            std::vector<long long> tmp;
+            std::vector<int> cls, rank;
+            for (long long p = pb0; p < pb1; p++) {
+                const long long b0 = start[p], c = counts[p];
+                if (c < 2) continue;
+                const int pxo = (int)(p % S.np[0]) * S.P[0];
+                const int pyo = (int)((p / S.np[0]) % S.np[1]) * S.P[1];
+                const int pzo = (int)(p / ((long long)S.np[0] * S.np[1])) * S.P[2];
+                int nb[32] = {0};
+                cls.resize(c);
+                rank.resize(c);
+                tmp.resize(c);
+                for (long long k = 0; k < c; k++) {
+                    const long long src = order[b0 + k];
+                    const long long lx = ip[src * 3] - pxo, ly = ip[src * 3 + 1] - pyo;
+                    const long long lz = dims == 3 ? ip[src * 3 + 2] - pzo : 0;
+                    const int b = (int)(((lz * S.BY + ly) * S.BX + lx) & 31);
+                    cls[k] = b;
+                    rank[k] = nb[b]++;
+                }
+                for (long long k = 0; k < c; k++) {
+                    const int b = cls[k], r = rank[k];
+                    long long pos = 0;
+                    for (int q = 0; q < 32; q++)
+                        pos += std::min(nb[q], r) + ((q < b && nb[q] > r) ? 1 : 0);
+                    tmp[pos] = order[b0 + k];
+                }
+                std::copy(tmp.begin(), tmp.end(), order.begin() + b0);
+            }
+        });
     }
     // the live particles packed in patch order (start[p] + c for the c-th of patch p) in
     // host staging arrays; the device scatters them to their slots. Only n particles
