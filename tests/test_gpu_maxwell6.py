@@ -171,3 +171,55 @@ def test_batch_refuses_mixed_solver_orders(binding):
     finally:
         for s in (a, b, c):
             s.close()
+
+
+def _group_velocity(order, k, dx, dt):
+    """dω/dk of the 1D discrete vacuum relation sin(ω dt/2) = (dt/2) K(k), where K is the
+    symbol of the staggered difference (Yee: (2/dx) sin(k dx/2); sixth order: the c_l sum)."""
+    c = (1.0,) if order == 2 else (75 / 64, -25 / 384, 3 / 640)
+
+    def omega(kk):
+        K = 2 / dx * sum(cl * np.sin((2 * l + 1) * kk * dx / 2) for l, cl in enumerate(c))
+        return 2 / dt * np.arcsin(dt * K / 2)
+
+    h = 1e-4
+    return (omega(k + h) - omega(k - h)) / (2 * h)
+
+
+@pytest.mark.parametrize("order,cfl", [(2, 0.95), (6, 0.76)])
+def test_laser_group_velocity_in_vacuum(binding, order, cfl):
+    """Sec. 2.1: the second-order scheme propagates a laser pulse slower than light and
+    the sixth-order one faster. A pulse uniform in y (no diffraction) crosses a vacuum
+    moving window in FP64; the lab-frame drift of its energy centroid gives the group
+    velocity, which must match the discrete dispersion relation at k0 = 1 within 10 %
+    of its offset from c and have the predicted sign."""
+    w = inputs.lwfa2d(nx=512, ny=32, n0=0.0, laser_back=24.0, tau=8.0, patch=(32, 32), cfl=cfl)
+    p = dict(w["params"], maxwell_order=order)
+    nx, ny = p["n"][0], p["n"][1]
+    dx, dt, xc = p["d"][0], p["dt"], p["xc"]
+    x = np.arange(nx) * dx
+    env = lambda s: np.exp(-2.0 * np.log(2.0) * (s - xc) ** 2 / 8.0 ** 2) * np.cos(s - xc)
+    E = [np.zeros((ny, nx)), np.repeat(env(x)[None, :], ny, 0), np.zeros((ny, nx))]
+    B = [np.zeros((ny, nx)), np.zeros((ny, nx)), np.repeat(env(x + 0.5 * dx - 0.5 * dt)[None, :], ny, 0)]
+    w = dict(w, params=p, E=E, B=B)
+    sim = binding.Sim(p, precision=binding.PIC_FP64, capacity=100000)
+    sim.load(w)
+
+    def centroid():
+        f = sim.fields()
+        ey2 = (f["Ey"] ** 2).sum(axis=0)
+        bz2 = (f["Bnz"] ** 2).sum(axis=0)
+        xs = (np.sum(x * ey2) + np.sum((x + 0.5 * dx) * bz2)) / (ey2.sum() + bz2.sum())
+        return xs + sim.step_info()[1] * dx  # window frame -> lab frame
+
+    n0, n1 = 20, int(round(46.0 / dt))
+    sim.step(n0)
+    x0 = centroid()
+    sim.step(n1 - n0)
+    x1 = centroid()
+    sim.close()
+    vg = (x1 - x0) / ((n1 - n0) * dt)
+    want = _group_velocity(order, 1.0, dx, dt)
+    print(f"\norder {order}: measured v_g - 1 = {vg - 1:.3e}, dispersion relation {want - 1:.3e}")
+    assert np.sign(vg - 1) == np.sign(want - 1) == (-1 if order == 2 else 1)
+    assert abs((vg - 1) - (want - 1)) < 0.1 * abs(want - 1)

@@ -251,3 +251,48 @@ def test_group_velocity_under_for_yee_over_for_sixth_order(m):
         w2, k2 = _omega(order, m + 1)
         v[order] = (w2 - w1) / (k2 - k1)
     assert v[2] < 1.0 < v[6], v
+
+
+@pytest.mark.parametrize("order,cfl", [(2, 0.95), (6, 0.76)])
+def test_pulse_group_velocity_matches_dispersion_relation(order, cfl):
+    """A laser pulse uniform in y (k0 = 1, dx = 0.125, 8-unit duration) crossing a vacuum
+    moving window: the lab-frame speed of its energy centroid is the group velocity of
+    the 1D discrete relation sin(w dt/2) = (dt/2) K(k) at k0, within 5 % of its offset
+    from c (below c for Yee, above for the sixth-order scheme, Sec. 2.1)."""
+    nx, ny, dx, dy = 512, 4, 0.125, 0.5
+    kappa = 1.0 if order == 2 else KAPPA6
+    dt = cfl / math.sqrt(1 / dx ** 2 + 1 / dy ** 2)
+    assert dt * kappa * math.sqrt(1 / dx ** 2 + 1 / dy ** 2) < 1
+    c = orc.make_config(2, (nx, ny), (dx, dy), dt, window=True, n0=0.0, order=order)
+    x = np.arange(nx) * dx
+    xc = 40.0
+    env = lambda s: np.exp(-2.0 * math.log(2.0) * (s - xc) ** 2 / 8.0 ** 2) * np.cos(s - xc)
+    E, B = _zeros(c), _zeros(c)
+    E[1][...] = env(x)[None, :]
+    B[2][...] = env(x + 0.5 * dx - 0.5 * dt)[None, :]
+    o = orc.OracleSim(c, 16)
+    o.set_particles({k: np.zeros(0) for k in ("x", "y", "z", "ux", "uy", "uz", "w")}
+                    | {"id": np.zeros(0, np.int32)})
+    o.set_fields(E, B)
+    o.set_rho_bg(None)
+
+    def centroid():
+        f = o.get_fields()
+        ey2, bz2 = (f["Ey"] ** 2).sum(axis=0), (f["Bnz"] ** 2).sum(axis=0)
+        xs = (np.sum(x * ey2) + np.sum((x + 0.5 * dx) * bz2)) / (ey2.sum() + bz2.sum())
+        return xs + o.shifts * dx
+
+    n0, n1 = 20, int(round(46.0 / dt))
+    o.step(n0)
+    x0 = centroid()
+    o.step(n1 - n0)
+    vg = (centroid() - x0) / ((n1 - n0) * dt)
+    coef = (1.0,) if order == 2 else C6
+
+    def omega(k):
+        K = 2 / dx * sum(cl * math.sin((2 * l + 1) * k * dx / 2) for l, cl in enumerate(coef))
+        return 2 / dt * math.asin(dt * K / 2)
+
+    want = (omega(1.0 + 1e-4) - omega(1.0 - 1e-4)) / 2e-4
+    assert (vg - 1) * (want - 1) > 0 and (want - 1 < 0) == (order == 2)
+    assert abs((vg - 1) - (want - 1)) < 0.05 * abs(want - 1), (vg - 1, want - 1)
