@@ -87,10 +87,12 @@ def parse():
                     help="cached: the layouts recorded in the package's tuning table (measured "
                          "there when missing); on: measure again; off: workload patch, --chunk")
     ap.add_argument("--workload", default="lwfa",
-                    choices=["lwfa", "lwfa3d", "stress3d", "thermal", "serve"])
+                    choices=["lwfa", "lwfa3d", "stress3d", "thermal", "serve", "batch"])
     ap.add_argument("--requests", type=int, default=256, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget")
+    ap.add_argument("--batch-sims", type=int, default=16,
+                    help="batch: simulations of the scan distribution stepped together")
     ap.add_argument("--mapping", default="queue", choices=["queue", "static"])
     ap.add_argument("--total", type=int, default=64 * 2 ** 20, help="stress3d particles")
     ap.add_argument("--maxwell-order", type=int, default=2, choices=[2, 6],
@@ -623,6 +625,88 @@ def launch_layout(args, w, precision):
     return dict(w, params=dict(w["params"], patch=c.patch)), c.chunk, rec
 
 
+def batch_arm(args):
+    """Batching: simulations of the parameter-scan distribution (mixed grids, particles
+    per cell and densities, so very uneven patch loads), FP32, stepped together in one
+    persistent particle launch per step (pic_batch) against the same simulations
+    stepped one at a time; value = the batched aggregate pushes/s."""
+    import torch
+
+    import __graft_entry__
+    from paper_1511_03878_gb300 import binding, serve
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    reqs = serve.scan_requests(n=args.batch_sims, rate=1.0, seed=1516)
+    sims = []
+    for r in reqs:
+        w = serve.request_workload(r)
+        sim = binding.Sim(w["params"], precision=binding.PIC_FP32,
+                          capacity=serve.request_capacity(r))
+        sim.load(w)
+        sims.append(sim)
+    for sim in sims:
+        sim.sync()
+    stream = torch.cuda.Stream()
+    handles = [s.h for s in sims]
+    nbytes = binding.pic_batch_required_bytes(handles)
+    arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    batch = binding.pic_batch_create(handles, (arena.data_ptr() + 255) // 256 * 256, nbytes,
+                                     stream.cuda_stream)
+    K, W = args.steps, args.warmup
+    clocks = ClockSampler(0)
+    binding.pic_batch_step(batch, W)
+    stream.synchronize()
+    n0 = sum(s.num_particles() for s in sims)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    ev0.record(stream)
+    binding.pic_batch_step(batch, K)
+    ev1.record(stream)
+    ev1.synchronize()
+    clocks.stop()
+    ms_batch = ev0.elapsed_time(ev1)
+    n1 = sum(s.num_particles() for s in sims)
+    pushes_batch = K * 0.5 * (n0 + n1)
+    binding.pic_batch_destroy(batch)
+    # the same simulations one at a time, each on its own stream and graph
+    ms_seq, pushes_seq = 0.0, 0.0
+    for sim in sims:
+        sim.step(W)
+        sim.sync()
+        a = sim.num_particles()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(K)
+        e1.record(sim.stream)
+        e1.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+        pushes_seq += K * 0.5 * (a + sim.num_particles())
+    for sim in sims:
+        sim.sync()
+        sim.close()
+    value = pushes_batch / (ms_batch * 1e-3)
+    seq = pushes_seq / (ms_seq * 1e-3)
+    counts = [r.nx * r.ny * r.ppc for r in reqs]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": ms_batch / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded LWFA parameter-scan requests)",
+        "config": {"workload": f"batched-lwfa-scan-{args.batch_sims}sims",
+                   "grids": sorted({f"{r.nx}x{r.ny}" for r in reqs}),
+                   "ppc": sorted({r.ppc for r in reqs}), "precision": "fp32",
+                   "particles": int(n0), "largest_over_smallest_sim": max(counts) / min(counts),
+                   "l2": "inputs larger than L2 in aggregate, no flush"},
+        "batching": {"sims": len(reqs), "batched_pushes_per_s": value,
+                     "one_at_a_time_pushes_per_s": seq, "batched_over_one_at_a_time": value / seq,
+                     "one_at_a_time_ms_per_step": ms_seq / K},
+        "gpu_launches": kernels_per_step(True) * K,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def serve_arm(args):
     """Served parameter scan: Poisson arrivals, HBM-budget admission, continuous
     batching; value = aggregate pushes/s, with p50/p99 time-to-completion."""
@@ -684,6 +768,9 @@ def main():
         return
     if args.workload == "serve":
         serve_arm(args)
+        return
+    if args.workload == "batch":
+        batch_arm(args)
         return
     import torch
 
