@@ -227,6 +227,17 @@ pic_status pic_gauss_residual_2d_static(long long n, const double* x, const doub
                                         int nx, int ny, double dx, double dy, int window,
                                         void* cuda_stream);
 
+/* Failure-path self-test of the bounded device waits. Every wait of the library's
+ * kernels on an asynchronous transfer (the mbarrier of a TMA tile load) gives up after
+ * about 2^31 SM clocks (about a second) and latches a status bit instead of hanging.
+ * This call launches one CTA that waits, through that same bounded wait, on an
+ * mbarrier phase that nothing completes, then synchronises cuda_stream and reads the
+ * status back. Expected result: PIC_ERR_TIMEOUT after about a second, with the CUDA
+ * context still usable. PIC_OK would mean the wait completed without its transfer;
+ * PIC_ERR_CUDA reports a failed launch or copy. Allocates 4 bytes of device memory
+ * for the status and frees them. */
+pic_status pic_selftest_bounded_wait(void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
 EXPORTS = ("pic_config_bytes", "pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
            "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
            "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
-           "pic_batch_destroy", "pic_gauss_residual_2d_static")
+           "pic_batch_destroy", "pic_gauss_residual_2d_static", "pic_selftest_bounded_wait")
 PIC_STATIC_MAX_CELLS = 1 << 20
 
 
@@ -109,6 +109,8 @@ def lib():
         L.pic_batch_step.argtypes = [vp, ctypes.c_int]
         L.pic_batch_destroy.restype = ctypes.c_int
         L.pic_batch_destroy.argtypes = [vp]
+        L.pic_selftest_bounded_wait.restype = ctypes.c_int
+        L.pic_selftest_bounded_wait.argtypes = [vp]
         L.pic_gauss_residual_2d_static.restype = ctypes.c_int
         L.pic_gauss_residual_2d_static.argtypes = (
             [ctypes.c_longlong, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, ctypes.c_int,
@@ -248,6 +250,12 @@ def pic_batch_step(b, nsteps: int):
 
 def pic_batch_destroy(b):
     _check(lib().pic_batch_destroy(b))
+
+
+def pic_selftest_bounded_wait(stream_ptr: int) -> int:
+    """Runs the bounded-wait self-test on a stream; returns the pic_status code
+    (PIC_ERR_TIMEOUT is the expected outcome, see include/pic.h)."""
+    return int(lib().pic_selftest_bounded_wait(ctypes.c_void_p(stream_ptr)))
 
 
 def pic_gauss_residual_2d_static(n, x_ptr, y_ptr, w_ptr, q, ex_ptr, ey_ptr, rho_bg_ptr, out_ptr,

@@ -550,6 +550,26 @@ cudaError_t launch_repack(const BatchDev* bd, int nsims, int max_patches, int pr
     return cudaGetLastError();
 }
 
+// ================================================================ failure-path self-test
+
+// One CTA waits, through the kernels' bounded wait, on an mbarrier phase that no
+// transfer and no thread completes, and latches ST_TIMEOUT when the wait gives up.
+__global__ void bounded_wait_selftest_kernel(int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_bounded_wait_selftest(int* status, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
+}
+
 // ================================================================ particle load
 
 // Places the particles a load staged, packed in patch order, in the repack scratch

@@ -505,6 +505,21 @@ uint64_t mix64(uint64_t x) {
 
 extern "C" size_t pic_config_bytes(void) { return sizeof(pic_config); }
 
+extern "C" pic_status pic_selftest_bounded_wait(void* cuda_stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PIC_ERR_CUDA;
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_bounded_wait_selftest(d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    std::string err;
+    return status_to_error(&err, h);
+}
+
 extern "C" size_t pic_required_bytes(const pic_config* cfg) {
     if (validate(cfg)) return 0;
     return plan(cfg, nullptr).bytes;

@@ -160,6 +160,8 @@ int push3d_smem(int prec, int P0, int P1, int P2);
 int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes);
 cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0, int P1, int P2,
                           int grid, cudaStream_t s);
+// failure-path self-test: a bounded wait on an mbarrier that nothing completes
+cudaError_t launch_bounded_wait_selftest(int* status, cudaStream_t s);
 // particle load: staged particles (repack scratch, patch order) to their slots
 cudaError_t launch_load_scatter(const BatchDev* bd, long long n, int prec, cudaStream_t s);
 cudaError_t launch_maxwell6(const BatchDev* bd, int nsims, long long max_ncell, int dims,
