@@ -263,6 +263,20 @@ struct Push2DShape<df64> {
     static constexpr int threads = PIC_DF64_THREADS, min_blocks = PIC_DF64_MINB;
 };
 
+// copy of a leaving particle's state (already stored in its slot) to arrival slot m
+template <typename T>
+__device__ __forceinline__ void handoff_copy(const SimDev& S, int slot, int m, int pid) {
+    if constexpr (uses_cell<T>()) S.mcell[m] = S.cell[slot];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+        reinterpret_cast<T*>(S.mxi[a])[m] = reinterpret_cast<const T*>(S.xi[a])[slot];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        reinterpret_cast<T*>(S.mu[a])[m] = reinterpret_cast<const T*>(S.u[a])[slot];
+    reinterpret_cast<T*>(S.mw)[m] = reinterpret_cast<const T*>(S.w)[slot];
+    S.mid[m] = pid;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_blocks)
     push2d_kernel(const BatchDev* __restrict__ bd, int static_map) {
@@ -270,11 +284,18 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int s_item;
+    // particles of the current item that leave its patch: their slot and destination
+    // (-1: deleted), handed off after the item so that the particle loop makes no
+    // global round trip for them
+    __shared__ int s_lv_n;
+    __shared__ int s_lv_slot[kLeaveList];
+    __shared__ int s_lv_dest[kLeaveList];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&mbar, 1);
         fence_mbar_init();
+        s_lv_n = 0;
     }
     __syncthreads();
 
@@ -563,19 +584,19 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 if (!del) {
                     dest = ix1 / P0 + S.np[0] * (iy1 / P1);
                     leave = dest != patch;
-                    if (!leave) {
-                        if constexpr (is_f64<T>::value) {
-                            reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
-                            reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
-                        } else {
-                            S.cell[slot] = ix1 | (iy1 << 16);
-                            reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
-                            reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
-                        }
-                        U0[slot] = u[0];
-                        U1[slot] = u[1];
-                        U2[slot] = u[2];
+                    // the new state goes to the particle's own slot, also when it leaves:
+                    // the hand-off after the item copies it from there
+                    if constexpr (is_f64<T>::value) {
+                        reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
+                        reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
+                    } else {
+                        S.cell[slot] = ix1 | (iy1 << 16);
+                        reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
+                        reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
                     }
+                    U0[slot] = u[0];
+                    U1[slot] = u[1];
+                    U2[slot] = u[2];
                 } else {
                     dest = -1;
                     leave = true;
@@ -588,11 +609,55 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 dest = -1;
             }
 
-            // ---- E. exchange hand-off (warp-aggregated counters); the loads it needs are
-            // issued before the two claims so that all their latencies overlap
+            // ---- E. exchange hand-off. A leaver is listed in shared memory; only when the
+            // list is full does it claim its slots here (warp-aggregated global counters)
             const bool lv = valid && leave;
-            const bool send = lv && dest >= 0;
-            if (__any_sync(0xffffffffu, lv)) {
+            bool over = false;
+            if (lv) {
+                const int li = atomicAdd(&s_lv_n, 1);
+                if (li < kLeaveList) {
+                    s_lv_slot[li] = slot;
+                    s_lv_dest[li] = dest;
+                } else {
+                    over = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, over)) {
+                const bool send = over && dest >= 0;
+                int pid = 0, mcap = 0, mb = 0;
+                if (over) pid = S.id[slot];
+                if (send) {
+                    mcap = S.mcap[dest];
+                    mb = S.mbase[dest];
+                }
+                const int2 cl = warp_claim2(S.hcount, patch, over, S.mcount, send ? dest : 0, send);
+                if (over) {
+                    S.holes[pb + cl.x] = slot;
+                    S.id[slot] = -1;
+                    if (send) {
+                        if (cl.y < mcap)
+                            handoff_copy<T>(S, slot, mb + cl.y, pid);
+                        else
+                            atomicOr(S.status, ST_MAILBOX);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- hand-off of the listed leavers: their holes and arrival slots are claimed
+        // a warp at a time, and each is copied from its slot to its destination's buffer
+        {
+            const int nl = s_lv_n < kLeaveList ? s_lv_n : kLeaveList;
+            for (int b0 = 0; b0 < nl; b0 += blockDim.x) {  // same trip count in every warp
+                const int t = b0 + tid;
+                const bool lv = t < nl;
+                int slot = 0, dest = -1;
+                if (lv) {
+                    slot = s_lv_slot[t];
+                    dest = s_lv_dest[t];
+                }
+                const bool send = lv && dest >= 0;
                 int pid = 0, mcap = 0, mb = 0;
                 if (lv) pid = S.id[slot];
                 if (send) {
@@ -600,34 +665,21 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     mb = S.mbase[dest];
                 }
                 const int2 cl = warp_claim2(S.hcount, patch, lv, S.mcount, send ? dest : 0, send);
-                const int hslot = cl.x, mslot = cl.y;
-              if (lv) {
-                S.holes[pb + hslot] = slot;
-                S.id[slot] = -1;
-                if (send) {
-                    if (mslot < mcap) {
-                        const int m = mb + mslot;
-                        if constexpr (is_f64<T>::value) {
-                            reinterpret_cast<double*>(S.mxi[0])[m] = xi1;
-                            reinterpret_cast<double*>(S.mxi[1])[m] = eta1;
-                        } else {
-                            S.mcell[m] = ix1 | (iy1 << 16);
-                            reinterpret_cast<T*>(S.mxi[0])[m] = fx1;
-                            reinterpret_cast<T*>(S.mxi[1])[m] = fy1;
-                        }
-                        reinterpret_cast<T*>(S.mu[0])[m] = u[0];
-                        reinterpret_cast<T*>(S.mu[1])[m] = u[1];
-                        reinterpret_cast<T*>(S.mu[2])[m] = u[2];
-                        reinterpret_cast<T*>(S.mw)[m] = w;
-                        S.mid[m] = pid;
-                    } else {
-                        atomicOr(S.status, ST_MAILBOX);
+                if (lv) {
+                    S.holes[pb + cl.x] = slot;
+                    if (send) {
+                        if (cl.y < mcap)
+                            handoff_copy<T>(S, slot, mb + cl.y, pid);
+                        else
+                            atomicOr(S.status, ST_MAILBOX);
                     }
+                    S.id[slot] = -1;
                 }
-              }
             }
         }
         __syncthreads();
+        if (tid == 0) s_lv_n = 0;  // every thread has read it; the next item's appends
+                                   // come after its own barriers
 
         // ---- flush the current tile (origin px0-2, py0-2) into the global FP64 J
         double* Jg = S.J[gen];

@@ -99,7 +99,8 @@ const char* validate(const pic_config* c) {
     }
     if (c->dims == 2 && c->n[2] != 1) return "2D needs n[2] = 1";
     if (c->dims == 2 && (c->n[0] >= 65536 || c->n[1] >= 32768)) return "grid too large";
-    if (c->dims == 2 && push2d_smem(c->precision, c->patch[0], c->patch[1]) > 227 * 1024)
+    if (c->dims == 2 &&
+        push2d_smem(c->precision, c->patch[0], c->patch[1]) + kPush2DStatic > 227 * 1024)
         return "2D patch tile does not fit in shared memory";
     if (c->dims == 3) {
         if (c->n[0] > 2048 || c->n[1] > 2048 || c->n[2] > 1024) return "3D grid too large";

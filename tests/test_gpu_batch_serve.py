@@ -79,10 +79,12 @@ def test_serve_same_alone_and_in_mix(binding):
 
     reqs = [serve.Request(rid=i, nx=nx, ny=ny, a0=a0, n0=n0, ppc=ppc, steps=st, arrival=t)
             for i, (nx, ny, a0, n0, ppc, st, t) in enumerate([
-                (256, 128, 3.0, 0.01, 4, 80, 0.0),
-                (512, 256, 5.0, 0.005, 2, 120, 0.01),
-                (256, 128, 2.0, 0.02, 8, 60, 0.02),
-                (512, 256, 4.0, 0.015, 1, 100, 0.03)])]
+                # all arrive together and run far longer than a preparation takes, so
+                # they are resident together whatever the GPU's speed
+                (256, 128, 3.0, 0.01, 4, 300, 0.0),
+                (512, 256, 5.0, 0.005, 2, 400, 0.0),
+                (256, 128, 2.0, 0.02, 8, 250, 0.0),
+                (512, 256, 4.0, 0.015, 1, 350, 0.0)])]
     srv = serve.Server(budget_bytes=40 << 30, quantum=20)
     res = srv.run(reqs)
     assert [r.rid for r in res] == [0, 1, 2, 3]
