@@ -124,6 +124,20 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
     }
 }
 
+// copy of a leaving particle's state (already stored in its slot) to arrival slot m
+template <typename T>
+__device__ __forceinline__ void handoff_copy3d(const SimDev& S, int slot, int m, int pid) {
+    if constexpr (uses_cell<T>()) S.mcell[m] = S.cell[slot];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        reinterpret_cast<T*>(S.mxi[a])[m] = reinterpret_cast<const T*>(S.xi[a])[slot];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        reinterpret_cast<T*>(S.mu[a])[m] = reinterpret_cast<const T*>(S.u[a])[slot];
+    reinterpret_cast<T*>(S.mw)[m] = reinterpret_cast<const T*>(S.w)[slot];
+    S.mid[m] = pid;
+}
+
 template <typename T>
 #ifndef PIC_DF64_3D_MINB
 #define PIC_DF64_3D_MINB 1
@@ -142,11 +156,16 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int s_item;
+    // leavers of the current item (slot, destination or -1), handed off after the item
+    __shared__ int s_lv_n;
+    __shared__ int s_lv_slot[kLeaveList];
+    __shared__ int s_lv_dest[kLeaveList];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&mbar, 1);
         fence_mbar_init();
+        s_lv_n = 0;
     }
     __syncthreads();
 
@@ -448,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                     }
                     dest = del ? -1 : dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
                     leave = del || dest != patch;
-                    if (!leave) {
+                    if (!del) {  // also a leaver: the hand-off copies its state from here
                         if constexpr (is_f64<T>::value) {
                             for (int a = 0; a < 3; a++)
                                 reinterpret_cast<double*>(S.xi[a])[slot] = xin[a];
@@ -467,10 +486,54 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                 leave = true;
                 dest = -1;
             }
-            // loads first, then both claims, so that all their latencies overlap
+            // exchange hand-off: a leaver is listed in shared memory; only when the list
+            // is full does it claim its slots here (warp-aggregated global counters)
             const bool lv = valid && leave;
-            const bool send = lv && dest >= 0;
-            if (__any_sync(0xffffffffu, lv)) {
+            bool over = false;
+            if (lv) {
+                const int li = atomicAdd(&s_lv_n, 1);
+                if (li < kLeaveList) {
+                    s_lv_slot[li] = slot;
+                    s_lv_dest[li] = dest;
+                } else {
+                    over = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, over)) {
+                const bool send = over && dest >= 0;
+                int pid = 0, mcap = 0, mb = 0;
+                if (over) pid = S.id[slot];
+                if (send) {
+                    mcap = S.mcap[dest];
+                    mb = S.mbase[dest];
+                }
+                const int2 cl = warp_claim2(S.hcount, patch, over, S.mcount, send ? dest : 0, send);
+                if (over) {
+                    S.holes[pb + cl.x] = slot;
+                    S.id[slot] = -1;
+                    if (send) {
+                        if (cl.y < mcap)
+                            handoff_copy3d<T>(S, slot, mb + cl.y, pid);
+                        else
+                            atomicOr(S.status, ST_MAILBOX);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // hand-off of the listed leavers, a warp-aggregated claim at a time
+        {
+            const int nl = s_lv_n < kLeaveList ? s_lv_n : kLeaveList;
+            for (int b0 = 0; b0 < nl; b0 += blockDim.x) {  // same trip count in every warp
+                const int t = b0 + tid;
+                const bool lv = t < nl;
+                int slot = 0, dest = -1;
+                if (lv) {
+                    slot = s_lv_slot[t];
+                    dest = s_lv_dest[t];
+                }
+                const bool send = lv && dest >= 0;
                 int pid = 0, mcap = 0, mb = 0;
                 if (lv) pid = S.id[slot];
                 if (send) {
@@ -478,33 +541,20 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                     mb = S.mbase[dest];
                 }
                 const int2 cl = warp_claim2(S.hcount, patch, lv, S.mcount, send ? dest : 0, send);
-                const int hslot = cl.x, mslot = cl.y;
-              if (lv) {
-                S.holes[pb + hslot] = slot;
-                S.id[slot] = -1;
-                if (send) {
-                    if (mslot < mcap) {
-                        const int m = mb + mslot;
-                        if constexpr (is_f64<T>::value) {
-                            for (int a = 0; a < 3; a++)
-                                reinterpret_cast<double*>(S.mxi[a])[m] = xin[a];
-                        } else {
-                            S.mcell[m] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
-                            for (int a = 0; a < 3; a++)
-                                reinterpret_cast<T*>(S.mxi[a])[m] = fn[a];
-                        }
-                        reinterpret_cast<T*>(S.mu[0])[m] = u[0];
-                        reinterpret_cast<T*>(S.mu[1])[m] = u[1];
-                        reinterpret_cast<T*>(S.mu[2])[m] = u[2];
-                        reinterpret_cast<T*>(S.mw)[m] = w;
-                        S.mid[m] = pid;
-                    } else {
-                        atomicOr(S.status, ST_MAILBOX);
+                if (lv) {
+                    S.holes[pb + cl.x] = slot;
+                    if (send) {
+                        if (cl.y < mcap)
+                            handoff_copy3d<T>(S, slot, mb + cl.y, pid);
+                        else
+                            atomicOr(S.status, ST_MAILBOX);
                     }
+                    S.id[slot] = -1;
                 }
-              }
             }
         }
+        __syncthreads();
+        if (tid == 0) s_lv_n = 0;  // read by every thread before the barrier above
         __syncthreads();
 
         // flush the current tile (origin p0 - 2) into the global FP64 J (periodic)

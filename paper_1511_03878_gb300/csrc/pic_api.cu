@@ -104,7 +104,8 @@ const char* validate(const pic_config* c) {
         return "2D patch tile does not fit in shared memory";
     if (c->dims == 3) {
         if (c->n[0] > 2048 || c->n[1] > 2048 || c->n[2] > 1024) return "3D grid too large";
-        if (push3d_smem(c->precision, c->patch[0], c->patch[1], c->patch[2]) > 227 * 1024)
+        if (push3d_smem(c->precision, c->patch[0], c->patch[1], c->patch[2]) + kPush2DStatic >
+            227 * 1024)
             return "3D patch tile does not fit in shared memory";
     }
     if (!(c->dt > 0) || !std::isfinite(c->dt)) return "dt must be positive";

@@ -25,9 +25,10 @@ constexpr int kMailboxDiv = 2;    // exchange-buffer slots per patch: capacity /
 constexpr int kMergeCells = 4096;  // largest patch (in cells) the merge kernel sorts
 constexpr int kSlotAlign = 32;    // per-patch particle and exchange-buffer bases are multiples
                                   // of this, so that a warp's particle loads start a line
-constexpr int kLeaveList = 512;   // leavers of one work item handed off after the item (2D);
+constexpr int kLeaveList = 512;   // leavers of one work item handed off after the item;
                                   // more than this are handed off on the spot
-constexpr int kPush2DStatic = 2 * 4 * kLeaveList + 64;  // static shared bytes of push2d
+constexpr int kPush2DStatic = 2 * 4 * kLeaveList + 64;  // static shared bytes of the push
+                                                        // kernels (2D and 3D)
 
 __host__ __device__ inline long long align_slots(long long v) {
     return (v + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
