@@ -283,7 +283,16 @@ __global__ void inject_kernel(const BatchDev* __restrict__ bd) {
     const double wgt = dens * dV / ((double)px * py * pz);
     const long long lat = ((((long long)k * ny + j) * pz + cz) * py + b) * px + a;
     const int dest = ((nx - 1) / S.P[0]) + S.np[0] * (j / S.P[1] + S.np[1] * (k / S.P[2]));
-    const int slot = atomicAdd(S.mcount + dest, 1);
+    // one claim per destination among the warp's remaining lanes (consecutive rows
+    // share a patch), instead of one global atomic per particle
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, dest);
+    const int leader = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    int first = 0;
+    if (lane == leader) first = atomicAdd(S.mcount + dest, __popc(peers));
+    first = __shfl_sync(peers, first, leader);
+    const int slot = first + __popc(peers & ((1u << lane) - 1u));
     if (slot >= S.mcap[dest]) {
         atomicOr(S.status, ST_MAILBOX);
         return;
