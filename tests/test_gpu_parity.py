@@ -389,3 +389,23 @@ def test_stress3d_fp32_error_stated(binding):
           f"energy {abs(e.sum() / eo.sum() - 1):.2e}")
     assert ux_err < 1e-4 and jx_err < 1e-3
     assert abs(e.sum() - eo.sum()) / eo.sum() < 1e-3
+
+
+@pytest.mark.parametrize("mapping,chunk", [(1, 0), (0, 16384)])
+def test_more_leavers_than_the_shared_list(binding, mapping, chunk):
+    """4x4 patches of 4096 particles (256 per cell), fast thermal particles (u_th = 1):
+    about 530 particles leave each patch per step, and with one work item per patch
+    (static mapping, or a chunk above the patch count) more than the 512 an item lists
+    in shared memory; the rest take the hand-off inside the particle loop. FP64 against
+    the oracle after 3 steps."""
+    w = inputs.thermal2d(nx=32, ny=32, ppc_side=16, uth=1.0, seed=9, patch=(4, 4))
+    n = len(w["particles"]["x"])
+    o = make_oracle(w)
+    o.step(3)
+    sim = binding.Sim(w["params"], precision=binding.PIC_FP64, capacity=3 * n, chunk=chunk,
+                      mapping=mapping)
+    sim.load(w)
+    sim.step(3)
+    compare(sim, o, w["params"], 1e-9)
+    assert sim.num_particles() == n
+    sim.close()
