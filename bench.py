@@ -59,6 +59,26 @@ def bytes_per_push(dt, w):
     pos = dims * es + (0 if dt == "fp64" else 4)
     ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
     return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
+
+
+def step_bytes_per_push(dt, w):
+    """Algorithmic HBM bytes of a whole step per push: the particle kernel's bytes plus,
+    per cell and shared by its particles, the field update's (E, B and the FP64 J read,
+    E and B written, the next J zeroed)."""
+    p = w["params"]
+    dims = p["dims"]
+    es = 4 if dt == "fp32" else 8
+    ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
+    return bytes_per_push(dt, w) + (6 * es + 3 * 8 + 6 * es + 3 * 8) / ppc
+
+
+def step_roofline(dt, w, pushes_per_s):
+    """The whole step's algorithmic bytes per second against the measured HBM peak."""
+    hbm = measured_peaks().get("hbm_gbs")
+    achieved = step_bytes_per_push(dt, w) * pushes_per_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if hbm else None,
+            "bytes_per_push": step_bytes_per_push(dt, w)}
 # kernels per step: queue build, push, [window injection], exchange, repack plan and its
 # two copy kernels (which return at once unless a patch needs room), Yee E, Yee B, end
 def kernels_per_step(window: bool, merge: bool = False) -> int:
@@ -818,6 +838,7 @@ def main():
         "config": config_dict(args, args.precision),
         "launch": layouts[args.precision][2],
         "roofline": main_run["roofline"],
+        "roofline_step": step_roofline(args.precision, wm, value),
         "cpu_baseline": cpu,
         "e2e": ({"value": e2e["value"], "unit": UNIT,
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
@@ -837,6 +858,8 @@ def main():
         line["variants"] = {v: {
             "value": job_value(r["pushes_all"], r["ms"]),
             "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
+            "roofline_step": step_roofline(v, layouts[v][0],
+                                           job_value(r["pushes_all"], r["ms"])),
             "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v],
             "capacity_repacks": r["repacks"],
             "launch": layouts[v][2]} for v, r in variants.items()}

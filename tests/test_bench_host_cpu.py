@@ -43,3 +43,16 @@ def test_oracle_sim_has_room_for_the_injected_columns():
     o.step(12)  # the window shifts about 11 times, dropping and injecting a column each time
     assert o.shifts >= 10
     assert abs(o.num_particles() - n0) <= 32 * 4
+
+
+def test_algorithmic_bytes_per_push():
+    """LWFA window at 4 particles per cell: the push's bytes (state read and written,
+    weight read, E and B read and FP64 J written per cell) and the whole step's (plus
+    the field update per cell)."""
+    from paper_1511_03878_gb300 import inputs
+
+    w = inputs.lwfa2d(nx=256, ny=64, ramp_x0=-8.0, patch=(32, 32))
+    assert bench.bytes_per_push("fp64", w) == 2 * (16 + 24) + 8 + (48 + 24) / 4
+    assert bench.bytes_per_push("fp32", w) == 2 * (12 + 12) + 4 + (24 + 24) / 4
+    assert bench.step_bytes_per_push("fp32", w) == 88.0
+    assert bench.step_bytes_per_push("fp64", w) == 142.0
