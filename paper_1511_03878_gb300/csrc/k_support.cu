@@ -581,46 +581,109 @@ cudaError_t launch_bounded_wait_selftest(int* status, cudaStream_t s) {
 
 // ================================================================ particle load
 
-// Places the particles a load staged, packed in patch order, in the repack scratch
-// arrays (a*): the k-th staged particle belongs to the patch p with
-// start[p] <= k < start[p+1] (start, one entry per patch, is in S.aux) and goes to slot
-// pbase[p] + k - start[p]. Free slots were cleared beforehand (id -1).
+// Offset of a particle in its cell, f in [0, 1), in a cell-based precision: rounding
+// to float32 (or to the double-word's leading float) must not reach 1.
+template <typename T>
+__device__ __forceinline__ T offset_below_one(double f) {
+    const T g(f);
+    if constexpr (std::is_same<T, df64>::value) {
+        if (g.hi >= 1.0f) return T(nextafterf(1.0f, 0.0f));
+    } else {
+        if (g >= 1.0f) return T(nextafterf(1.0f, 0.0f));
+    }
+    return g;
+}
+
+// One chunk of a particle load: m particles of the caller's FP64 arrays, copied as they
+// are into the repack scratch (positions in axi, momenta in au, weights in aw, ids in
+// aid), and the slot the host's binning gave each (in holes). Each particle is converted
+// to the sim's representation (FP64: position in cell units; FP32 and double-word: the
+// packed cell index plus the offset in the cell) and stored in its slot. Free slots were
+// cleared beforehand (id -1).
 template <typename T>
 __global__ void __launch_bounds__(256) load_scatter_kernel(const BatchDev* __restrict__ bd,
-                                                           long long n) {
+                                                           long long m) {
     const SimDev& S = bd->sims[0];
-    const int* start = S.aux;
-    const int np = S.npatch, dims = S.dims;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+    const int dims = S.dims;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
          k += (long long)gridDim.x * blockDim.x) {
-        // largest p with start[p] <= k (empty patches share the next one's start)
-        int lo = 0, hi = np - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (start[mid] <= k) lo = mid;
-            else hi = mid - 1;
+        const long long dst = S.holes[k];
+        int cellv = 0;
+        for (int a = 0; a < dims; a++) {
+            const double c =
+                cell_coord(reinterpret_cast<const double*>(S.axi[a])[k], S.d[a], S.n[a]);
+            if constexpr (uses_cell<T>()) {
+                const int i = (int)floor(c);
+                reinterpret_cast<T*>(S.xi[a])[dst] = offset_below_one<T>(c - (double)i);
+                cellv |= i << (dims == 2 ? 16 * a : 11 * a);
+            } else {
+                reinterpret_cast<T*>(S.xi[a])[dst] = T(c);
+            }
         }
-        const long long dst = S.pbase[lo] + (k - start[lo]);
-        if constexpr (uses_cell<T>()) S.cell[dst] = S.acell[k];
-        for (int a = 0; a < dims; a++)
-            reinterpret_cast<T*>(S.xi[a])[dst] = reinterpret_cast<const T*>(S.axi[a])[k];
+        if constexpr (uses_cell<T>()) S.cell[dst] = cellv;
 #pragma unroll
         for (int a = 0; a < 3; a++)
-            reinterpret_cast<T*>(S.u[a])[dst] = reinterpret_cast<const T*>(S.au[a])[k];
-        reinterpret_cast<T*>(S.w)[dst] = reinterpret_cast<const T*>(S.aw)[k];
+            reinterpret_cast<T*>(S.u[a])[dst] = T(reinterpret_cast<const double*>(S.au[a])[k]);
+        reinterpret_cast<T*>(S.w)[dst] = T(reinterpret_cast<const double*>(S.aw)[k]);
         S.id[dst] = S.aid[k];
     }
 }
 
-cudaError_t launch_load_scatter(const BatchDev* bd, long long n, int prec, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+static int elementwise_grid(long long n) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
     const long long want = (n + 255) / 256;
-    const int grid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
-    PIC_DISPATCH(prec, (load_scatter_kernel<T><<<grid, 256, 0, s>>>(bd, n)));
+    return (int)(want < 8LL * nsm ? want : 8LL * nsm);
+}
+
+cudaError_t launch_load_scatter(const BatchDev* bd, long long m, int prec, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const int grid = elementwise_grid(m);
+    PIC_DISPATCH(prec, (load_scatter_kernel<T><<<grid, 256, 0, s>>>(bd, m)));
+    return cudaGetLastError();
+}
+
+// Field load: the caller's E (staged in J[0]) and B (in J[1]), three arrays of ncell
+// values each with x fastest, to the padded arrays of generation 0 in the sim's
+// precision: F holds E then B, H holds B. Guard cells take the periodic image (zero
+// below and above x in a moving window); the last x column is zero.
+template <typename T>
+__global__ void __launch_bounds__(256) load_fields_kernel(const SimDev* __restrict__ sd) {
+    const SimDev& S = *sd;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const long long fs = S.fstride, nc = S.ncell;
+    const double* E = S.J[0];
+    const double* B = S.J[1];
+    T* F = reinterpret_cast<T*>(S.F[0]);
+    T* H = reinterpret_cast<T*>(S.H[0]);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < fs;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int ip = (int)(idx % S.NX) - kGuard;
+        const long long r = idx / S.NX;
+        const int jp = (int)(r % S.NY) - kGuard;
+        const int kp = S.dims == 3 ? (int)(r / S.NY) - kGuard : 0;
+        int i = -1;
+        if (ip >= 0 && ip < nx) i = ip;
+        else if (!S.window && ip < nx + 2) i = (ip + nx) % nx;
+        const int j = (jp + ny) % ny;
+        const int k = S.dims == 3 ? (kp + nz) % nz : 0;
+        const long long src = ((long long)k * ny + j) * nx + i;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double e = i >= 0 ? E[a * nc + src] : 0.0;
+            const double b = i >= 0 ? B[a * nc + src] : 0.0;
+            F[a * fs + idx] = T(e);
+            F[(3 + a) * fs + idx] = T(b);
+            H[a * fs + idx] = T(b);
+        }
+    }
+}
+
+cudaError_t launch_load_fields(const SimDev* sd, long long fstride, int prec, cudaStream_t s) {
+    const int grid = elementwise_grid(fstride);
+    PIC_DISPATCH(prec, (load_fields_kernel<T><<<grid, 256, 0, s>>>(sd)));
     return cudaGetLastError();
 }
 

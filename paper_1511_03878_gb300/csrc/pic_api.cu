@@ -424,33 +424,6 @@ int push_grid_size(int dims, int prec, const int P[3], bool static_map, int npat
     return static_map ? std::max(1, npatch) : nsm * per;
 }
 
-// Padded device layout of a host [nz][ny][nx] array (guards: periodic images, or
-// zero along a window axis).
-template <typename T>
-void pad_field(const SimDev& S, const double* src, T* dst) {
-    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-    const bool px = !S.window;
-    const int zlo = S.dims == 3 ? -1 : 0, zhi = S.dims == 3 ? nz + 2 : 1;
-    for (int kp = zlo; kp < zhi; kp++) {
-        if (S.dims == 3 && kp + kGuard >= S.NZ) continue;
-        const int k = S.dims == 3 ? ((kp % nz) + nz) % nz : 0;
-        const long long zoff = S.dims == 3 ? (long long)(kp + kGuard) * S.NY * S.NX : 0;
-        for (int jp = -1; jp < ny + 2; jp++) {
-            const int j = ((jp % ny) + ny) % ny;
-            for (int ip = -1; ip < S.NX - 1; ip++) {
-                double v = 0.0;
-                if (ip >= 0 && ip < nx) {
-                    v = src[((long long)k * ny + j) * nx + ip];
-                } else if (px && ip < nx + 2) {
-                    const int i = ((ip % nx) + nx) % nx;
-                    v = src[((long long)k * ny + j) * nx + i];
-                }
-                dst[zoff + (long long)(jp + kGuard) * S.NX + (ip + kGuard)] = (T)v;
-            }
-        }
-    }
-}
-
 template <typename T>
 void unpad_field(const SimDev& S, const T* src, double* dst) {
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
@@ -466,32 +439,10 @@ void unpad_field(const SimDev& S, const T* src, double* dst) {
 
 size_t elem_size(int prec) { return prec == PIC_FP32 ? 4 : 8; }
 
-// one real number of the sim's precision in a host buffer
-void store_real(int prec, void* a, long long i, double v) {
-    if (prec == PIC_FP64)
-        static_cast<double*>(a)[i] = v;
-    else if (prec == PIC_FP32)
-        static_cast<float*>(a)[i] = (float)v;
-    else
-        static_cast<df64*>(a)[i] = df64(v);
-}
-
 double load_real(int prec, const void* a, long long i) {
     if (prec == PIC_FP64) return static_cast<const double*>(a)[i];
     if (prec == PIC_FP32) return (double)static_cast<const float*>(a)[i];
     return (double)static_cast<const df64*>(a)[i];
-}
-
-// offset in [0, 1) of a cell-based position, kept below 1 after rounding
-double cell_offset(int prec, double f) {
-    if (prec == PIC_FP32) {
-        float g = (float)f;
-        if (g >= 1.0f) g = std::nextafter(1.0f, 0.0f);
-        return g;
-    }
-    df64 g(f);
-    if (g.hi >= 1.0f || (g.hi == 1.0f && g.lo >= 0.0f)) return (double)std::nextafter(1.0f, 0.0f);
-    return f;
 }
 
 uint64_t mix64(uint64_t x) {
@@ -609,34 +560,74 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     CK(cudaStreamSynchronize(s->stream), "sync before load");
     const int dims = S.dims;
     const double* pos[3] = {x, y, z};
+    const double* mom[3] = {ux, uy, uz};
     const int nt = load_threads(n);
-    std::vector<int> ip(n * 3);
-    std::vector<double> xi(n * 3);
-    std::vector<int> patch(n);
-    // per-thread patch counts, largest id and first invalid particle (index, code)
+    const long long n1 = std::max(n, 1LL);
+    // the caller's arrays go to the device as they are, in chunks that fit the repack
+    // scratch (FP64 values, so a 4-byte precision takes half its slots per chunk)
+    const size_t es = elem_size(S.prec);
+    const long long cap = S.capacity;
+    const long long chunk = cap * (long long)es / (long long)sizeof(double);
+    auto copy_chunk = [&](long long k0, long long m) -> cudaError_t {
+        const size_t db = m * sizeof(double);
+        cudaError_t e = cudaSuccess;
+        for (int a = 0; a < dims && e == cudaSuccess; a++)
+            e = cudaMemcpyAsync(S.axi[a], pos[a] + k0, db, cudaMemcpyHostToDevice, s->stream);
+        for (int a = 0; a < 3 && e == cudaSuccess; a++)
+            e = cudaMemcpyAsync(S.au[a], mom[a] + k0, db, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S.aw, w + k0, db, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S.aid, id + k0, m * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+        return e;
+    };
+    // chunk 0 needs nothing from the host's binning: a helper thread copies it while the
+    // host validates and orders (from pageable memory a copy occupies its calling thread).
+    // Every return waits for it and for the stream, so no copy outlives the call.
+    cudaError_t early = cudaSuccess;
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "device");
+    std::thread early_copy;
+    if (n > 0)
+        early_copy = std::thread([&, dev] {
+            early = cudaSetDevice(dev);
+            if (early == cudaSuccess) early = copy_chunk(0, std::min(chunk, n));
+        });
+    struct Drain {
+        std::thread& t;
+        cudaStream_t st;
+        void join() {
+            if (t.joinable()) t.join();
+        }
+        ~Drain() {
+            join();
+            cudaStreamSynchronize(st);
+        }
+    } drain{early_copy, s->stream};
+    // per particle: its patch and the shared-memory bank class of its cell in the patch's
+    // field tile (the tile address modulo 32); uninitialised, every entry is written
+    std::unique_ptr<int[]> patch(new int[n1]);
+    std::unique_ptr<unsigned char[]> cls(new unsigned char[n1]);
+    // per thread: patch counts, largest id, largest |w|, first invalid particle (index, code)
     std::vector<std::vector<int>> tcount(nt, std::vector<int>(S.npatch, 0));
     std::vector<int> tmaxid(nt, -1);
+    std::vector<double> twmax(nt, 0.0);
     std::vector<long long> tbad(nt, -1);
     std::vector<int> tcode(nt, 0);
     parallel_ranges(n, nt, [&](long long b, long long e, int t) {
         std::vector<int>& cnt = tcount[t];
         int mid = -1;
+        double wm = 0.0;
         for (long long p = b; p < e; p++) {
-            int pc[3] = {0, 0, 0};
+            int ic[3] = {0, 0, 0};
             int code = 0;
-            for (int a = 0; a < dims && !code; a++) {
+            for (int a = 0; a < dims; a++) {
                 const double v = pos[a][p];
-                const double L = S.n[a] * S.d[a];
-                if (!std::isfinite(v) || v < 0.0 || v >= L) {
+                if (!std::isfinite(v) || v < 0.0 || v >= S.n[a] * S.d[a]) {
                     code = 1;
                     break;
                 }
-                double c = v / S.d[a];
-                if (c >= (double)S.n[a]) c = std::nextafter((double)S.n[a], 0.0);
-                const int i = (int)std::floor(c);
-                xi[p * 3 + a] = c;
-                ip[p * 3 + a] = i;
-                pc[a] = i / S.P[a];
+                ic[a] = (int)std::floor(cell_coord(v, S.d[a], S.n[a]));
             }
             if (!code && (!std::isfinite(ux[p]) || !std::isfinite(uy[p]) ||
                           !std::isfinite(uz[p]) || !std::isfinite(w[p])))
@@ -648,10 +639,17 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
                 return;  // the first invalid particle of this range
             }
             mid = std::max(mid, id[p]);
-            patch[p] = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
-            cnt[patch[p]]++;
+            wm = std::max(wm, std::fabs(w[p]));
+            const int pc[3] = {ic[0] / S.P[0], ic[1] / S.P[1], ic[2] / S.P[2]};
+            const int pp = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
+            const long long lx = ic[0] - pc[0] * S.P[0], ly = ic[1] - pc[1] * S.P[1];
+            const long long lz = ic[2] - pc[2] * S.P[2];
+            patch[p] = pp;
+            cls[p] = (unsigned char)(((lz * S.BY + ly) * S.BX + lx) & 31);
+            cnt[pp]++;
         }
         tmaxid[t] = mid;
+        twmax[t] = wm;
     });
     for (int t = 0; t < nt; t++) {  // the first invalid particle overall
         if (tbad[t] < 0) continue;
@@ -661,8 +659,10 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     }
     std::vector<int> counts(S.npatch, 0);
     int maxid = -1;
+    double wmax = 0.0;
     for (int t = 0; t < nt; t++) {
         maxid = std::max(maxid, tmaxid[t]);
+        wmax = std::max(wmax, twmax[t]);
         for (int p = 0; p < S.npatch; p++) counts[p] += tcount[t][p];
     }
     // per-patch capacity: the free slots are shared half by count, half evenly; every
@@ -683,10 +683,14 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     if (acc > S.capacity || macc > S.mtotal)
         return fail(&s->err, PIC_ERR_CAPACITY, "capacity split failed");
     // stable binning (thread t's particles of patch p follow those of threads < t), then
-    // a fixed pseudo-random order inside each patch so that the lanes of a warp rarely
-    // share a cell (spreads shared-memory atomics)
-    std::vector<long long> order(n), start(S.npatch);
+    // per patch a fixed pseudo-random order, so that the lanes of a warp rarely share a
+    // cell (spreads shared-memory atomics), and an interleave of the 32 bank classes:
+    // run r of the patch's slots holds the r-th particle of every class that has one, in
+    // class order, so the lanes of a warp read and add into different banks. The result
+    // is each particle's slot.
+    std::unique_ptr<int[]> order(new int[n1]), slot(new int[n1]);
     {
+        std::vector<long long> start(S.npatch);
         long long a = 0;
         for (int p = 0; p < S.npatch; p++) {
             start[p] = a;
@@ -702,115 +706,60 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
         }
         parallel_ranges(n, nt, [&](long long b, long long e, int t) {
             std::vector<long long>& cur = cursor[t];
-            for (long long p = b; p < e; p++) order[cur[patch[p]]++] = p;
+            for (long long p = b; p < e; p++) order[cur[patch[p]]++] = (int)p;
         });
         parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
+            std::vector<int> list;
+            std::vector<unsigned char> lc;
             for (long long p = pb0; p < pb1; p++) {
-                const long long b0 = start[p], c = counts[p];
+                int* seg = order.get() + start[p];
+                const long long c = counts[p];
+                // Fisher-Yates; the draw in [0, k] is the high word of a 64-bit hash times k + 1
                 for (long long k = c - 1; k > 0; k--) {
+                    const uint64_t h = mix64(((uint64_t)p << 32) ^ (uint64_t)k);
                     const long long r =
-                        (long long)(mix64(((uint64_t)p << 32) ^ (uint64_t)k) % (uint64_t)(k + 1));
-                    std::swap(order[b0 + k], order[b0 + r]);
+                        (long long)(((unsigned __int128)h * (uint64_t)(k + 1)) >> 64);
+                    std::swap(seg[k], seg[r]);
                 }
-            }
-        });
-        // then interleave the 32 shared-memory bank classes of the particles' cells (the
-        // cell's field-tile address modulo 32): run j of 32 consecutive particles takes the
-        // j-th particle of every class that has one, so the lanes of a warp read and add
-        // into different banks and never share a cell
-        parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
-            std::vector<long long> tmp;
-            std::vector<int> cls, rank;
-            for (long long p = pb0; p < pb1; p++) {
-                const long long b0 = start[p], c = counts[p];
-                if (c < 2) continue;
-                const int pxo = (int)(p % S.np[0]) * S.P[0];
-                const int pyo = (int)((p / S.np[0]) % S.np[1]) * S.P[1];
-                const int pzo = (int)(p / ((long long)S.np[0] * S.np[1])) * S.P[2];
-                int nb[32] = {0};
-                cls.resize(c);
-                rank.resize(c);
-                tmp.resize(c);
-                for (long long k = 0; k < c; k++) {
-                    const long long src = order[b0 + k];
-                    const long long lx = ip[src * 3] - pxo, ly = ip[src * 3 + 1] - pyo;
-                    const long long lz = dims == 3 ? ip[src * 3 + 2] - pzo : 0;
-                    const int b = (int)(((lz * S.BY + ly) * S.BX + lx) & 31);
-                    cls[k] = b;
-                    rank[k] = nb[b]++;
+                // each class's particles in the shuffled order, then emitted run by run
+                lc.resize(c);
+                int nb[32] = {0}, off[32], fill[32];
+                for (long long k = 0; k < c; k++) nb[lc[k] = cls[seg[k]]]++;
+                int maxnb = 0;
+                for (int q = 0, o = 0; q < 32; q++) {
+                    off[q] = fill[q] = o;
+                    o += nb[q];
+                    maxnb = std::max(maxnb, nb[q]);
                 }
-                for (long long k = 0; k < c; k++) {
-                    const int b = cls[k], r = rank[k];
-                    long long pos = 0;
+                list.resize(c);
+                for (long long k = 0; k < c; k++) list[fill[lc[k]]++] = seg[k];
+                int next = pbase[p];
+                for (int r = 0; r < maxnb; r++)
                     for (int q = 0; q < 32; q++)
-                        pos += std::min(nb[q], r) + ((q < b && nb[q] > r) ? 1 : 0);
-                    tmp[pos] = order[b0 + k];
-                }
-                std::copy(tmp.begin(), tmp.end(), order.begin() + b0);
+                        if (nb[q] > r) slot[list[off[q] + r]] = next++;
             }
         });
     }
-    // the live particles packed in patch order (start[p] + c for the c-th of patch p) in
-    // host staging arrays; the device scatters them to their slots. Only n particles
-    // cross the link, and the free slots are cleared on the device.
-    const size_t es = elem_size(S.prec);
-    const long long cap = S.capacity;
-    std::unique_ptr<char[]> hx[3], hu[3], hw(new char[std::max(n, 1LL) * es]);
-    std::unique_ptr<int[]> hid(new int[std::max(n, 1LL)]), hcell;
-    for (int a = 0; a < dims; a++) hx[a].reset(new char[std::max(n, 1LL) * es]);
-    for (int a = 0; a < 3; a++) hu[a].reset(new char[std::max(n, 1LL) * es]);
-    if (S.prec != PIC_FP64) hcell.reset(new int[std::max(n, 1LL)]);
-    parallel_ranges(n, nt, [&](long long k0, long long k1, int) {
-        for (long long k = k0; k < k1; k++) {
-            const long long src = order[k];
-            if (S.prec == PIC_FP64) {
-                for (int a = 0; a < dims; a++)
-                    reinterpret_cast<double*>(hx[a].get())[k] = xi[src * 3 + a];
-            } else {
-                int cellv = 0;
-                for (int a = 0; a < dims; a++) {
-                    const int i = ip[src * 3 + a];
-                    const double f = cell_offset(S.prec, xi[src * 3 + a] - (double)i);
-                    store_real(S.prec, hx[a].get(), k, f);
-                    cellv |= i << (dims == 2 ? 16 * a : 11 * a);
-                }
-                hcell[k] = cellv;
-            }
-            store_real(S.prec, hu[0].get(), k, ux[src]);
-            store_real(S.prec, hu[1].get(), k, uy[src]);
-            store_real(S.prec, hu[2].get(), k, uz[src]);
-            store_real(S.prec, hw.get(), k, w[src]);
-            hid[k] = id[src];
-        }
-    });
-    std::vector<int> hstart(S.npatch);
-    for (int p = 0; p < S.npatch; p++) hstart[p] = (int)start[p];
-    // free slots: zero state, id -1
+    // device side: clear every slot (zero state, id -1), then per chunk the particles'
+    // slots; the device converts the chunk and places it
+    drain.join();
+    CK(early, "copy particles");
     for (int a = 0; a < dims; a++) CK(cudaMemsetAsync(S.xi[a], 0, cap * es, s->stream), "clear x");
     for (int a = 0; a < 3; a++) CK(cudaMemsetAsync(S.u[a], 0, cap * es, s->stream), "clear u");
     CK(cudaMemsetAsync(S.w, 0, cap * es, s->stream), "clear w");
     CK(cudaMemsetAsync(S.id, 0xFF, cap * sizeof(int), s->stream), "clear id");
     if (S.prec != PIC_FP64) CK(cudaMemsetAsync(S.cell, 0, cap * sizeof(int), s->stream), "clear cell");
-    if (n > 0) {
-        for (int a = 0; a < dims; a++)
-            CK(cudaMemcpyAsync(S.axi[a], hx[a].get(), n * es, cudaMemcpyHostToDevice, s->stream),
-               "copy x");
-        for (int a = 0; a < 3; a++)
-            CK(cudaMemcpyAsync(S.au[a], hu[a].get(), n * es, cudaMemcpyHostToDevice, s->stream),
-               "copy u");
-        CK(cudaMemcpyAsync(S.aw, hw.get(), n * es, cudaMemcpyHostToDevice, s->stream), "copy w");
-        CK(cudaMemcpyAsync(S.aid, hid.get(), n * sizeof(int), cudaMemcpyHostToDevice, s->stream),
-           "copy id");
-        if (S.prec != PIC_FP64)
-            CK(cudaMemcpyAsync(S.acell, hcell.get(), n * sizeof(int), cudaMemcpyHostToDevice,
-                               s->stream), "copy cell");
+    for (long long k0 = 0; k0 < n; k0 += chunk) {
+        const long long m = std::min(chunk, n - k0);
+        if (k0 > 0) CK(copy_chunk(k0, m), "copy particles");
+        CK(cudaMemcpyAsync(S.holes, slot.get() + k0, m * sizeof(int), cudaMemcpyHostToDevice,
+                           s->stream), "copy slots");
+        CK(launch_load_scatter(s->L.db, m, S.prec, s->stream), "place particles");
     }
     const size_t pb = S.npatch * sizeof(int);
     CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
     CK(cudaMemcpyAsync(S.pcap, pcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcap");
     CK(cudaMemcpyAsync(S.pcount, counts.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcount");
-    CK(cudaMemcpyAsync(S.aux, hstart.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy start");
-    CK(launch_load_scatter(s->L.db, n, S.prec, s->stream), "scatter particles");
     CK(cudaMemcpyAsync(S.mbase, mbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mbase");
     CK(cudaMemcpyAsync(S.mcap, mcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mcap");
     CK(cudaMemsetAsync(S.hcount, 0, pb, s->stream), "zero hcount");
@@ -819,8 +768,6 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     // bound of one particle's current contribution (|cumulative DS| <= 1, |v| < 1):
     // sets the double-word fixed-point current scale
     {
-        double wmax = 0.0;
-        for (long long p = 0; p < n; p++) wmax = std::max(wmax, std::fabs(w[p]));
         if (S.window) {
             const double dV = S.d[0] * S.d[1] * (S.dims == 3 ? S.d[2] : 1.0);
             wmax = std::max(wmax, std::fabs(S.n0) * dV /
@@ -851,25 +798,18 @@ extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], cons
     const SimDev& S = s->L.S;
     CK(cudaStreamSynchronize(s->stream), "sync before fields");
     const size_t es = elem_size(S.prec);
-    const long long fs = S.fstride;
-    std::vector<char> hF(6 * fs * es, 0), hH(3 * fs * es, 0);
-    auto pad_all = [&](auto* F, auto* H) {
-        for (int a = 0; a < 3; a++) {
-            pad_field(S, E[a], F + a * fs);
-            pad_field(S, B[a], F + (3 + a) * fs);
-            pad_field(S, B[a], H + a * fs);
-        }
-    };
-    if (S.prec == PIC_FP64)
-        pad_all(reinterpret_cast<double*>(hF.data()), reinterpret_cast<double*>(hH.data()));
-    else if (S.prec == PIC_FP32)
-        pad_all(reinterpret_cast<float*>(hF.data()), reinterpret_cast<float*>(hH.data()));
-    else
-        pad_all(reinterpret_cast<df64*>(hF.data()), reinterpret_cast<df64*>(hH.data()));
-    CK(cudaMemcpyAsync(S.F[0], hF.data(), hF.size(), cudaMemcpyHostToDevice, s->stream), "copy F");
-    CK(cudaMemcpyAsync(S.H[0], hH.data(), hH.size(), cudaMemcpyHostToDevice, s->stream), "copy H");
-    CK(cudaMemsetAsync(S.F[1], 0, hF.size(), s->stream), "zero F1");
-    CK(cudaMemsetAsync(S.H[1], 0, hH.size(), s->stream), "zero H1");
+    const long long fs = S.fstride, nc = S.ncell;
+    // the caller's arrays go as they are to the current buffers (3 fstride >= 3 ncell
+    // values each), the device pads them into generation 0 in the sim's precision
+    for (int a = 0; a < 3; a++) {
+        CK(cudaMemcpyAsync(S.J[0] + a * nc, E[a], nc * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream), "copy E");
+        CK(cudaMemcpyAsync(S.J[1] + a * nc, B[a], nc * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream), "copy B");
+    }
+    CK(launch_load_fields(s->L.ds, fs, S.prec, s->stream), "pad fields");
+    CK(cudaMemsetAsync(S.F[1], 0, 6 * fs * es, s->stream), "zero F1");
+    CK(cudaMemsetAsync(S.H[1], 0, 3 * fs * es, s->stream), "zero H1");
     CK(cudaMemsetAsync(S.J[0], 0, 3 * fs * sizeof(double), s->stream), "zero J0");
     CK(cudaMemsetAsync(S.J[1], 0, 3 * fs * sizeof(double), s->stream), "zero J1");
     // the fields belong to step 0

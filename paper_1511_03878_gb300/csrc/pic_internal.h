@@ -10,9 +10,19 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace pic {
+
+// position along an axis in cell units, c = v / d, kept below the cell count n when v
+// lies just under the domain's end; host and device compute it identically (IEEE
+// division), so the host's binning and the device's conversion see the same cell
+__host__ __device__ inline double cell_coord(double v, double d, int n) {
+    double c = v / d;
+    if (c >= (double)n) c = nextafter((double)n, 0.0);
+    return c;
+}
 
 constexpr int kGuard = 1;        // guard cells below each axis in the padded field arrays
 constexpr int kThreads = 256;    // threads per CTA of the particle kernel
@@ -166,8 +176,13 @@ cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0,
                           int grid, cudaStream_t s);
 // failure-path self-test: a bounded wait on an mbarrier that nothing completes
 cudaError_t launch_bounded_wait_selftest(int* status, cudaStream_t s);
-// particle load: staged particles (repack scratch, patch order) to their slots
-cudaError_t launch_load_scatter(const BatchDev* bd, long long n, int prec, cudaStream_t s);
+// particle load, one chunk: m particles of the caller's FP64 arrays staged in the repack
+// scratch (positions axi, momenta au, weights aw, ids aid; slots in holes), converted to
+// the sim's representation and stored in their slots
+cudaError_t launch_load_scatter(const BatchDev* bd, long long m, int prec, cudaStream_t s);
+// field load: E staged in J[0] and B in J[1] (three ncell arrays each, x fastest) to the
+// padded F (E, B) and H (B) of generation 0 in the sim's precision
+cudaError_t launch_load_fields(const SimDev* sd, long long fstride, int prec, cudaStream_t s);
 cudaError_t launch_maxwell6(const BatchDev* bd, int nsims, long long max_ncell, int dims,
                            int prec, cudaStream_t s);
 cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int prec,

@@ -169,6 +169,84 @@ def test_energy_diag_matches_oracle(binding):
 
 # ------------------------------------------------------------------ edge cases
 
+def _as_stored(v, prec):
+    """A FP64 value as a precision stores it and reads back: FP32 rounds to float32,
+    double-word keeps a float32 pair (hi, lo = v - hi rounded)."""
+    if prec == 0:
+        return v
+    hi = v.astype(np.float32)
+    if prec == 1:
+        return hi.astype(np.float64)
+    lo = (v - hi.astype(np.float64)).astype(np.float32)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def _position_as_stored(v, d, n, prec):
+    """Read-back of a loaded position: c = v / d in cell units, kept below n (a value
+    just under the domain's end can round to n); FP64 stores c, the cell precisions the
+    cell floor(c) and the offset, kept below 1 when its rounding reaches 1."""
+    c = v / d
+    c = np.where(c >= n, np.nextafter(float(n), 0.0), c)
+    if prec == 0:
+        return c * d
+    i = np.floor(c)
+    f = c - i
+    hi = f.astype(np.float32)
+    below = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    return (i + np.where(hi >= 1.0, below, _as_stored(f, prec))) * d
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("dims", [2, 3])
+@pytest.mark.parametrize("capfactor", [1, 4])
+def test_load_places_and_converts_every_particle(binding, prec, dims, capfactor):
+    """The device converts the caller's FP64 arrays during the load, in chunks of the
+    repack scratch; FP32 at a capacity of n takes two. It also pads the fields. Read
+    back right after the load, every particle is present once. Its position, momenta
+    and weight match the precision's storage rule, including the conversion's edge
+    cases: the domain's origin, a cell face, a position whose offset rounds to 1 in
+    float32, and one just under the domain's end whose cell coordinate rounds to n.
+    The fields come back as given."""
+    if dims == 2:
+        w = inputs.thermal2d(nx=64, ny=48, d=0.65, seed=3, patch=(16, 16))
+    else:
+        w = inputs.stress3d(n=(32, 16, 16), d=0.65, patch=(8, 8, 8), total=30000, seed=5)
+    par = w["params"]
+    q0 = {k: np.array(v, copy=True) for k, v in w["particles"].items()}
+    keys = ("x", "y", "z")[:dims]
+    for a, k in enumerate(keys):
+        n_a, d_a = par["n"][a], par["d"][a]
+        q0[k][0] = 0.0
+        q0[k][1] = 3 * d_a
+        q0[k][2] = np.nextafter(n_a * d_a, 0.0)
+        q0[k][3] = (7 + (1 - 2.0 ** -30)) * d_a
+    if dims == 2:  # 48 cells of 0.65: the position just under the end rounds to 48 cells
+        assert q0["y"][2] / 0.65 >= 48
+    rng = np.random.default_rng(11)
+    E = [rng.normal(size=w["E"][0].shape) for _ in range(3)]
+    B = [rng.normal(size=w["B"][0].shape) for _ in range(3)]
+    n = len(q0["x"])
+    sim = binding.Sim(par, precision=prec, capacity=capfactor * n)
+    try:
+        sim.load(dict(w, particles=q0, E=E, B=B))
+        q = sim.particles()
+        f = sim.fields()
+    finally:
+        sim.close()
+    assert np.array_equal(q["id"], np.sort(q0["id"]))
+    order = np.argsort(q0["id"])
+    for a, k in enumerate(keys):
+        want = _position_as_stored(q0[k][order], par["d"][a], par["n"][a], prec)
+        assert np.array_equal(q[k], want), k
+    for k in ("ux", "uy", "uz", "w"):
+        assert np.array_equal(q[k], _as_stored(q0[k][order], prec)), k
+    for a, c in enumerate("xyz"):
+        assert np.array_equal(f["E" + c], _as_stored(E[a], prec))
+        assert np.array_equal(f["B" + c], _as_stored(B[a], prec))
+        assert np.array_equal(f["Bn" + c], _as_stored(B[a], prec))
+        assert not f["J" + c].any()
+
+
 def test_empty_and_single_particle(binding):
     w = inputs.thermal2d(nx=32, ny=32, d=0.1, seed=1, patch=(16, 16))
     empty = {k: v[:0] for k, v in w["particles"].items()}
@@ -272,6 +350,49 @@ def test_invalid_particles_rejected(binding):
     with pytest.raises(binding.PicError) as e:
         binding.pic_load_particles(sim.h, p)
     assert e.value.code == binding.PIC_ERR_NUMERIC
+    # a rejected load leaves the sim usable: the valid workload loads and steps as the
+    # oracle does
+    sim.load(w)
+    sim.step(1)
+    o = make_oracle(w)
+    o.step(1)
+    compare(sim, o, w["params"], 1e-12)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec,capfactor", [(0, 2), (1, 1)])
+def test_load_from_pinned_host_memory(binding, prec, capfactor):
+    """Page-locked host arrays take the asynchronous copy path of the load (the
+    first chunk overlapping the host's binning); the loaded state equals the one from
+    pageable arrays bit for bit. FP32 at a capacity of n covers the later chunks. (After
+    steps, the FP64 atomics of the current flush make runs differ in the last bits.)"""
+    import torch
+
+    w = inputs.thermal2d(nx=64, ny=64, d=0.1, seed=9, patch=(16, 16))
+    keep = []
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.from_numpy(np.ascontiguousarray(a)).dtype,
+                        pin_memory=True)
+        keep.append(t)
+        out = t.numpy()
+        out[...] = a
+        return out
+
+    wp = dict(w, particles={k: pinned(v) for k, v in w["particles"].items()},
+              E=[pinned(a) for a in w["E"]], B=[pinned(a) for a in w["B"]])
+    n = len(w["particles"]["x"])
+    got = []
+    for work in (w, wp):
+        sim = binding.Sim(w["params"], precision=prec, capacity=capfactor * n)
+        sim.load(work)
+        got.append((sim.particles(), sim.fields()))
+        sim.close()
+    (qa, fa), (qb, fb) = got
+    for k in qa:
+        assert np.array_equal(qa[k], qb[k]), k
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
 
 
 # ------------------------------------------------------------------ FP32 path
