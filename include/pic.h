@@ -129,9 +129,14 @@ pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes
 
 /* Load n particles from host SoA arrays (float64 physical positions, momenta
  * u = gamma v, weights; int32 ids, unique and >= 0). z may be NULL in 2D. Positions
- * must lie in [0, n[a] d[a]). Particles are binned by patch on the host and copied;
- * per-patch capacities split the free slots half by count, half evenly.
- * Returns PIC_ERR_CAPACITY if n > capacity. Resets the step counter to 0. */
+ * must lie in [0, n[a] d[a]). The host validates the particles and bins them by patch;
+ * the arrays are copied to the device as they are (page-locked arrays copy
+ * asynchronously while the host bins) and converted there. Per-patch capacities split
+ * the free slots half by count, half evenly. The arrays are not retained: every copy
+ * has completed when the call returns, on success and on error. Returns
+ * PIC_ERR_CAPACITY if n > capacity, PIC_ERR_INVALID for a position outside the grid or
+ * a negative id, PIC_ERR_NUMERIC for a non-finite momentum or weight; a rejected load
+ * leaves the sim as it was. Resets the step counter to 0. */
 pic_status pic_load_particles(pic_sim* sim, long long n, const double* x, const double* y,
                               const double* z, const double* ux, const double* uy,
                               const double* uz, const double* w, const int* id);
@@ -139,7 +144,8 @@ pic_status pic_load_particles(pic_sim* sim, long long n, const double* x, const 
 /* Load fields from host arrays [nz][ny][nx]: E at t = 0, B at t = +dt/2 (the first
  * push uses that B at integer time too). rho_bg: immobile background charge on
  * nodes for the Gauss diagnostic; NULL = minus the charge density of the particles
- * loaded now. Zeroes the current. */
+ * loaded now. Zeroes the current. The arrays are copied as they are and padded with
+ * guard cells on the device; they are not retained. */
 pic_status pic_load_fields(pic_sim* sim, const double* const E[3], const double* const B[3],
                            const double* rho_bg);
 
