@@ -9,10 +9,12 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <numeric>
 #include <memory>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -336,6 +338,41 @@ pic_status cuda_fail(std::string* err, cudaError_t e, const char* where) {
     return fail(err, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// No C++ exception crosses the C ABI. A failed host allocation or thread start inside an
+// entry point becomes PIC_ERR_NOMEM; any other exception becomes PIC_ERR_INVALID. The
+// message is kept when there is memory for it.
+pic_status note(std::string* err, pic_status st, const char* msg) noexcept {
+    try {
+        if (err) *err = msg;
+    } catch (...) {
+    }
+    return st;
+}
+
+template <typename F>
+pic_status guarded(std::string* err, F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return note(err, PIC_ERR_NOMEM, "host memory allocation failed");
+    } catch (const std::system_error& e) {
+        return note(err, PIC_ERR_NOMEM, e.what());
+    } catch (const std::exception& e) {
+        return note(err, PIC_ERR_INVALID, e.what());
+    } catch (...) {
+        return note(err, PIC_ERR_INVALID, "unexpected host exception");
+    }
+}
+
+template <typename F>
+size_t guarded_size(F&& body) noexcept {
+    try {
+        return body();
+    } catch (...) {
+        return 0;
+    }
+}
+
 #define CK(call, where)                                                \
     do {                                                               \
         cudaError_t e_ = (call);                                       \
@@ -458,7 +495,7 @@ uint64_t mix64(uint64_t x) {
 
 extern "C" size_t pic_config_bytes(void) { return sizeof(pic_config); }
 
-extern "C" pic_status pic_selftest_bounded_wait(void* cuda_stream) {
+static pic_status selftest_bounded_wait_body(void* cuda_stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     int* d = nullptr;
     if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PIC_ERR_CUDA;
@@ -473,13 +510,21 @@ extern "C" pic_status pic_selftest_bounded_wait(void* cuda_stream) {
     return status_to_error(&err, h);
 }
 
-extern "C" size_t pic_required_bytes(const pic_config* cfg) {
+extern "C" pic_status pic_selftest_bounded_wait(void* cuda_stream) {
+    return guarded(nullptr, [&] { return selftest_bounded_wait_body(cuda_stream); });
+}
+
+static size_t required_bytes_body(const pic_config* cfg) {
     if (validate(cfg)) return 0;
     return plan(cfg, nullptr).bytes;
 }
 
-extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
-                                 void* cuda_stream, pic_sim** out) {
+extern "C" size_t pic_required_bytes(const pic_config* cfg) {
+    return guarded_size([&] { return required_bytes_body(cfg); });
+}
+
+static pic_status create_body(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
+                              void* cuda_stream, pic_sim** out) {
     if (!out) return PIC_ERR_INVALID;
     *out = nullptr;
     if (validate(cfg)) return PIC_ERR_INVALID;
@@ -522,6 +567,12 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
     return PIC_OK;
 }
 
+extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
+                                 void* cuda_stream, pic_sim** out) {
+    return guarded(nullptr,
+                   [&] { return create_body(cfg, dev_arena, arena_bytes, cuda_stream, out); });
+}
+
 // Host threads of the particle load: binning and laying out millions of particles is
 // the bulk of loading a sim, and it splits into independent ranges.
 static int load_threads(long long n) {
@@ -530,7 +581,9 @@ static int load_threads(long long n) {
     return (int)std::max(1u, std::min(hc == 0 ? 4u : hc, 32u));
 }
 
-// f(begin, end, t) on nt contiguous ranges of [0, n), in parallel
+// f(begin, end, t) on nt contiguous ranges of [0, n), in parallel. A range whose thread
+// cannot be started runs on the calling thread, so every range runs exactly once. An
+// exception in any range is rethrown on the calling thread after all ranges finished.
 template <typename F>
 static void parallel_ranges(long long n, int nt, F&& f) {
     if (nt <= 1) {
@@ -538,19 +591,33 @@ static void parallel_ranges(long long n, int nt, F&& f) {
         return;
     }
     std::vector<std::thread> th;
+    std::vector<std::exception_ptr> errs(nt);
     th.reserve(nt);
     const long long chunk = (n + nt - 1) / nt;
     for (int t = 0; t < nt; t++) {
         const long long b = std::min(n, (long long)t * chunk), e = std::min(n, b + chunk);
-        th.emplace_back([&f, b, e, t] { f(b, e, t); });
+        auto run = [&f, &errs, b, e, t] {
+            try {
+                f(b, e, t);
+            } catch (...) {
+                errs[t] = std::current_exception();
+            }
+        };
+        try {
+            th.emplace_back(run);
+        } catch (const std::system_error&) {
+            run();
+        }
     }
     for (auto& x : th) x.join();
+    for (auto& x : errs)
+        if (x) std::rethrow_exception(x);
 }
 
-extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* x,
-                                         const double* y, const double* z, const double* ux,
-                                         const double* uy, const double* uz, const double* w,
-                                         const int* id) {
+static pic_status load_particles_body(pic_sim* s, long long n, const double* x,
+                                      const double* y, const double* z, const double* ux,
+                                      const double* uy, const double* uz, const double* w,
+                                      const int* id) {
     if (!s) return PIC_ERR_INVALID;
     const SimDev& S = s->L.S;
     if (n < 0) return fail(&s->err, PIC_ERR_INVALID, "negative particle count");
@@ -790,8 +857,16 @@ extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* 
     return PIC_OK;
 }
 
-extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], const double* const B[3],
-                                      const double* rho_bg) {
+extern "C" pic_status pic_load_particles(pic_sim* s, long long n, const double* x,
+                                         const double* y, const double* z, const double* ux,
+                                         const double* uy, const double* uz, const double* w,
+                                         const int* id) {
+    return guarded(s ? &s->err : nullptr,
+                   [&] { return load_particles_body(s, n, x, y, z, ux, uy, uz, w, id); });
+}
+
+static pic_status load_fields_body(pic_sim* s, const double* const E[3],
+                                   const double* const B[3], const double* rho_bg) {
     if (!s || !E || !B) return PIC_ERR_INVALID;
     for (int a = 0; a < 3; a++)
         if (!E[a] || !B[a]) return fail(&s->err, PIC_ERR_INVALID, "null field array");
@@ -832,6 +907,11 @@ extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], cons
     return PIC_OK;
 }
 
+extern "C" pic_status pic_load_fields(pic_sim* s, const double* const E[3], const double* const B[3],
+                                      const double* rho_bg) {
+    return guarded(s ? &s->err : nullptr, [&] { return load_fields_body(s, E, B, rho_bg); });
+}
+
 extern "C" pic_status pic_step(pic_sim* s, int nsteps) {
     if (!s || nsteps < 0) return PIC_ERR_INVALID;
     for (int i = 0; i < nsteps; i++) CK(cudaGraphLaunch(s->gexec, s->stream), "graph launch");
@@ -846,7 +926,7 @@ extern "C" pic_status pic_sync(pic_sim* s) {
     return status_to_error(&s->err, st);
 }
 
-extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes, size_t* written) {
+static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, size_t* written) {
     if (!s) return PIC_ERR_INVALID;
     if (written) *written = 0;
     pic_status rc = pic_sync(s);
@@ -1020,7 +1100,12 @@ extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes
     }
 }
 
-extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) {
+extern "C" pic_status pic_diag(pic_sim* s, int kind, void* out, size_t out_bytes, size_t* written) {
+    return guarded(s ? &s->err : nullptr,
+                   [&] { return diag_body(s, kind, out, out_bytes, written); });
+}
+
+static pic_status profile_body(pic_sim* s, int nsteps, double* ms, int n_ms) {
     if (!s || nsteps < 0 || !ms || n_ms < 8) return PIC_ERR_INVALID;
     const SimDev& S = s->L.S;
     cudaEvent_t ev[8];
@@ -1064,6 +1149,10 @@ extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) 
     }
     for (int i = 0; i < 8; i++) cudaEventDestroy(ev[i]);
     return rc;
+}
+
+extern "C" pic_status pic_profile(pic_sim* s, int nsteps, double* ms, int n_ms) {
+    return guarded(s ? &s->err : nullptr, [&] { return profile_body(s, nsteps, ms, n_ms); });
 }
 
 extern "C" pic_status pic_destroy(pic_sim* s) {
@@ -1130,13 +1219,17 @@ const char* batch_check(pic_sim* const* sims, int nsims) {
 }
 }  // namespace
 
-extern "C" size_t pic_batch_required_bytes(pic_sim* const* sims, int nsims) {
+static size_t batch_required_bytes_body(pic_sim* const* sims, int nsims) {
     if (batch_check(sims, nsims)) return 0;
     return plan_batch(sims, nsims, nullptr).bytes;
 }
 
-extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
-                                       size_t arena_bytes, void* cuda_stream, pic_batch** out) {
+extern "C" size_t pic_batch_required_bytes(pic_sim* const* sims, int nsims) {
+    return guarded_size([&] { return batch_required_bytes_body(sims, nsims); });
+}
+
+static pic_status batch_create_body(pic_sim* const* sims, int nsims, void* dev_arena,
+                                    size_t arena_bytes, void* cuda_stream, pic_batch** out) {
     if (!out) return PIC_ERR_INVALID;
     *out = nullptr;
     if (batch_check(sims, nsims)) return PIC_ERR_INVALID;
@@ -1144,8 +1237,9 @@ extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* de
     BatchLayout bl = plan_batch(sims, nsims, nullptr);
     if (arena_bytes < bl.bytes) return PIC_ERR_NOMEM;
     bl = plan_batch(sims, nsims, static_cast<char*>(dev_arena));
-    pic_batch* b = new (std::nothrow) pic_batch();
-    if (!b) return PIC_ERR_NOMEM;
+    std::unique_ptr<pic_batch> owner(new (std::nothrow) pic_batch());
+    if (!owner) return PIC_ERR_NOMEM;
+    pic_batch* b = owner.get();
     b->sims.assign(sims, sims + nsims);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     std::vector<SimDev> hsims(nsims);
@@ -1193,11 +1287,17 @@ extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* de
                          S0.order, sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge);
     if (e != cudaSuccess) {
         destroy_graph_owner(o);
-        delete b;
         return PIC_ERR_CUDA;
     }
-    *out = b;
+    *out = owner.release();
     return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
+                                       size_t arena_bytes, void* cuda_stream, pic_batch** out) {
+    return guarded(nullptr, [&] {
+        return batch_create_body(sims, nsims, dev_arena, arena_bytes, cuda_stream, out);
+    });
 }
 
 extern "C" pic_status pic_batch_step(pic_batch* b, int nsteps) {
