@@ -117,13 +117,35 @@ cudaError_t launch_yee3d(const BatchDev* bd, int nsims, long long max_ncell, int
 
 // ---------------------------------------------------------------- diagnostics (3D)
 
+// Charge density on the nodes, one CTA per patch: the particles' order-2 weights add
+// into a shared tile of the patch's nodes plus one below and two above each axis, which is
+// then added to the global array once (27 shared atomics per particle, one global atomic
+// per touched node). A tap that would fall outside the tile (a particle outside its
+// patch) goes to the global array directly. tiled = 0: every tap goes there.
 template <typename T>
-__global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double sign) {
+__global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double sign, int tiled) {
+    extern __shared__ double tile[];
     const SimDev& S = *sd;
     const int p = blockIdx.x;
     if (p >= S.npatch) return;
     const int b0 = S.pbase[p], cnt = S.pcount[p];
     const int n[3] = {S.n[0], S.n[1], S.n[2]};
+    const int TX = S.P[0] + 3, TY = S.P[1] + 3, TZ = S.P[2] + 3;
+    const int o[3] = {(p % S.np[0]) * S.P[0] - 1, ((p / S.np[0]) % S.np[1]) * S.P[1] - 1,
+                      (p / (S.np[0] * S.np[1])) * S.P[2] - 1};  // tile origin (node index)
+    if (tiled) {
+        for (int e = threadIdx.x; e < TX * TY * TZ; e += blockDim.x) tile[e] = 0.0;
+        __syncthreads();
+    }
+    // global node of a tap: periodic wrap, or -1 outside a moving window's x range
+    auto node = [&](int ii, int jj, int kk) -> long long {
+        if (S.window) {
+            if (ii < 0 || ii >= n[0]) return -1;
+        } else {
+            ii = wrapi(ii, n[0]);
+        }
+        return ((long long)wrapi(kk, n[2]) * n[1] + wrapi(jj, n[1])) * n[0] + ii;
+    };
     const double qdv = sign * S.q / (S.d[0] * S.d[1] * S.d[2]);
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         const int t = b0 + k;
@@ -150,22 +172,30 @@ __global__ void rho3d_kernel(const SimDev* __restrict__ sd, double* rho, double 
             shape3(f[a] - h, Sw[a]);
         }
         const double qw = qdv * (double)reinterpret_cast<const T*>(S.w)[t];
-        for (int c3 = 0; c3 < 3; c3++) {
-            const int kk = wrapi(nd[2] + c3 - 1, n[2]);
-            for (int b = 0; b < 3; b++) {
-                const int jj = wrapi(nd[1] + b - 1, n[1]);
+        // first tap in tile coordinates; the 3x3x3 block fits when all are in [0, T - 3]
+        const int tx = nd[0] - 1 - o[0], ty = nd[1] - 1 - o[1], tz = nd[2] - 1 - o[2];
+        const bool in = tiled && (unsigned)tx <= (unsigned)(TX - 3) &&
+                        (unsigned)ty <= (unsigned)(TY - 3) && (unsigned)tz <= (unsigned)(TZ - 3);
+        for (int c3 = 0; c3 < 3; c3++)
+            for (int b = 0; b < 3; b++)
                 for (int a = 0; a < 3; a++) {
-                    int ii = nd[0] + a - 1;
-                    if (S.window) {
-                        if (ii < 0 || ii >= n[0]) continue;  // outside the window
+                    const double v = qw * Sw[0][a] * Sw[1][b] * Sw[2][c3];
+                    if (in) {
+                        atomicAdd(&tile[((tz + c3) * TY + ty + b) * TX + tx + a], v);
                     } else {
-                        ii = wrapi(ii, n[0]);
+                        const long long g = node(nd[0] + a - 1, nd[1] + b - 1, nd[2] + c3 - 1);
+                        if (g >= 0) atomicAdd(rho + g, v);
                     }
-                    atomicAdd(rho + ((long long)kk * n[1] + jj) * n[0] + ii,
-                              qw * Sw[0][a] * Sw[1][b] * Sw[2][c3]);
                 }
-            }
-        }
+    }
+    if (!tiled) return;
+    __syncthreads();
+    for (int e = threadIdx.x; e < TX * TY * TZ; e += blockDim.x) {
+        const double v = tile[e];
+        if (v == 0.0) continue;
+        const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
+        const long long g = node(o[0] + ex, o[1] + ey, o[2] + ez);
+        if (g >= 0) atomicAdd(rho + g, v);
     }
 }
 
@@ -191,7 +221,16 @@ cudaError_t launch_gauss3d(const SimDev* sd, const SimDev& hs, int prec, int mod
     cudaError_t e = cudaMemsetAsync(target, 0, hs.ncell * sizeof(double), s);
     if (e != cudaSuccess) return e;
     const double sign = mode == 0 ? -1.0 : 1.0;
-    PIC_DISPATCH(prec, (rho3d_kernel<T><<<hs.npatch, 256, 0, s>>>(sd, target, sign)));
+    // the node tile of one patch in shared memory when the device grants it
+    const size_t tile = (size_t)(hs.P[0] + 3) * (hs.P[1] + 3) * (hs.P[2] + 3) * sizeof(double);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int tiled = tile <= (size_t)optin ? 1 : 0;
+    const size_t smem = tiled ? tile : 0;
+    PIC_DISPATCH(prec, (cudaFuncSetAttribute(rho3d_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem),
+                        rho3d_kernel<T><<<hs.npatch, 256, smem, s>>>(sd, target, sign, tiled)));
     if (mode == 1) {
         const unsigned g2 = (unsigned)((hs.ncell + 255) / 256);
         PIC_DISPATCH(prec, (gauss3d_kernel<T><<<g2, 256, 0, s>>>(sd)));

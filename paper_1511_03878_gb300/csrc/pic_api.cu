@@ -966,10 +966,26 @@ static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, s
             if (written) *written = b;
             return PIC_OK;
         }
-        case PIC_DIAG_FIELDS:
         case PIC_DIAG_EX_AXIS: {
+            // the row (j, k) = (ny/2, nz/2) of Ex is contiguous in the padded array
+            const int nx = S.n[0];
+            const size_t b = nx * sizeof(double);
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            const long long row =
+                ((long long)(S.dims == 3 ? S.n[2] / 2 + kGuard : 0) * S.NY + (S.n[1] / 2 + kGuard)) *
+                    S.NX + kGuard;
+            std::vector<char> h(nx * es);
+            CK(cudaMemcpy(h.data(), static_cast<const char*>(S.F[g]) + row * es, h.size(),
+                          cudaMemcpyDeviceToHost),
+               "read Ex");
+            double* o = static_cast<double*>(out);
+            for (int i = 0; i < nx; i++) o[i] = load_real(S.prec, h.data(), i);
+            if (written) *written = b;
+            return PIC_OK;
+        }
+        case PIC_DIAG_FIELDS: {
             const long long nc = S.ncell, fs = S.fstride;
-            const size_t b = kind == PIC_DIAG_FIELDS ? 12 * nc * sizeof(double) : S.n[0] * sizeof(double);
+            const size_t b = 12 * nc * sizeof(double);
             if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
             std::vector<char> hF(6 * fs * es), hH(3 * fs * es);
             std::vector<double> hJ(3 * fs);
@@ -992,12 +1008,7 @@ static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, s
             else
                 unpad_all(reinterpret_cast<df64*>(hF.data()), reinterpret_cast<df64*>(hH.data()));
             for (int a = 0; a < 3; a++) unpad_field(S, hJ.data() + a * fs, &all[(9 + a) * nc]);
-            if (kind == PIC_DIAG_FIELDS) {
-                memcpy(out, all.data(), b);
-            } else {
-                const long long row = ((long long)(S.n[2] / 2) * S.n[1] + S.n[1] / 2) * S.n[0];
-                memcpy(out, &all[row], b);
-            }
+            memcpy(out, all.data(), b);
             if (written) *written = b;
             return PIC_OK;
         }

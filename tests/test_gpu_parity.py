@@ -206,7 +206,7 @@ def test_load_places_and_converts_every_particle(binding, prec, dims, capfactor)
     and weight match the precision's storage rule, including the conversion's edge
     cases: the domain's origin, a cell face, a position whose offset rounds to 1 in
     float32, and one just under the domain's end whose cell coordinate rounds to n.
-    The fields come back as given."""
+    The fields come back as given, and the on-axis diagnostic is their Ex row."""
     if dims == 2:
         w = inputs.thermal2d(nx=64, ny=48, d=0.65, seed=3, patch=(16, 16))
     else:
@@ -231,8 +231,12 @@ def test_load_places_and_converts_every_particle(binding, prec, dims, capfactor)
         sim.load(dict(w, particles=q0, E=E, B=B))
         q = sim.particles()
         f = sim.fields()
+        axis = sim.ex_axis()
     finally:
         sim.close()
+    # the axis diagnostic reads the row (ny/2, nz/2) of Ex alone
+    row = f["Ex"][par["n"][1] // 2] if dims == 2 else f["Ex"][par["n"][2] // 2, par["n"][1] // 2]
+    assert np.array_equal(axis, row)
     assert np.array_equal(q["id"], np.sort(q0["id"]))
     order = np.argsort(q0["id"])
     for a, k in enumerate(keys):
