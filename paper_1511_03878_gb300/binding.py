@@ -297,9 +297,11 @@ class Sim:
         self.npatch = int(np.prod([n[a] // self.cfg.patch[a] for a in range(self.cfg.dims)]))
 
     def close(self):
+        """Destroys the sim (after its stream drains) and releases its arena."""
         if getattr(self, "h", None) is not None and self.h.value:
             pic_destroy(self.h)
             self.h = None
+        self.arena = None
 
     def __del__(self):
         try:
