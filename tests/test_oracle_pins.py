@@ -11,7 +11,8 @@ form or an invariant of the published scheme it restates:
     total current q w v / dV;
   * Yee: discrete dispersion relation of vacuum modes, dispersion-free 1D transport
     at dt = dx;
-  * full step: Gauss's law preserved to round-off for 100 steps;
+  * full step: Gauss's law preserved to round-off for 100 steps; a cold plasma mode
+    oscillates at the plasma frequency;
   * moving window: shift count floor(n dt/dx), exact field translation, injection.
 A plausible mistake anywhere (a dropped term, a sign, a stagger, a transposed
 index) breaks at least one of these.
@@ -368,6 +369,46 @@ def test_gauss_law_preserved_100_steps():
     # and the plasma did evolve: fields are not zero
     f = s.get_fields()
     assert np.abs(f["Ex"]).max() > 1e-4
+
+
+def test_cold_plasma_oscillates_at_the_plasma_frequency():
+    """Full loop, closed form: a cold electron plasma of density 1 (q = -1, m = 1, so
+    omega_p = 1) over a neutralising background starts with E = 0 and a small
+    longitudinal velocity mode u_x = u0 sin(k x). It oscillates at the plasma frequency.
+    The leapfrog makes that (2/dt) asin(omega_p dt/2), and the order-2 shapes lower it by
+    a fraction of (k dx)^2, a few tenths of a percent at k dx = 0.1. Zero crossings of
+    the mode's momentum over three periods give the frequency within 1 %. A wrong
+    charge, mass, weight or current factor moves it much further: a factor 2 in the
+    current would give sqrt(2)."""
+    nx, ny, d = 64, 4, 0.1
+    w = inputs.thermal2d(nx=nx, ny=ny, d=d, uth=0.0, seed=3, patch=(16, 4))
+    p = w["params"]
+    q = {k: np.array(v, copy=True) for k, v in w["particles"].items()}
+    kx = 2.0 * math.pi / (nx * d)
+    q["ux"] = 1e-3 * np.sin(kx * q["x"])
+    q["uy"][:] = 0.0
+    q["uz"][:] = 0.0
+    dt = p["dt"]
+    c = orc.make_config(2, p["n"][:2], p["d"][:2], dt)
+    s = orc.OracleSim(c, len(q["x"]))
+    s.set_particles(q)
+    s.set_fields(w["E"], w["B"])
+    s.set_rho_bg(None)
+    mode = []
+    for _ in range(int(3 * 2 * math.pi / dt) + 5):
+        s.step(1)
+        r = s.get_particles()
+        mode.append(float(np.sum(r["w"] * r["ux"] * np.sin(kx * r["x"]))))
+    m = np.array(mode)
+    # momenta live at half steps: m[j] is at t = (j + 1/2) dt
+    t = (np.arange(len(m)) + 0.5) * dt
+    i = np.nonzero(np.sign(m[:-1]) != np.sign(m[1:]))[0]
+    zeros = t[i] - m[i] * (t[i + 1] - t[i]) / (m[i + 1] - m[i])
+    assert len(zeros) >= 5
+    omega = math.pi / np.mean(np.diff(zeros))
+    want = 2.0 / dt * math.asin(dt / 2.0)
+    assert abs(omega / want - 1.0) < 1e-2, (omega, want)
+    assert omega < want  # the shapes' filtering lowers it
 
 
 def test_gauss_law_preserved_3d():
