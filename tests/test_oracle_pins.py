@@ -371,7 +371,21 @@ def test_gauss_law_preserved_100_steps():
     assert np.abs(f["Ex"]).max() > 1e-4
 
 
-def test_cold_plasma_oscillates_at_the_plasma_frequency():
+def _cold_plasma(dims, nx, d, side):
+    """Cold electrons of density 1 on a side^dims lattice per cell of an nx x 4 (x 4)
+    grid: positions, zero momenta, weights dV / ppc, ids."""
+    n = (nx, 4, 4)[:dims]
+    ax = [(np.arange(n[a])[:, None] + (np.arange(side) + 0.5)[None, :] / side).ravel() * d
+          for a in range(dims)]
+    pos = [g.ravel() for g in np.meshgrid(*ax, indexing="ij")]
+    N = pos[0].size
+    z = pos[2] if dims == 3 else np.zeros(N)
+    return n, dict(x=pos[0], y=pos[1], z=z, ux=np.zeros(N), uy=np.zeros(N), uz=np.zeros(N),
+                   w=np.full(N, d ** dims / side ** dims), id=np.arange(N, dtype=np.int32))
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_cold_plasma_oscillates_at_the_plasma_frequency(dims):
     """Full loop, closed form: a cold electron plasma of density 1 (q = -1, m = 1, so
     omega_p = 1) over a neutralising background starts with E = 0 and a small
     longitudinal velocity mode u_x = u0 sin(k x). It oscillates at the plasma frequency.
@@ -380,19 +394,16 @@ def test_cold_plasma_oscillates_at_the_plasma_frequency():
     the mode's momentum over three periods give the frequency within 1 %. A wrong
     charge, mass, weight or current factor moves it much further: a factor 2 in the
     current would give sqrt(2)."""
-    nx, ny, d = 64, 4, 0.1
-    w = inputs.thermal2d(nx=nx, ny=ny, d=d, uth=0.0, seed=3, patch=(16, 4))
-    p = w["params"]
-    q = {k: np.array(v, copy=True) for k, v in w["particles"].items()}
+    nx, d = 64, 0.1
+    n, q = _cold_plasma(dims, nx, d, 4 if dims == 2 else 2)
     kx = 2.0 * math.pi / (nx * d)
     q["ux"] = 1e-3 * np.sin(kx * q["x"])
-    q["uy"][:] = 0.0
-    q["uz"][:] = 0.0
-    dt = p["dt"]
-    c = orc.make_config(2, p["n"][:2], p["d"][:2], dt)
+    dt = inputs.cfl_dt((d,) * dims)
+    c = orc.make_config(dims, n, (d,) * dims, dt)
     s = orc.OracleSim(c, len(q["x"]))
     s.set_particles(q)
-    s.set_fields(w["E"], w["B"])
+    zero = np.zeros(n[::-1])
+    s.set_fields([zero] * 3, [zero] * 3)
     s.set_rho_bg(None)
     mode = []
     for _ in range(int(3 * 2 * math.pi / dt) + 5):
