@@ -13,6 +13,7 @@ form or an invariant of the published scheme it restates:
     at dt = dx;
   * full step: Gauss's law preserved to round-off for 100 steps; a cold plasma mode
     oscillates at the plasma frequency;
+  * energy diagnostic: closed-form field and kinetic energies;
   * moving window: shift count floor(n dt/dx), exact field translation, injection.
 A plausible mistake anywhere (a dropped term, a sign, a stagger, a transposed
 index) breaks at least one of these.
@@ -369,6 +370,30 @@ def test_gauss_law_preserved_100_steps():
     # and the plasma did evolve: fields are not zero
     f = s.get_fields()
     assert np.abs(f["Ex"]).max() > 1e-4
+
+
+def test_energy_diagnostic_closed_forms():
+    """Field energy (1/2) sum E^2 dV and B^2 alike, kinetic energy sum w m (gamma - 1),
+    on states with closed-form values. One period of sin sampled at N >= 3 points sums
+    its squares to N/2 exactly, so a unit sine in Ey holds V/4. A uniform Bz = 2 holds
+    2 V. Momenta on Pythagorean triples give exact gamma: u = 3/4 gives 5/4, and
+    u = 4/3 gives 5/3. The mass 2.5 catches a dropped m."""
+    n, d = (16, 8), (0.1, 0.2)
+    V = n[0] * d[0] * n[1] * d[1]
+    c = orc.make_config(2, n, d, 0.05, m=2.5)
+    s = orc.OracleSim(c, 8)
+    x = np.arange(n[0])
+    zero = np.zeros((n[1], n[0]))
+    ey = np.repeat(np.sin(2 * np.pi * x / n[0])[None, :], n[1], 0)
+    s.set_fields([zero, ey, zero], [zero, zero, np.full_like(zero, 2.0)])
+    p = dict(x=np.array([0.3, 0.5, 0.7]), y=np.array([0.4, 0.4, 0.4]), z=np.zeros(3),
+             ux=np.array([0.75, 0.0, 0.0]), uy=np.zeros(3), uz=np.array([0.0, 0.0, 4.0 / 3.0]),
+             w=np.array([2.0, 5.0, 3.0]), id=np.arange(3, dtype=np.int32))
+    s.set_particles(p)
+    we, wb, wk = s.energy()
+    assert abs(we - V / 4) < 1e-14 * V
+    assert abs(wb - 2.0 * V) < 1e-14 * V
+    assert abs(wk - 2.5 * (2.0 * 0.25 + 3.0 * 2.0 / 3.0)) < 1e-14
 
 
 def _cold_plasma(dims, nx, d, side):
