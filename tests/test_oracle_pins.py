@@ -14,6 +14,7 @@ form or an invariant of the published scheme it restates:
   * full step: Gauss's law preserved to round-off for 100 steps; a cold plasma mode
     oscillates at the plasma frequency;
   * energy diagnostic: closed-form field and kinetic energies;
+  * charge density: its total and first two moments from the spline's moments;
   * moving window: shift count floor(n dt/dx), exact field translation, injection.
 A plausible mistake anywhere (a dropped term, a sign, a stagger, a transposed
 index) breaks at least one of these.
@@ -370,6 +371,41 @@ def test_gauss_law_preserved_100_steps():
     # and the plasma did evolve: fields are not zero
     f = s.get_fields()
     assert np.abs(f["Ex"]).max() > 1e-4
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_charge_density_moments(dims):
+    """Charge density on the nodes from order-2 shapes: with E = 0 and no background,
+    the Gauss residual is -rho. Its moments are fixed by the quadratic B-spline. The
+    total is sum rho dV = q sum w. The first moment along x is q sum w x. The second is
+    q sum w (x^2 + dx^2/4), since the spline's variance is a quarter cell. This holds
+    for particles away from the periodic seam, where node positions do not wrap."""
+    rng = np.random.default_rng(5 + dims)
+    n = (16, 16, 8)[:dims]
+    d = (0.1, 0.2, 0.15)[:dims]
+    q_e = -1.0
+    c = orc.make_config(dims, n, d, 0.01, q=q_e)
+    N = 300
+    L = [n[a] * d[a] for a in range(dims)]
+    pos = [rng.uniform(0.3 * L[a], 0.7 * L[a], N) for a in range(dims)]
+    p = dict(x=pos[0], y=pos[1], z=pos[2] if dims == 3 else np.zeros(N), ux=np.zeros(N),
+             uy=np.zeros(N), uz=np.zeros(N), w=rng.uniform(0.5, 2.0, N),
+             id=np.arange(N, dtype=np.int32))
+    s = orc.OracleSim(c, N)
+    s.set_particles(p)
+    zero = np.zeros(n[::-1])
+    s.set_fields([zero] * 3, [zero] * 3)
+    s.set_rho_bg(zero)
+    rho = -s.gauss()
+    dV = float(np.prod(d))
+    xn = np.arange(n[0]) * d[0]  # nodes along x (last array axis)
+    tot = q_e * p["w"].sum()
+    assert abs(rho.sum() * dV - tot) < 1e-12 * abs(tot)
+    m1 = (rho * xn).sum() * dV
+    assert abs(m1 - q_e * np.sum(p["w"] * p["x"])) < 1e-12 * abs(tot) * L[0]
+    m2 = (rho * xn ** 2).sum() * dV
+    want = q_e * np.sum(p["w"] * (p["x"] ** 2 + d[0] ** 2 / 4))
+    assert abs(m2 - want) < 1e-12 * abs(tot) * L[0] ** 2
 
 
 def test_energy_diagnostic_closed_forms():
