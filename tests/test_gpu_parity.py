@@ -97,7 +97,7 @@ PREC64 = {"fp64": 0, "df64": 2}  # IEEE FP64 and double-word FP32 pairs: same to
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (20, 1e-9)])
 def test_thermal_fp64_full_size(binding, steps, tol, prec):
-    """configs[0]-sized thermal plasma: 128x128, 16 ppc (262 144 particles)."""
+    """The thermal plasma at full size: 128x128, 16 ppc (262 144 particles)."""
     w = inputs.thermal2d(seed=1511)
     n = len(w["particles"]["x"])
     sim = binding.Sim(w["params"], precision=PREC64[prec], capacity=2 * n)
