@@ -49,7 +49,7 @@ typedef struct pic_batch pic_batch;
 typedef enum {
     PIC_OK = 0,
     PIC_ERR_INVALID = -1,  /* bad argument or configuration */
-    PIC_ERR_NOMEM = -2,    /* arena or output buffer too small */
+    PIC_ERR_NOMEM = -2,    /* arena or output buffer too small, or a host allocation failed */
     PIC_ERR_CAPACITY = -3, /* a patch or exchange buffer overflowed on the device */
     PIC_ERR_CUDA = -4,     /* a CUDA runtime call failed */
     PIC_ERR_NUMERIC = -5,  /* non-finite particle state or a move of a cell or more */
