@@ -72,3 +72,31 @@ def test_field_solver_order_and_stability_limit(lib):
     b2 = binding.pic_required_bytes(binding.make_config(w, capacity=1000))
     b6 = binding.pic_required_bytes(binding.make_config(dict(w, maxwell_order=6), capacity=1000))
     assert 3 * 64 * 8 <= b6 - b2 <= 3 * 64 * 8 + 512
+
+
+def test_null_handles_are_rejected_without_a_gpu(lib):
+    """Every entry point checks its handle before any CUDA call: a null sim or batch
+    gives PIC_ERR_INVALID (0 bytes for the size queries), never a crash."""
+    import ctypes
+    nul = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)()
+    ip = ctypes.POINTER(ctypes.c_int)()
+    inv = binding.PIC_ERR_INVALID
+    assert lib.pic_load_particles(nul, 0, dp, dp, dp, dp, dp, dp, dp, ip) == inv
+    three = (ctypes.POINTER(ctypes.c_double) * 3)()
+    assert lib.pic_load_fields(nul, three, three, dp) == inv
+    assert lib.pic_step(nul, 1) == inv
+    assert lib.pic_sync(nul) == inv
+    written = ctypes.c_size_t(7)
+    buf = ctypes.create_string_buffer(64)
+    assert lib.pic_diag(nul, 0, buf, 64, ctypes.byref(written)) == inv
+    ms = (ctypes.c_double * 8)()
+    assert lib.pic_profile(nul, 1, ms, 8) == inv
+    assert lib.pic_destroy(nul) == inv
+    assert lib.pic_last_error(nul) == b"null sim"
+    assert lib.pic_batch_required_bytes(None, 0) == 0
+    out = ctypes.c_void_p()
+    assert lib.pic_batch_create(None, 0, ctypes.c_void_p(4096), 1 << 20, None,
+                                ctypes.byref(out)) == inv
+    assert lib.pic_batch_step(nul, 1) == inv
+    assert lib.pic_batch_destroy(nul) == inv
