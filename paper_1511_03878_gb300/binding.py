@@ -269,6 +269,28 @@ def pic_gauss_residual_2d_static(n, x_ptr, y_ptr, w_ptr, q, ex_ptr, ey_ptr, rho_
         float(dy), int(window), vp(stream_ptr) if stream_ptr else None))
 
 
+def check_workload(workload: dict, ncell: int, rho_bg=None):
+    """Raises ValueError unless the arrays have the sizes the C ABI reads: every particle
+    array given as long as x (ids required), and E, B (three arrays each) and rho_bg with
+    ncell values. The library reads exactly those counts from the host pointers."""
+    p = workload["particles"]
+    n = len(p["x"])
+    for k in ("x", "y", "z", "ux", "uy", "uz", "w", "id"):
+        if k not in p and k != "id":  # the loader passes zeros for an absent array
+            continue
+        if np.size(p[k]) != n:
+            raise ValueError(f"particle array {k!r} has {np.size(p[k])} entries, x has {n}")
+    for name in ("E", "B"):
+        arrs = workload[name]
+        if len(arrs) != 3:
+            raise ValueError(f"{name} needs three components, got {len(arrs)}")
+        for a, arr in enumerate(arrs):
+            if np.size(arr) != ncell:
+                raise ValueError(f"{name}[{a}] has {np.size(arr)} values, the grid {ncell}")
+    if rho_bg is not None and np.size(rho_bg) != ncell:
+        raise ValueError(f"rho_bg has {np.size(rho_bg)} values, the grid {ncell}")
+
+
 # ------------------------------------------------------------------ convenience object
 
 class Sim:
@@ -310,6 +332,7 @@ class Sim:
             pass
 
     def load(self, workload: dict, rho_bg=None):
+        check_workload(workload, self.ncell, rho_bg)
         pic_load_particles(self.h, workload["particles"])
         pic_load_fields(self.h, workload["E"], workload["B"], rho_bg)
 

@@ -100,3 +100,27 @@ def test_null_handles_are_rejected_without_a_gpu(lib):
                                 ctypes.byref(out)) == inv
     assert lib.pic_batch_step(nul, 1) == inv
     assert lib.pic_batch_destroy(nul) == inv
+
+
+def test_workload_sizes_checked_before_the_library_reads_them():
+    """Sim.load checks array sizes first (the library reads n particles and ncell field
+    values from the host pointers): every generator's workload passes, a short field or
+    particle array is refused."""
+    import numpy as np
+
+    cases = [inputs.thermal2d(nx=32, ny=16, patch=(16, 16)),
+             inputs.lwfa2d(nx=128, ny=64, patch=(32, 32)),
+             inputs.stress3d(n=(16, 8, 8), patch=(8, 8, 8), total=2000),
+             inputs.lwfa3d(nx=32, ny=8, nz=8, patch=(16, 8, 8))]
+    for w in cases:
+        n = w["params"]["n"]
+        ncell = n[0] * n[1] * (n[2] if w["params"]["dims"] == 3 else 1)
+        binding.check_workload(w, ncell)
+        binding.check_workload(w, ncell, np.zeros(ncell))
+        with pytest.raises(ValueError):
+            binding.check_workload(dict(w, E=[w["E"][0][:-1], w["E"][1], w["E"][2]]), ncell)
+        with pytest.raises(ValueError):
+            binding.check_workload(w, ncell, np.zeros(ncell - 1))
+        short = dict(w["particles"], ux=w["particles"]["ux"][:-1])
+        with pytest.raises(ValueError):
+            binding.check_workload(dict(w, particles=short), ncell)
