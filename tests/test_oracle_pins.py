@@ -5,7 +5,7 @@ standard second-order field scheme), so each part of the oracle is pinned by a c
 form or an invariant of the published scheme it restates:
   * quadratic B-spline: partition of unity, first moment, variance 1/4, continuity;
   * Boris: |u| conservation, exact discrete rotation angle, gyration radius of the
-    discrete orbit, rotation sense, E x B drift;
+    discrete orbit, rotation sense, E x B drift, relativistic uniform-E acceleration;
   * interpolation: exact reproduction of fields linear in position, per stagger;
   * Esirkepov: discrete continuity equation for one particle, zero current at rest,
     total current q w v / dV;
@@ -136,6 +136,36 @@ def test_full_step_gyration_radius_period_and_drift():
     assert np.allclose(step_ang, 2 * math.atan(b), rtol=0, atol=1e-11)  # electron: +z sense
     # continuum limit O(dt^2): R_exact -> Larmor radius gamma v / (|q| B)
     assert abs(R_exact / (u0 / Bz) - 1) < (b * b)
+
+
+def test_uniform_e_acceleration_follows_the_relativistic_trajectory():
+    """A test particle (negligible weight) in a uniform Ex, with no B, starting at rest
+    at t = -dt/2. Boris has no rotation here, so u^(N-1/2) = (q E / m) N dt exactly.
+    The leapfrog positions follow the relativistic hyperbola
+    x(t) = x0 + (sqrt(1 + a^2 (t + dt/2)^2) - sqrt(1 + a^2 dt^2/4)) / a, with a = q E / m,
+    to second order in dt. The error falls by 4 when dt halves, out to u = 5. Dropping
+    the 1/gamma of the move would put the particle several units off."""
+    errs = []
+    for dt in (0.05, 0.025):
+        c = orc.make_config(2, (32, 32), (0.1, 0.1), dt)
+        s = orc.OracleSim(c, 4)
+        s.set_particles(dict(x=np.array([1.6]), y=np.array([1.6]), z=np.zeros(1),
+                             ux=np.zeros(1), uy=np.zeros(1), uz=np.zeros(1),
+                             w=np.array([1e-15]), id=np.zeros(1, np.int32)))
+        zero = np.zeros((32, 32))
+        s.set_fields([np.full((32, 32), 0.5), zero, zero], [zero, zero, zero])
+        s.set_rho_bg(None)
+        N = int(round(10.0 / dt))
+        s.step(N)
+        r = s.get_particles()
+        a = -0.5  # q E / m for an electron
+        assert abs(r["ux"][0] - a * N * dt) < 1e-12 * abs(a * N * dt)
+        assert abs(r["uy"][0]) < 1e-15 and abs(r["uz"][0]) < 1e-15
+        t = N * dt
+        x = 1.6 + (math.sqrt(1 + (a * (t + dt / 2)) ** 2) - math.sqrt(1 + (a * dt / 2) ** 2)) / a
+        errs.append(abs(((r["x"][0] - x + 1.6) % 3.2) - 1.6))  # periodic box of 3.2
+    assert errs[0] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5
 
 
 def test_e_cross_b_drift():
