@@ -217,6 +217,66 @@ def test_interp_reproduces_linear_fields(dims):
             assert max(abs(v) for v in others) == 0.0
 
 
+def _stag_pos(n, d, comp, axis):
+    """Positions of a component's stored values along one axis: index i sits at
+    (i + s/2) d, s the component's stagger bit on that axis (Yee 1966)."""
+    return (np.arange(n[axis]) + 0.5 * STAG[comp][axis]) * d[axis]
+
+
+@pytest.mark.parametrize("window", [True, False])
+@pytest.mark.parametrize("axis", [1, 2])
+def test_interp_3d_reproduces_fields_linear_in_y_and_z(window, axis):
+    # Quadratic B-splines reproduce linear functions exactly (first moment = delta), so
+    # a 3D field linear along y or z comes back exactly at any position whose three taps
+    # along that axis stay on the same side of the periodic seam -- but only if the
+    # oracle uses each component's own y and z stagger. A wrong stagger bit shifts the
+    # result by b d/2 (b the slope), far above the 1e-13 bound.
+    n = (12, 16, 20)
+    d = (0.2, 0.3, 0.25)
+    c = orc.make_config(3, n, d, 0.05, window=window)
+    shp = orc.field_shape(c)  # (nz, ny, nx)
+    rng = np.random.default_rng(11 + axis + 2 * window)
+    for comp in range(6):
+        a, b = rng.uniform(-2, 2, 2)
+        F = [np.zeros(shp) for _ in range(6)]
+        coord = _stag_pos(n, d, comp, axis)
+        prof = a + b * coord
+        F[comp][...] = prof[:, None, None] if axis == 2 else prof[None, :, None]
+        L = n[axis] * d[axis]
+        for _ in range(25):
+            pos = [rng.uniform(3 * d[0], (n[0] - 3) * d[0]), rng.uniform(0, n[1] * d[1]),
+                   rng.uniform(0, n[2] * d[2])]
+            pos[axis] = rng.uniform(3 * d[axis], L - 3 * d[axis])  # away from the seam
+            out = orc.interp(c, F, pos)
+            assert abs(out[comp] - (a + b * pos[axis])) < 1e-13, (comp, axis)
+            assert max(abs(out[k]) for k in range(6) if k != comp) == 0.0
+
+
+@pytest.mark.parametrize("window", [True, False])
+def test_interp_3d_reproduces_fields_linear_in_all_axes(window):
+    # f = a + bx x + by y + bz z on every component's own staggered nodes: the tensor
+    # product of three quadratic splines reproduces it exactly, for each of the six
+    # staggerings at once (a transposed axis or a wrong stagger bit fails here)
+    n = (14, 12, 16)
+    d = (0.15, 0.35, 0.2)
+    c = orc.make_config(3, n, d, 0.05, window=window)
+    shp = orc.field_shape(c)
+    rng = np.random.default_rng(5 + window)
+    coef = rng.uniform(-3, 3, (6, 4))
+    F = []
+    for comp in range(6):
+        X = _stag_pos(n, d, comp, 0)[None, None, :]
+        Y = _stag_pos(n, d, comp, 1)[None, :, None]
+        Z = _stag_pos(n, d, comp, 2)[:, None, None]
+        F.append(np.broadcast_to(coef[comp, 0] + coef[comp, 1] * X + coef[comp, 2] * Y
+                                 + coef[comp, 3] * Z, shp).copy())
+    for _ in range(40):
+        pos = [rng.uniform(3 * d[a], (n[a] - 3) * d[a]) for a in range(3)]
+        out = orc.interp(c, F, pos)
+        want = coef[:, 0] + coef[:, 1:] @ np.array(pos)
+        assert np.abs(out - want).max() < 1e-12
+
+
 def test_interp_periodic_constant_and_y_linear():
     c = orc.make_config(2, (16, 16), (0.1, 0.2), 0.05)
     rng = np.random.default_rng(2)
