@@ -115,20 +115,27 @@ typedef struct {
 } pic_config;
 
 /* sizeof(pic_config) as this library was built: a binding compares it with its own
- * layout of the struct before passing one. */
+ * layout of the struct before passing one. The paper has no counterpart. */
 size_t pic_config_bytes(void);
 
-/* Device bytes one arena needs for this configuration (0 if the config is invalid). */
+/* Device bytes one arena needs for this configuration (0 if the config is invalid):
+ * the fields and the super-particles of every patch plus the exchange buffers (Sec.
+ * 3.1: a patch holds the fields and SP of its sub-domain). Used to admit simulations
+ * into a fixed device budget. */
 size_t pic_required_bytes(const pic_config* cfg);
 
 /* Create a sim in a caller-owned device arena (>= pic_required_bytes, 256-byte
- * aligned). cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all
+ * aligned). The grid is cut into patches of cfg->patch cells, each owning its fields
+ * and its SP (Sec. 3.1, "Dynamic load balancing": many small patches per process, so
+ * that load can be traded patch by patch). cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all
  * work of this sim is ordered. On success *out owns host-side state only. */
 pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes,
                       void* cuda_stream, pic_sim** out);
 
 /* Load n particles from host SoA arrays (float64 physical positions, momenta
- * u = gamma v, weights; int32 ids, unique and >= 0). z may be NULL in 2D. Positions
+ * u = gamma v, weights; int32 ids, unique and >= 0). Each SP is binned into the patch
+ * that holds it; the SP count per patch is the load measure (Sec. 3: the load of a
+ * region is its number of SP) that orders the work queue. z may be NULL in 2D. Positions
  * must lie in [0, n[a] d[a]). The host validates the particles and bins them by patch;
  * the arrays are copied to the device as they are (page-locked arrays copy
  * asynchronously while the host bins) and converted there. Per-patch capacities split
@@ -141,8 +148,10 @@ pic_status pic_load_particles(pic_sim* sim, long long n, const double* x, const 
                               const double* z, const double* ux, const double* uy,
                               const double* uz, const double* w, const int* id);
 
-/* Load fields from host arrays [nz][ny][nx]: E at t = 0, B at t = +dt/2 (the first
- * push uses that B at integer time too). rho_bg: immobile background charge on
+/* Load fields from host arrays [nz][ny][nx] on the staggered Yee nodes of the
+ * second-order scheme (Sec. 2.1): E at t = 0, B at t = +dt/2 (the first
+ * push uses that B at integer time too). For laser-wakefield runs these hold the laser
+ * pulse at the foot of the density ramp (Sec. 2.2). rho_bg: immobile background charge on
  * nodes for the Gauss diagnostic; NULL = minus the charge density of the particles
  * loaded now. Zeroes the current. The arrays are copied as they are and padded with
  * guard cells on the device; they are not retained. */
@@ -150,14 +159,21 @@ pic_status pic_load_fields(pic_sim* sim, const double* const E[3], const double*
                            const double* rho_bg);
 
 /* Enqueue nsteps steps on the sim's stream (asynchronous: returns before the GPU
- * finishes). Each step is one replay of a CUDA graph of the kernels above. */
+ * finishes). Each step is one replay of a CUDA graph of the kernels above: one PIC
+ * cycle (Sec. 3: the per-SP work of interpolation, push and deposition, then the field
+ * update, Sec. 2.1), with the exchange of SP between neighbouring patches that
+ * independent patches need (Sec. 3.1). */
 pic_status pic_step(pic_sim* sim, int nsteps);
 
-/* Wait for the sim's stream; returns any latched device error. */
+/* Wait for the sim's stream; returns any latched device error. The paper has no
+ * counterpart. */
 pic_status pic_sync(pic_sim* sim);
 
 /* Diagnostics (synchronise first, then copy to the host buffer out of out_bytes;
- * *written = bytes written). Kinds: */
+ * *written = bytes written). PATCH_COUNTS is the SP count per patch, the load measure
+ * whose spread across the domain the paper plots (Sec. 3, Fig. 2: SP per process in a
+ * 3D run); ENERGY and EX_AXIS are the energy and wake-field diagnostics of a
+ * laser-wakefield run (Sec. 2.2). Kinds: */
 enum {
     PIC_DIAG_ENERGY = 0,        /* 3 float64: W_E, W_B (with B^n), W_kin          */
     PIC_DIAG_GAUSS = 1,         /* ncell float64: div E - rho - rho_bg on nodes    */
@@ -182,18 +198,24 @@ pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t*
  * build, particle push/deposit, window injection, particle exchange, capacity repack
  * (kernels that return at once unless a patch needs room), Yee E+B, end of step, and
  * the whole steps. n_ms must be >= 8. Same kernels and launch shapes as pic_step; the
- * state advances by nsteps. */
+ * state advances by nsteps. The paper has no counterpart (it reports wall times per
+ * process, Fig. 4; this is the per-kernel breakdown on one GPU). */
 pic_status pic_profile(pic_sim* sim, int nsteps, double* ms, int n_ms);
 
-/* Destroy the host-side state (synchronises; does not free the arena). */
+/* Destroy the host-side state (synchronises; does not free the arena). The paper has
+ * no counterpart (resource management of this library). */
 pic_status pic_destroy(pic_sim* sim);
 
-/* One-line description of the last error on this sim (never NULL). */
+/* One-line description of the last error on this sim (never NULL). The paper has no
+ * counterpart. */
 const char* pic_last_error(const pic_sim* sim);
 
 /* ---- batching: many sims stepped together, one persistent particle launch ----
  * All sims of a batch share dims and precision; each keeps its own arena, state
- * and step counter. The batch needs a small arena of its own (work queue). */
+ * and step counter. The batch needs a small arena of its own (work queue). The patches
+ * of all sims share one work queue ordered by SP count, so uneven sims balance the way
+ * uneven patches do (Sec. 3.1: work distributed by patch load), which serves the
+ * parameter-scan campaigns of Sec. 2.2. */
 size_t pic_batch_required_bytes(pic_sim* const* sims, int nsims);
 pic_status pic_batch_create(pic_sim* const* sims, int nsims, void* dev_arena,
                             size_t arena_bytes, void* cuda_stream, pic_batch** out);
@@ -210,7 +232,9 @@ pic_status pic_batch_destroy(pic_batch* batch);
  * PIC_STATIC_MAX_CELLS float64 (8 MiB), which every GPU that loads the library
  * holds until the process exits.
  *   x, y, w : n particle positions (physical, in [0, nx dx) x [0, ny dy)) and
- *             weights, device float64; particles outside the grid are skipped.
+ *             weights, device float64; particles outside the grid are skipped. The
+ *             cell coordinate is x / dx in IEEE division, kept below nx for a position
+ *             just under the end (as pic_load_particles computes it).
  *   q       : species charge.
  *   Ex, Ey  : device float64 [ny][nx], Yee staggering (Ex at (i+1/2, j), Ey at
  *             (i, j+1/2)).
@@ -224,8 +248,10 @@ pic_status pic_batch_destroy(pic_batch* batch);
  * call clears the part it uses before depositing. Calls that overlap on the GPU
  * (other streams, other host threads) race on that array: serialise them.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. */
+ * (cudaGetSymbolAddress) with that device current, and looks it up again when the
+ * device's context has changed since (after a cudaDeviceReset, for instance); make
+ * the first call on a device, and the first after a reset, before any stream
+ * capture. */
 #define PIC_STATIC_MAX_CELLS (1 << 20)
 pic_status pic_gauss_residual_2d_static(long long n, const double* x, const double* y,
                                         const double* w, double q, const double* Ex,
@@ -233,7 +259,7 @@ pic_status pic_gauss_residual_2d_static(long long n, const double* x, const doub
                                         int nx, int ny, double dx, double dy, int window,
                                         void* cuda_stream);
 
-/* Failure-path self-test of the bounded device waits. Every wait of the library's
+/* Failure-path self-test of the bounded device waits (the paper has no counterpart). Every wait of the library's
  * kernels on an asynchronous transfer (the mbarrier of a TMA tile load) gives up after
  * about 2^31 SM clocks (about a second) and latches a status bit instead of hanging.
  * This call launches one CTA that waits, through that same bounded wait, on an

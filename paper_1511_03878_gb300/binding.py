@@ -174,15 +174,49 @@ def pic_required_bytes(cfg: PicConfig) -> int:
     return int(lib().pic_required_bytes(ctypes.byref(cfg)))
 
 
+# cells of the grid of every live handle made by pic_create (the library reads that
+# many values from each host field array)
+_ncell = {}
+
+
 def pic_create(cfg: PicConfig, arena_ptr: int, arena_bytes: int, stream_ptr: int):
     h = ctypes.c_void_p()
     _check(lib().pic_create(ctypes.byref(cfg), ctypes.c_void_p(arena_ptr), arena_bytes,
                             ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    _ncell[h.value] = int(cfg.n[0]) * int(cfg.n[1]) * (int(cfg.n[2]) if cfg.dims == 3 else 1)
     return h
 
 
+def _check_particles(p: dict) -> int:
+    """n from x; every other array given (ids required) must hold n entries, since the
+    library reads n values from each pointer."""
+    n = int(np.size(p["x"]))
+    if "id" not in p:
+        raise ValueError("particle ids are required")
+    for k in ("y", "z", "ux", "uy", "uz", "w", "id"):
+        if k in p and np.size(p[k]) != n:
+            raise ValueError(f"particle array {k!r} has {np.size(p[k])} entries, x has {n}")
+    return n
+
+
+def _check_fields(h, E, B, rho_bg):
+    """Three components each for E and B, all (and rho_bg) with the grid's cell count."""
+    ncell = _ncell.get(h.value if isinstance(h, ctypes.c_void_p) else h)
+    for name, arrs in (("E", E), ("B", B)):
+        if len(arrs) != 3:
+            raise ValueError(f"{name} needs three components, got {len(arrs)}")
+    sizes = [np.size(a) for a in list(E) + list(B)]
+    if rho_bg is not None:
+        sizes.append(np.size(rho_bg))
+    want = ncell if ncell is not None else sizes[0]
+    for k, sz in enumerate(sizes):
+        if sz != want:
+            what = ("E", "B")[k // 3] + f"[{k % 3}]" if k < 6 else "rho_bg"
+            raise ValueError(f"{what} has {sz} values, the grid {want}")
+
+
 def pic_load_particles(h, p: dict):
-    n = len(p["x"])
+    n = _check_particles(p)
     arrs = [np.ascontiguousarray(p.get(k, np.zeros(n)), dtype=np.float64)
             for k in ("x", "y", "z", "ux", "uy", "uz", "w")]
     ids = np.ascontiguousarray(p["id"], dtype=np.int32)
@@ -190,6 +224,7 @@ def pic_load_particles(h, p: dict):
 
 
 def pic_load_fields(h, E, B, rho_bg=None):
+    _check_fields(h, E, B, rho_bg)
     E = [np.ascontiguousarray(a, dtype=np.float64) for a in E]
     B = [np.ascontiguousarray(a, dtype=np.float64) for a in B]
     Ep = (ctypes.POINTER(ctypes.c_double) * 3)(*[_dp(a) for a in E])
@@ -224,6 +259,7 @@ def pic_profile(h, nsteps: int) -> dict:
 
 
 def pic_destroy(h):
+    _ncell.pop(h.value if isinstance(h, ctypes.c_void_p) else h, None)
     _check(lib().pic_destroy(h))
 
 

@@ -1,7 +1,9 @@
 // 3D3V particle kernel: the 2D kernel's structure with a 4D TMA box (x, y, z,
 // component), 27-tap order-2 interpolation and the 3D Esirkepov weights
 //   W_a = DS_a ((S0_b + DS_b/2) S0_c + (S0_b/2 + DS_b/3) DS_c),
-// J_a the running sum of -(q w/dV)(d_a/dt) W_a along +a. All axes periodic.
+// J_a the running sum of -(q w/dV)(d_a/dt) W_a along +a. y and z are periodic; x is
+// periodic or a moving window (particles leaving [0, nx) are absorbed, the shift is
+// applied in the particle store, contributions outside the window are dropped).
 // FP32 cells pack (ix | iy << 11 | iz << 22).
 #include <cuda_runtime.h>
 

@@ -124,3 +124,35 @@ def test_workload_sizes_checked_before_the_library_reads_them():
         short = dict(w["particles"], ux=w["particles"]["ux"][:-1])
         with pytest.raises(ValueError):
             binding.check_workload(dict(w, particles=short), ncell)
+
+
+def test_module_level_loads_check_sizes_before_the_library_reads_them():
+    """The same-name wrappers pic_load_particles / pic_load_fields refuse short arrays
+    themselves (n from x; the grid's cell count remembered from pic_create, else the
+    first array's), so no path into the C ABI hands the library a short host array."""
+    import ctypes
+
+    import numpy as np
+
+    w = inputs.thermal2d(nx=32, ny=16, patch=(16, 16))
+    h = ctypes.c_void_p(0)  # never reached: the checks raise first
+    short = dict(w["particles"], w=w["particles"]["w"][:-1])
+    with pytest.raises(ValueError):
+        binding.pic_load_particles(h, short)
+    noid = {k: v for k, v in w["particles"].items() if k != "id"}
+    with pytest.raises(ValueError):
+        binding.pic_load_particles(h, noid)
+    E, B = w["E"], w["B"]
+    with pytest.raises(ValueError):
+        binding.pic_load_fields(h, [E[0], E[1], E[2][:, :-1]], B)
+    with pytest.raises(ValueError):
+        binding.pic_load_fields(h, E, B[:2])
+    with pytest.raises(ValueError):
+        binding.pic_load_fields(h, E, B, np.zeros(E[0].size - 1))
+    # a handle made by pic_create is checked against its own grid
+    binding._ncell[12345] = E[0].size + 1
+    try:
+        with pytest.raises(ValueError):
+            binding.pic_load_fields(ctypes.c_void_p(12345), E, B)
+    finally:
+        binding._ncell.pop(12345, None)
