@@ -92,9 +92,15 @@ def test_serve_same_alone_and_in_mix(binding):
     for r, q in zip(res, reqs):
         e, ax, n = serve.run_alone(q)
         assert r.particles == n
-        assert abs(r.energy.sum() - e.sum()) / e.sum() < 1e-3, (q.rid, r.energy, e)
+        de = abs(r.energy.sum() - e.sum()) / e.sum()
         err = np.linalg.norm(r.ex_axis - ax) / max(np.linalg.norm(ax), 1e-30)
-        assert err < 1e-2, (q.rid, err)
+        print(f"serve alone-vs-mix rid={q.rid} energy_rel={de:.3e} ex_axis_l2={err:.3e}")
+        # The same FP32 kernels on the same inputs: alone and in the mix differ only in
+        # the order of the FP64 global current atomics, measured on a GB300 at up to
+        # 2.9e-8 (energy) and 5.7e-6 (Ex on axis) after 250-400 steps. The gates sit
+        # about ten times above that, so a batching error of even 1e-4 fails.
+        assert de < 3e-7, (q.rid, r.energy, e)
+        assert err < 6e-5, (q.rid, err)
 
 
 def test_serve_admission_respects_budget(binding):
