@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or (
         os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
                                            os.path.getmtime(_SRC[:-2] + ".h"))):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                "-o", _LIB_PATH, _SRC, "-lm"]
         subprocess.check_call(cmd)
     return _LIB_PATH
@@ -87,6 +87,7 @@ def lib():
         L.orc_get_fields.argtypes = [ctypes.c_void_p, _dp]
         L.orc_set_rho_bg.argtypes = [ctypes.c_void_p, _dp]
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_step_mt.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.orc_steps_done.restype = ctypes.c_longlong
         L.orc_steps_done.argtypes = [ctypes.c_void_p]
         L.orc_shifts_done.restype = ctypes.c_longlong
@@ -280,8 +281,12 @@ class OracleSim:
             a = np.ascontiguousarray(rho_bg, dtype=np.float64)
             lib().orc_set_rho_bg(self._h, _ptr(a))
 
-    def step(self, n: int = 1):
-        rc = lib().orc_step(self._h, int(n))
+    def step(self, n: int = 1, threads: int = 1):
+        """n steps; threads > 1 runs the threaded form (bit-identical results)."""
+        if threads > 1:
+            rc = lib().orc_step_mt(self._h, int(n), int(threads))
+        else:
+            rc = lib().orc_step(self._h, int(n))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
 

@@ -21,6 +21,7 @@
 #include "pic_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -73,6 +74,26 @@ static double at(const orc_config* c, const double* a, long i, long j, long k) {
 static void add_at(const orc_config* c, double* a, long i, long j, long k, double v) {
     long long t = flat(c, i, j, k);
     if (t >= 0) a[t] += v;
+}
+
+/* Index along the slowest array axis (y in 2D, z in 3D; always a periodic axis) of
+ * flat index t. */
+static long slow_index(const orc_config* c, long long t) {
+    return c->dims == 3 ? (long)(t / ((long long)c->n[0] * c->n[1])) : (long)(t / c->n[0]);
+}
+
+static long slow_extent(const orc_config* c) { return c->dims == 3 ? c->n[2] : c->n[1]; }
+
+/* add_at restricted to the elements whose slow-axis index lies in [band[0], band[1]).
+ * The plain step passes the whole axis, so it is add_at; the threaded step gives each
+ * thread its own band of the current, so every element still receives the same
+ * additions in the same order. */
+static void add_band(const orc_config* c, const long band[2], double* a, long i, long j,
+                     long k, double v) {
+    long long t = flat(c, i, j, k);
+    if (t < 0) return;
+    long sl = slow_index(c, t);
+    if (sl >= band[0] && sl < band[1]) a[t] += v;
 }
 
 long long orc_shift_count(const orc_config* c, long long step) {
@@ -156,7 +177,7 @@ static int esirkepov_shapes(double xi0, double xi1, long* node0, double S0[5],
 }
 
 static int deposit2d(const orc_config* c, const double pos0[3], const double pos1[3],
-                     double vz, double qw, double* const J[3]) {
+                     double vz, double qw, double* const J[3], const long band[2]) {
     long n0[2];
     double S0[2][5], DS[2][5];
     for (int a = 0; a < 2; a++)
@@ -171,7 +192,7 @@ static int deposit2d(const orc_config* c, const double pos0[3], const double pos
         double acc = 0.0;
         for (int k = 0; k < 4; k++) {
             acc += DS[0][k] * (S0[1][l] + 0.5 * DS[1][l]);
-            add_at(c, J[0], n0[0] + k - 2, n0[1] + l - 2, 0, cx * acc);
+            add_band(c, band, J[0], n0[0] + k - 2, n0[1] + l - 2, 0, cx * acc);
         }
     }
     /* Jy at (i, j+1/2): running sum of Wy = DSy (S0x + DSx/2) along +y */
@@ -179,7 +200,7 @@ static int deposit2d(const orc_config* c, const double pos0[3], const double pos
         double acc = 0.0;
         for (int l = 0; l < 4; l++) {
             acc += DS[1][l] * (S0[0][k] + 0.5 * DS[0][k]);
-            add_at(c, J[1], n0[0] + k - 2, n0[1] + l - 2, 0, cy * acc);
+            add_band(c, band, J[1], n0[0] + k - 2, n0[1] + l - 2, 0, cy * acc);
         }
     }
     /* Jz at nodes: vz times the path-averaged shape Wz */
@@ -187,7 +208,7 @@ static int deposit2d(const orc_config* c, const double pos0[3], const double pos
         for (int k = 0; k < 5; k++) {
             double wz = S0[0][k] * S0[1][l] + 0.5 * DS[0][k] * S0[1][l] +
                         0.5 * S0[0][k] * DS[1][l] + DS[0][k] * DS[1][l] / 3.0;
-            add_at(c, J[2], n0[0] + k - 2, n0[1] + l - 2, 0, cz * wz);
+            add_band(c, band, J[2], n0[0] + k - 2, n0[1] + l - 2, 0, cz * wz);
         }
     return 0;
 }
@@ -195,7 +216,7 @@ static int deposit2d(const orc_config* c, const double pos0[3], const double pos
 /* 3D: W_a = DS_a (S0_b S0_c + DS_b S0_c/2 + S0_b DS_c/2 + DS_b DS_c/3) for the two
  * other axes b, c; J_a is the running sum of -(qw/dV)(d_a/dt) W_a along +a. */
 static int deposit3d(const orc_config* c, const double pos0[3], const double pos1[3],
-                     double qw, double* const J[3]) {
+                     double qw, double* const J[3], const long band[2]) {
     long n0[3];
     double S0[3][5], DS[3][5];
     for (int a = 0; a < 3; a++)
@@ -217,7 +238,7 @@ static int deposit3d(const orc_config* c, const double pos0[3], const double pos
                     idx[a] = n0[a] + ia - 2;
                     idx[b] = n0[b] + ib - 2;
                     idx[e] = n0[e] + ie - 2;
-                    add_at(c, J[a], idx[0], idx[1], idx[2], coef * acc);
+                    add_band(c, band, J[a], idx[0], idx[1], idx[2], coef * acc);
                 }
             }
     }
@@ -226,10 +247,11 @@ static int deposit3d(const orc_config* c, const double pos0[3], const double pos
 
 void orc_deposit(const orc_config* c, const double pos0[3], const double pos1[3],
                  double vz, double qw, double* const J[3]) {
+    const long all[2] = {0, slow_extent(c)};
     if (c->dims == 2)
-        deposit2d(c, pos0, pos1, vz, qw, J);
+        deposit2d(c, pos0, pos1, vz, qw, J, all);
     else
-        deposit3d(c, pos0, pos1, qw, J);
+        deposit3d(c, pos0, pos1, qw, J, all);
 }
 
 void orc_rho(const orc_config* c, long long n, const double* x, const double* y,
@@ -298,12 +320,16 @@ static double dplus(const orc_config* c, const double* F, int a, long i, long j,
     return s / c->d[a];
 }
 
-void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
-               const double* const J[3]) {
+/* The field updates over the cells whose slow-axis index lies in [lo, hi) (the whole
+ * grid for the plain step; one band per thread for the threaded one: every cell's new
+ * value depends only on the old arrays, so the bands are independent). */
+static void yee_e_band(const orc_config* c, double* const E[3], const double* const B[3],
+                       const double* const J[3], long lo, long hi) {
     double dt = c->dt;
     int d3 = c->dims == 3;
-    for (long k = 0; k < c->n[2]; k++)
-        for (long j = 0; j < c->n[1]; j++)
+    long k0 = d3 ? lo : 0, k1 = d3 ? hi : 1, j0 = d3 ? 0 : lo, j1 = d3 ? c->n[1] : hi;
+    for (long k = k0; k < k1; k++)
+        for (long j = j0; j < j1; j++)
             for (long i = 0; i < c->n[0]; i++) {
                 long long t = flat(c, i, j, k);
                 const double *Bx = B[0], *By = B[1], *Bz = B[2];
@@ -322,11 +348,18 @@ void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3]
             }
 }
 
-void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]) {
+void orc_yee_e(const orc_config* c, double* const E[3], const double* const B[3],
+               const double* const J[3]) {
+    yee_e_band(c, E, B, J, 0, slow_extent(c));
+}
+
+static void yee_b_band(const orc_config* c, const double* const E[3], double* const B[3],
+                       long lo, long hi) {
     double dt = c->dt;
     int d3 = c->dims == 3;
-    for (long k = 0; k < c->n[2]; k++)
-        for (long j = 0; j < c->n[1]; j++)
+    long k0 = d3 ? lo : 0, k1 = d3 ? hi : 1, j0 = d3 ? 0 : lo, j1 = d3 ? c->n[1] : hi;
+    for (long k = k0; k < k1; k++)
+        for (long j = j0; j < j1; j++)
             for (long i = 0; i < c->n[0]; i++) {
                 long long t = flat(c, i, j, k);
                 const double *Ex = E[0], *Ey = E[1], *Ez = E[2];
@@ -341,6 +374,10 @@ void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]
                 B[1][t] -= dt * cy;
                 B[2][t] -= dt * cz;
             }
+}
+
+void orc_yee_b(const orc_config* c, const double* const E[3], double* const B[3]) {
+    yee_b_band(c, E, B, 0, slow_extent(c));
 }
 
 void orc_div_e(const orc_config* c, const double* const E[3], double* out) {
@@ -581,6 +618,7 @@ int orc_step(orc_sim* s, int nsteps) {
     double L[3] = {c->n[0] * c->d[0], c->n[1] * c->d[1], c->n[2] * c->d[2]};
     double* Bold[3];
     for (int a = 0; a < 3; a++) Bold[a] = (double*)malloc((size_t)s->ncell * sizeof(double));
+    const long all[2] = {0, slow_extent(c)};
     int rc = 0;
     for (int it = 0; it < nsteps && rc == 0; it++) {
         for (int a = 0; a < 3; a++) memset(s->J[a], 0, (size_t)s->ncell * sizeof(double));
@@ -594,8 +632,8 @@ int orc_step(orc_sim* s, int nsteps) {
             double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             double pos1[3] = {pos0[0], pos0[1], pos0[2]};
             for (int a = 0; a < dims; a++) pos1[a] = pos0[a] + c->dt * u[a] / gamma;
-            int bad = dims == 2 ? deposit2d(c, pos0, pos1, u[2] / gamma, c->q * s->w[p], s->J)
-                                : deposit3d(c, pos0, pos1, c->q * s->w[p], s->J);
+            int bad = dims == 2 ? deposit2d(c, pos0, pos1, u[2] / gamma, c->q * s->w[p], s->J, all)
+                                : deposit3d(c, pos0, pos1, c->q * s->w[p], s->J, all);
             if (bad) rc = -2;
             s->x[p] = pos1[0];
             s->y[p] = pos1[1];
@@ -626,6 +664,217 @@ int orc_step(orc_sim* s, int nsteps) {
             if (window_shift(s)) rc = -3;
     }
     for (int a = 0; a < 3; a++) free(Bold[a]);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ threaded step
+ *
+ * orc_step_mt computes exactly what orc_step computes, on several host threads, with
+ * results identical bit for bit (it is the oracle's all-core timing and long-run
+ * form; tests check the identity). Each phase of the step is split so that no value
+ * is summed in a different order:
+ *   - the particle update (interpolation, Boris, move) is independent per particle:
+ *     threads take contiguous particle ranges;
+ *   - the current: thread t owns a band of rows along the slowest axis of J (y in 2D,
+ *     z in 3D) and walks ALL particles in index order, depositing only into its band.
+ *     Every element of J thus receives the same additions in the same order as in the
+ *     single-thread loop (per-thread copies of J summed afterwards would not: the
+ *     association of the sums would change);
+ *   - the field updates are independent per cell: threads take bands;
+ *   - particle boundaries, the window shift and the diagnostics stay single-threaded. */
+
+#define ORC_MAX_THREADS 256
+
+typedef struct {
+    void (*fn)(void*, int, int);
+    void* arg;
+    int tid, nt;
+} par_job;
+
+static void* par_entry(void* p) {
+    par_job* j = (par_job*)p;
+    j->fn(j->arg, j->tid, j->nt);
+    return NULL;
+}
+
+/* runs fn(arg, t, nt) for t = 0..nt-1, thread 0 on the calling thread */
+static void par_run(int nt, void (*fn)(void*, int, int), void* arg) {
+    pthread_t th[ORC_MAX_THREADS];
+    par_job job[ORC_MAX_THREADS];
+    int started[ORC_MAX_THREADS];
+    for (int t = 0; t < nt; t++) {
+        job[t].fn = fn;
+        job[t].arg = arg;
+        job[t].tid = t;
+        job[t].nt = nt;
+        started[t] = 0;
+    }
+    for (int t = 1; t < nt; t++)
+        started[t] = pthread_create(&th[t], NULL, par_entry, &job[t]) == 0;
+    fn(arg, 0, nt);
+    for (int t = 1; t < nt; t++) {
+        if (started[t])
+            pthread_join(th[t], NULL);
+        else
+            fn(arg, t, nt); /* no thread: do its share here */
+    }
+}
+
+static void range_of(long long n, int t, int nt, long long* lo, long long* hi) {
+    *lo = n * t / nt;
+    *hi = n * (t + 1) / nt;
+}
+
+typedef struct {
+    orc_sim* s;
+    double *x0, *y0, *z0, *vz, *qw; /* per particle: old position, v_z, q w */
+    double* Bold[3];
+    int bad;                        /* a particle moved by more than one node */
+} mt_ctx;
+
+static void mt_push(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    orc_sim* s = m->s;
+    const orc_config* c = &s->c;
+    const double* F[6] = {s->E[0], s->E[1], s->E[2], s->Bn[0], s->Bn[1], s->Bn[2]};
+    long long lo, hi;
+    range_of(s->np, t, nt, &lo, &hi);
+    for (long long p = lo; p < hi; p++) {
+        double pos0[3] = {s->x[p], s->y[p], s->z[p]};
+        double EB[6];
+        orc_interp(c, F, pos0, EB);
+        double u[3] = {s->ux[p], s->uy[p], s->uz[p]};
+        orc_boris(c->q, c->m, c->dt, EB, EB + 3, u);
+        double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double pos1[3] = {pos0[0], pos0[1], pos0[2]};
+        for (int a2 = 0; a2 < c->dims; a2++) pos1[a2] = pos0[a2] + c->dt * u[a2] / gamma;
+        m->x0[p] = pos0[0];
+        m->y0[p] = pos0[1];
+        m->z0[p] = pos0[2];
+        m->vz[p] = u[2] / gamma;
+        m->qw[p] = c->q * s->w[p];
+        s->x[p] = pos1[0];
+        s->y[p] = pos1[1];
+        s->z[p] = pos1[2];
+        s->ux[p] = u[0];
+        s->uy[p] = u[1];
+        s->uz[p] = u[2];
+    }
+}
+
+static void mt_deposit(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    orc_sim* s = m->s;
+    const orc_config* c = &s->c;
+    const int sa = c->dims == 3 ? 2 : 1; /* slow axis */
+    const long ns = slow_extent(c);
+    long long lo, hi;
+    range_of(ns, t, nt, &lo, &hi);
+    const long band[2] = {(long)lo, (long)hi};
+    if (lo >= hi) return;
+    int bad = 0;
+    for (long long p = 0; p < s->np; p++) {
+        const double pos0[3] = {m->x0[p], m->y0[p], m->z0[p]};
+        /* the deposit touches slow-axis nodes node0 - 2 .. node0 + 2 (wrapped) */
+        const long node0 = (long)floor(pos0[sa] / c->d[sa] + 0.5);
+        int touches = 0;
+        for (long r = node0 - 2; r <= node0 + 2 && !touches; r++) {
+            long rw = wrap(r, ns);
+            touches = rw >= band[0] && rw < band[1];
+        }
+        if (!touches) continue;
+        const double pos1[3] = {s->x[p], s->y[p], s->z[p]};
+        int b = c->dims == 2 ? deposit2d(c, pos0, pos1, m->vz[p], m->qw[p], s->J, band)
+                             : deposit3d(c, pos0, pos1, m->qw[p], s->J, band);
+        if (b) bad = 1;
+    }
+    if (bad) m->bad = 1; /* every writer stores the same value */
+}
+
+static void mt_zero_j(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    long long lo, hi;
+    range_of(m->s->ncell, t, nt, &lo, &hi);
+    for (int k = 0; k < 3; k++)
+        memset(m->s->J[k] + lo, 0, (size_t)(hi - lo) * sizeof(double));
+}
+
+static void mt_yee_e(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    orc_sim* s = m->s;
+    long long lo, hi;
+    range_of(slow_extent(&s->c), t, nt, &lo, &hi);
+    yee_e_band(&s->c, s->E, (const double* const*)s->Bh, (const double* const*)s->J, (long)lo,
+               (long)hi);
+    /* keep B^{n+1/2} for the average (the cells of this band only) */
+    long long c0 = lo * (s->ncell / slow_extent(&s->c)), c1 = hi * (s->ncell / slow_extent(&s->c));
+    for (int k = 0; k < 3; k++)
+        memcpy(m->Bold[k] + c0, s->Bh[k] + c0, (size_t)(c1 - c0) * sizeof(double));
+}
+
+static void mt_yee_b(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    orc_sim* s = m->s;
+    long long lo, hi;
+    range_of(slow_extent(&s->c), t, nt, &lo, &hi);
+    yee_b_band(&s->c, (const double* const*)s->E, s->Bh, (long)lo, (long)hi);
+}
+
+static void mt_average(void* a, int t, int nt) {
+    mt_ctx* m = (mt_ctx*)a;
+    orc_sim* s = m->s;
+    long long lo, hi;
+    range_of(s->ncell, t, nt, &lo, &hi);
+    for (int k = 0; k < 3; k++)
+        for (long long i = lo; i < hi; i++) s->Bn[k][i] = 0.5 * (m->Bold[k][i] + s->Bh[k][i]);
+}
+
+int orc_step_mt(orc_sim* s, int nsteps, int nthreads) {
+    const orc_config* c = &s->c;
+    int nt = nthreads < 1 ? 1 : (nthreads > ORC_MAX_THREADS ? ORC_MAX_THREADS : nthreads);
+    if (nt > slow_extent(c)) nt = (int)slow_extent(c);
+    double L[3] = {c->n[0] * c->d[0], c->n[1] * c->d[1], c->n[2] * c->d[2]};
+    mt_ctx m;
+    memset(&m, 0, sizeof m);
+    m.s = s;
+    long long cap = s->cap > 0 ? s->cap : 1;
+    m.x0 = (double*)malloc((size_t)cap * sizeof(double));
+    m.y0 = (double*)malloc((size_t)cap * sizeof(double));
+    m.z0 = (double*)malloc((size_t)cap * sizeof(double));
+    m.vz = (double*)malloc((size_t)cap * sizeof(double));
+    m.qw = (double*)malloc((size_t)cap * sizeof(double));
+    for (int a = 0; a < 3; a++) m.Bold[a] = (double*)malloc((size_t)s->ncell * sizeof(double));
+    int rc = 0;
+    if (!m.x0 || !m.y0 || !m.z0 || !m.vz || !m.qw || !m.Bold[0] || !m.Bold[1] || !m.Bold[2])
+        rc = -4;
+    for (int it = 0; it < nsteps && rc == 0; it++) {
+        par_run(nt, mt_zero_j, &m);
+        par_run(nt, mt_push, &m);
+        m.bad = 0;
+        par_run(nt, mt_deposit, &m);
+        if (m.bad) rc = -2;
+        /* particle boundaries: as in orc_step */
+        unsigned char* keep = (unsigned char*)malloc((size_t)(s->np > 0 ? s->np : 1));
+        for (long long p = 0; p < s->np; p++) {
+            keep[p] = 1;
+            if (c->window)
+                keep[p] = s->x[p] >= 0.0 && s->x[p] < L[0];
+            else
+                wrap_pos(&s->x[p], L[0]);
+            wrap_pos(&s->y[p], L[1]);
+            if (c->dims == 3) wrap_pos(&s->z[p], L[2]);
+        }
+        compact(s, keep);
+        free(keep);
+        par_run(nt, mt_yee_e, &m);
+        par_run(nt, mt_yee_b, &m);
+        par_run(nt, mt_average, &m);
+        s->step++;
+        if (c->window && orc_shift_count(c, s->step) > orc_shift_count(c, s->step - 1))
+            if (window_shift(s)) rc = -3;
+    }
+    free(m.x0), free(m.y0), free(m.z0), free(m.vz), free(m.qw);
+    for (int a = 0; a < 3; a++) free(m.Bold[a]);
     return rc;
 }
 

@@ -112,6 +112,12 @@ int orc_get_fields(const orc_sim* s, double* out12);
  * density at the time of the call. */
 int orc_set_rho_bg(orc_sim* s, const double* rho_bg);
 int orc_step(orc_sim* s, int nsteps);
+/* The same steps on up to `nthreads` host threads, with results identical bit for bit
+ * to orc_step: particles are pushed in parallel, and each thread deposits every
+ * particle's current (in particle order) into its own band of rows of J only, so each
+ * element of J sums the same terms in the same order. Returns as orc_step (-4 if a
+ * host allocation fails). */
+int orc_step_mt(orc_sim* s, int nsteps, int nthreads);
 long long orc_steps_done(const orc_sim* s);
 long long orc_shifts_done(const orc_sim* s);
 /* {W_E, W_B, W_kin} at integer time (B^n for W_B). */
