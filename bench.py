@@ -4,8 +4,13 @@
 One "step" is one pass of the whole hot path (work-queue build, particle
 interpolation + Boris push + Esirkepov deposition, window injection, particle
 exchange, Yee E and B) over the 2048 x 512-cell LWFA window: 4 particles per cell,
-window full of plasma (4 194 304 particles), a0 = 4 Gaussian laser. Prints one JSON
-line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+a0 = 4 Gaussian laser focused at the foot of a density ramp. The run starts from that
+initial condition (plasma from the pulse centre, 1 048 576 particles) and is developed
+for 1800 untimed steps: the window is then full of plasma (4.2M particles) and the
+wake has formed, so the timed steps see the uneven patch loads of the configured
+2000-step run. Prints one JSON line (rank 0), with a bounded served parameter-scan
+sample (p50/p99 time to completion, aggregate pushes/s). `--impl reference` times the
+FP64 CPU oracle instead.
 
 Timing: W untimed warm-up steps, then K steps between CUDA events on the sim's
 stream with a synchronize (and a barrier under torchrun) on both sides; the
@@ -49,36 +54,38 @@ FLOPS_PER_PUSH_3D = 742
 DTYPE = {"fp64": "f64", "fp32": "f32", "df64": "f32x2 (double-word, ~48-bit)"}
 
 
-def bytes_per_push(dt, w):
+def _ppc(w, n):
+    p = w["params"]
+    n = len(w["particles"]["x"]) if n is None else n
+    return n / float(np.prod(p["n"][:p["dims"]]))
+
+
+def bytes_per_push(dt, w, n=None):
     """Algorithmic HBM bytes of the particle kernel per push: particle state read and
     written once, weight read once; E and B^n read once and J (FP64) written once per
-    cell, shared by the particles per cell. dt: "fp64", "fp32" or "df64"."""
-    p = w["params"]
-    dims = p["dims"]
+    cell, shared by the particles per cell (n particles on the grid: the timed state's
+    count; the workload's when None). dt: "fp64", "fp32" or "df64"."""
+    dims = w["params"]["dims"]
     es = 4 if dt == "fp32" else 8
     pos = dims * es + (0 if dt == "fp64" else 4)
-    ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
-    return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / ppc
+    return 2 * (pos + 3 * es) + es + (6 * es + 3 * 8) / _ppc(w, n)
 
 
-def step_bytes_per_push(dt, w):
+def step_bytes_per_push(dt, w, n=None):
     """Algorithmic HBM bytes of a whole step per push: the particle kernel's bytes plus,
     per cell and shared by its particles, the field update's (E, B and the FP64 J read,
     E and B written, the next J zeroed)."""
-    p = w["params"]
-    dims = p["dims"]
     es = 4 if dt == "fp32" else 8
-    ppc = len(w["particles"]["x"]) / float(np.prod(p["n"][:dims]))
-    return bytes_per_push(dt, w) + (6 * es + 3 * 8 + 6 * es + 3 * 8) / ppc
+    return bytes_per_push(dt, w, n) + (6 * es + 3 * 8 + 6 * es + 3 * 8) / _ppc(w, n)
 
 
-def step_roofline(dt, w, pushes_per_s):
+def step_roofline(dt, w, pushes_per_s, n=None):
     """The whole step's algorithmic bytes per second against the measured HBM peak."""
     hbm = measured_peaks().get("hbm_gbs")
-    achieved = step_bytes_per_push(dt, w) * pushes_per_s / 1e9
+    achieved = step_bytes_per_push(dt, w, n) * pushes_per_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if hbm else None,
-            "bytes_per_push": step_bytes_per_push(dt, w)}
+            "bytes_per_push": step_bytes_per_push(dt, w, n)}
 # kernels per step: queue build, push, [window injection], exchange, repack plan and its
 # two copy kernels (which return at once unless a patch needs room), Yee E, Yee B, end
 def kernels_per_step(window: bool, merge: bool = False) -> int:
@@ -118,6 +125,17 @@ def parse():
     ap.add_argument("--maxwell-order", type=int, default=2, choices=[2, 6],
                     help="field solver: 2 = Yee, 6 = sixth-order staggered differences "
                          "(time step 0.76 of Yee's limit instead of 0.95)")
+    ap.add_argument("--lwfa-start", default="ramp", choices=["ramp", "full"],
+                    help="lwfa: ramp = the configured initial condition (plasma from the "
+                         "pulse centre); full = the window already full of plasma")
+    ap.add_argument("--develop", type=int, default=-1,
+                    help="untimed steps before the warm-up (-1: 1800 for the lwfa ramp "
+                         "start, when the window is full of plasma and the wake has formed; "
+                         "0 otherwise)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the bounded serving sample in the default line (0: off)")
+    ap.add_argument("--serve-rate", type=float, default=8.0,
+                    help="mean arrivals per second of the serving sample")
     ap.add_argument("--no-variant", action="store_true", help="skip the other precision")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -129,9 +147,29 @@ def parse():
     return ap.parse_args()
 
 
-def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20, order=2):
+def develop_steps(args):
+    """Untimed steps that bring the workload to the state the timed steps measure."""
+    if args.develop >= 0:
+        return args.develop
+    return 1800 if args.workload == "lwfa" and args.lwfa_start == "ramp" else 0
+
+
+def capacity_for(w):
+    """Particle slots of a sim: three times the largest count the run reaches (the
+    window full of plasma for LWFA), twice the count for 3D."""
+    p = w["params"]
+    n = len(w["particles"]["x"])
+    if p["dims"] == 2 and p.get("window"):
+        full = p["n"][0] * p["n"][1] * p["inject_ppc"][0] * p["inject_ppc"][1]
+        return 3 * max(n, full)
+    return 3 * n if p["dims"] == 2 else 2 * n
+
+
+def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20, order=2, start="full"):
     """The synthetic workload; with the sixth-order solver the time step is 0.76 of
-    Yee's limit (the sixth-order scheme is stable below 120/149 = 0.805 of it)."""
+    Yee's limit (the sixth-order scheme is stable below 120/149 = 0.805 of it).
+    LWFA `start`: "ramp" = the configured initial condition (plasma from the pulse
+    centre, ramp of 64 cells), "full" = the window already full of plasma."""
     from paper_1511_03878_gb300 import inputs
 
     cfl = 0.76 if order == 6 else 0.95
@@ -144,6 +182,8 @@ def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20, order=2):
     elif kind == "lwfa3d":
         # 512x128x128 window full of plasma, 2 particles per cell (16 777 216)
         w = inputs.lwfa3d(ramp_x0=-8.0, ppc=(2, 1, 1), cfl=cfl)
+    elif start == "ramp":
+        w = inputs.lwfa2d(nx=nx, ny=ny, cfl=cfl)
     else:
         # the window full of plasma: density ramp placed before x = 0
         w = inputs.lwfa2d(nx=nx, ny=ny, ramp_x0=-8.0, cfl=cfl)
@@ -323,11 +363,9 @@ def trace_run(args, w, precision, chunk):
     from paper_1511_03878_gb300 import binding
 
     prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
-    n = len(w["particles"]["x"])
-    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
-    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping,
-                      merge_above=args.merge_above, merge_dp=args.merge_dp)
+    sim = binding.Sim(w["params"], precision=prec, capacity=capacity_for(w), chunk=chunk,
+                      mapping=mapping, merge_above=args.merge_above, merge_dp=args.merge_dp)
     rows = []
     try:
         sim.load(w)
@@ -352,23 +390,36 @@ def trace_run(args, w, precision, chunk):
             "rows": rows}
 
 
-def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
-    """Returns timing + roofline of one precision on this rank's GPU."""
+def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0, snapshot=False):
+    """Returns timing + roofline of one precision on this rank's GPU (and, with
+    `snapshot`, the developed state as a host workload for the end-to-end run)."""
     import torch
 
     from paper_1511_03878_gb300 import binding
 
     prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
-    n = len(w["particles"]["x"])
-    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
+    cap = capacity_for(w)
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
     sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping,
                       merge_above=args.merge_above, merge_dp=args.merge_dp)
     sim.load(w)
     counts0 = sim.patch_counts()
     stream = sim.stream
+    dev = develop_steps(args)
+    if dev > 0:
+        sim.step(dev)  # untimed: the run up to the state the timed steps measure
+        sim.sync()
+    counts_dev = sim.patch_counts().astype(np.float64)
+    state = None
+    if snapshot:
+        # the developed state on the host, for the end-to-end measurement (x in the window
+        # frame, B at the half step as the loader takes it)
+        q = sim.particles()
+        f = sim.fields()
+        state = dict(w, particles=q, E=[f["Ex"], f["Ey"], f["Ez"]], B=[f["Bx"], f["By"], f["Bz"]])
     sim.step(W)
     sim.sync()
+    counts_t0 = sim.patch_counts().astype(np.float64)
     n0 = sim.num_particles()
     if clocks:
         clocks.start()
@@ -405,10 +456,10 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
                 "kernel": f"push{dims}d_kernel<double>",
                 "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit counts x clock)",
-                "hbm_frac_of_measured": (bytes_per_push(dt, w) * n_push / (push_ms * 1e-3) / 1e9
-                                         / hbm) if hbm else None}
+                "hbm_frac_of_measured": (bytes_per_push(dt, w, n_push) * n_push
+                                         / (push_ms * 1e-3) / 1e9 / hbm) if hbm else None}
     else:
-        achieved = bytes_per_push(dt, w) * n_push / (push_ms * 1e-3) / 1e9
+        achieved = bytes_per_push(dt, w, n_push) * n_push / (push_ms * 1e-3) / 1e9
         peak = hbm if hbm else 6800.0
         tname = "float" if precision == "fp32" else "df64"
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -424,7 +475,12 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0):
                               "(profiles/traffic.md)" if roof["traffic"] is not None else
                               "no capture of the current kernel sources in this layout")
     out = dict(ms=ms, pushes=pushes, pushes_all=pushes_all, n=n_push, profile={k: v / K for k, v in prof.items()},
-               roofline=roof, push_ms=push_ms, repacks=repacks)
+               roofline=roof, push_ms=push_ms, repacks=repacks, state=state,
+               timed_state={"developed_steps": dev, "steps_before_timing": dev + W,
+                            "particles": int(counts_t0.sum()),
+                            "max_over_mean_patch": float(counts_t0.max() / counts_t0.mean()),
+                            "max_over_mean_patch_at_load": float(counts0.max() / counts0.mean()),
+                            "max_patch": int(counts_t0.max())})
     if args.merge_above > 0:
         counts1 = sim.patch_counts()
         out["merge"] = {"above": args.merge_above, "dp": args.merge_dp,
@@ -443,15 +499,15 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     """Same metric through the public C ABI with host buffers, all inside the timed
     region: load the particles and fields from pinned host arrays (H2D), then K steps,
     each followed by a read of its step record (step count and window shifts, 24 bytes
-    D2H, which waits for the step), and at the end the energy and the axis wake field."""
+    D2H, which waits for the step), and at the end the energy and the axis wake field.
+    `w` is the state the device-timed steps start from (the developed run)."""
     import torch
 
     from paper_1511_03878_gb300 import binding
 
     prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
     n = len(w["particles"]["x"])
-    cap = 3 * n if w["params"]["dims"] == 2 else 2 * n
-    sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk)
+    sim = binding.Sim(w["params"], precision=prec, capacity=capacity_for(w), chunk=chunk)
     # the inputs sit in page-locked host memory, as a serving process would keep them
     keep = []
 
@@ -514,12 +570,15 @@ def oracle_sample(args, frac):
     columns shrink with it), or every k-th particle of the same grid (thermal, 3D
     stress). Returns the workload and a description of the cut."""
     order = args.maxwell_order
-    w = workload(args.nx, args.ny, args.workload, args.total, order)
+    # LWFA: the window full of plasma, the particle count of the developed state the GPU
+    # steps are timed on (the oracle cannot be developed 1800 steps in a bounded sample)
+    w = workload(args.nx, args.ny, args.workload, args.total, order, start="full")
     if frac >= 1.0:
-        return w, "the full workload"
+        return w, "the full workload (window full of plasma)"
     if args.workload == "lwfa":
         ny = max(32, int(args.ny * frac) // 32 * 32)
-        return workload(args.nx, ny, "lwfa", order=order), f"{args.nx}x{ny} rows of the window"
+        return (workload(args.nx, ny, "lwfa", order=order, start="full"),
+                f"{args.nx}x{ny} rows of the window full of plasma")
     if args.workload == "lwfa3d":
         from paper_1511_03878_gb300 import inputs
 
@@ -534,14 +593,15 @@ def oracle_sample(args, frac):
     return w, f"one particle in {k} on the same grid"
 
 
-def oracle_rate(args, n_full, seconds_budget, max_steps=50):
-    """Pushes/s of the FP64 CPU oracle (single thread, as it stands) on a bounded
-    number of steps of the same workload (at most 5M particles of it)."""
+def oracle_rate(args, n_full, seconds_budget, max_steps=50, threads=1):
+    """Pushes/s of the FP64 CPU oracle (as it stands: its plain step on one thread, or
+    its threaded step, identical bit for bit, on `threads`) on a bounded number of
+    steps of the same workload (at most 5M particles of it)."""
     w, what = oracle_sample(args, min(1.0, 5e6 / n_full))
     n = len(w["particles"]["x"])
     o = oracle_sim(w, max_steps)
     t0 = time.perf_counter()
-    o.step(1)
+    o.step(1, threads=threads)
     t1 = time.perf_counter()
     steps = 1
     budget_steps = int(max(0, min(max_steps - 1, seconds_budget / max(t1 - t0, 1e-6) - 1)))
@@ -549,7 +609,7 @@ def oracle_rate(args, n_full, seconds_budget, max_steps=50):
     if budget_steps > 0:
         n1 = o.num_particles()
         t2 = time.perf_counter()
-        o.step(budget_steps)
+        o.step(budget_steps, threads=threads)
         t3 = time.perf_counter()
         steps += budget_steps
         pushes += n1 * budget_steps
@@ -564,8 +624,9 @@ def reference_arm(args):
     import oracle as orc
 
     orc.build()
+    threads = os.cpu_count() or 1
     n_full = len(workload(args.nx, args.ny, args.workload, args.total,
-                          args.maxwell_order)["particles"]["x"])
+                          args.maxwell_order, start="full")["particles"]["x"])
     total = args.steps + args.warmup
     # each step is a bounded sample: a cut of the same workload (at most 5M particles,
     # fewer if K+W steps would exceed about three minutes), timed after one probe step
@@ -573,7 +634,7 @@ def reference_arm(args):
     w, what = oracle_sample(args, frac)
     o = oracle_sim(w, total)
     t0 = time.perf_counter()
-    o.step(1)
+    o.step(1, threads=threads)
     t_step = time.perf_counter() - t0
     done = 1
     need = min(1.0, 180.0 / max(total * t_step, 1e-9))
@@ -582,10 +643,10 @@ def reference_arm(args):
         o = oracle_sim(w, total)
         done = 0
     n = len(w["particles"]["x"])
-    o.step(max(0, args.warmup - done))
+    o.step(max(0, args.warmup - done), threads=threads)
     n0 = o.num_particles()
     t0 = time.perf_counter()
-    o.step(args.steps)
+    o.step(args.steps, threads=threads)
     el = time.perf_counter() - t0
     n1 = o.num_particles()
     value = args.steps * 0.5 * (n0 + n1) / el
@@ -596,8 +657,9 @@ def reference_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded, shaped like the paper's runs)",
         "config": config_dict(args, "fp64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 C oracle, single thread, {what} of {name} "
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"FP64 C oracle, threaded step (bit-identical to the plain "
+                                   f"one) on {threads} host threads, {what} of {name} "
                                    f"({n} particles), {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -615,6 +677,12 @@ def config_dict(args, precision):
     elif args.workload == "thermal":
         base = {"workload": "thermal2d-128x128-ppc16", "grid": [128, 128], "dx": 0.1,
                 "particles_per_cell": 16}
+    elif args.lwfa_start == "ramp":
+        dev = develop_steps(args)
+        base = {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-from-step{dev}",
+                "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
+                "laser_a0": 4.0, "initial_condition": "plasma from the pulse centre, "
+                "64-cell ramp (the configured 2000-step run)", "timed_from_step": dev}
     else:
         base = {"workload": f"lwfa2d-{args.nx}x{args.ny}-ppc4-fullwindow",
                 "grid": [args.nx, args.ny], "dx": 0.125, "dy": 0.5, "particles_per_cell": 4,
@@ -739,6 +807,28 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_sample(args, main_run):
+    """A bounded, saturated sample of the served parameter scan (the metric's second
+    half): `--serve-requests` requests of the scan distribution arriving at
+    `--serve-rate` per second, FP32, admitted by HBM budget and stepped together with
+    continuous batching. Returns p50/p99 time to completion, the aggregate pushes/s and
+    the ratio to the FP64 single-simulation rate measured above."""
+    from paper_1511_03878_gb300 import serve
+
+    reqs = serve.scan_requests(n=args.serve_requests, rate=args.serve_rate, seed=1517)
+    serve.Server(budget_bytes=8 << 30).run([serve.Request(rid=0, nx=256, ny=128, a0=3.0,
+                                                          n0=0.01, ppc=2, steps=20)])
+    srv = serve.Server(budget_bytes=int(args.budget_gb * (1 << 30)), quantum=25)
+    res = srv.run(reqs)
+    summ = serve.summarize(res)
+    fp64 = main_run["pushes"] / (main_run["ms"] * 1e-3) if args.precision == "fp64" else None
+    return {**summ, "max_resident": srv.max_resident, "precision": "fp32",
+            "rate_per_s": args.serve_rate, "budget_gb": args.budget_gb,
+            "distribution": "grids {256x128, 512x256, 1024x256, 2048x512}, a0 U[2,6], "
+                            "n0 U[0.003,0.02] n_c, ppc {1,2,4,8}, 500-2000 steps, seed 1517",
+            "served_over_fp64_single": (summ["aggregate_pushes_per_s"] / fp64) if fp64 else None}
+
+
 def serve_arm(args):
     """Served parameter scan: Poisson arrivals, HBM-budget admission, continuous
     batching; value = aggregate pushes/s, with p50/p99 time-to-completion."""
@@ -816,27 +906,44 @@ def main():
     if rank != 0:
         __graft_entry__.build()
 
-    w = workload(args.nx, args.ny, args.workload, args.total, args.maxwell_order)
+    w = workload(args.nx, args.ny, args.workload, args.total, args.maxwell_order,
+                 start=args.lwfa_start)
+    # layouts are tuned on the window full of plasma (the grid and particle count of the
+    # developed state) and applied to the run from its initial condition
+    wt = workload(args.nx, args.ny, args.workload, args.total, args.maxwell_order, start="full")
     clocks = ClockSampler(local)
     others = [] if args.no_variant or args.variants == "none" else [
         v for v in args.variants.split(",") if v and v != args.precision]
-    layouts = {v: launch_layout(args, w, v) for v in [args.precision] + others}
+    layouts = {}
+    for v in [args.precision] + others:
+        wl, ch, rec = launch_layout(args, wt, v)
+        layouts[v] = (dict(w, params=dict(w["params"], patch=wl["params"]["patch"])), ch, rec)
     wm, chunk_m, _ = layouts[args.precision]
-    main_run = run_gpu(args, wm, args.precision, args.steps, args.warmup, world, clocks, chunk_m)
+    main_run = run_gpu(args, wm, args.precision, args.steps, args.warmup, world, clocks, chunk_m,
+                       snapshot=not args.no_e2e)
     variants = {v: run_gpu(args, layouts[v][0], v, args.steps, args.warmup, world,
                            chunk=layouts[v][1]) for v in others}
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, wm, args.precision, args.steps, chunk_m, world)
+        e2e = run_e2e(args, main_run["state"] or wm, args.precision, args.steps, chunk_m, world)
+    main_run["state"] = None
     trace = None
     if rank == 0 and args.trace_steps > 0:
         trace = trace_run(args, wm, args.precision, chunk_m)
+    serving = None
+    if rank == 0 and args.serve_requests > 0 and args.workload == "lwfa" and world == 1:
+        serving = serve_sample(args, main_run)
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        rate, steps, n, what = oracle_rate(args, len(w["particles"]["x"]), args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, single thread, {steps} steps of {what} of "
-                         f"{config_dict(args, 'fp64')['workload']} ({n} particles)"}
+        n_full = len(wt["particles"]["x"])
+        threads = os.cpu_count() or 1
+        rate, steps, n, what = oracle_rate(args, n_full, args.cpu_seconds, threads=threads)
+        rate1, steps1, _, _ = oracle_rate(args, n_full, args.cpu_seconds / 2, max_steps=10)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 C oracle, threaded step (bit-identical to the plain one) on "
+                         f"{threads} host threads, {steps} steps of {what} of "
+                         f"{config_dict(args, 'fp64')['workload']} ({n} particles)",
+               "single_thread": {"value": rate1, "cores": 1, "steps": steps1}}
     if rank != 0:
         return
     value = job_value(main_run["pushes_all"], main_run["ms"])
@@ -850,7 +957,7 @@ def main():
         "config": config_dict(args, args.precision),
         "launch": layouts[args.precision][2],
         "roofline": main_run["roofline"],
-        "roofline_step": step_roofline(args.precision, wm, value),
+        "roofline_step": step_roofline(args.precision, wm, value, main_run["n"]),
         "cpu_baseline": cpu,
         "e2e": ({"value": e2e["value"], "unit": UNIT,
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
@@ -860,8 +967,11 @@ def main():
         "clocks": clocks.summary(),
         "kernel_ms_per_step": main_run["profile"],
         "particles": main_run["n"],
+        "timed_state": main_run["timed_state"],
         "capacity_repacks": main_run["repacks"],
     }
+    if serving is not None:
+        line["serving"] = serving
     if "merge" in main_run:
         line["merge"] = main_run["merge"]
     if trace is not None:
@@ -871,7 +981,7 @@ def main():
             "value": job_value(r["pushes_all"], r["ms"]),
             "ms_per_step": r["ms"] / args.steps, "roofline": r["roofline"],
             "roofline_step": step_roofline(v, layouts[v][0],
-                                           job_value(r["pushes_all"], r["ms"])),
+                                           job_value(r["pushes_all"], r["ms"]), r["n"]),
             "kernel_ms_per_step": r["profile"], "dtype": DTYPE[v],
             "capacity_repacks": r["repacks"],
             "launch": layouts[v][2]} for v, r in variants.items()}

@@ -56,3 +56,24 @@ def test_algorithmic_bytes_per_push():
     assert bench.bytes_per_push("fp32", w) == 2 * (12 + 12) + 4 + (24 + 24) / 4
     assert bench.step_bytes_per_push("fp32", w) == 88.0
     assert bench.step_bytes_per_push("fp64", w) == 142.0
+
+
+def test_lwfa_line_is_timed_on_the_developed_run():
+    """The default LWFA line starts from the configured initial condition (plasma from
+    the pulse centre) and develops it 1800 steps before timing; its capacity covers the
+    window full of plasma; the workload name says where the timing starts."""
+    from paper_1511_03878_gb300 import inputs
+
+    a = _args(lwfa_start="ramp", develop=-1, gpus=1)
+    assert bench.develop_steps(a) == 1800
+    assert bench.develop_steps(_args(lwfa_start="full", develop=-1)) == 0
+    assert bench.develop_steps(_args(workload="stress3d", lwfa_start="ramp", develop=-1)) == 0
+    assert bench.develop_steps(_args(lwfa_start="ramp", develop=5)) == 5
+    assert bench.config_dict(a, "fp64")["workload"] == "lwfa2d-2048x512-ppc4-from-step1800"
+    w = bench.workload(2048, 32, "lwfa", start="ramp")
+    full = 2048 * 32 * 4
+    assert len(w["particles"]["x"]) < full / 2  # plasma from the pulse centre only
+    assert bench.capacity_for(w) == 3 * full
+    wf = bench.workload(2048, 32, "lwfa", start="full")
+    assert len(wf["particles"]["x"]) == full
+    assert w["params"]["ramp_x0"] == inputs.lwfa2d(nx=2048, ny=32)["params"]["ramp_x0"]
