@@ -1,0 +1,194 @@
+// 2^62 fixed-point arithmetic for the FP64 particle kernels.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate, while its integer units run at half the
+// FP32 rate, so an FP64 particle kernel is bound by the FP64 pipe. Every quantity of the
+// order-2 PIC cycle that is not itself a physical result of FP64 arithmetic -- a
+// particle's in-cell offset, its quadratic B-spline weights, the Esirkepov shape
+// differences, path-averaged weights and running sums, and the products that form a
+// current contribution -- is computed here exactly or to 2^-62 in int64 / 128-bit
+// integer arithmetic. That is finer than FP64 rounding for values in [-1, 1] (2^-53
+// relative, 2^-54 absolute near 1), so the FP64 results built from them (fields at the
+// particle, current) agree with an all-FP64 evaluation to rounding.
+#pragma once
+#include <stdint.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr long long kOne62 = 1LL << 62;
+constexpr long long kHalf62 = 1LL << 61;
+// round(2^62 / 3): the 1/3 of the path-averaged weight of Esirkepov's transverse current
+constexpr long long kThird62 = 1537228672809129301LL;
+
+// floor(x) and the fractional part x - floor(x) in 2^62 fixed point ([0, 2^62)), from the
+// bit pattern of x with integer operations only. Exact for |x| < 2^30 (a fraction below
+// 2^-62 is truncated). Non-finite or larger |x| give i = -2^30, f = 0 (outside any grid).
+__device__ __forceinline__ void split62(double x, int& i, long long& f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7FFu);
+    const int e = eb - 1023;  // unbiased exponent
+    if (eb == 0) {            // zero or subnormal: below the 2^-62 resolution
+        i = 0;
+        f = 0;
+        return;
+    }
+    if (e >= 30) {
+        i = -(1 << 30);
+        f = 0;
+        return;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);  // x = m 2^(e-52)
+    unsigned long long ip, fr;
+    if (e < -10) {
+        ip = 0;
+        const int s = -(e + 10);
+        fr = s < 64 ? (m >> s) : 0;
+    } else if (e < 0) {
+        ip = 0;
+        fr = m << (e + 10);  // below 2^62
+    } else {
+        ip = m >> (52 - e);
+        fr = (m << (e + 10)) & (unsigned long long)(kOne62 - 1);
+    }
+    if (b >> 63) {  // negative: floor is -(ip + 1) unless x is an integer
+        if (fr == 0) {
+            i = -(int)ip;
+            f = 0;
+        } else {
+            i = -(int)ip - 1;
+            f = kOne62 - (long long)fr;
+        }
+    } else {
+        i = (int)ip;
+        f = (long long)fr;
+    }
+}
+
+// Quadratic B-spline weights of nodes (i-1, i, i+1) for delta = D 2^-62 in [-1/2, 1/2]
+// (S[k] in 2^62 fixed point): S0 = (1/2 - delta)^2 / 2, S1 = 3/4 - delta^2,
+// S2 = (1/2 + delta)^2 / 2, written as q -/+ delta/2 with q = delta^2/2 + 1/8.
+__device__ __forceinline__ void shape62(long long D, long long S[3]) {
+    const unsigned long long a = (unsigned long long)(D < 0 ? -D : D);  // <= 2^61
+    const unsigned long long hi = __umul64hi(a, a);
+    const unsigned long long lo = a * a;
+    const long long d2 = (long long)((hi << 2) | (lo >> 62));  // delta^2 2^62 <= 2^60
+    const long long h = D >> 1;                                 // delta/2
+    const long long q = (d2 >> 1) + (1LL << 59);                // delta^2/2 + 1/8
+    S[0] = q - h;
+    S[1] = 3LL * (1LL << 60) - d2;
+    S[2] = q + h;
+}
+
+// 2D Esirkepov deposition in fixed point when the particle keeps its nearest nodes on
+// both axes: DS lives on stencil nodes 1..3, the running sums have two non-zero
+// entries (their sum over the three nodes is zero), 6 + 6 + 9 tile atomics, the three
+// rows in a rolled loop (a smaller body: fewer instruction-fetch stalls). Q* are the
+// charge factors (tile scale 2^k included) as integers; S0*, S1* old and new shapes.
+__device__ __forceinline__ void deposit2d_fast_fix(long long* jx, long long* jy, long long* jz,
+                                                   int JX, const long long S0x[3],
+                                                   const long long S0y[3], const long long S1x[3],
+                                                   const long long S1y[3], long long QX,
+                                                   long long QY, long long QZ) {
+    long long A[3], B[3], WY[3], WX[3], WZ[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        A[k] = S1x[k] - S0x[k];
+        B[k] = S1y[k] - S0y[k];
+        WY[k] = S0y[k] + (B[k] >> 1);                     // S0y + DSy/2
+        WX[k] = S0x[k] + (A[k] >> 1);                     // S0x + DSx/2
+        WZ[k] = (S0y[k] >> 1) + fixmul62(B[k], kThird62);  // S0y/2 + DSy/3
+    }
+    const long long CX1 = fixmul62(QX, A[0]), CX2 = fixmul62(QX, A[0] + A[1]);
+    const long long CY1 = fixmul62(QY, B[0]), CY2 = fixmul62(QY, B[0] + B[1]);
+    // rows l = 0..2 (their weights rotating through registers):
+    // Wz = S0x (S0y + DSy/2) + DSx (S0y/2 + DSy/3)
+    long long wy0 = WY[0], wy1 = WY[1], wy2 = WY[2], wz0 = WZ[0], wz1 = WZ[1], wz2 = WZ[2];
+#pragma unroll 1
+    for (int l = 0; l < 3; l++) {
+        jatomic(jx + l * JX + 0, fixmul62(CX1, wy0));
+        jatomic(jx + l * JX + 1, fixmul62(CX2, wy0));
+        const long long QWY = fixmul62(QZ, wy0), QWZ = fixmul62(QZ, wz0);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            jatomic(jz + l * JX + k, fixmul62(QWY, S0x[k]) + fixmul62(QWZ, A[k]));
+        wy0 = wy1, wy1 = wy2, wz0 = wz1, wz1 = wz2;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        jatomic(jy + 0 * JX + k, fixmul62(CY1, WX[k]));
+        jatomic(jy + 1 * JX + k, fixmul62(CY2, WX[k]));
+    }
+}
+
+// Esirkepov data of one axis on a four-node window that always holds both the old and
+// the new support (the window starts one node before min(old node, new node)), in 2^62
+// fixed point; `start` = window start minus (old node - 2): 0 or 1.
+__device__ __forceinline__ void esirkepov_axis4_fix(const long long s0[3], const long long s1[3],
+                                                    int shift, Axis4<long long>& a) {
+    const bool m = shift < 0, p = shift > 0;
+    a.S0[0] = m ? 0 : s0[0];
+    a.S0[1] = m ? s0[0] : s0[1];
+    a.S0[2] = m ? s0[1] : s0[2];
+    a.S0[3] = m ? s0[2] : 0;
+    a.DS[0] = (p ? 0 : s1[0]) - a.S0[0];
+    a.DS[1] = (p ? s1[0] : s1[1]) - a.S0[1];
+    a.DS[2] = (p ? s1[1] : s1[2]) - a.S0[2];
+    a.DS[3] = (p ? s1[2] : 0) - a.S0[3];
+    a.start = m ? 0 : 1;
+}
+
+// General 2D Esirkepov deposition in fixed point (any shift in {-1, 0, 1} per axis) on a
+// fixed four-node window per axis: running sums of three entries along each axis (the
+// fourth is zero), 12 + 16 + 12 tile atomics, no per-node predicates, and rolled row
+// and column loops whose weights rotate through registers (a compact body: the
+// cell-crossing path is taken by many warps once a wake forms, and an unrolled body
+// stalls them on instruction fetch). `jx/jy/jz` point at stencil node (0, 0) of the
+// five-node numbering (old node - 2 on both axes).
+__device__ __forceinline__ void deposit2d_general_fix(long long* jx, long long* jy, long long* jz,
+                                                      int JX, const long long S0x[3],
+                                                      const long long S0y[3],
+                                                      const long long S1x[3],
+                                                      const long long S1y[3], int sx, int sy,
+                                                      long long QX, long long QY, long long QZ) {
+    Axis4<long long> ax, ay;
+    esirkepov_axis4_fix(S0x, S1x, sx, ax);
+    esirkepov_axis4_fix(S0y, S1y, sy, ay);
+    const int o = ay.start * JX + ax.start;
+    const long long cx1 = fixmul62(QX, ax.DS[0]), cx2 = fixmul62(QX, ax.DS[0] + ax.DS[1]),
+                    cx3 = fixmul62(QX, ax.DS[0] + ax.DS[1] + ax.DS[2]);
+    const long long cy1 = fixmul62(QY, ay.DS[0]), cy2 = fixmul62(QY, ay.DS[0] + ay.DS[1]),
+                    cy3 = fixmul62(QY, ay.DS[0] + ay.DS[1] + ay.DS[2]);
+    // per-row weights S0y + DSy/2 and S0y/2 + DSy/3, rotating through registers
+    long long wy0 = ay.S0[0] + (ay.DS[0] >> 1), wy1 = ay.S0[1] + (ay.DS[1] >> 1),
+              wy2 = ay.S0[2] + (ay.DS[2] >> 1), wy3 = ay.S0[3] + (ay.DS[3] >> 1);
+    long long wz0 = ay.S0[0] >> 1, wz1 = ay.S0[1] >> 1, wz2 = ay.S0[2] >> 1, wz3 = ay.S0[3] >> 1;
+#pragma unroll 1
+    for (int l = 0; l < 4; l++) {
+        const long long wz = wz0 + fixmul62(ay.DS[0], kThird62);
+        long long* rx = jx + o + l * JX;
+        jatomic(rx + 0, fixmul62(cx1, wy0));
+        jatomic(rx + 1, fixmul62(cx2, wy0));
+        jatomic(rx + 2, fixmul62(cx3, wy0));
+        const long long qwy = fixmul62(QZ, wy0), qwz = fixmul62(QZ, wz);
+        long long* rz = jz + o + l * JX;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            jatomic(rz + k, fixmul62(qwy, ax.S0[k]) + fixmul62(qwz, ax.DS[k]));
+        wy0 = wy1, wy1 = wy2, wy2 = wy3;
+        wz0 = wz1, wz1 = wz2, wz2 = wz3;
+        ay.DS[0] = ay.DS[1], ay.DS[1] = ay.DS[2], ay.DS[2] = ay.DS[3];
+    }
+    long long wx0 = ax.S0[0] + (ax.DS[0] >> 1), wx1 = ax.S0[1] + (ax.DS[1] >> 1),
+              wx2 = ax.S0[2] + (ax.DS[2] >> 1), wx3 = ax.S0[3] + (ax.DS[3] >> 1);
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+        long long* cy = jy + o + k;
+        jatomic(cy + 0 * JX, fixmul62(cy1, wx0));
+        jatomic(cy + 1 * JX, fixmul62(cy2, wx0));
+        jatomic(cy + 2 * JX, fixmul62(cy3, wx0));
+        wx0 = wx1, wx1 = wx2, wx2 = wx3;
+    }
+}
+
+}  // namespace pic

@@ -6,6 +6,7 @@
 // persistent CTAs, so no CTA idles while dense patches are pushed.
 #include <cuda_runtime.h>
 
+#include "fix62.cuh"
 #include "pic_device.cuh"
 #include "pic_internal.h"
 
@@ -409,197 +410,315 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             const bool valid = k < cnt;
             const int slot = base + (valid ? k : 0);
 
-            // ---- A. take the prefetched state, start loading the next one
-            int ix = 0, iy = 0;
-            T fx = T(0), fy = T(0);
-            double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
-            T u[3] = {nu0, nu1, nu2};
-            T w = nw;
-            if (valid) {
-                if constexpr (is_f64<T>::value) {
-                    xi0 = nx0;
-                    eta0 = ny0;
-                    ix = floor_to_int(xi0);
-                    iy = floor_to_int(eta0);
-                    // floors widened back with integer operations (exact)
-                    fx = xi0 - fixed_to_f64(ix, 0);
-                    fy = eta0 - fixed_to_f64(iy, 0);
-                } else {
-                    ix = nc & 0xFFFF;
-                    iy = (nc >> 16) & 0xFFFF;
-                    fx = nfx;
-                    fy = nfy;
+            bool ok = false, leave = false;
+            int dest = patch;
+            if constexpr (std::is_same<T, double>::value) {
+                // ---- FP64: in-cell offsets, shapes and every deposit weight, running sum and
+                // tap product in 2^62 fixed point (integer units, 32 times the FP64 rate on
+                // this GPU); the gather, Boris, the move and the charge factors in FP64
+                const double xi0 = nx0, eta0 = ny0;
+                double u[3] = {nu0, nu1, nu2};
+                const double w = nw;
+                int ix = 0, iy = 0;
+                long long FX = 0, FY = 0;
+                if (valid) {
+                    split62(xi0, ix, FX);
+                    split62(eta0, iy, FY);
                 }
-            }
-            if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
-            // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
-            bool hx, hy;
-            if constexpr (is_f64<T>::value) {
-                hx = ge_half(fx), hy = ge_half(fy);  // 0 <= f < 1
-            } else {
-                hx = fx >= T(0.5), hy = fy >= T(0.5);
-            }
-            const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
-            const T dxp = hx ? fx - T(1) : fx, dyp = hy ? fy - T(1) : fy;
-            const T dxd = fx - T(0.5), dyd = fy - T(0.5);
-            // tile-local first-tap indices (field tile origin at px0 - 1, py0 - 1)
-            const int txp = nxp - px0, txd = ix - px0;
-            const int typ = nyp - py0, tyd = iy - py0;
-            bool ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
-                      (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
-
-            // ---- B. interpolate, push, move
-            T Sxp[3], Syp[3];
-            T dxp1 = T(0), dyp1 = T(0), fx1 = T(0), fy1 = T(0), vz = T(0);
-            int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
-            double xi1 = 0.0, eta1 = 0.0;
-            if (ok) {
-                T Sxd[3], Syd[3];
-                shape3(dxp, Sxp);
-                shape3(dxd, Sxd);
-                shape3(dyp, Syp);
-                shape3(dyd, Syd);
-                const int pl = BX * BY;
-                T E[3], B[3];
-                if constexpr (std::is_same<T, df64>::value) {
-                    // one rolled loop over Ex Ey Ez Bx By Bz: x primal for Ey Ez Bx,
-                    // y primal for Ex Ez By; results rotate through six registers
-                    T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
-#pragma unroll 1
-                    for (int c = 0; c < 6; c++) {
-                        const bool xp = c >= 1 && c <= 3, yp = (c & 1) == 0;
-                        T sx[3], sy[3];
+                if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
+                // primal node = ix + (f >= 1/2), dual node = ix
+                const bool hx = FX >= kHalf62, hy = FY >= kHalf62;
+                const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
+                const int txp = nxp - px0, txd = ix - px0;
+                const int typ = nyp - py0, tyd = iy - py0;
+                ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
+                     (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
+                long long SXP[3], SYP[3], S1X[3], S1Y[3];
+                int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
+                double xi1 = 0.0, eta1 = 0.0, vz = 0.0;
+                if (ok) {
+                    long long SXD[3], SYD[3];
+                    shape62(hx ? FX - kOne62 : FX, SXP);
+                    shape62(hy ? FY - kOne62 : FY, SYP);
+                    shape62(FX - kHalf62, SXD);
+                    shape62(FY - kHalf62, SYD);
+                    const int pl = BX * BY;
+                    double E[3], B[3];
+                    double Sxp[3], Syp[3], Sxd[3], Syd[3];
 #pragma unroll
-                        for (int k = 0; k < 3; k++) {
-                            sx[k] = xp ? Sxp[k] : Sxd[k];
-                            sy[k] = yp ? Syp[k] : Syd[k];
-                        }
-                        const T g = gather9(Ft + c * pl + (yp ? typ : tyd) * BX + (xp ? txp : txd),
-                                            BX, sx, sy);
-                        r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5, r5 = g;
+                    for (int k2 = 0; k2 < 3; k2++) {
+                        Sxp[k2] = fixed_to_f64(SXP[k2], 62);
+                        Syp[k2] = fixed_to_f64(SYP[k2], 62);
+                        Sxd[k2] = fixed_to_f64(SXD[k2], 62);
+                        Syd[k2] = fixed_to_f64(SYD[k2], 62);
                     }
-                    E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
-                } else {
                     E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
                     E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
                     E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
                     B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
                     B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
                     B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+                    const double ig = boris(eps, E, B, u);
+                    vz = u[2] * ig;
+                    xi1 = xi0 + dtdx * (u[0] * ig);
+                    eta1 = eta0 + dtdy * (u[1] * ig);
+                    long long FX1, FY1;
+                    split62(xi1, ix1, FX1);
+                    split62(eta1, iy1, FY1);
+                    const bool h1x = FX1 >= kHalf62, h1y = FY1 >= kHalf62;
+                    shape62(h1x ? FX1 - kOne62 : FX1, S1X);
+                    shape62(h1y ? FY1 - kOne62 : FY1, S1Y);
+                    sx = ix1 + (h1x ? 1 : 0) - nxp;
+                    sy = iy1 + (h1y ? 1 : 0) - nyp;
+                    ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
                 }
-
-                const T ig = boris(eps, E, B, u);
-                const T vx = u[0] * ig, vy = u[1] * ig;
-                vz = u[2] * ig;
-                int nxp1, nyp1;
-                if constexpr (is_f64<T>::value) {
-                    xi1 = xi0 + dtdx * vx;
-                    eta1 = eta0 + dtdy * vy;
-                    const double hx1 = xi1 + 0.5, hy1 = eta1 + 0.5;
-                    nxp1 = floor_to_int(hx1);
-                    nyp1 = floor_to_int(hy1);
-                    dxp1 = xi1 - fixed_to_f64(nxp1, 0);
-                    dyp1 = eta1 - fixed_to_f64(nyp1, 0);
-                } else {
-                    fx1 = fx + dtdx * vx;
-                    fy1 = fy + dtdy * vy;
-                    ix1 = ix;
-                    iy1 = iy;
-                    if (fx1 < T(0)) {
-                        fx1 += T(1);
-                        ix1 -= 1;
-                        if (fx1 >= T(1)) { fx1 = T(0); ix1 += 1; }
-                    } else if (fx1 >= T(1)) {
-                        fx1 -= T(1);
-                        ix1 += 1;
-                    }
-                    if (fy1 < T(0)) {
-                        fy1 += T(1);
-                        iy1 -= 1;
-                        if (fy1 >= T(1)) { fy1 = T(0); iy1 += 1; }
-                    } else if (fy1 >= T(1)) {
-                        fy1 -= T(1);
-                        iy1 += 1;
-                    }
-                    const bool h1x = fx1 >= T(0.5), h1y = fy1 >= T(0.5);
-                    nxp1 = ix1 + (h1x ? 1 : 0);
-                    nyp1 = iy1 + (h1y ? 1 : 0);
-                    dxp1 = h1x ? fx1 - T(1) : fx1;
-                    dyp1 = h1y ? fy1 - T(1) : fy1;
-                }
-                sx = nxp1 - nxp;
-                sy = nyp1 - nyp;
-                ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
-            }
-
-            // ---- C. Esirkepov deposition into the shared tile (origin px0-2, py0-2);
-            // warp-uniform choice of the no-crossing fast path
-            const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
-            bool leave = false;
-            int dest = patch;
-            if (ok) {
-                const T qx = cjxs * w, qy = cjys * w, qz = cjzs * w * vz;
-                const int t0 = typ * JX + txp;  // stencil node 0 of both axes
-                if (fast) {
-                    const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
-                    deposit2d_fast<T, JT>(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX, Sxp,
-                                          Syp, dxp1, dyp1, qx, qy, qz);
-                } else {
-                    if constexpr (std::is_same<T, df64>::value)
-                        deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
-                                                 JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
-                    else
-                        deposit2d_general5<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
-                                                  JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
-                }
-
-                // ---- D. boundaries and destination patch
-                bool del = false;
-                if constexpr (is_f64<T>::value) {
-                    // the comparisons with 0 and n are taken on integer floors (the
-                    // same decisions as comparing the doubles, off the FP64 pipe)
-                    const int fxi = floor_to_int(xi1);
-                    double xs = xi1 - (double)shift;
-                    if (window) {
-                        del = fxi < 0 || fxi >= nx || fxi - shift < 0;
+                const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
+                if (ok) {
+                    // charge factors (carrying the tile's 2^k) as integers
+                    const long long QX = f64_to_fixed(cjxs * w), QY = f64_to_fixed(cjys * w);
+                    const long long QZ = f64_to_fixed(cjzs * w * vz);
+                    const int t0 = typ * JX + txp;  // stencil node 0 of both axes
+                    if (fast) {
+                        const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
+                        deposit2d_fast_fix(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX,
+                                           SXP, SYP, S1X, S1Y, QX, QY, QZ);
                     } else {
-                        if (fxi - shift < 0) xs += (double)nx;
-                        if (floor_to_int(xs) >= nx) xs -= (double)nx;
+                        deposit2d_general_fix(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0, JX,
+                                              SXP, SYP, S1X, S1Y, sx, sy, QX, QY, QZ);
                     }
-                    if (floor_to_int(eta1) < 0) eta1 += (double)ny;
-                    if (floor_to_int(eta1) >= ny) eta1 -= (double)ny;
-                    xi1 = xs;
-                    ix1 = floor_to_int(xi1);
-                    iy1 = floor_to_int(eta1);
-                } else {
+                    // ---- boundaries and destination patch (decisions on the integer floors)
+                    bool del = false;
+                    double xs = xi1;
                     if (window) {
-                        del = ix1 < 0 || ix1 >= nx;
+                        del = ix1 < 0 || ix1 >= nx || ix1 - shift < 0;
+                        if (shift) xs = xi1 - 1.0;
                         ix1 -= shift;
-                        del = del || ix1 < 0;
                     } else {
-                        ix1 = wrapi(ix1, nx);
+                        if (ix1 < 0) {
+                            xs = xi1 + (double)nx;
+                            ix1 += nx;
+                        } else if (ix1 >= nx) {
+                            xs = xi1 - (double)nx;
+                            ix1 -= nx;
+                        }
                     }
-                    iy1 = wrapi(iy1, ny);
-                }
-                if (!del) {
-                    dest = ix1 / P0 + S.np[0] * (iy1 / P1);
-                    leave = dest != patch;
-                    // the new state goes to the particle's own slot, also when it leaves:
-                    // the hand-off after the item copies it from there
-                    if constexpr (is_f64<T>::value) {
-                        reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
+                    if (iy1 < 0) {
+                        eta1 += (double)ny;
+                        iy1 += ny;
+                    } else if (iy1 >= ny) {
+                        eta1 -= (double)ny;
+                        iy1 -= ny;
+                    }
+                    if (!del) {
+                        // a wrap or shift by whole cells keeps the floor: recheck it on the
+                        // stored double (a position just below a wrap can round onto it)
+                        ix1 = floor_to_int(xs);
+                        iy1 = floor_to_int(eta1);
+                        if (!window && ix1 >= nx) { xs -= (double)nx; ix1 -= nx; }
+                        if (iy1 >= ny) { eta1 -= (double)ny; iy1 -= ny; }
+                        dest = ix1 / P0 + S.np[0] * (iy1 / P1);
+                        leave = dest != patch;
+                        reinterpret_cast<double*>(S.xi[0])[slot] = xs;
                         reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
+                        U0[slot] = u[0];
+                        U1[slot] = u[1];
+                        U2[slot] = u[2];
                     } else {
-                        S.cell[slot] = ix1 | (iy1 << 16);
-                        reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
-                        reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
+                        dest = -1;
+                        leave = true;
                     }
-                    U0[slot] = u[0];
-                    U1[slot] = u[1];
-                    U2[slot] = u[2];
+                }
+            } else {
+                // ---- A. take the prefetched state, start loading the next one
+                int ix = 0, iy = 0;
+                T fx = T(0), fy = T(0);
+                double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
+                T u[3] = {nu0, nu1, nu2};
+                T w = nw;
+                if (valid) {
+                    if constexpr (is_f64<T>::value) {
+                        xi0 = nx0;
+                        eta0 = ny0;
+                        ix = floor_to_int(xi0);
+                        iy = floor_to_int(eta0);
+                        // floors widened back with integer operations (exact)
+                        fx = xi0 - fixed_to_f64(ix, 0);
+                        fy = eta0 - fixed_to_f64(iy, 0);
+                    } else {
+                        ix = nc & 0xFFFF;
+                        iy = (nc >> 16) & 0xFFFF;
+                        fx = nfx;
+                        fy = nfy;
+                    }
+                }
+                if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
+                // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
+                bool hx, hy;
+                if constexpr (is_f64<T>::value) {
+                    hx = ge_half(fx), hy = ge_half(fy);  // 0 <= f < 1
                 } else {
-                    dest = -1;
-                    leave = true;
+                    hx = fx >= T(0.5), hy = fy >= T(0.5);
+                }
+                const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
+                const T dxp = hx ? fx - T(1) : fx, dyp = hy ? fy - T(1) : fy;
+                const T dxd = fx - T(0.5), dyd = fy - T(0.5);
+                // tile-local first-tap indices (field tile origin at px0 - 1, py0 - 1)
+                const int txp = nxp - px0, txd = ix - px0;
+                const int typ = nyp - py0, tyd = iy - py0;
+                ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
+                     (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
+
+                // ---- B. interpolate, push, move
+                T Sxp[3], Syp[3];
+                T dxp1 = T(0), dyp1 = T(0), fx1 = T(0), fy1 = T(0), vz = T(0);
+                int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
+                double xi1 = 0.0, eta1 = 0.0;
+                if (ok) {
+                    T Sxd[3], Syd[3];
+                    shape3(dxp, Sxp);
+                    shape3(dxd, Sxd);
+                    shape3(dyp, Syp);
+                    shape3(dyd, Syd);
+                    const int pl = BX * BY;
+                    T E[3], B[3];
+                    if constexpr (std::is_same<T, df64>::value) {
+                        // one rolled loop over Ex Ey Ez Bx By Bz: x primal for Ey Ez Bx,
+                        // y primal for Ex Ez By; results rotate through six registers
+                        T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
+    #pragma unroll 1
+                        for (int c = 0; c < 6; c++) {
+                            const bool xp = c >= 1 && c <= 3, yp = (c & 1) == 0;
+                            T sx[3], sy[3];
+    #pragma unroll
+                            for (int k = 0; k < 3; k++) {
+                                sx[k] = xp ? Sxp[k] : Sxd[k];
+                                sy[k] = yp ? Syp[k] : Syd[k];
+                            }
+                            const T g = gather9(Ft + c * pl + (yp ? typ : tyd) * BX + (xp ? txp : txd),
+                                                BX, sx, sy);
+                            r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5, r5 = g;
+                        }
+                        E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
+                    } else {
+                        E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
+                        E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                        E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
+                        B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
+                        B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
+                        B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+                    }
+
+                    const T ig = boris(eps, E, B, u);
+                    const T vx = u[0] * ig, vy = u[1] * ig;
+                    vz = u[2] * ig;
+                    int nxp1, nyp1;
+                    if constexpr (is_f64<T>::value) {
+                        xi1 = xi0 + dtdx * vx;
+                        eta1 = eta0 + dtdy * vy;
+                        const double hx1 = xi1 + 0.5, hy1 = eta1 + 0.5;
+                        nxp1 = floor_to_int(hx1);
+                        nyp1 = floor_to_int(hy1);
+                        dxp1 = xi1 - fixed_to_f64(nxp1, 0);
+                        dyp1 = eta1 - fixed_to_f64(nyp1, 0);
+                    } else {
+                        fx1 = fx + dtdx * vx;
+                        fy1 = fy + dtdy * vy;
+                        ix1 = ix;
+                        iy1 = iy;
+                        if (fx1 < T(0)) {
+                            fx1 += T(1);
+                            ix1 -= 1;
+                            if (fx1 >= T(1)) { fx1 = T(0); ix1 += 1; }
+                        } else if (fx1 >= T(1)) {
+                            fx1 -= T(1);
+                            ix1 += 1;
+                        }
+                        if (fy1 < T(0)) {
+                            fy1 += T(1);
+                            iy1 -= 1;
+                            if (fy1 >= T(1)) { fy1 = T(0); iy1 += 1; }
+                        } else if (fy1 >= T(1)) {
+                            fy1 -= T(1);
+                            iy1 += 1;
+                        }
+                        const bool h1x = fx1 >= T(0.5), h1y = fy1 >= T(0.5);
+                        nxp1 = ix1 + (h1x ? 1 : 0);
+                        nyp1 = iy1 + (h1y ? 1 : 0);
+                        dxp1 = h1x ? fx1 - T(1) : fx1;
+                        dyp1 = h1y ? fy1 - T(1) : fy1;
+                    }
+                    sx = nxp1 - nxp;
+                    sy = nyp1 - nyp;
+                    ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
+                }
+
+                // ---- C. Esirkepov deposition into the shared tile (origin px0-2, py0-2);
+                // warp-uniform choice of the no-crossing fast path
+                const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
+                if (ok) {
+                    const T qx = cjxs * w, qy = cjys * w, qz = cjzs * w * vz;
+                    const int t0 = typ * JX + txp;  // stencil node 0 of both axes
+                    if (fast) {
+                        const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
+                        deposit2d_fast<T, JT>(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX, Sxp,
+                                              Syp, dxp1, dyp1, qx, qy, qz);
+                    } else {
+                        if constexpr (std::is_same<T, df64>::value)
+                            deposit2d_general<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
+                                                     JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
+                        else
+                            deposit2d_general5<T, JT>(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0,
+                                                      JX, Sxp, Syp, dxp1, dyp1, sx, sy, qx, qy, qz);
+                    }
+
+                    // ---- D. boundaries and destination patch
+                    bool del = false;
+                    if constexpr (is_f64<T>::value) {
+                        // the comparisons with 0 and n are taken on integer floors (the
+                        // same decisions as comparing the doubles, off the FP64 pipe)
+                        const int fxi = floor_to_int(xi1);
+                        double xs = xi1 - (double)shift;
+                        if (window) {
+                            del = fxi < 0 || fxi >= nx || fxi - shift < 0;
+                        } else {
+                            if (fxi - shift < 0) xs += (double)nx;
+                            if (floor_to_int(xs) >= nx) xs -= (double)nx;
+                        }
+                        if (floor_to_int(eta1) < 0) eta1 += (double)ny;
+                        if (floor_to_int(eta1) >= ny) eta1 -= (double)ny;
+                        xi1 = xs;
+                        ix1 = floor_to_int(xi1);
+                        iy1 = floor_to_int(eta1);
+                    } else {
+                        if (window) {
+                            del = ix1 < 0 || ix1 >= nx;
+                            ix1 -= shift;
+                            del = del || ix1 < 0;
+                        } else {
+                            ix1 = wrapi(ix1, nx);
+                        }
+                        iy1 = wrapi(iy1, ny);
+                    }
+                    if (!del) {
+                        dest = ix1 / P0 + S.np[0] * (iy1 / P1);
+                        leave = dest != patch;
+                        // the new state goes to the particle's own slot, also when it leaves:
+                        // the hand-off after the item copies it from there
+                        if constexpr (is_f64<T>::value) {
+                            reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
+                            reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
+                        } else {
+                            S.cell[slot] = ix1 | (iy1 << 16);
+                            reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
+                            reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
+                        }
+                        U0[slot] = u[0];
+                        U1[slot] = u[1];
+                        U2[slot] = u[2];
+                    } else {
+                        dest = -1;
+                        leave = true;
+                    }
                 }
             }
             if (valid && !ok) {
