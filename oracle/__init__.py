@@ -97,6 +97,8 @@ def lib():
         L.orc_merge_group.restype = ctypes.c_int
         L.orc_merge_group.argtypes = [ctypes.c_longlong, _dp, _dp, _dp, _dp, _ip, _dp, _dp,
                                       ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_split.restype = ctypes.c_longlong
+        L.orc_split.argtypes = [ctypes.c_void_p, _ip, ctypes.c_longlong, ctypes.c_double]
         L.orc_merge.restype = ctypes.c_longlong
         L.orc_merge.argtypes = [ctypes.c_void_p, _ip, ctypes.c_longlong, ctypes.c_double]
         _lib = L
@@ -305,6 +307,15 @@ class OracleSim:
         r = lib().orc_merge(self._h, pt.ctypes.data_as(_ip), int(above), float(dp))
         if r < 0:
             raise MemoryError("oracle merge")
+        return int(r)
+
+    def split(self, patch, below: int, wmin: float) -> int:
+        """Split particles of cells holding fewer than `below` (and at least one)
+        particles (weights >= 2 wmin, increasing id); returns the number of splits."""
+        pt = np.ascontiguousarray(list(patch) + [1] * (3 - len(patch)), dtype=np.int32)
+        r = lib().orc_split(self._h, pt.ctypes.data_as(_ip), int(below), float(wmin))
+        if r < 0:
+            raise MemoryError("oracle split (capacity)")
         return int(r)
 
     def energy(self):

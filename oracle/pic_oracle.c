@@ -1094,3 +1094,83 @@ long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp) 
         free(gid), free(hot);
     return removed;
 }
+
+/* ------------------------------------------------------------------ splitting */
+
+long long orc_split(orc_sim* s, const int patch[3], long long below, double wmin) {
+    const orc_config* c = &s->c;
+    if (below <= 1) return 0;
+    long np_[3];
+    for (int a = 0; a < 3; a++) np_[a] = a < c->dims ? c->n[a] / patch[a] : 1;
+    const long P[3] = {patch[0], c->dims >= 2 ? patch[1] : 1, c->dims == 3 ? patch[2] : 1};
+    const long long ncell = s->ncell;
+    const long long n0 = s->np;
+    /* cell of every particle, and particles per cell */
+    long long* cnt = (long long*)calloc((size_t)ncell, sizeof(long long));
+    long long* pc = (long long*)malloc((size_t)(n0 > 0 ? n0 : 1) * sizeof(long long));
+    if (!cnt || !pc) {
+        free(cnt), free(pc);
+        return -1;
+    }
+    for (long long p = 0; p < n0; p++) {
+        long ic[3];
+        cell_of(s, p, ic);
+        pc[p] = ((long long)ic[2] * c->n[1] + ic[1]) * c->n[0] + ic[0];
+        cnt[pc[p]]++;
+    }
+    long long done = 0;
+    /* patches in index order, cells in local order, parents in increasing id */
+    for (long pz = 0; pz < np_[2]; pz++)
+        for (long py = 0; py < np_[1]; py++)
+            for (long px = 0; px < np_[0]; px++)
+                for (long lz = 0; lz < P[2]; lz++)
+                    for (long ly = 0; ly < P[1]; ly++)
+                        for (long lx = 0; lx < P[0]; lx++) {
+                            const long long cell =
+                                ((long long)(pz * P[2] + lz) * c->n[1] + (py * P[1] + ly)) * c->n[0] +
+                                (px * P[0] + lx);
+                            const long long n = cnt[cell];
+                            if (n < 1 || n >= below) continue;
+                            long long room = below - n;
+                            int last = -2147483647 - 1;
+                            while (room > 0) {
+                                /* the next eligible particle of this cell by id */
+                                long long q = -1;
+                                for (long long p = 0; p < n0; p++)
+                                    if (pc[p] == cell && s->id[p] > last && s->w[p] >= 2.0 * wmin &&
+                                        (q < 0 || s->id[p] < s->id[q]))
+                                        q = p;
+                                if (q < 0) break;
+                                last = s->id[q];
+                                if (s->np >= s->cap) {
+                                    free(cnt), free(pc);
+                                    return -1;
+                                }
+                                const double pos[3] = {s->x[q], s->y[q], s->z[q]};
+                                double d[3] = {0.0, 0.0, 0.0};
+                                for (int a = 0; a < c->dims; a++) {
+                                    const double xi = pos[a] / c->d[a];
+                                    const double f = xi - floor(xi);
+                                    d[a] = 0.5 * (f < 1.0 - f ? f : 1.0 - f) * c->d[a];
+                                }
+                                const long long k = s->np++;
+                                s->x[k] = pos[0] - d[0];
+                                s->y[k] = pos[1] - d[1];
+                                s->z[k] = pos[2] - d[2];
+                                s->x[q] = pos[0] + d[0];
+                                s->y[q] = pos[1] + d[1];
+                                s->z[q] = pos[2] + d[2];
+                                s->ux[k] = s->ux[q];
+                                s->uy[k] = s->uy[q];
+                                s->uz[k] = s->uz[q];
+                                s->w[q] *= 0.5;
+                                s->w[k] = s->w[q];
+                                s->id[k] = (int)(s->next_id + done);
+                                done++;
+                                room--;
+                            }
+                        }
+    s->next_id += done;
+    free(cnt), free(pc);
+    return done;
+}

@@ -157,6 +157,24 @@ int orc_merge_group(long long n, const double* ux, const double* uy, const doubl
  * order otherwise kept. Returns the number removed. */
 long long orc_merge(orc_sim* s, const int patch[3], long long above, double dp);
 
+/* ---- load limiting by particle splitting ----
+ * The paper splits SP in cells of low SP number density and merges them in cells of
+ * high density, conserving the physics (Sec. 3.2); the algorithm itself is in a reference
+ * that is not available, so this rule is built from the conservation laws:
+ *   a cell holding n particles, 1 <= n < below, is under-populated; its particles of
+ *   weight w >= 2 wmin, taken in increasing id, are split one by one until the cell
+ *   holds `below` particles or each of them has been split once. A split replaces
+ *   (x, u, w) by (x + delta, u, w/2), keeping the id, and (x - delta, u, w/2), with a new
+ *   id; delta_a = min(f_a, 1 - f_a) d_a / 2 on every axis, f_a the in-cell offset.
+ * Halving is exact, so the total weight (charge), momentum sum w u and kinetic energy
+ * sum w (gamma - 1) are kept exactly; both halves stay in the parent's cell (and patch),
+ * the charge centroid is kept, and the second moment of the charge grows by w delta_a^2
+ * per axis. New ids are next_id + the split's rank in (patch, cell, parent id) order,
+ * patches numbered x fastest and cells in increasing local index (x fastest); next_id
+ * then advances by the number of splits. Returns the number of splits, -1 on error
+ * (capacity or allocation). */
+long long orc_split(orc_sim* s, const int patch[3], long long below, double wmin);
+
 #ifdef __cplusplus
 }
 #endif
