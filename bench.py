@@ -88,10 +88,11 @@ def step_roofline(dt, w, pushes_per_s, n=None):
             "bytes_per_push": step_bytes_per_push(dt, w, n)}
 # kernels per step: queue build, push, [window injection], exchange, repack plan and its
 # two copy kernels (which return at once unless a patch needs room), Yee E, Yee B, end
-def kernels_per_step(window: bool, merge: bool = False) -> int:
+def kernels_per_step(window: bool, merge: bool = False, split: bool = False) -> int:
     """Kernels in one captured step: queue build, push, 2 Yee, exchange, repack plan + 2
-    copies, end step; injection with the window; the merge kernel with load limiting."""
-    return (10 if window else 9) + (1 if merge else 0)
+    copies, end step; injection with the window; the merge kernel and the three split
+    kernels (count, id offsets, apply) with load limiting."""
+    return (10 if window else 9) + (1 if merge else 0) + (3 if split else 0)
 
 
 def parse():
@@ -110,6 +111,9 @@ def parse():
     ap.add_argument("--merge-above", type=int, default=0,
                     help="load limiting: merge particle groups in patches above this count")
     ap.add_argument("--merge-dp", type=float, default=0.05, help="merge momentum-bin width")
+    ap.add_argument("--split-below", type=int, default=0,
+                    help="load limiting: split particles of cells holding fewer than this many")
+    ap.add_argument("--split-wmin", type=float, default=0.0, help="weight floor of splitting")
     ap.add_argument("--autotune", default="cached", choices=["cached", "on", "off"],
                     help="cached: the layouts recorded in the package's tuning table (measured "
                          "there when missing); on: measure again; off: workload patch, --chunk")
@@ -365,7 +369,8 @@ def trace_run(args, w, precision, chunk):
     prec = {"fp64": binding.PIC_FP64, "fp32": binding.PIC_FP32, "df64": binding.PIC_DF64}[precision]
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
     sim = binding.Sim(w["params"], precision=prec, capacity=capacity_for(w), chunk=chunk,
-                      mapping=mapping, merge_above=args.merge_above, merge_dp=args.merge_dp)
+                      mapping=mapping, merge_above=args.merge_above, merge_dp=args.merge_dp,
+                      split_below=args.split_below, split_wmin=args.split_wmin)
     rows = []
     try:
         sim.load(w)
@@ -401,7 +406,8 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0, snapshot=Fals
     cap = capacity_for(w)
     mapping = binding.PIC_MAP_STATIC if args.mapping == "static" else binding.PIC_MAP_QUEUE
     sim = binding.Sim(w["params"], precision=prec, capacity=cap, chunk=chunk, mapping=mapping,
-                      merge_above=args.merge_above, merge_dp=args.merge_dp)
+                      merge_above=args.merge_above, merge_dp=args.merge_dp,
+                      split_below=args.split_below, split_wmin=args.split_wmin)
     sim.load(w)
     counts0 = sim.patch_counts()
     stream = sim.stream
@@ -481,6 +487,9 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0, snapshot=Fals
                             "max_over_mean_patch": float(counts_t0.max() / counts_t0.mean()),
                             "max_over_mean_patch_at_load": float(counts0.max() / counts0.mean()),
                             "max_patch": int(counts_t0.max())})
+    if args.split_below > 0:
+        out["split"] = {"below": args.split_below, "wmin": args.split_wmin,
+                        "added": sim.split_count()}
     if args.merge_above > 0:
         counts1 = sim.patch_counts()
         out["merge"] = {"above": args.merge_above, "dp": args.merge_dp,
@@ -963,7 +972,7 @@ def main():
                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
                 if e2e else None),
         "gpu_launches": kernels_per_step(bool(w["params"].get("window")),
-                                         args.merge_above > 0) * args.steps,
+                                         args.merge_above > 0, args.split_below > 0) * args.steps,
         "clocks": clocks.summary(),
         "kernel_ms_per_step": main_run["profile"],
         "particles": main_run["n"],
@@ -974,6 +983,8 @@ def main():
         line["serving"] = serving
     if "merge" in main_run:
         line["merge"] = main_run["merge"]
+    if "split" in main_run:
+        line["split"] = main_run["split"]
     if trace is not None:
         line["trace"] = trace
     if variants:

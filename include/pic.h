@@ -112,6 +112,20 @@ typedef struct {
                            Esirkepov's current conserves charge for the two-point
                            divergence, so with order 6 the GAUSS diagnostic is no longer
                            preserved to round-off. */
+    int split_below;    /* load limiting (Sec. 3.2: SP are split in cells of low SP density):
+                           at the end of every step (after merging), a cell holding n
+                           particles with 1 <= n < split_below has its particles of weight
+                           >= 2 split_wmin, in increasing id, split until it holds
+                           split_below particles or each has been split once. A split
+                           replaces (x, u, w) by (x + delta, u, w/2) and (x - delta, u, w/2)
+                           with delta_a = min(f_a, 1 - f_a) d_a / 2 (f_a the in-cell offset),
+                           so charge, momentum, energy and the charge centroid are kept and
+                           both halves stay in the cell; the new particle's id is the next
+                           free id in (patch, cell, parent id) order. 0 = off; at most 64;
+                           needs patches of at most 4096 cells. A patch without room for its
+                           new particles latches PIC_ERR_CAPACITY (size capacity for them). */
+    double split_wmin;  /* weight floor of splitting (>= 0): a particle splits only while
+                           its weight is at least 2 split_wmin */
 } pic_config;
 
 /* sizeof(pic_config) as this library was built: a binding compares it with its own
@@ -186,7 +200,8 @@ enum {
     PIC_DIAG_STEP = 6,          /* 3 int64: steps taken, window shifts, capacity
                                    repacks (per-patch capacities re-split on the
                                    device when a patch nears its capacity); a 4th,
-                                   particles removed by merging, when out_bytes
+                                   particles removed by merging, and a 5th,
+                                   particles added by splitting, when out_bytes
                                    allows                                         */
     PIC_DIAG_EX_AXIS = 7        /* nx float64: Ex on the row (and plane) ny/2      */
 };

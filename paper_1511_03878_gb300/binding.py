@@ -60,6 +60,8 @@ class PicConfig(ctypes.Structure):
         ("merge_above", ctypes.c_int),
         ("merge_dp", ctypes.c_double),
         ("maxwell_order", ctypes.c_int),
+        ("split_below", ctypes.c_int),
+        ("split_wmin", ctypes.c_double),
     ]
 
 
@@ -137,7 +139,8 @@ def _check(rc, handle=None):
 
 def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chunk: int = 0,
                 mapping: int = PIC_MAP_QUEUE, merge_above: int = 0,
-                merge_dp: float = 0.0) -> PicConfig:
+                merge_dp: float = 0.0, split_below: int = 0,
+                split_wmin: float = 0.0) -> PicConfig:
     c = PicConfig()
     c.dims = int(params["dims"])
     for a in range(3):
@@ -163,6 +166,8 @@ def make_config(params: dict, precision: int = PIC_FP64, capacity: int = 0, chun
     c.merge_above = int(merge_above)
     c.merge_dp = float(merge_dp)
     c.maxwell_order = int(params.get("maxwell_order", 2))
+    c.split_below = int(split_below)
+    c.split_wmin = float(split_wmin)
     return c
 
 
@@ -334,13 +339,15 @@ class Sim:
 
     def __init__(self, params: dict, precision: int = PIC_FP64, capacity: int = 0,
                  chunk: int = 0, mapping: int = PIC_MAP_QUEUE, stream=None, device="cuda",
-                 merge_above: int = 0, merge_dp: float = 0.0):
+                 merge_above: int = 0, merge_dp: float = 0.0, split_below: int = 0,
+                 split_wmin: float = 0.0):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA GPU is required (the library has no CPU path)")
         self.params = params
-        self.cfg = make_config(params, precision, capacity, chunk, mapping, merge_above, merge_dp)
+        self.cfg = make_config(params, precision, capacity, chunk, mapping, merge_above, merge_dp,
+                               split_below, split_wmin)
         self.nbytes = pic_required_bytes(self.cfg)
         if self.nbytes == 0:
             raise PicError(PIC_ERR_INVALID, "invalid configuration")
@@ -416,6 +423,10 @@ class Sim:
     def merged(self) -> int:
         """Particles removed by merging so far."""
         return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 32), dtype=np.int64)[3])
+
+    def split_count(self) -> int:
+        """Particles added by splitting so far."""
+        return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 40), dtype=np.int64)[4])
 
     def repacks(self) -> int:
         return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)[2])

@@ -257,6 +257,253 @@ __global__ void __launch_bounds__(512) merge_kernel(const BatchDev* __restrict__
     }
 }
 
+// ---------------------------------------------------------------- splitting
+//
+// Load limiting in low-density cells (Sec. 3.2: SP are split where the SP density is
+// low, merged where it is high). The oracle's rule: a cell holding n particles,
+// 1 <= n < split_below, has its particles of weight >= 2 split_wmin, in increasing id,
+// split until it holds split_below particles or each has been split once; a split keeps
+// (x + delta, u, w/2) under the parent's id and adds (x - delta, u, w/2) with
+// delta_a = min(f_a, 1 - f_a) d_a / 2, f_a the in-cell offset, so both halves stay in the
+// cell. New ids are the next free id plus the split's rank in (patch, cell, parent id)
+// order. Three passes: splits per patch (shared cell histograms), the id offsets (a scan
+// over the patches, one CTA per sim), the splits themselves (counting sort of the slots
+// by cell, one thread per cell sorting its few particles by id). All three return at
+// once when a sim's split_below is 0.
+
+template <typename T>
+__device__ __forceinline__ bool split_eligible(const SimDev& S, int slot) {
+    return to_f64(reinterpret_cast<const T*>(S.w)[slot]) >= 2.0 * S.split_wmin;
+}
+
+// splits of one cell from its particle and eligible counts
+__device__ __forceinline__ int split_cell_count(int n, int e, int below) {
+    return (n >= 1 && n < below) ? min(e, below - n) : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) split_count_kernel(const BatchDev* __restrict__ bd) {
+    __shared__ int cnt[kMergeCells];
+    __shared__ int elig[kMergeCells];
+    __shared__ int s_tot;
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int below = S.split_below;
+    if (below <= 0) return;
+    const int cells = S.P[0] * S.P[1] * S.P[2];
+    if (cells > kMergeCells) return;
+    const int tid = threadIdx.x;
+    for (int p = blockIdx.x; p < S.npatch; p += gridDim.x) {
+        __syncthreads();
+        for (int c = tid; c < cells; c += blockDim.x) cnt[c] = 0, elig[c] = 0;
+        if (tid == 0) s_tot = 0;
+        __syncthreads();
+        const int n = S.pcount[p], base = S.pbase[p];
+        const int o[3] = {(p % S.np[0]) * S.P[0], ((p / S.np[0]) % S.np[1]) * S.P[1],
+                          (p / (S.np[0] * S.np[1])) * S.P[2]};
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int c = merge_local_cell<T>(S, base + k, o);
+            atomicAdd(&cnt[c], 1);
+            if (split_eligible<T>(S, base + k)) atomicAdd(&elig[c], 1);
+        }
+        __syncthreads();
+        int m = 0;
+        for (int c = tid; c < cells; c += blockDim.x) m += split_cell_count(cnt[c], elig[c], below);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+        if ((tid & 31) == 0 && m) atomicAdd(&s_tot, m);
+        __syncthreads();
+        if (tid == 0) S.soff[p] = s_tot;
+    }
+}
+
+// soff[p] <- first free id + (splits of the patches before p); soff[npatch] <- the next
+// free id. The column injected by this step's window shift already holds ids from
+// next_id on (the end of the step advances next_id past them), so the first free id is
+// past that column.
+__global__ void __launch_bounds__(1024) split_scan_kernel(const BatchDev* __restrict__ bd) {
+    __shared__ int warp_sums[32];
+    const int sim = blockIdx.x;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    if (S.split_below <= 0) return;
+    long long column = 0;
+    if (S.st->shift) {
+        column = (long long)S.n[1] * S.ippc[0] * S.ippc[1];
+        if (S.dims == 3) column *= (long long)S.n[2] * S.ippc[2];
+    }
+    const long long first = S.st->next_id + column;
+    long long carry = 0;
+    for (int p0 = 0; p0 < S.npatch; p0 += blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        const int v = p < S.npatch ? S.soff[p] : 0;
+        int tot;
+        const int ex = block_exclusive_scan(v, warp_sums, &tot);
+        if (p < S.npatch) S.soff[p] = (int)(first + carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        S.soff[S.npatch] = (int)(first + carry);
+        S.st->next_id += carry;  // the end of the step adds the injected column
+        S.st->nsplit += carry;
+    }
+}
+
+// one split: the parent keeps its id at x + delta, the new particle (slot cs, id nid)
+// goes to x - delta; both with half the weight and the parent's momentum
+template <typename T>
+__device__ void split_one(const SimDev& S, int s, int cs, int nid) {
+    for (int a = 0; a < S.dims; a++) {
+        T* X = reinterpret_cast<T*>(S.xi[a]);
+        if constexpr (is_f64<T>::value) {
+            const double xi = X[s];  // global cell-unit position
+            const double fl = floor(xi);
+            const double f = xi - fl;
+            const double dl = 0.5 * fmin(f, 1.0 - f);
+            double xp = xi + dl;
+            if (floor(xp) != fl) xp = xi;  // rounding onto the next cell: keep the parent
+            X[s] = xp;
+            X[cs] = xi - dl;
+        } else {
+            const T f = X[s];  // in-cell offset in [0, 1)
+            const T g = T(1.0f) - f;
+            const T dl = T(0.5f) * (g < f ? g : f);
+            T fp = f + dl;
+            if (!(fp < T(1.0f))) fp = f;
+            X[s] = fp;
+            X[cs] = f - dl;
+        }
+    }
+    if constexpr (uses_cell<T>()) S.cell[cs] = S.cell[s];
+    for (int a = 0; a < 3; a++) {
+        T* U = reinterpret_cast<T*>(S.u[a]);
+        U[cs] = U[s];
+    }
+    T* W = reinterpret_cast<T*>(S.w);
+    const T wh = W[s] * T(0.5f);
+    W[s] = wh;
+    W[cs] = wh;
+    S.id[cs] = nid;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) split_apply_kernel(const BatchDev* __restrict__ bd) {
+    extern __shared__ int sh[];  // start, cursor, new-particle offsets: kMergeCells each
+    __shared__ int warp_sums[32];
+    int* start = sh;
+    int* cursor = sh + kMergeCells;
+    int* coff = sh + 2 * kMergeCells;
+    const int sim = blockIdx.y;
+    if (sim >= bd->nsims) return;
+    const SimDev& S = bd->sims[sim];
+    const int below = S.split_below;
+    if (below <= 0) return;
+    const int cells = S.P[0] * S.P[1] * S.P[2];
+    if (cells > kMergeCells) return;
+    const int tid = threadIdx.x;
+    int* ord = S.aid;  // scratch: slots in cell order
+    for (int p = blockIdx.x; p < S.npatch; p += gridDim.x) {
+        __syncthreads();
+        const int total = S.soff[p + 1] - S.soff[p];
+        if (total == 0) continue;  // uniform over the CTA
+        const int n = S.pcount[p], base = S.pbase[p];
+        if (n + total > S.pcap[p]) {  // no room for the new particles
+            if (tid == 0) atomicOr(S.status, ST_CAPACITY);
+            continue;
+        }
+        const int o[3] = {(p % S.np[0]) * S.P[0], ((p / S.np[0]) % S.np[1]) * S.P[1],
+                          (p / (S.np[0] * S.np[1])) * S.P[2]};
+        for (int c = tid; c < cells; c += blockDim.x) start[c] = 0, coff[c] = 0;
+        __syncthreads();
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int c = merge_local_cell<T>(S, base + k, o);
+            atomicAdd(&start[c], 1);
+            if (split_eligible<T>(S, base + k)) atomicAdd(&coff[c], 1);
+        }
+        __syncthreads();
+        // per-cell splits, then exclusive prefixes of the counts (slot order) and of the
+        // splits (new-particle order): a contiguous run of cells per thread, then a scan
+        const int per = (cells + blockDim.x - 1) / blockDim.x;
+        const int c0 = tid * per, c1 = min(c0 + per, cells);
+        int run_n = 0, run_m = 0;
+        for (int c = c0; c < c1; c++) {
+            coff[c] = split_cell_count(start[c], coff[c], below);
+            run_n += start[c];
+            run_m += coff[c];
+        }
+        int tot_n, tot_m;
+        int acc_n = block_exclusive_scan(run_n, warp_sums, &tot_n);
+        int acc_m = block_exclusive_scan(run_m, warp_sums, &tot_m);
+        for (int c = c0; c < c1; c++) {
+            const int h = start[c], m = coff[c];
+            start[c] = acc_n;
+            cursor[c] = acc_n;
+            coff[c] = acc_m;
+            acc_n += h;
+            acc_m += m;
+        }
+        __syncthreads();
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int s = base + k;
+            ord[base + atomicAdd(&cursor[merge_local_cell<T>(S, s, o)], 1)] = s;
+        }
+        __syncthreads();
+        const int first_id = S.soff[p];
+        for (int c = tid; c < cells; c += blockDim.x) {
+            const int m = (c + 1 < cells ? coff[c + 1] : tot_m) - coff[c];
+            if (m == 0) continue;
+            const int nc = cursor[c] - start[c];  // < below <= 64
+            int* q = ord + base + start[c];
+            for (int i = 1; i < nc; i++) {  // by id
+                const int x = q[i];
+                int j = i - 1;
+                while (j >= 0 && S.id[q[j]] > S.id[x]) {
+                    q[j + 1] = q[j];
+                    j--;
+                }
+                q[j + 1] = x;
+            }
+            int j = 0;
+            for (int i = 0; i < nc && j < m; i++) {
+                const int s = q[i];
+                if (!split_eligible<T>(S, s)) continue;
+                split_one<T>(S, s, base + n + coff[c] + j, first_id + coff[c] + j);
+                j++;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) S.pcount[p] = n + total;
+    }
+}
+
+constexpr int kSplitDynSmem = 3 * kMergeCells * (int)sizeof(int);
+
+cudaError_t split_setup() {
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < 3 && e == cudaSuccess; p++)
+        PIC_DISPATCH(p, (e = cudaFuncSetAttribute(split_apply_kernel<T>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kSplitDynSmem)));
+    return e;
+}
+
+cudaError_t launch_split(const BatchDev* bd, int nsims, int max_patches, int prec,
+                         cudaStream_t s) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    dim3 grid(max_patches < 2 * nsm ? max_patches : 2 * nsm, nsims);
+    PIC_DISPATCH(prec, (split_count_kernel<T><<<grid, 512, 0, s>>>(bd)));
+    split_scan_kernel<<<nsims, 1024, 0, s>>>(bd);
+    PIC_DISPATCH(prec, (split_apply_kernel<T><<<grid, 512, kSplitDynSmem, s>>>(bd)));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge(const BatchDev* bd, int nsims, int max_patches, int prec,
                          cudaStream_t s) {
     static int nsm = 0;

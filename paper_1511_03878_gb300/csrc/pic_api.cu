@@ -133,6 +133,14 @@ const char* validate(const pic_config* c) {
         for (int a = 0; a < c->dims; a++) cells *= c->patch[a];
         if (cells > kMergeCells) return "merging needs patches of at most 4096 cells";
     }
+    if (c->split_below < 0 || c->split_below > kSplitBelowMax) return "split_below in [0, 64]";
+    if (c->split_below > 0) {
+        if (!(c->split_wmin >= 0) || !std::isfinite(c->split_wmin))
+            return "split_wmin must be finite and >= 0";
+        long long cells = 1;
+        for (int a = 0; a < c->dims; a++) cells *= c->patch[a];
+        if (cells > kMergeCells) return "splitting needs patches of at most 4096 cells";
+    }
     if (c->window) {
         if (!(c->ramp_len > 0)) return "ramp_len must be positive";
         for (int a = 0; a < c->dims; a++)
@@ -152,6 +160,8 @@ Layout plan(const pic_config* c, char* base) {
     S.mapping = c->mapping;
     S.merge_above = c->merge_above;
     S.merge_dp = c->merge_dp;
+    S.split_below = c->split_below;
+    S.split_wmin = c->split_wmin;
     S.order = c->maxwell_order == 6 ? 6 : 2;
     for (int a = 0; a < 3; a++) {
         S.n[a] = a < c->dims ? c->n[a] : 1;
@@ -260,6 +270,7 @@ Layout plan(const pic_config* c, char* base) {
     S.mpend = cv.take<int>(S.npatch);
     S.mpoff = cv.take<int>(S.npatch);
     S.mlast = cv.take<int>(S.npatch);
+    S.soff = cv.take<int>(S.npatch + 1);
     // sixth order in a moving window: E^{n+1} of the column the shift drops, which the
     // B update of the new frame's first columns still reads
     S.ecol = S.order == 6 && c->window ? cv.take<char>(3 * (long long)S.n[1] * S.n[2] * es)
@@ -404,7 +415,8 @@ struct GraphOwner {
 // second branch) | (injection -> exchange) -> end of step.
 cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_patches,
                          int max_ncell, int max_column, int dims, int prec, int order,
-                         int mapping, const int P[3], int grid, bool window, bool merge) {
+                         int mapping, const int P[3], int grid, bool window, bool merge,
+                         bool split) {
     cudaError_t e;
     if (!*o.cap0) {
         if ((e = cudaStreamCreateWithFlags(o.cap0, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -423,6 +435,7 @@ cudaError_t capture_step(GraphOwner o, const BatchDev* db, int nsims, int max_pa
     if (le == cudaSuccess && window) le = launch_inject(db, nsims, max_column, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_exchange(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess && merge) le = launch_merge(db, nsims, max_patches, prec, *o.cap0);
+    if (le == cudaSuccess && split) le = launch_split(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess) le = launch_repack(db, nsims, max_patches, prec, *o.cap0);
     if (le == cudaSuccess) le = cudaStreamWaitEvent(*o.cap0, *o.ev_join, 0);
     if (le == cudaSuccess) le = launch_end_step(db, nsims, max_patches, *o.cap0);
@@ -558,10 +571,11 @@ static pic_status create_body(const pic_config* cfg, void* dev_arena, size_t are
         return bail(PIC_ERR_CUDA);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bail(PIC_ERR_CUDA);
     s->push_grid = push_grid_size(S.dims, S.prec, S.P, cfg->mapping == PIC_MAP_STATIC, S.npatch);
+    if (S.split_below > 0 && split_setup() != cudaSuccess) return bail(PIC_ERR_CUDA);
     GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
     if (capture_step(o, s->L.db, 1, S.npatch, (int)S.ncell, s->column_pts, S.dims, S.prec,
                      S.order, S.mapping, S.P, s->push_grid, S.window != 0,
-                     S.merge_above > 0) != cudaSuccess)
+                     S.merge_above > 0, S.split_below > 0) != cudaSuccess)
         return bail(PIC_ERR_CUDA);
     *out = s;
     return PIC_OK;
@@ -1040,6 +1054,10 @@ static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, s
                 o[3] = st.nmerged;
                 wb = 4 * sizeof(long long);
             }
+            if (out_bytes >= 5 * sizeof(long long)) {
+                o[4] = st.nsplit;
+                wb = 5 * sizeof(long long);
+            }
             if (written) *written = wb;
             return PIC_OK;
         }
@@ -1136,6 +1154,8 @@ static pic_status profile_body(pic_sim* s, int nsteps, double* ms, int n_ms) {
         if (e == cudaSuccess) e = launch_exchange(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess && S.merge_above > 0)
             e = launch_merge(s->L.db, 1, S.npatch, S.prec, s->stream);
+        if (e == cudaSuccess && S.split_below > 0)
+            e = launch_split(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s->stream);
         if (e == cudaSuccess) e = launch_repack(s->L.db, 1, S.npatch, S.prec, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s->stream);
@@ -1291,11 +1311,15 @@ static pic_status batch_create_body(pic_sim* const* sims, int nsims, void* dev_a
     const int grid = push_grid_size(S0.dims, S0.prec, S0.P, sims[0]->cfg.mapping == PIC_MAP_STATIC,
                                     prefix[nsims]);
     GraphOwner o{&b->cap0, &b->cap1, &b->ev_fork, &b->ev_join, &b->graph, &b->gexec};
-    bool any_merge = false;
-    for (int i = 0; i < nsims; i++) any_merge = any_merge || hsims[i].merge_above > 0;
+    bool any_merge = false, any_split = false;
+    for (int i = 0; i < nsims; i++) {
+        any_merge = any_merge || hsims[i].merge_above > 0;
+        any_split = any_split || hsims[i].split_below > 0;
+    }
     if (e == cudaSuccess)
         e = capture_step(o, bl.db, nsims, max_patches, max_ncell, max_column, S0.dims, S0.prec,
-                         S0.order, sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge);
+                         S0.order, sims[0]->cfg.mapping, S0.P, grid, any_window, any_merge,
+                         any_split);
     if (e != cudaSuccess) {
         destroy_graph_owner(o);
         return PIC_ERR_CUDA;

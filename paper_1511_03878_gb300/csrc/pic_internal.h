@@ -33,6 +33,8 @@ constexpr int kMailboxDiv = 2;    // exchange-buffer slots per patch: capacity /
                                   // (a compressed 3D LWFA patch took in more than 1/4 of its
                                   // capacity in one step)
 constexpr int kMergeCells = 4096;  // largest patch (in cells) the merge kernel sorts
+constexpr int kSplitBelowMax = 64; // largest split_below (a cell's particles sorted by one
+                                   // thread)
 constexpr int kSlotAlign = 32;    // per-patch particle and exchange-buffer bases are multiples
                                   // of this, so that a warp's particle loads start a line
 constexpr int kLeaveList = 512;   // leavers of one work item handed off after the item;
@@ -62,6 +64,7 @@ struct StepState {
     int repack;         // set by the exchange when a patch nears or exceeds its capacity
     int nrepack;        // repacks done
     long long nmerged;  // particles removed by merging
+    long long nsplit;   // particles added by splitting
 };
 
 struct SimDev {
@@ -92,6 +95,8 @@ struct SimDev {
     int cmax_exp;      // one particle's current contribution stays below 2^cmax_exp
     int merge_above;   // load limiting: patches above this count are merged (0: off)
     double merge_dp;   // momentum-bin width of the merge
+    int split_below;   // load limiting: cells below this count are split (0: off)
+    double split_wmin; // weight floor of the split
     // fields
     void* F[2];      // [6][NZ][NY][NX]: Ex Ey Ez Bnx Bny Bnz (B^n for the push)
     void* H[2];      // [3][...]: B^{n+1/2}
@@ -125,6 +130,8 @@ struct SimDev {
     int* mpend;      // arrivals left in the exchange buffer for want of room (repack places them)
     int* mpoff;      // offset of the first of them in the patch's exchange buffer
     int* mlast;      // per patch: count after its last merge pass (0 = none yet)
+    int* soff;       // [npatch + 1] splitting: splits per patch, then the first new id of
+                     // each patch (soff[npatch] = the next free id after the pass)
     void* ecol;      // sixth order with the window: [3][nz][ny] E^{n+1} of the column a
                      // shift drops (old-frame x = 0), read by the B update
     // state and scratch
@@ -168,6 +175,12 @@ cudaError_t launch_end_step(const BatchDev* bd, int nsims, int max_patches, cuda
 // load limiting by merging (no-op for sims with merge_above = 0)
 cudaError_t launch_merge(const BatchDev* bd, int nsims, int max_patches, int prec,
                          cudaStream_t s);
+// load limiting by splitting (no-op for sims with split_below = 0): count, id offsets,
+// apply
+cudaError_t launch_split(const BatchDev* bd, int nsims, int max_patches, int prec,
+                         cudaStream_t s);
+// the split kernel's shared-memory opt-in (once, outside any stream capture)
+cudaError_t split_setup();
 // 3D variants
 int push2d_smem(int prec, int P0, int P1);
 int push3d_smem(int prec, int P0, int P1, int P2);

@@ -9,6 +9,7 @@ def test_kernels_per_step_counts_injection_and_merge():
     assert bench.kernels_per_step(True) == 10
     assert bench.kernels_per_step(False, True) == 10
     assert bench.kernels_per_step(True, True) == 11
+    assert bench.kernels_per_step(True, True, True) == 14
 
 
 def _args(**kw):

@@ -156,3 +156,15 @@ def test_module_level_loads_check_sizes_before_the_library_reads_them():
             binding.pic_load_fields(ctypes.c_void_p(12345), E, B)
     finally:
         binding._ncell.pop(12345, None)
+
+
+def test_split_configuration_is_validated():
+    """split_below in [0, 64] and a finite split_wmin >= 0 (pure host-side validation:
+    pic_required_bytes returns 0 for an invalid config)."""
+    w = inputs.thermal2d(nx=64, ny=64, patch=(16, 16))
+    ok = binding.make_config(w["params"], capacity=1000, split_below=4, split_wmin=0.1)
+    assert binding.pic_required_bytes(ok) > 0
+    for kw in (dict(split_below=65, split_wmin=0.1), dict(split_below=-1),
+               dict(split_below=4, split_wmin=-1.0), dict(split_below=4, split_wmin=float("nan"))):
+        bad = binding.make_config(w["params"], capacity=1000, **kw)
+        assert binding.pic_required_bytes(bad) == 0, kw
