@@ -203,7 +203,17 @@ enum {
                                    particles removed by merging, and a 5th,
                                    particles added by splitting, when out_bytes
                                    allows                                         */
-    PIC_DIAG_EX_AXIS = 7        /* nx float64: Ex on the row (and plane) ny/2      */
+    PIC_DIAG_EX_AXIS = 7,       /* nx float64: Ex on the row (and plane) ny/2      */
+    PIC_DIAG_QUEUE = 8          /* int32 m, then m x 4 int32 {sim, patch, first,
+                                   count}: the work items of the last step's queue
+                                   (built from the patch counts at the start of that
+                                   step): full chunks of `chunk` particles in patch
+                                   order, then each patch's remainder in 64 buckets of
+                                   decreasing size (an approximate largest-first order;
+                                   the order inside a bucket is not fixed); with the
+                                   static mapping one item per non-empty patch in patch
+                                   order. Sec. 3: load = SP count, so the largest loads
+                                   are handed out first                          */
 };
 pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);
 

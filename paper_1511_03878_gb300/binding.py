@@ -19,7 +19,8 @@ PIC_ERR_CUDA, PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT = -4, -5, -6
 PIC_FP64, PIC_FP32, PIC_DF64 = 0, 1, 2
 PIC_MAP_QUEUE, PIC_MAP_STATIC = 0, 1
 (PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_FIELDS, PIC_DIAG_PARTICLES,
- PIC_DIAG_NUM_PARTICLES, PIC_DIAG_PATCH_COUNTS, PIC_DIAG_STEP, PIC_DIAG_EX_AXIS) = range(8)
+ PIC_DIAG_NUM_PARTICLES, PIC_DIAG_PATCH_COUNTS, PIC_DIAG_STEP, PIC_DIAG_EX_AXIS,
+ PIC_DIAG_QUEUE) = range(9)
 
 STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
                 -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NUMERIC",
@@ -430,6 +431,16 @@ class Sim:
 
     def repacks(self) -> int:
         return int(np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)[2])
+
+    def queue(self):
+        """The last step's work items as an (m, 4) int32 array {sim, patch, first, count}."""
+        cap = 4 + 16 * (2 * self.npatch + int(self.cfg.capacity) // max(1, self.chunk_used()) + 64)
+        b = pic_diag(self.h, PIC_DIAG_QUEUE, cap)
+        m = int(np.frombuffer(b[:4], dtype=np.int32)[0])
+        return np.frombuffer(b[4:4 + 16 * m], dtype=np.int32).reshape(m, 4).copy()
+
+    def chunk_used(self) -> int:
+        return int(self.cfg.chunk) if self.cfg.chunk > 0 else 2048
 
     def ex_axis(self):
         return np.frombuffer(pic_diag(self.h, PIC_DIAG_EX_AXIS, 8 * self.cfg.n[0]),

@@ -1124,6 +1124,20 @@ static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, s
             if (written) *written = b;
             return PIC_OK;
         }
+        case PIC_DIAG_QUEUE: {
+            int nitems = 0;
+            CK(cudaMemcpy(&nitems, s->L.B.nitems, sizeof(int), cudaMemcpyDeviceToHost),
+               "read queue length");
+            const size_t b = sizeof(int) + (size_t)nitems * sizeof(int4);
+            if (!need(b)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            static_cast<int*>(out)[0] = nitems;
+            if (nitems > 0)
+                CK(cudaMemcpy(static_cast<int*>(out) + 1, s->L.B.items, nitems * sizeof(int4),
+                              cudaMemcpyDeviceToHost),
+                   "read queue");
+            if (written) *written = b;
+            return PIC_OK;
+        }
         default:
             return fail(&s->err, PIC_ERR_INVALID, "unknown diagnostic kind");
     }
