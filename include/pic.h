@@ -284,6 +284,30 @@ pic_status pic_gauss_residual_2d_static(long long n, const double* x, const doub
                                         int nx, int ny, double dx, double dy, int window,
                                         void* cuda_stream);
 
+/* ---- patch decomposition across ranks (host only; Sec. 3.1, Figs. 3-4) ----
+ * The paper balances load between MPI processes by ordering the patches along a
+ * Hilbert curve, giving each process a contiguous segment of that order whose total
+ * load (SP count, Sec. 3) is balanced, and moving patches between processes when the
+ * loads change. These two calls compute the order and the segments; moving the patches'
+ * particles and fields is the caller's (paper_1511_03878_gb300/decomp.py does it over
+ * torch.distributed). Neither touches a GPU.
+ *
+ * pic_hilbert_order: order[k] = the index (x fastest) of the k-th patch along the
+ * Hilbert curve of the smallest 2^b x 2^b (x 2^b) box holding the np[0] x np[1]
+ * (x np[2]) patches, restricted to the patches that exist (consecutive patches are
+ * face neighbours when every np[a] is the same power of two). order holds
+ * np[0] np[1] (np[2]) ints, caller-owned. PIC_ERR_INVALID for dims other than 2 or 3,
+ * np[a] < 1 or more than 2^30 patches. */
+pic_status pic_hilbert_order(int dims, const int np[3], int* order);
+
+/* pic_partition: splits n loads (>= 0, in curve order) into nranks contiguous segments,
+ * each of at least one patch, with the largest segment load as small as possible
+ * (within 1e-12 relative): rank r owns positions first[r] .. first[r+1]-1; first holds
+ * nranks + 1 ints (first[nranks] = n), caller-owned. *max_load (if not NULL) receives the
+ * largest segment load. PIC_ERR_INVALID for nranks outside [1, n] or a negative or
+ * non-finite load. */
+pic_status pic_partition(int n, const double* load, int nranks, int* first, double* max_load);
+
 /* Failure-path self-test of the bounded device waits (the paper has no counterpart). Every wait of the library's
  * kernels on an asynchronous transfer (the mbarrier of a TMA tile load) gives up after
  * about 2^31 SM clocks (about a second) and latches a status bit instead of hanging.

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
 EXPORTS = ("pic_config_bytes", "pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
            "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
            "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
-           "pic_batch_destroy", "pic_gauss_residual_2d_static", "pic_selftest_bounded_wait")
+           "pic_batch_destroy", "pic_gauss_residual_2d_static", "pic_selftest_bounded_wait",
+           "pic_hilbert_order", "pic_partition")
 PIC_STATIC_MAX_CELLS = 1 << 20
 
 
@@ -114,6 +115,10 @@ def lib():
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_selftest_bounded_wait.restype = ctypes.c_int
         L.pic_selftest_bounded_wait.argtypes = [vp]
+        L.pic_hilbert_order.restype = ctypes.c_int
+        L.pic_hilbert_order.argtypes = [ctypes.c_int, ip, ip]
+        L.pic_partition.restype = ctypes.c_int
+        L.pic_partition.argtypes = [ctypes.c_int, dp, ctypes.c_int, ip, dp]
         L.pic_gauss_residual_2d_static.restype = ctypes.c_int
         L.pic_gauss_residual_2d_static.argtypes = (
             [ctypes.c_longlong, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, ctypes.c_int,
@@ -309,6 +314,24 @@ def pic_gauss_residual_2d_static(n, x_ptr, y_ptr, w_ptr, q, ex_ptr, ey_ptr, rho_
         int(n), vp(x_ptr), vp(y_ptr), vp(w_ptr), float(q), vp(ex_ptr), vp(ey_ptr),
         vp(rho_bg_ptr) if rho_bg_ptr else None, vp(out_ptr), int(nx), int(ny), float(dx),
         float(dy), int(window), vp(stream_ptr) if stream_ptr else None))
+
+
+def pic_hilbert_order(dims: int, np_patches) -> np.ndarray:
+    """Patch indices (x fastest) in Hilbert-curve order (host only)."""
+    n3 = np.ascontiguousarray(list(np_patches) + [1] * (3 - len(np_patches)), dtype=np.int32)
+    out = np.zeros(int(np.prod(n3[:dims])), dtype=np.int32)
+    _check(lib().pic_hilbert_order(int(dims), _ip(n3), _ip(out)))
+    return out
+
+
+def pic_partition(load, nranks: int):
+    """Contiguous segments of `load` (curve order) for `nranks` ranks with the smallest
+    largest segment load (host only): returns (first[nranks + 1], max_load)."""
+    load = np.ascontiguousarray(load, dtype=np.float64)
+    first = np.zeros(nranks + 1, dtype=np.int32)
+    mx = ctypes.c_double(0.0)
+    _check(lib().pic_partition(len(load), _dp(load), int(nranks), _ip(first), ctypes.byref(mx)))
+    return first, mx.value
 
 
 def check_workload(workload: dict, ncell: int, rho_bg=None):
