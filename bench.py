@@ -923,6 +923,8 @@ def main():
     clocks = ClockSampler(local)
     others = [] if args.no_variant or args.variants == "none" else [
         v for v in args.variants.split(",") if v and v != args.precision]
+    if w["params"]["dims"] == 3:  # the double-word precision is 2D only
+        others = [v for v in others if v != "df64"]
     layouts = {}
     for v in [args.precision] + others:
         wl, ch, rec = launch_layout(args, wt, v)

@@ -62,7 +62,8 @@ typedef enum {
  *   PIC_DF64  double-word: every real held and computed as a pair of binary32 numbers
  *             (hi + lo, about 48 significant bits), particles as cell index + pair
  *             offset. FP64-class accuracy (relative errors of a few 2^-48) from FP32
- *             arithmetic, for GPUs whose FP64 units are a small fraction of FP32. */
+ *             arithmetic, for GPUs whose FP64 units are a small fraction of FP32. 2D
+ *             only (a 3D config with it is invalid). */
 enum { PIC_FP64 = 0, PIC_FP32 = 1, PIC_DF64 = 2 };
 
 /* Work distribution of the particle kernel. */

@@ -12,6 +12,21 @@
 
 namespace pic {
 
+// 3D kernels exist in FP64 and FP32; the double-word precision is 2D only (in 3D it
+// measured no faster than FP64: 6.19e8 against 6.51e8 pushes/s on the 3D LWFA window,
+// at 255 registers and one CTA per SM). Other codes run nothing.
+#define PIC_DISPATCH_3D(prec, body) \
+    do {                            \
+        if ((prec) == 0) {          \
+            using T = double;       \
+            body;                   \
+        } else if ((prec) == 1) {   \
+            using T = float;        \
+            body;                   \
+        }                           \
+    } while (0)
+
+
 template <typename T>
 __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, const T Sx[3],
                                       const T Sy[3], const T Sz[3]) {
@@ -27,31 +42,6 @@ __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, 
         r += Sz[c] * plane;
     }
     return r;
-}
-
-// double-word: compensated dot products, the three z planes in a rolled loop (the plane
-// weight rotating through registers) to keep the kernel's code within the
-// instruction cache
-__device__ __forceinline__ df64 gather27(const df64* __restrict__ f, int BX, int BXY,
-                                        const df64 Sx[3], const df64 Sy[3], const df64 Sz[3]) {
-    Dot2 outer;
-    df64 z0 = Sz[0], z1 = Sz[1], z2 = Sz[2];
-#pragma unroll 1
-    for (int c = 0; c < 3; c++) {
-        Dot2 plane;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            const df64* row = f + c * BXY + b * BX;
-            Dot2 inner;
-            inner.add(Sx[0], row[0]);
-            inner.add(Sx[1], row[1]);
-            inner.add(Sx[2], row[2]);
-            plane.add(Sy[b], inner.result());
-        }
-        outer.add(z0, plane.result());
-        z0 = z1, z1 = z2;
-    }
-    return outer.result();
 }
 
 template <typename T>
@@ -97,8 +87,9 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
     for (int a = 0; a < 3; a++) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
         const T c1 = q[a] * DS[a][0], c2 = q[a] * (DS[a][0] + DS[a][1]);
-        if constexpr (std::is_same<T, df64>::value) {
-            // rolled over kc, the c-axis weights rotating through registers
+        if constexpr (is_f64<T>::value) {
+            // FP64: rolled over kc, the c-axis weights rotating through registers (a
+            // compact body; FP32 keeps the unrolled loops)
             T s0 = S0[c][0], s1 = S0[c][1], s2 = S0[c][2];
             T d0 = DS[c][0], d1_ = DS[c][1], d2 = DS[c][2];
 #pragma unroll 1
@@ -140,19 +131,10 @@ __device__ __forceinline__ void handoff_copy3d(const SimDev& S, int slot, int m,
     S.mid[m] = pid;
 }
 
+// FP64: one CTA per SM (236 registers). Two (128 registers, with spills) measured 1 %
+// slower on the 3D stress case.
 template <typename T>
-#ifndef PIC_DF64_3D_MINB
-#define PIC_DF64_3D_MINB 1
-#endif
-// FP64: one CTA per SM (210 registers). Two (128 registers, 564 bytes of spills) measured
-// 1 % slower on the 3D stress case.
-#ifndef PIC_F64_3D_MINB
-#define PIC_F64_3D_MINB 1
-#endif
-__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
-                                                ? 2
-                                                : (std::is_same<T, df64>::value ? PIC_DF64_3D_MINB
-                                                                               : PIC_F64_3D_MINB))
+__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 1)
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType3D<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -305,35 +287,12 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                 }
                 T E[3], B[3];
                 // Ex (d,p,p) Ey (p,d,p) Ez (p,p,d) Bx (p,d,d) By (d,p,d) Bz (d,d,p)
-                if constexpr (std::is_same<T, df64>::value) {
-                    // one rolled loop over the six components; results rotate
-                    T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
-#pragma unroll 1
-                    for (int c = 0; c < 6; c++) {
-                        const bool xd = c == 0 || c == 4 || c == 5;
-                        const bool yd = c == 1 || c == 3 || c == 5;
-                        const bool zd = c == 2 || c == 3 || c == 4;
-                        T sx[3], sy[3], sz[3];
-#pragma unroll
-                        for (int k = 0; k < 3; k++) {
-                            sx[k] = xd ? Sd[0][k] : Sp[0][k];
-                            sy[k] = yd ? Sd[1][k] : Sp[1][k];
-                            sz[k] = zd ? Sd[2][k] : Sp[2][k];
-                        }
-                        const T g = gather27(Ft + c * BXY * BZ + (zd ? td[2] : tp[2]) * BXY +
-                                                 (yd ? td[1] : tp[1]) * BX + (xd ? td[0] : tp[0]),
-                                             BX, BXY, sx, sy, sz);
-                        r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5, r5 = g;
-                    }
-                    E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
-                } else {
                 E[0] = gather27(Ft + 0 * BXY * BZ + tp[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sp[2]);
                 E[1] = gather27(Ft + 1 * BXY * BZ + tp[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sp[2]);
                 E[2] = gather27(Ft + 2 * BXY * BZ + td[2] * BXY + tp[1] * BX + tp[0], BX, BXY, Sp[0], Sp[1], Sd[2]);
                 B[0] = gather27(Ft + 3 * BXY * BZ + td[2] * BXY + td[1] * BX + tp[0], BX, BXY, Sp[0], Sd[1], Sd[2]);
                 B[1] = gather27(Ft + 4 * BXY * BZ + td[2] * BXY + tp[1] * BX + td[0], BX, BXY, Sd[0], Sp[1], Sd[2]);
                 B[2] = gather27(Ft + 5 * BXY * BZ + tp[2] * BXY + td[1] * BX + td[0], BX, BXY, Sd[0], Sd[1], Sp[2]);
-                }
                 const T ig = boris(eps, E, B, u);
                 const T v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
                 int np1[3], sh[3];
@@ -409,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;
-                        if constexpr (std::is_same<T, df64>::value) {
+                        if constexpr (is_f64<T>::value) {
                             T s0 = ax[c].S0[0], s1 = ax[c].S0[1], s2 = ax[c].S0[2], s3 = ax[c].S0[3];
                             T d0 = ax[c].DS[0], d1 = ax[c].DS[1], d2 = ax[c].DS[2], d3 = ax[c].DS[3];
 #pragma unroll 1
@@ -595,7 +554,7 @@ int smem_bytes_3d(int P0, int P1, int P2) {
 
 int push3d_smem(int prec, int P0, int P1, int P2) {
     int sb = 0;
-    PIC_DISPATCH(prec, (sb = smem_bytes_3d<T>(P0, P1, P2)));
+    PIC_DISPATCH_3D(prec, (sb = smem_bytes_3d<T>(P0, P1, P2)));
     return sb;
 }
 
@@ -617,7 +576,7 @@ int push3d_occupancy(int prec, int P0, int P1, int P2, int* smem_bytes) {
     const int sb = push3d_smem(prec, P0, P1, P2);
     *smem_bytes = sb;
     int blocks = 0;
-    PIC_DISPATCH(prec, (blocks = occupancy_3d<T>(sb)));
+    PIC_DISPATCH_3D(prec, (blocks = occupancy_3d<T>(sb)));
     return blocks;
 }
 
@@ -625,7 +584,8 @@ cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0,
                           int grid, cudaStream_t s) {
     const int sb = push3d_smem(prec, P0, P1, P2);
     const int static_map = mapping == 1;
-    PIC_DISPATCH(prec, (push3d_kernel<T><<<grid, kThreads, sb, s>>>(bd_dev, static_map)));
+    if (prec != 0 && prec != 1) return cudaErrorInvalidValue;
+    PIC_DISPATCH_3D(prec, (push3d_kernel<T><<<grid, kThreads, sb, s>>>(bd_dev, static_map)));
     return cudaGetLastError();
 }
 

@@ -105,6 +105,7 @@ const char* validate(const pic_config* c) {
         push2d_smem(c->precision, c->patch[0], c->patch[1]) + kPush2DStatic > 227 * 1024)
         return "2D patch tile does not fit in shared memory";
     if (c->dims == 3) {
+        if (c->precision == PIC_DF64) return "the double-word precision is 2D only";
         if (c->n[0] > 2048 || c->n[1] > 2048 || c->n[2] > 1024) return "3D grid too large";
         if (push3d_smem(c->precision, c->patch[0], c->patch[1], c->patch[2]) + kPush2DStatic >
             227 * 1024)

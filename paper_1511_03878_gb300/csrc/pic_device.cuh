@@ -202,20 +202,15 @@ struct JType<df64> {
     using type = long long;  // int64 fixed-point shared-memory current (see jprod)
 };
 
-// 3D tile type: the 3D FP64 kernel keeps FP64 shared atomics unless built with
-// PIC_3D_F64_FIXED (its occupancy is register-bound, one CTA per SM, and the integer
-// conversion of 54 to 144 contributions per particle costs more issue slots than the
-// FP64 pipe time it frees)
+// 3D tile type: the same as 2D (int64 fixed point for FP64: shared FP64 atomics run on
+// the FP64 pipe). With the FP64 kernel's deposit loops rolled, the integer conversion of
+// the 54 to 144 contributions per particle is hidden: measured level with the FP64 tile
+// on the 3D stress case and 7 % faster on the 3D LWFA window (the FP64 tile with
+// unrolled loops was the faster of the unrolled pair, by 24 %).
 template <typename T>
 struct JType3D {
     using type = typename JType<T>::type;
 };
-#ifndef PIC_3D_F64_FIXED
-template <>
-struct JType3D<double> {
-    using type = double;
-};
-#endif
 
 // fixed-point exponent of an item of `count` particles: a tile entry sums at most
 // `count` contributions, each below 2^cmax_exp, and must stay below 2^62 (int64 tile)

@@ -120,7 +120,7 @@ def test_lwfa_2d_window(binding, prec, steps, tol):
     assert steps == 1 or shifts >= 10
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("prec", ["fp64"])  # the double-word precision is 2D only
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (12, 1e-9)])
 def test_3d_periodic(binding, prec, steps, tol):
     w = sixth(inputs.stress3d(n=(32, 16, 16), patch=(8, 8, 8), total=60000, cfl=CFL6))
@@ -130,7 +130,7 @@ def test_3d_periodic(binding, prec, steps, tol):
     assert not bad, (bad, errs)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("prec", ["fp64"])  # the double-word precision is 2D only
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (12, 1e-9)])
 def test_3d_window(binding, prec, steps, tol):
     w = small_lwfa3d()

@@ -207,6 +207,8 @@ def test_load_places_and_converts_every_particle(binding, prec, dims, capfactor)
     cases: the domain's origin, a cell face, a position whose offset rounds to 1 in
     float32, and one just under the domain's end whose cell coordinate rounds to n.
     The fields come back as given, and the on-axis diagnostic is their Ex row."""
+    if dims == 3 and prec == 2:
+        pytest.skip("the double-word precision is 2D only")
     if dims == 2:
         w = inputs.thermal2d(nx=64, ny=48, d=0.65, seed=3, patch=(16, 16))
     else:
@@ -459,7 +461,7 @@ def compare3d(sim, o, params, tol):
     return errs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("prec", ["fp64"])  # the double-word precision is 2D only
 @pytest.mark.parametrize("steps,tol", [(1, 1e-12), (10, 1e-9)])
 def test_stress3d_fp64(binding, steps, tol, prec):
     w = stress3d_small()

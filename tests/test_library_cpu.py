@@ -168,3 +168,13 @@ def test_split_configuration_is_validated():
                dict(split_below=4, split_wmin=-1.0), dict(split_below=4, split_wmin=float("nan"))):
         bad = binding.make_config(w["params"], capacity=1000, **kw)
         assert binding.pic_required_bytes(bad) == 0, kw
+
+
+def test_double_word_precision_is_2d_only():
+    """A 3D config with the double-word precision is invalid (in 3D it measured no faster
+    than FP64, so only FP64 and FP32 kernels are built for 3D); 2D accepts it."""
+    w3 = inputs.stress3d(n=(16, 8, 8), patch=(8, 8, 8), total=2000)
+    w2 = inputs.thermal2d(nx=32, ny=16, patch=(16, 16))
+    assert binding.pic_required_bytes(binding.make_config(w3["params"], binding.PIC_DF64, 4000)) == 0
+    assert binding.pic_required_bytes(binding.make_config(w3["params"], binding.PIC_FP64, 4000)) > 0
+    assert binding.pic_required_bytes(binding.make_config(w2["params"], binding.PIC_DF64, 4000)) > 0
