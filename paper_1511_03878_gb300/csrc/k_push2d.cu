@@ -529,36 +529,21 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     }
                 }
             } else {
+                // ---- FP32 and double-word: cell index + offset in [0, 1)
                 // ---- A. take the prefetched state, start loading the next one
                 int ix = 0, iy = 0;
                 T fx = T(0), fy = T(0);
-                double xi0 = 0.0, eta0 = 0.0;  // FP64 path: global cell-unit position
                 T u[3] = {nu0, nu1, nu2};
                 T w = nw;
                 if (valid) {
-                    if constexpr (is_f64<T>::value) {
-                        xi0 = nx0;
-                        eta0 = ny0;
-                        ix = floor_to_int(xi0);
-                        iy = floor_to_int(eta0);
-                        // floors widened back with integer operations (exact)
-                        fx = xi0 - fixed_to_f64(ix, 0);
-                        fy = eta0 - fixed_to_f64(iy, 0);
-                    } else {
-                        ix = nc & 0xFFFF;
-                        iy = (nc >> 16) & 0xFFFF;
-                        fx = nfx;
-                        fy = nfy;
-                    }
+                    ix = nc & 0xFFFF;
+                    iy = (nc >> 16) & 0xFFFF;
+                    fx = nfx;
+                    fy = nfy;
                 }
                 if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
                 // nodes and deltas: primal node = ix + (f >= 1/2), dual node = ix
-                bool hx, hy;
-                if constexpr (is_f64<T>::value) {
-                    hx = ge_half(fx), hy = ge_half(fy);  // 0 <= f < 1
-                } else {
-                    hx = fx >= T(0.5), hy = fy >= T(0.5);
-                }
+                const bool hx = fx >= T(0.5), hy = fy >= T(0.5);
                 const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
                 const T dxp = hx ? fx - T(1) : fx, dyp = hy ? fy - T(1) : fy;
                 const T dxd = fx - T(0.5), dyd = fy - T(0.5);
@@ -572,7 +557,6 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 T Sxp[3], Syp[3];
                 T dxp1 = T(0), dyp1 = T(0), fx1 = T(0), fy1 = T(0), vz = T(0);
                 int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
-                double xi1 = 0.0, eta1 = 0.0;
                 if (ok) {
                     T Sxd[3], Syd[3];
                     shape3(dxp, Sxp);
@@ -585,11 +569,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                         // one rolled loop over Ex Ey Ez Bx By Bz: x primal for Ey Ez Bx,
                         // y primal for Ex Ez By; results rotate through six registers
                         T r0(0.0f), r1(0.0f), r2(0.0f), r3(0.0f), r4(0.0f), r5(0.0f);
-    #pragma unroll 1
+#pragma unroll 1
                         for (int c = 0; c < 6; c++) {
                             const bool xp = c >= 1 && c <= 3, yp = (c & 1) == 0;
                             T sx[3], sy[3];
-    #pragma unroll
+#pragma unroll
                             for (int k = 0; k < 3; k++) {
                                 sx[k] = xp ? Sxp[k] : Sxd[k];
                                 sy[k] = yp ? Syp[k] : Syd[k];
@@ -612,15 +596,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     const T vx = u[0] * ig, vy = u[1] * ig;
                     vz = u[2] * ig;
                     int nxp1, nyp1;
-                    if constexpr (is_f64<T>::value) {
-                        xi1 = xi0 + dtdx * vx;
-                        eta1 = eta0 + dtdy * vy;
-                        const double hx1 = xi1 + 0.5, hy1 = eta1 + 0.5;
-                        nxp1 = floor_to_int(hx1);
-                        nyp1 = floor_to_int(hy1);
-                        dxp1 = xi1 - fixed_to_f64(nxp1, 0);
-                        dyp1 = eta1 - fixed_to_f64(nyp1, 0);
-                    } else {
+                    {
                         fx1 = fx + dtdx * vx;
                         fy1 = fy + dtdy * vy;
                         ix1 = ix;
@@ -673,45 +649,22 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
 
                     // ---- D. boundaries and destination patch
                     bool del = false;
-                    if constexpr (is_f64<T>::value) {
-                        // the comparisons with 0 and n are taken on integer floors (the
-                        // same decisions as comparing the doubles, off the FP64 pipe)
-                        const int fxi = floor_to_int(xi1);
-                        double xs = xi1 - (double)shift;
-                        if (window) {
-                            del = fxi < 0 || fxi >= nx || fxi - shift < 0;
-                        } else {
-                            if (fxi - shift < 0) xs += (double)nx;
-                            if (floor_to_int(xs) >= nx) xs -= (double)nx;
-                        }
-                        if (floor_to_int(eta1) < 0) eta1 += (double)ny;
-                        if (floor_to_int(eta1) >= ny) eta1 -= (double)ny;
-                        xi1 = xs;
-                        ix1 = floor_to_int(xi1);
-                        iy1 = floor_to_int(eta1);
+                    if (window) {
+                        del = ix1 < 0 || ix1 >= nx;
+                        ix1 -= shift;
+                        del = del || ix1 < 0;
                     } else {
-                        if (window) {
-                            del = ix1 < 0 || ix1 >= nx;
-                            ix1 -= shift;
-                            del = del || ix1 < 0;
-                        } else {
-                            ix1 = wrapi(ix1, nx);
-                        }
-                        iy1 = wrapi(iy1, ny);
+                        ix1 = wrapi(ix1, nx);
                     }
+                    iy1 = wrapi(iy1, ny);
                     if (!del) {
                         dest = ix1 / P0 + S.np[0] * (iy1 / P1);
                         leave = dest != patch;
                         // the new state goes to the particle's own slot, also when it leaves:
                         // the hand-off after the item copies it from there
-                        if constexpr (is_f64<T>::value) {
-                            reinterpret_cast<double*>(S.xi[0])[slot] = xi1;
-                            reinterpret_cast<double*>(S.xi[1])[slot] = eta1;
-                        } else {
-                            S.cell[slot] = ix1 | (iy1 << 16);
-                            reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
-                            reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
-                        }
+                        S.cell[slot] = ix1 | (iy1 << 16);
+                        reinterpret_cast<T*>(S.xi[0])[slot] = fx1;
+                        reinterpret_cast<T*>(S.xi[1])[slot] = fy1;
                         U0[slot] = u[0];
                         U1[slot] = u[1];
                         U2[slot] = u[2];

@@ -277,9 +277,6 @@ __device__ __forceinline__ int floor_to_int(double x) {
     if (neg) ip = ((ip << sh) != m) ? -(ip + 1) : -ip;
     return (int)ip;
 }
-// x >= 1/2 for x >= 0, from the high word (0.5 = 0x3FE00000 00000000)
-__device__ __forceinline__ bool ge_half(double x) { return __double2hiint(x) >= 0x3FE00000; }
-__device__ __forceinline__ bool ge_half(float x) { return x >= 0.5f; }
 
 // double -> float rounded to nearest even with integer operations only when the result
 // is a normal float or zero (the conversion instruction runs on the FP64 pipe); other
