@@ -2,13 +2,16 @@
 //
 // GB300 executes FP64 at 1/64 of its FP32 rate, while its integer units run at half the
 // FP32 rate, so an FP64 particle kernel is bound by the FP64 pipe. Every quantity of the
-// order-2 PIC cycle that is not itself a physical result of FP64 arithmetic -- a
-// particle's in-cell offset, its quadratic B-spline weights, the Esirkepov shape
-// differences, path-averaged weights and running sums, and the products that form a
-// current contribution -- is computed here exactly or to 2^-62 in int64 / 128-bit
-// integer arithmetic. That is finer than FP64 rounding for values in [-1, 1] (2^-53
-// relative, 2^-54 absolute near 1), so the FP64 results built from them (fields at the
-// particle, current) agree with an all-FP64 evaluation to rounding.
+// order-2 PIC cycle that is not itself a result of the FP64 push -- a particle's in-cell
+// offset, its quadratic B-spline weights, the field gather (from a fixed-point copy of
+// the staged field tile), the Esirkepov shape differences, path-averaged weights and
+// running sums, and the products that form a current contribution -- is computed here
+// exactly or to a few units of 2^-62 (2^-60 of the tile's largest field for the gather)
+// in int64 arithmetic built from 32x32->64-bit products. That is finer than FP64
+// rounding for values in [-1, 1] (2^-53 relative, 2^-54 absolute near 1), so the FP64
+// results built from them (fields at the particle, current) agree with an all-FP64
+// evaluation to rounding. The FP64 pipe keeps the Boris push, the move and the charge
+// factors.
 #pragma once
 #include <stdint.h>
 
@@ -69,15 +72,90 @@ __device__ __forceinline__ void split62(double x, int& i, long long& f) {
 // (S[k] in 2^62 fixed point): S0 = (1/2 - delta)^2 / 2, S1 = 3/4 - delta^2,
 // S2 = (1/2 + delta)^2 / 2, written as q -/+ delta/2 with q = delta^2/2 + 1/8.
 __device__ __forceinline__ void shape62(long long D, long long S[3]) {
-    const unsigned long long a = (unsigned long long)(D < 0 ? -D : D);  // <= 2^61
-    const unsigned long long hi = __umul64hi(a, a);
-    const unsigned long long lo = a * a;
-    const long long d2 = (long long)((hi << 2) | (lo >> 62));  // delta^2 2^62 <= 2^60
+    // delta^2 2^62 (<= 2^60) from |D| = ah 2^31 + al: ah^2 + 2 ah al 2^-31, the al^2 term
+    // (below one unit) left out; within two units below the exact square
+    const long long a = D < 0 ? -D : D;  // <= 2^61
+    const int ah = (int)(a >> 31), al = (int)(a & 0x7FFFFFFFLL);
+    const long long d2 = (long long)ah * ah + (((long long)ah * al) >> 30);
     const long long h = D >> 1;                                 // delta/2
     const long long q = (d2 >> 1) + (1LL << 59);                // delta^2/2 + 1/8
     S[0] = q - h;
     S[1] = 3LL * (1LL << 60) - d2;
     S[2] = q + h;
+}
+
+// ---- Field gather in fixed point. The FP64 kernel converts its staged field tile once per
+// load: each component gets the exponent s that puts the tile's largest magnitude just
+// below 2^60, and each entry F becomes round(F 2^s) = h 2^31 + l (0 <= l < 2^31, |h| <
+// 2^29), stored as the 32-bit pair (l, h) in the 8 bytes of the double it replaces.
+
+// exponent s of a component whose largest biased FP64 exponent field is emax:
+// |F| < 2^(emax - 1022), so |F| 2^s < 2^60
+__device__ __forceinline__ int fix_field_exp(int emax) { return 1082 - emax; }
+
+// In-place conversion of the staged FP64 field tile (6 components of `pl` entries) to
+// split fixed point; s_emax[6] (zeroed by the caller before the barrier that precedes
+// this call) receives each component's largest exponent field (0x7FF: a non-finite
+// entry). Every thread of the CTA calls it; it ends before the caller's next barrier
+// only for the calling thread, so the caller synchronises before the tile is read.
+__device__ __forceinline__ void fix_field_tile(double* F, int pl, int* s_emax) {
+    for (int c = 0; c < 6; c++) {
+        int m = 0;
+        for (int i = threadIdx.x; i < pl; i += blockDim.x) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(F[c * pl + i]);
+            m = max(m, (int)((b >> 52) & 0x7FFu));
+        }
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_emax[c], m);
+    }
+    __syncthreads();  // exponents complete; every entry read before any is overwritten
+    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
+        const int c = e / pl;
+        const int s = fix_field_exp(s_emax[c]);
+        // round(F 2^s): the scaling as an exponent addition (exact), then the hardware
+        // FP64 -> int64 conversion; magnitudes below 1/2 after scaling round to 0
+        const long long b = __double_as_longlong(F[e]);
+        const int eb = (int)((b >> 52) & 0x7FFu);
+        const long long u = (eb == 0 || eb + s < 1022)
+                                ? 0LL
+                                : __double2ll_rn(__longlong_as_double(b + ((long long)s << 52)));
+        reinterpret_cast<int2*>(F)[e] = make_int2((int)(u & 0x7FFFFFFFLL), (int)(u >> 31));
+    }
+}
+
+// A 2^62 weight split as S = h 2^31 + l (0 <= l < 2^31; S >= 0, so h >= 0)
+struct W31 {
+    int h, l;
+};
+__device__ __forceinline__ W31 w31(long long S) {
+    return W31{(int)(S >> 31), (int)(S & 0x7FFFFFFFLL)};
+}
+
+// Order-2 gather of one staggered component from the split fixed-point tile (f: first
+// tap, BX: row stride): sum_b Sy_b sum_a Sx_a F(a, b) in the component's units 2^-s, to
+// within 8 units below. Weights of an axis are non-negative and sum to at most 2^62, so
+// each row's products accumulate in one int64 before a single shift: h-by-h products
+// below 2^60, the cross products below 2^63 together, the l-by-l ones (under a unit
+// each after the shift) left out. Integer multiply-adds only.
+__device__ __forceinline__ long long gather9_fix(const int2* __restrict__ f, int BX,
+                                                 const W31 sx[3], const W31 sy[3]) {
+    long long hh = 0, mid = 0;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const int2* row = f + b * BX;
+        long long rh = 0, rm = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int2 v = row[a];  // (l, h)
+            rh += (long long)sx[a].h * v.y;
+            rm += (long long)sx[a].h * v.x + (long long)sx[a].l * v.y;
+        }
+        const long long r = rh + (rm >> 31);  // |r| < 2^60: split like a tile entry
+        const int rhi = (int)(r >> 31), rlo = (int)(r & 0x7FFFFFFFLL);
+        hh += (long long)sy[b].h * rhi;
+        mid += (long long)sy[b].h * rlo + (long long)sy[b].l * rhi;
+    }
+    return hh + (mid >> 31);
 }
 
 // 2D Esirkepov deposition in fixed point when the particle keeps its nearest nodes on

@@ -248,12 +248,18 @@ __device__ __forceinline__ df64 gather9(const df64* __restrict__ f, int BX, cons
 #ifndef PIC_DF64_MINB
 #define PIC_DF64_MINB 2
 #endif
+#ifndef PIC_F64_THREADS
+#define PIC_F64_THREADS 256
+#endif
+#ifndef PIC_F64_MINB
+#define PIC_F64_MINB 2
+#endif
 #ifndef PIC_F32_MINB
 #define PIC_F32_MINB 3
 #endif
 template <typename T>
 struct Push2DShape {
-    static constexpr int threads = kThreads, min_blocks = 2;
+    static constexpr int threads = PIC_F64_THREADS, min_blocks = PIC_F64_MINB;
 };
 template <>
 struct Push2DShape<float> {
@@ -291,6 +297,9 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
     __shared__ int s_lv_n;
     __shared__ int s_lv_slot[kLeaveList];
     __shared__ int s_lv_dest[kLeaveList];
+    // FP64: largest exponent field of each component of the staged field tile, which
+    // holds the fields in split fixed point (see fix_field_tile)
+    __shared__ int s_femax[6];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -337,6 +346,9 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         }
 
         if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
+            if constexpr (std::is_same<T, double>::value) {
+                if (tid < 6) s_femax[tid] = 0;
+            }
             if (tid == 0) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&mbar, (uint32_t)fbytes);
@@ -349,11 +361,13 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 if (tid == 0) atomicOr(S.status, ST_TIMEOUT);
                 return;
             }
+            if constexpr (std::is_same<T, double>::value)
+                fix_field_tile(reinterpret_cast<double*>(Ft), BX * BY, s_femax);
             loaded_sim = item.x;
             loaded_patch = patch;
             loaded_gen = gen;
         }
-        __syncthreads();  // J tile zeroed
+        __syncthreads();  // J tile zeroed (FP64: field tile converted)
 
         // per-sim constants in the working precision (precomputed on the host)
         T dtdx, dtdy, eps, cjx, cjy, cjz;
@@ -416,6 +430,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 // ---- FP64: in-cell offsets, shapes and every deposit weight, running sum and
                 // tap product in 2^62 fixed point (integer units, 32 times the FP64 rate on
                 // this GPU); the gather, Boris, the move and the charge factors in FP64
+                // a field tile holding a non-finite value cannot be converted: its
+                // particles are reported and dropped like non-finite particles
+                const bool ftile_ok = s_femax[0] < 0x7FF && s_femax[1] < 0x7FF &&
+                                      s_femax[2] < 0x7FF && s_femax[3] < 0x7FF &&
+                                      s_femax[4] < 0x7FF && s_femax[5] < 0x7FF;
                 const double xi0 = nx0, eta0 = ny0;
                 double u[3] = {nu0, nu1, nu2};
                 const double w = nw;
@@ -431,8 +450,9 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
                 const int txp = nxp - px0, txd = ix - px0;
                 const int typ = nyp - py0, tyd = iy - py0;
-                ok = valid && (unsigned)txp <= (unsigned)P0 && (unsigned)typ <= (unsigned)P1 &&
-                     (unsigned)txd < (unsigned)P0 && (unsigned)tyd < (unsigned)P1;
+                ok = valid && ftile_ok && (unsigned)txp <= (unsigned)P0 &&
+                     (unsigned)typ <= (unsigned)P1 && (unsigned)txd < (unsigned)P0 &&
+                     (unsigned)tyd < (unsigned)P1;
                 long long SXP[3], SYP[3], S1X[3], S1Y[3];
                 int sx = 0, sy = 0, ix1 = 0, iy1 = 0;
                 double xi1 = 0.0, eta1 = 0.0, vz = 0.0;
@@ -443,21 +463,29 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     shape62(FX - kHalf62, SXD);
                     shape62(FY - kHalf62, SYD);
                     const int pl = BX * BY;
+                    // the gather on the integer units, from the fixed-point field tile
+                    const int2* Fi = reinterpret_cast<const int2*>(Ft);
                     double E[3], B[3];
-                    double Sxp[3], Syp[3], Sxd[3], Syd[3];
+                    W31 Sxp[3], Syp[3], Sxd[3], Syd[3];
 #pragma unroll
                     for (int k2 = 0; k2 < 3; k2++) {
-                        Sxp[k2] = fixed_to_f64(SXP[k2], 62);
-                        Syp[k2] = fixed_to_f64(SYP[k2], 62);
-                        Sxd[k2] = fixed_to_f64(SXD[k2], 62);
-                        Syd[k2] = fixed_to_f64(SYD[k2], 62);
+                        Sxp[k2] = w31(SXP[k2]);
+                        Syp[k2] = w31(SYP[k2]);
+                        Sxd[k2] = w31(SXD[k2]);
+                        Syd[k2] = w31(SYD[k2]);
                     }
-                    E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
-                    E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                    E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
-                    B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                    B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
-                    B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
+                    E[0] = scaled_to_f64(gather9_fix(Fi + 0 * pl + typ * BX + txd, BX, Sxd, Syp),
+                                        fix_field_exp(s_femax[0]));
+                    E[1] = scaled_to_f64(gather9_fix(Fi + 1 * pl + tyd * BX + txp, BX, Sxp, Syd),
+                                        fix_field_exp(s_femax[1]));
+                    E[2] = scaled_to_f64(gather9_fix(Fi + 2 * pl + typ * BX + txp, BX, Sxp, Syp),
+                                        fix_field_exp(s_femax[2]));
+                    B[0] = scaled_to_f64(gather9_fix(Fi + 3 * pl + tyd * BX + txp, BX, Sxp, Syd),
+                                        fix_field_exp(s_femax[3]));
+                    B[1] = scaled_to_f64(gather9_fix(Fi + 4 * pl + typ * BX + txd, BX, Sxd, Syp),
+                                        fix_field_exp(s_femax[4]));
+                    B[2] = scaled_to_f64(gather9_fix(Fi + 5 * pl + tyd * BX + txd, BX, Sxd, Syd),
+                                        fix_field_exp(s_femax[5]));
                     const double ig = boris(eps, E, B, u);
                     vz = u[2] * ig;
                     xi1 = xi0 + dtdx * (u[0] * ig);
@@ -475,8 +503,8 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
                 if (ok) {
                     // charge factors (carrying the tile's 2^k) as integers
-                    const long long QX = f64_to_fixed(cjxs * w), QY = f64_to_fixed(cjys * w);
-                    const long long QZ = f64_to_fixed(cjzs * w * vz);
+                    const long long QX = __double2ll_rn(cjxs * w), QY = __double2ll_rn(cjys * w);
+                    const long long QZ = __double2ll_rn(cjzs * w * vz);
                     const int t0 = typ * JX + txp;  // stencil node 0 of both axes
                     if (fast) {
                         const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)

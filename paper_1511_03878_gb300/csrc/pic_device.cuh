@@ -343,12 +343,29 @@ __device__ __forceinline__ long long f64_to_fixed_shift(double x, int s) {
 }
 // round(x) as int64 (see above)
 __device__ __forceinline__ long long f64_to_fixed(double x) { return f64_to_fixed_shift(x, 0); }
-// round(a w / 2^62) for a weight w held in 2^62 fixed point (|w| <= 2^62, |a| < 2^62),
-// from the 128-bit product: integer multiplies instead of an FP64 one
+// a w / 2^62 for a weight w held in 2^62 fixed point (|a|, |w| < 2^62), to within one
+// unit either side, unbiased for operands whose low 31 bits are spread evenly, and
+// exactly 0 for a zero operand. Both operands split at bit 31 (the high parts fit 32
+// bits): the high-by-high product and the two cross products (their sum below 2^63),
+// shifted with an offset of 3/4 of a unit; the low-by-low product, below one unit after
+// the division and a quarter on average, is left out, and the offset restores the
+// quarter and the half that the shift's truncation loses on average. Three 32x32->64
+// integer multiply-adds instead of an FP64 multiply (GB300 runs FP64 at 1/64 of its
+// FP32 rate) or a full 128-bit product.
 __device__ __forceinline__ long long fixmul62(long long a, long long w) {
-    const long long hi = __mul64hi(a, w);
-    const unsigned long long lo = (unsigned long long)a * (unsigned long long)w;
-    return hi * 4 + (long long)(lo >> 62) + (long long)((lo >> 61) & 1ULL);
+    const int ah = (int)(a >> 31), wh = (int)(w >> 31);
+    const int al = (int)(a & 0x7FFFFFFFLL), wl = (int)(w & 0x7FFFFFFFLL);
+    long long mid = (long long)ah * wl + (3LL << 29);
+    mid += (long long)al * wh;
+    return (long long)ah * wh + (mid >> 31);
+}
+// v 2^-k as a double: the hardware int64 -> FP64 conversion (one FP64-pipe instruction,
+// rounded to nearest) and the scaling by 2^-k as an exponent subtraction (exact); a
+// result below the normal range flushes to zero
+__device__ __forceinline__ double scaled_to_f64(long long v, int k) {
+    const long long b = __double_as_longlong(__ll2double_rn(v));
+    const int e = (int)((b >> 52) & 0x7FF) - k;
+    return (v == 0 || e <= 0) ? 0.0 : __longlong_as_double(b - ((long long)k << 52));
 }
 // tile value of the product a*b; for the fixed-point tile `a` already carries the factor
 // 2^k (see jscale)
@@ -402,14 +419,21 @@ __device__ __forceinline__ float jscale<int, float>(float q, float scale) {
 __device__ __forceinline__ void jatomic(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jatomic(int* p, int v) { atomicAdd(p, v); }
+// 64-bit tile add as two 32-bit shared-memory atomics (measured: 64-bit shared-memory
+// atomic adds run at a sixth of the 32-bit rate on this GPU). The low word's add returns
+// the word it replaced, which gives the carry into the high word exactly: after all adds
+// the 64-bit entry holds the exact sum, whatever their order.
 __device__ __forceinline__ void jatomic(long long* p, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+    unsigned* w = reinterpret_cast<unsigned*>(p);  // little-endian: low word first
+    const unsigned lo = (unsigned)v;
+    const unsigned old = atomicAdd(w, lo);
+    atomicAdd(reinterpret_cast<int*>(w + 1), (int)(v >> 32) + (old + lo < old ? 1 : 0));
 }
 // tile entry -> FP64 for the global current (k: the fixed-point exponent)
 __device__ __forceinline__ double jflush(float v, int) { return widen_f32(v); }
 __device__ __forceinline__ double jflush(double v, int) { return v; }
-__device__ __forceinline__ double jflush(long long v, int k) { return fixed_to_f64(v, k); }
-__device__ __forceinline__ double jflush(int v, int k) { return fixed_to_f64((long long)v, k); }
+__device__ __forceinline__ double jflush(long long v, int k) { return scaled_to_f64(v, k); }
+__device__ __forceinline__ double jflush(int v, int k) { return scaled_to_f64((long long)v, k); }
 
 
 // Esirkepov data of one axis on a four-node window that always holds both the old
