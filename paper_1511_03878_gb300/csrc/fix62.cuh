@@ -76,7 +76,7 @@ __device__ __forceinline__ void shape62(long long D, long long S[3]) {
     // (below one unit) left out; within two units below the exact square
     const long long a = D < 0 ? -D : D;  // <= 2^61
     const int ah = (int)(a >> 31), al = (int)(a & 0x7FFFFFFFLL);
-    const long long d2 = (long long)ah * ah + (((long long)ah * al) >> 30);
+    const long long d2 = mad_wide(ah, ah, mad_wide(ah, al, 0LL) >> 30);
     const long long h = D >> 1;                                 // delta/2
     const long long q = (d2 >> 1) + (1LL << 59);                // delta^2/2 + 1/8
     S[0] = q - h;
@@ -147,13 +147,13 @@ __device__ __forceinline__ long long gather9_fix(const int2* __restrict__ f, int
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const int2 v = row[a];  // (l, h)
-            rh += (long long)sx[a].h * v.y;
-            rm += (long long)sx[a].h * v.x + (long long)sx[a].l * v.y;
+            rh = mad_wide(sx[a].h, v.y, rh);
+            rm = mad_wide(sx[a].l, v.y, mad_wide(sx[a].h, v.x, rm));
         }
         const long long r = rh + (rm >> 31);  // |r| < 2^60: split like a tile entry
         const int rhi = (int)(r >> 31), rlo = (int)(r & 0x7FFFFFFFLL);
-        hh += (long long)sy[b].h * rhi;
-        mid += (long long)sy[b].h * rlo + (long long)sy[b].l * rhi;
+        hh = mad_wide(sy[b].h, rhi, hh);
+        mid = mad_wide(sy[b].l, rhi, mad_wide(sy[b].h, rlo, mid));
     }
     return hh + (mid >> 31);
 }

@@ -444,7 +444,6 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     split62(xi0, ix, FX);
                     split62(eta0, iy, FY);
                 }
-                if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
                 // primal node = ix + (f >= 1/2), dual node = ix
                 const bool hx = FX >= kHalf62, hy = FY >= kHalf62;
                 const int nxp = ix + (hx ? 1 : 0), nyp = iy + (hy ? 1 : 0);
@@ -474,18 +473,26 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                         Sxd[k2] = w31(SXD[k2]);
                         Syd[k2] = w31(SYD[k2]);
                     }
-                    E[0] = scaled_to_f64(gather9_fix(Fi + 0 * pl + typ * BX + txd, BX, Sxd, Syp),
-                                        fix_field_exp(s_femax[0]));
-                    E[1] = scaled_to_f64(gather9_fix(Fi + 1 * pl + tyd * BX + txp, BX, Sxp, Syd),
-                                        fix_field_exp(s_femax[1]));
-                    E[2] = scaled_to_f64(gather9_fix(Fi + 2 * pl + typ * BX + txp, BX, Sxp, Syp),
-                                        fix_field_exp(s_femax[2]));
-                    B[0] = scaled_to_f64(gather9_fix(Fi + 3 * pl + tyd * BX + txp, BX, Sxp, Syd),
-                                        fix_field_exp(s_femax[3]));
-                    B[1] = scaled_to_f64(gather9_fix(Fi + 4 * pl + typ * BX + txd, BX, Sxd, Syp),
-                                        fix_field_exp(s_femax[4]));
-                    B[2] = scaled_to_f64(gather9_fix(Fi + 5 * pl + tyd * BX + txd, BX, Sxd, Syd),
-                                        fix_field_exp(s_femax[5]));
+                    {
+                        // one rolled loop over Ex Ey Ez Bx By Bz: x primal for Ey Ez Bx, y
+                        // primal for Ex Ez By; results rotate through six registers
+                        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0, r5 = 0.0;
+#pragma unroll 1
+                        for (int c = 0; c < 6; c++) {
+                            const bool xp = c >= 1 && c <= 3, yp = (c & 1) == 0;
+                            W31 gx[3], gy[3];
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; k2++) {
+                                gx[k2] = xp ? Sxp[k2] : Sxd[k2];
+                                gy[k2] = yp ? Syp[k2] : Syd[k2];
+                            }
+                            const long long v = gather9_fix(
+                                Fi + c * pl + (yp ? typ : tyd) * BX + (xp ? txp : txd), BX, gx, gy);
+                            r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5;
+                            r5 = scaled_to_f64(v, fix_field_exp(s_femax[c]));
+                        }
+                        E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
+                    }
                     const double ig = boris(eps, E, B, u);
                     vz = u[2] * ig;
                     xi1 = xi0 + dtdx * (u[0] * ig);
@@ -500,21 +507,15 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     sy = iy1 + (h1y ? 1 : 0) - nyp;
                     ok = (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1);
                 }
-                const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
+                long long QX = 0, QY = 0, QZ = 0;
                 if (ok) {
                     // charge factors (carrying the tile's 2^k) as integers
-                    const long long QX = __double2ll_rn(cjxs * w), QY = __double2ll_rn(cjys * w);
-                    const long long QZ = __double2ll_rn(cjzs * w * vz);
-                    const int t0 = typ * JX + txp;  // stencil node 0 of both axes
-                    if (fast) {
-                        const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
-                        deposit2d_fast_fix(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX,
-                                           SXP, SYP, S1X, S1Y, QX, QY, QZ);
-                    } else {
-                        deposit2d_general_fix(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0, JX,
-                                              SXP, SYP, S1X, S1Y, sx, sy, QX, QY, QZ);
-                    }
-                    // ---- boundaries and destination patch (decisions on the integer floors)
+                    QX = __double2ll_rn(cjxs * w);
+                    QY = __double2ll_rn(cjys * w);
+                    QZ = __double2ll_rn(cjzs * w * vz);
+                    // ---- boundaries, destination patch (decisions on the integer floors) and
+                    // the new state, stored before the deposit so that only the shapes and
+                    // charge factors stay live through it
                     bool del = false;
                     double xs = xi1;
                     if (window) {
@@ -554,6 +555,20 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                     } else {
                         dest = -1;
                         leave = true;
+                    }
+                }
+                // the next particle's state loads while this one deposits
+                if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
+                const bool fast = __all_sync(0xffffffffu, !ok || (sx == 0 && sy == 0));
+                if (ok) {
+                    const int t0 = typ * JX + txp;  // stencil node 0 of both axes
+                    if (fast) {
+                        const int t1 = t0 + JX + 1;  // stencil nodes (1, 1)
+                        deposit2d_fast_fix(Jt + t1, Jt + jplane + t1, Jt + 2 * jplane + t1, JX,
+                                           SXP, SYP, S1X, S1Y, QX, QY, QZ);
+                    } else {
+                        deposit2d_general_fix(Jt + t0, Jt + jplane + t0, Jt + 2 * jplane + t0, JX,
+                                              SXP, SYP, S1X, S1Y, sx, sy, QX, QY, QZ);
                     }
                 }
             } else {

@@ -343,6 +343,13 @@ __device__ __forceinline__ long long f64_to_fixed_shift(double x, int s) {
 }
 // round(x) as int64 (see above)
 __device__ __forceinline__ long long f64_to_fixed(double x) { return f64_to_fixed_shift(x, 0); }
+// a b + c for 32-bit a, b and a 64-bit c, as one multiply-add instruction (written out:
+// the compiler emits a separate 64-bit addition for the same C++ expression)
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
 // a w / 2^62 for a weight w held in 2^62 fixed point (|a|, |w| < 2^62), to within one
 // unit either side, unbiased for operands whose low 31 bits are spread evenly, and
 // exactly 0 for a zero operand. Both operands split at bit 31 (the high parts fit 32
@@ -355,9 +362,8 @@ __device__ __forceinline__ long long f64_to_fixed(double x) { return f64_to_fixe
 __device__ __forceinline__ long long fixmul62(long long a, long long w) {
     const int ah = (int)(a >> 31), wh = (int)(w >> 31);
     const int al = (int)(a & 0x7FFFFFFFLL), wl = (int)(w & 0x7FFFFFFFLL);
-    long long mid = (long long)ah * wl + (3LL << 29);
-    mid += (long long)al * wh;
-    return (long long)ah * wh + (mid >> 31);
+    const long long mid = mad_wide(al, wh, mad_wide(ah, wl, 3LL << 29));
+    return mad_wide(ah, wh, mid >> 31);
 }
 // v 2^-k as a double: the hardware int64 -> FP64 conversion (one FP64-pipe instruction,
 // rounded to nearest) and the scaling by 2^-k as an exponent subtraction (exact); a
