@@ -158,6 +158,23 @@ __device__ __forceinline__ long long gather9_fix(const int2* __restrict__ f, int
     return hh + (mid >> 31);
 }
 
+// Order-2 gather of one staggered component in 3D: three planes gathered as above
+// (|plane| < 2^60, split like a tile entry), combined with the z weights the same way; to
+// within 12 units below.
+__device__ __forceinline__ long long gather27_fix(const int2* __restrict__ f, int BX, int BXY,
+                                                  const W31 sx[3], const W31 sy[3],
+                                                  const W31 sz[3]) {
+    long long hh = 0, mid = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const long long p = gather9_fix(f + c * BXY, BX, sx, sy);
+        const int phi = (int)(p >> 31), plo = (int)(p & 0x7FFFFFFFLL);
+        hh = mad_wide(sz[c].h, phi, hh);
+        mid = mad_wide(sz[c].l, phi, mad_wide(sz[c].h, plo, mid));
+    }
+    return hh + (mid >> 31);
+}
+
 // 2D Esirkepov deposition in fixed point when the particle keeps its nearest nodes on
 // both axes: DS lives on stencil nodes 1..3, the running sums have two non-zero
 // entries (their sum over the three nodes is zero), 6 + 6 + 9 tile atomics, the three
@@ -266,6 +283,93 @@ __device__ __forceinline__ void deposit2d_general_fix(long long* jx, long long* 
         jatomic(cy + 1 * JX, fixmul62(cy2, wx0));
         jatomic(cy + 2 * JX, fixmul62(cy3, wx0));
         wx0 = wx1, wx1 = wx2, wx2 = wx3;
+    }
+}
+
+// 3D Esirkepov weights of a node, W_a = DS_a (wa_b S0_c + wb_b DS_c) with
+// wa = S0 + DS/2 and wb = S0/2 + DS/3, in 2^62 fixed point per axis
+__device__ __forceinline__ void esirkepov_w3(long long S0, long long DS, long long& wa,
+                                             long long& wb) {
+    wa = S0 + (DS >> 1);
+    wb = (S0 >> 1) + fixmul62(DS, kThird62);
+}
+
+// 3D deposition in fixed point when no axis changes its nearest node: S0 and DS on
+// stencil nodes 1..3 of every axis, two non-zero running-sum entries per line, 54 tile
+// adds. jt[a]: stencil node (1, 1, 1) of component a; Q[a]: the charge factors (tile
+// scale included) as integers.
+__device__ __forceinline__ void deposit3d_fast_fix(long long* const jt[3], int JX, int JXY,
+                                                   const long long S0[3][3],
+                                                   const long long S1[3][3],
+                                                   const long long Q[3]) {
+    long long DS[3][3], wa[3][3], wb[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            DS[a][k] = S1[a][k] - S0[a][k];
+            esirkepov_w3(S0[a][k], DS[a][k], wa[a][k], wb[a][k]);
+        }
+    const int st[3] = {1, JX, JXY};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const long long c1 = fixmul62(Q[a], DS[a][0]), c2 = fixmul62(Q[a], DS[a][0] + DS[a][1]);
+        // rolled over the c-axis nodes, their weights rotating through registers
+        long long s0 = S0[c][0], s1 = S0[c][1], s2 = S0[c][2];
+        long long d0 = DS[c][0], d1 = DS[c][1], d2 = DS[c][2];
+#pragma unroll 1
+        for (int kc = 0; kc < 3; kc++) {
+#pragma unroll
+            for (int kb = 0; kb < 3; kb++) {
+                const long long A = fixmul62(wa[b][kb], s0) + fixmul62(wb[b][kb], d0);
+                long long* p = jt[a] + kb * st[b] + kc * st[c];
+                jatomic(p, fixmul62(c1, A));
+                jatomic(p + st[a], fixmul62(c2, A));
+            }
+            s0 = s1, s1 = s2, d0 = d1, d1 = d2;
+        }
+    }
+}
+
+// General 3D deposition in fixed point (any shift in {-1, 0, 1} per axis) on a fixed
+// four-node window per axis: 3 x 16 x 3 tile adds. j0: stencil node (0, 0, 0) of
+// component 0 (old nodes - 2), jvol: the tile volume of one component.
+__device__ __forceinline__ void deposit3d_general_fix(long long* j0, int jvol, int JX, int JXY,
+                                                      const long long S0[3][3],
+                                                      const long long S1[3][3],
+                                                      const int sh[3], const long long Q[3]) {
+    Axis4<long long> ax[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) esirkepov_axis4_fix(S0[a], S1[a], sh[a], ax[a]);
+    long long wa[3][4], wb[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) esirkepov_w3(ax[a].S0[q], ax[a].DS[q], wa[a][q], wb[a][q]);
+    const int st[3] = {1, JX, JXY};
+    const int o = ax[2].start * JXY + ax[1].start * JX + ax[0].start;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const long long c1 = fixmul62(Q[a], ax[a].DS[0]);
+        const long long c2 = fixmul62(Q[a], ax[a].DS[0] + ax[a].DS[1]);
+        const long long c3 = fixmul62(Q[a], ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
+        long long* jt = j0 + a * jvol + o;
+        long long s0 = ax[c].S0[0], s1 = ax[c].S0[1], s2 = ax[c].S0[2], s3 = ax[c].S0[3];
+        long long d0 = ax[c].DS[0], d1 = ax[c].DS[1], d2 = ax[c].DS[2], d3 = ax[c].DS[3];
+#pragma unroll 1
+        for (int kc = 0; kc < 4; kc++) {
+#pragma unroll
+            for (int kb = 0; kb < 4; kb++) {
+                const long long A = fixmul62(wa[b][kb], s0) + fixmul62(wb[b][kb], d0);
+                long long* p = jt + kb * st[b] + kc * st[c];
+                jatomic(p, fixmul62(c1, A));
+                jatomic(p + st[a], fixmul62(c2, A));
+                jatomic(p + 2 * st[a], fixmul62(c3, A));
+            }
+            s0 = s1, s1 = s2, s2 = s3, d0 = d1, d1 = d2, d2 = d3;
+        }
     }
 }
 

@@ -4,9 +4,13 @@
 // J_a the running sum of -(q w/dV)(d_a/dt) W_a along +a. y and z are periodic; x is
 // periodic or a moving window (particles leaving [0, nx) are absorbed, the shift is
 // applied in the particle store, contributions outside the window are dropped).
-// FP32 cells pack (ix | iy << 11 | iz << 22).
+// FP32 cells pack (ix | iy << 11 | iz << 22). The FP64 kernel runs everything but the Boris
+// push, the move and the charge factors in 2^62 fixed point on the integer units, as the
+// 2D one does (fix62.cuh): offsets, shapes, the 27-tap gather from a fixed-point copy of
+// the field tile, the Esirkepov weights and products.
 #include <cuda_runtime.h>
 
+#include "fix62.cuh"
 #include "pic_device.cuh"
 #include "pic_internal.h"
 
@@ -87,33 +91,15 @@ __device__ __forceinline__ void deposit3d_fast(JT* const jt[3], int JX, int JXY,
     for (int a = 0; a < 3; a++) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
         const T c1 = q[a] * DS[a][0], c2 = q[a] * (DS[a][0] + DS[a][1]);
-        if constexpr (is_f64<T>::value) {
-            // FP64: rolled over kc, the c-axis weights rotating through registers (a
-            // compact body; FP32 keeps the unrolled loops)
-            T s0 = S0[c][0], s1 = S0[c][1], s2 = S0[c][2];
-            T d0 = DS[c][0], d1_ = DS[c][1], d2 = DS[c][2];
-#pragma unroll 1
-            for (int kc = 0; kc < 3; kc++) {
 #pragma unroll
-                for (int kb = 0; kb < 3; kb++) {
-                    const T A = wa[b][kb] * s0 + wb[b][kb] * d0;
-                    JT* p = jt[a] + kb * st[b] + kc * st[c];
-                    jatomic(p, jprod<JT>(c1, A));
-                    jatomic(p + st[a], jprod<JT>(c2, A));
-                }
-                s0 = s1, s1 = s2, d0 = d1_, d1_ = d2;
+        for (int kc = 0; kc < 3; kc++)
+#pragma unroll
+            for (int kb = 0; kb < 3; kb++) {
+                const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
+                JT* p = jt[a] + kb * st[b] + kc * st[c];
+                jatomic(p, jprod<JT>(c1, A));
+                jatomic(p + st[a], jprod<JT>(c2, A));
             }
-        } else {
-#pragma unroll
-            for (int kc = 0; kc < 3; kc++)
-#pragma unroll
-                for (int kb = 0; kb < 3; kb++) {
-                    const T A = wa[b][kb] * S0[c][kc] + wb[b][kb] * DS[c][kc];
-                    JT* p = jt[a] + kb * st[b] + kc * st[c];
-                    jatomic(p, jprod<JT>(c1, A));
-                    jatomic(p + st[a], jprod<JT>(c2, A));
-                }
-        }
     }
 }
 
@@ -144,6 +130,9 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
     __shared__ int s_lv_n;
     __shared__ int s_lv_slot[kLeaveList];
     __shared__ int s_lv_dest[kLeaveList];
+    // FP64: largest exponent field of each component of the staged field tile, which then
+    // holds the fields in split fixed point (see fix_field_tile)
+    __shared__ int s_femax[6];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -188,6 +177,9 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
         for (int e = tid; e < 3 * jvol; e += blockDim.x) Jt[e] = JT(0);
 
         if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
+            if constexpr (is_f64<T>::value) {
+                if (tid < 6) s_femax[tid] = 0;
+            }
             if (tid == 0) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&mbar, (uint32_t)fbytes);
@@ -200,11 +192,13 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                 if (tid == 0) atomicOr(S.status, ST_TIMEOUT);
                 return;
             }
+            if constexpr (is_f64<T>::value)
+                fix_field_tile(reinterpret_cast<double*>(Ft), BXY * BZ, s_femax);
             loaded_sim = item.x;
             loaded_patch = patch;
             loaded_gen = gen;
         }
-        __syncthreads();
+        __syncthreads();  // J tile zeroed (FP64: field tile converted)
 
         T dtd[3], cj[3], eps;
         if constexpr (is_f64<T>::value) {
@@ -240,7 +234,12 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
         T nw = T(0);
         auto fetch = [&](int kk) {
             const int sl = base + kk;
-            split_pos<T>(S, sl, nic, nf, nxi);
+            if constexpr (is_f64<T>::value) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) nxi[a] = reinterpret_cast<const double*>(S.xi[a])[sl];
+            } else {
+                split_pos<T>(S, sl, nic, nf, nxi);
+            }
             nu[0] = U0[sl];
             nu[1] = U1[sl];
             nu[2] = U2[sl];
@@ -252,15 +251,139 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
             const int k = k0 + tid;
             const bool valid = k < cnt;
             const int slot = base + (valid ? k : 0);
+            bool ok = valid;
+            bool leave = false;
+            int dest = patch;
+            if constexpr (is_f64<T>::value) {
+                // ---- FP64: offsets, shapes, gather, deposit weights and products in 2^62
+                // fixed point on the integer units; Boris, the move and the charge factors
+                // in FP64. A field tile holding a non-finite value cannot be converted: its
+                // particles are reported and dropped like non-finite particles.
+                const bool ftile_ok = s_femax[0] < 0x7FF && s_femax[1] < 0x7FF &&
+                                      s_femax[2] < 0x7FF && s_femax[3] < 0x7FF &&
+                                      s_femax[4] < 0x7FF && s_femax[5] < 0x7FF;
+                const double xi0[3] = {nxi[0], nxi[1], nxi[2]};
+                double u[3] = {nu[0], nu[1], nu[2]};
+                const double w = nw;
+                int ic[3] = {0, 0, 0}, np_[3], tp[3], td[3];
+                long long F[3] = {0, 0, 0};
+                bool hp[3];
+                ok = ok && ftile_ok;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (valid) split62(xi0[a], ic[a], F[a]);
+                    hp[a] = F[a] >= kHalf62;  // primal node = ic + (f >= 1/2), dual = ic
+                    np_[a] = ic[a] + (hp[a] ? 1 : 0);
+                    tp[a] = np_[a] - p0[a];
+                    td[a] = ic[a] - p0[a];
+                    ok = ok && (unsigned)tp[a] <= (unsigned)P[a] && (unsigned)td[a] < (unsigned)P[a];
+                }
+                long long S0[3][3], S1[3][3], Q[3] = {0, 0, 0};
+                int sh[3] = {0, 0, 0};
+                if (ok) {
+                    W31 Wp[3][3], Wd[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        long long SD[3];
+                        shape62(hp[a] ? F[a] - kOne62 : F[a], S0[a]);
+                        shape62(F[a] - kHalf62, SD);
+#pragma unroll
+                        for (int q = 0; q < 3; q++) {
+                            Wp[a][q] = w31(S0[a][q]);
+                            Wd[a][q] = w31(SD[q]);
+                        }
+                    }
+                    // one rolled loop over Ex (d,p,p) Ey (p,d,p) Ez (p,p,d) Bx (p,d,d)
+                    // By (d,p,d) Bz (d,d,p); results rotate through six registers
+                    const int2* Fi = reinterpret_cast<const int2*>(Ft);
+                    const int vol = BXY * BZ;
+                    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0, r5 = 0.0;
+#pragma unroll 1
+                    for (int c = 0; c < 6; c++) {
+                        const bool xp = c >= 1 && c <= 3, yp = c == 0 || c == 2 || c == 4,
+                                   zp = c == 0 || c == 1 || c == 5;
+                        W31 gx[3], gy[3], gz[3];
+#pragma unroll
+                        for (int q = 0; q < 3; q++) {
+                            gx[q] = xp ? Wp[0][q] : Wd[0][q];
+                            gy[q] = yp ? Wp[1][q] : Wd[1][q];
+                            gz[q] = zp ? Wp[2][q] : Wd[2][q];
+                        }
+                        const int off = (zp ? tp[2] : td[2]) * BXY + (yp ? tp[1] : td[1]) * BX +
+                                        (xp ? tp[0] : td[0]);
+                        const long long v = gather27_fix(Fi + c * vol + off, BX, BXY, gx, gy, gz);
+                        r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5;
+                        r5 = scaled_to_f64(v, fix_field_exp(s_femax[c]));
+                    }
+                    const double E[3] = {r0, r1, r2}, B[3] = {r3, r4, r5};
+                    const double ig = boris(eps, E, B, u);
+                    double xin[3];
+                    int icn[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        xin[a] = xi0[a] + dtd[a] * (u[a] * ig);
+                        long long F1;
+                        split62(xin[a], icn[a], F1);
+                        const bool h1 = F1 >= kHalf62;
+                        sh[a] = icn[a] + (h1 ? 1 : 0) - np_[a];
+                        ok = ok && sh[a] >= -1 && sh[a] <= 1;
+                        shape62(h1 ? F1 - kOne62 : F1, S1[a]);
+                        Q[a] = __double2ll_rn(cjs[a] * w);  // charge factor, tile scale included
+                    }
+                    // ---- boundaries, destination patch and the new state, stored before
+                    // the deposit: periodic, except a moving-window x axis (this step's
+                    // shift applied, particles leaving [0, nx) absorbed)
+                    if (ok) {
+                        bool del = false;
+                        if (window) {
+                            del = xin[0] < 0.0 || xin[0] >= (double)n[0];
+                            xin[0] -= (double)shift;
+                            del = del || xin[0] < 0.0;
+                        }
+                        int dp_[3];
+#pragma unroll
+                        for (int a = 0; a < 3; a++) {
+                            if (!(window && a == 0)) {
+                                if (xin[a] < 0.0) xin[a] += (double)n[a];
+                                if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
+                            }
+                            icn[a] = floor_to_int(xin[a]);
+                            dp_[a] = icn[a] / P[a];
+                        }
+                        dest = del ? -1 : dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
+                        leave = del || dest != patch;
+                        if (!del) {  // also a leaver: the hand-off copies its state from here
+                            for (int a = 0; a < 3; a++)
+                                reinterpret_cast<double*>(S.xi[a])[slot] = xin[a];
+                            U0[slot] = u[0];
+                            U1[slot] = u[1];
+                            U2[slot] = u[2];
+                        }
+                    }
+                }
+                // the next particle's state loads while this one deposits
+                if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
+                const bool fast =
+                    __all_sync(0xffffffffu, !ok || (sh[0] == 0 && sh[1] == 0 && sh[2] == 0));
+                if (ok) {
+                    const int t000 = tp[2] * JXY + tp[1] * JX + tp[0];
+                    if (fast) {
+                        long long* jt3[3];
+                        const int t111 = t000 + JXY + JX + 1;
+                        for (int a = 0; a < 3; a++) jt3[a] = Jt + a * jvol + t111;
+                        deposit3d_fast_fix(jt3, JX, JXY, S0, S1, Q);
+                    } else {
+                        deposit3d_general_fix(Jt + t000, jvol, JX, JXY, S0, S1, sh, Q);
+                    }
+                }
+            } else {
             int ic[3] = {nic[0], nic[1], nic[2]};
             T f[3] = {nf[0], nf[1], nf[2]};
-            double xi0[3] = {nxi[0], nxi[1], nxi[2]};
             T u[3] = {nu[0], nu[1], nu[2]};
             T w = nw;
             if (k + (int)blockDim.x < cnt) fetch(k + blockDim.x);
             int np_[3], tp[3], td[3];
             T dp[3], dd[3];
-            bool ok = valid;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const bool h = f[a] >= T(0.5);
@@ -271,11 +394,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                 td[a] = ic[a] - p0[a];
                 ok = ok && (unsigned)tp[a] <= (unsigned)P[a] && (unsigned)td[a] < (unsigned)P[a];
             }
-            bool leave = false;
-            int dest = patch;
             int icn[3] = {0, 0, 0};
             T fn[3] = {T(0), T(0), T(0)};
-            double xin[3] = {0.0, 0.0, 0.0};
             T S0keep[3][3] = {}, d1keep[3] = {T(0), T(0), T(0)};
             int shkeep[3] = {0, 0, 0};
             if (ok) {
@@ -299,27 +419,21 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                 T dp1[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    if constexpr (is_f64<T>::value) {
-                        xin[a] = xi0[a] + dtd[a] * v[a];
-                        np1[a] = floor_to_int(xin[a] + 0.5);
-                        dp1[a] = xin[a] - fixed_to_f64(np1[a], 0);
-                    } else {
-                        T g = f[a] + dtd[a] * v[a];
-                        int i1 = ic[a];
-                        if (g < T(0)) {
-                            g += T(1);
-                            i1 -= 1;
-                            if (g >= T(1)) { g = T(0); i1 += 1; }
-                        } else if (g >= T(1)) {
-                            g -= T(1);
-                            i1 += 1;
-                        }
-                        const bool h1 = g >= T(0.5);
-                        np1[a] = i1 + (h1 ? 1 : 0);
-                        dp1[a] = h1 ? g - T(1) : g;
-                        icn[a] = i1;
-                        fn[a] = g;
+                    T g = f[a] + dtd[a] * v[a];
+                    int i1 = ic[a];
+                    if (g < T(0)) {
+                        g += T(1);
+                        i1 -= 1;
+                        if (g >= T(1)) { g = T(0); i1 += 1; }
+                    } else if (g >= T(1)) {
+                        g -= T(1);
+                        i1 += 1;
                     }
+                    const bool h1 = g >= T(0.5);
+                    np1[a] = i1 + (h1 ? 1 : 0);
+                    dp1[a] = h1 ? g - T(1) : g;
+                    icn[a] = i1;
+                    fn[a] = g;
                     sh[a] = np1[a] - np_[a];
                     ok = ok && sh[a] >= -1 && sh[a] <= 1;
                 }
@@ -368,22 +482,6 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                         const T c1 = qa * ax[a].DS[0], c2 = qa * (ax[a].DS[0] + ax[a].DS[1]),
                                 c3 = qa * (ax[a].DS[0] + ax[a].DS[1] + ax[a].DS[2]);
                         JT* jt = Jt + a * jvol + o3;
-                        if constexpr (is_f64<T>::value) {
-                            T s0 = ax[c].S0[0], s1 = ax[c].S0[1], s2 = ax[c].S0[2], s3 = ax[c].S0[3];
-                            T d0 = ax[c].DS[0], d1 = ax[c].DS[1], d2 = ax[c].DS[2], d3 = ax[c].DS[3];
-#pragma unroll 1
-                            for (int kc = 0; kc < 4; kc++) {
-#pragma unroll
-                                for (int kb = 0; kb < 4; kb++) {
-                                    const T A = wa[b][kb] * s0 + wb[b][kb] * d0;
-                                    JT* p = jt + kb * st3[b] + kc * st3[c];
-                                    jatomic(p, jprod<JT>(c1, A));
-                                    jatomic(p + st3[a], jprod<JT>(c2, A));
-                                    jatomic(p + 2 * st3[a], jprod<JT>(c3, A));
-                                }
-                                s0 = s1, s1 = s2, s2 = s3, d0 = d1, d1 = d2, d2 = d3;
-                            }
-                        } else {
 #pragma unroll
                         for (int kc = 0; kc < 4; kc++)
 #pragma unroll
@@ -394,7 +492,6 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                                 jatomic(p + st3[a], jprod<JT>(c2, A));
                                 jatomic(p + 2 * st3[a], jprod<JT>(c3, A));
                             }
-                        }
                     }
                     }
                 }
@@ -402,45 +499,27 @@ __global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 
                     // axis (this step's shift applied, particles leaving [0, nx) absorbed)
                     bool del = false;
                     if (window) {
-                        if constexpr (is_f64<T>::value) {
-                            del = xin[0] < 0.0 || xin[0] >= (double)n[0];
-                            xin[0] -= (double)shift;
-                            del = del || xin[0] < 0.0;
-                        } else {
-                            del = icn[0] < 0 || icn[0] >= n[0];
-                            icn[0] -= shift;
-                            del = del || icn[0] < 0;
-                        }
+                        del = icn[0] < 0 || icn[0] >= n[0];
+                        icn[0] -= shift;
+                        del = del || icn[0] < 0;
                     }
                     int dp_[3];
 #pragma unroll
                     for (int a = 0; a < 3; a++) {
-                        if constexpr (is_f64<T>::value) {
-                            if (!(window && a == 0)) {
-                                if (xin[a] < 0.0) xin[a] += (double)n[a];
-                                if (xin[a] >= (double)n[a]) xin[a] -= (double)n[a];
-                            }
-                            icn[a] = floor_to_int(xin[a]);
-                        } else if (!(window && a == 0)) {
-                            icn[a] = wrapi(icn[a], n[a]);
-                        }
+                        if (!(window && a == 0)) icn[a] = wrapi(icn[a], n[a]);
                         dp_[a] = icn[a] / P[a];
                     }
                     dest = del ? -1 : dp_[0] + S.np[0] * (dp_[1] + S.np[1] * dp_[2]);
                     leave = del || dest != patch;
                     if (!del) {  // also a leaver: the hand-off copies its state from here
-                        if constexpr (is_f64<T>::value) {
-                            for (int a = 0; a < 3; a++)
-                                reinterpret_cast<double*>(S.xi[a])[slot] = xin[a];
-                        } else {
-                            S.cell[slot] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
-                            for (int a = 0; a < 3; a++)
-                                reinterpret_cast<T*>(S.xi[a])[slot] = fn[a];
-                        }
+                        S.cell[slot] = icn[0] | (icn[1] << 11) | (icn[2] << 22);
+                        for (int a = 0; a < 3; a++)
+                            reinterpret_cast<T*>(S.xi[a])[slot] = fn[a];
                         U0[slot] = u[0];
                         U1[slot] = u[1];
                         U2[slot] = u[2];
                     }
+            }
             }
             if (valid && !ok) {
                 atomicOr(S.status, ST_NUMERIC);

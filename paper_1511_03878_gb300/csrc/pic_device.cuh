@@ -350,19 +350,19 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
     asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
     return d;
 }
-// a w / 2^62 for a weight w held in 2^62 fixed point (|a|, |w| < 2^62), to within one
-// unit either side, unbiased for operands whose low 31 bits are spread evenly, and
-// exactly 0 for a zero operand. Both operands split at bit 31 (the high parts fit 32
-// bits): the high-by-high product and the two cross products (their sum below 2^63),
-// shifted with an offset of 3/4 of a unit; the low-by-low product, below one unit after
-// the division and a quarter on average, is left out, and the offset restores the
-// quarter and the half that the shift's truncation loses on average. Three 32x32->64
-// integer multiply-adds instead of an FP64 multiply (GB300 runs FP64 at 1/64 of its
-// FP32 rate) or a full 128-bit product.
+// round(a w / 2^62) for a weight w held in 2^62 fixed point (|a|, |w| < 2^62), exact
+// except within 2^-30 of a unit from a tie, and 0 for a zero operand. Both operands split
+// at bit 31 (the high parts fit 32 bits): the high-by-high product and the two cross
+// products (their sum below 2^63) in 32x32->64 multiply-adds, and the low-by-low
+// product through its high word only (one 32-bit multiply; the low word is below 2^-30
+// of a unit after the division). Integer operations instead of an FP64 multiply (GB300
+// runs FP64 at 1/64 of its FP32 rate) or a full 128-bit product.
 __device__ __forceinline__ long long fixmul62(long long a, long long w) {
     const int ah = (int)(a >> 31), wh = (int)(w >> 31);
     const int al = (int)(a & 0x7FFFFFFFLL), wl = (int)(w & 0x7FFFFFFFLL);
-    const long long mid = mad_wide(al, wh, mad_wide(ah, wl, 3LL << 29));
+    // (al wl) / 2^31 in the cross products' units, plus half a unit for the rounding
+    const unsigned ll = 2u * __umulhi((unsigned)al, (unsigned)wl) + (1u << 30);
+    const long long mid = mad_wide(al, wh, mad_wide(ah, wl, (long long)ll));
     return mad_wide(ah, wh, mid >> 31);
 }
 // v 2^-k as a double: the hardware int64 -> FP64 conversion (one FP64-pipe instruction,
