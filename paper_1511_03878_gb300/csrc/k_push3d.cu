@@ -117,10 +117,24 @@ __device__ __forceinline__ void handoff_copy3d(const SimDev& S, int slot, int m,
     S.mid[m] = pid;
 }
 
-// FP64: one CTA per SM (236 registers). Two (128 registers, with spills) measured 1 %
-// slower on the 3D stress case.
+// CTA shape per precision: threads per CTA and the CTAs per SM the register budget is
+// sized for. FP64 tiles of an 8x8x8 patch take about 122 KB of shared memory, so one CTA
+// per SM; 512 threads (128 registers) measured 2-4 % faster than 256 (255 registers) and
+// level with 384 on the 3D stress case, 4 % faster than both on the 3D LWFA window.
+#ifndef PIC_F64_3D_THREADS
+#define PIC_F64_3D_THREADS 512
+#endif
 template <typename T>
-__global__ void __launch_bounds__(kThreads, std::is_same<T, float>::value ? 2 : 1)
+struct Push3DShape {
+    static constexpr int threads = PIC_F64_3D_THREADS, min_blocks = 1;
+};
+template <>
+struct Push3DShape<float> {
+    static constexpr int threads = kThreads, min_blocks = 2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(Push3DShape<T>::threads, Push3DShape<T>::min_blocks)
     push3d_kernel(const BatchDev* __restrict__ bd, int static_map) {
     using JT = typename JType3D<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -645,7 +659,8 @@ static int occupancy_3d(int sb) {
         return 0;
     cudaFuncSetAttribute(push3d_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<T>, kThreads, sb) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, push3d_kernel<T>,
+                                                      Push3DShape<T>::threads, sb) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -664,7 +679,8 @@ cudaError_t launch_push3d(const BatchDev* bd_dev, int prec, int mapping, int P0,
     const int sb = push3d_smem(prec, P0, P1, P2);
     const int static_map = mapping == 1;
     if (prec != 0 && prec != 1) return cudaErrorInvalidValue;
-    PIC_DISPATCH_3D(prec, (push3d_kernel<T><<<grid, kThreads, sb, s>>>(bd_dev, static_map)));
+    PIC_DISPATCH_3D(prec, (push3d_kernel<T><<<grid, Push3DShape<T>::threads, sb, s>>>(
+                              bd_dev, static_map)));
     return cudaGetLastError();
 }
 
