@@ -552,9 +552,11 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     barrier(world)
     t0 = time.perf_counter()
     sim.load(wp)
+    tl = time.perf_counter()
     for _ in range(K):
         sim.step(1)
         sim.step_info()
+    ts = time.perf_counter()
     e = sim.energy()
     ax = sim.ex_axis()
     t1 = time.perf_counter()
@@ -562,14 +564,17 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     cfg = sim.cfg
     ncell = cfg.n[0] * cfg.n[1] * (cfg.n[2] if dims == 3 else 1)
     # the loader copies the caller's arrays as they are (FP64 positions, momenta and
-    # weights, int32 ids) with each particle's int32 slot, five per-patch int arrays and
-    # the FP64 fields E and B; the device converts, places and pads
-    h2d = n * (8 * (dims + 4) + 4 + 4) + 6 * ncell * 8 + 5 * sim.npatch * 4
-    d2h = 24 * K + e.nbytes + ax.nbytes
+    # weights, int32 ids), five per-patch int arrays and the FP64 fields E and B; the
+    # device validates, bins, orders, converts, places and pads; the host reads back the
+    # per-(patch, bank class) counts and three reductions
+    h2d = n * (8 * (dims + 4) + 4) + 6 * ncell * 8 + 5 * sim.npatch * 4 + 24
+    d2h = 24 * K + e.nbytes + ax.nbytes + 32 * 4 * sim.npatch + 24
     sim.close()
     seconds = max_over_ranks(t1 - t0, world)
     return dict(value=job_value(sum_over_ranks(n * K, world), 1e3 * seconds), h2d=h2d / K,
-                d2h=d2h / K, seconds=seconds)
+                d2h=d2h / K, seconds=seconds,
+                split_ms={"load": 1e3 * (tl - t0), "steps": 1e3 * (ts - tl),
+                          "readback": 1e3 * (t1 - ts)})
 
 
 def oracle_sim(w, steps):
@@ -989,7 +994,8 @@ def main():
         "roofline_step": step_roofline(args.precision, wm, value, main_run["n"]),
         "cpu_baseline": cpu,
         "e2e": ({"value": e2e["value"], "unit": UNIT,
-                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                 "split_ms": e2e["split_ms"]}
                 if e2e else None),
         "gpu_launches": kernels_per_step(bool(w["params"].get("window")),
                                          args.merge_above > 0, args.split_below > 0) * args.steps,

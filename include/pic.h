@@ -151,11 +151,12 @@ pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t arena_bytes
  * u = gamma v, weights; int32 ids, unique and >= 0). Each SP is binned into the patch
  * that holds it; the SP count per patch is the load measure (Sec. 3: the load of a
  * region is its number of SP) that orders the work queue. z may be NULL in 2D. Positions
- * must lie in [0, n[a] d[a]). The host validates the particles and bins them by patch;
- * the arrays are copied to the device as they are (page-locked arrays copy
- * asynchronously while the host bins) and converted there. Per-patch capacities split
- * the free slots half by count, half evenly. The arrays are not retained: every copy
- * has completed when the call returns, on success and on error. Returns
+ * must lie in [0, n[a] d[a]). The arrays are copied to the device as they are (in
+ * chunks of the repack scratch); the device validates the particles, bins them by patch
+ * and orders each patch's particles by shared-memory bank class, and the host reads back
+ * only the per-patch counts to split the capacities: the free slots half by count, half
+ * evenly. The arrays are not retained: every copy has completed when the call returns,
+ * on success and on error. Returns
  * PIC_ERR_CAPACITY if n > capacity, PIC_ERR_INVALID for a position outside the grid or
  * a negative id, PIC_ERR_NUMERIC for a non-finite momentum or weight; a rejected load
  * leaves the sim as it was. Resets the step counter to 0. */

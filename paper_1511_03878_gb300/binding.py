@@ -228,7 +228,9 @@ def _check_fields(h, E, B, rho_bg):
 
 def pic_load_particles(h, p: dict):
     n = _check_particles(p)
-    arrs = [np.ascontiguousarray(p.get(k, np.zeros(n)), dtype=np.float64)
+    # an absent z is passed as NULL (2D); other absent arrays as zeros, built only then
+    arrs = [np.ascontiguousarray(p[k], dtype=np.float64) if k in p
+            else (None if k == "z" else np.zeros(n))
             for k in ("x", "y", "z", "ux", "uy", "uz", "w")]
     ids = np.ascontiguousarray(p["id"], dtype=np.int32)
     _check(lib().pic_load_particles(h, n, *[_dp(a) for a in arrs], _ip(ids)), h)

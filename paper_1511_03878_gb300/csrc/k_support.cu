@@ -594,20 +594,125 @@ __device__ __forceinline__ T offset_below_one(double f) {
     return g;
 }
 
-// One chunk of a particle load: m particles of the caller's FP64 arrays, copied as they
-// are into the repack scratch (positions in axi, momenta in au, weights in aw, ids in
-// aid), and the slot the host's binning gave each (in holes). Each particle is converted
-// to the sim's representation (FP64: position in cell units; FP32 and double-word: the
-// packed cell index plus the offset in the cell) and stored in its slot. Free slots were
-// cleared beforehand (id -1).
+// ================================================================ particle load
+// The caller's FP64 arrays are staged chunk by chunk in the repack scratch as they are
+// (positions in axi, momenta in au, weights in aw, ids in aid); chunk index k holds the
+// call's particle k0 + k. Three passes place them.
+
+// Pass 1, per particle: validation (the first invalid particle of the call by index, with
+// its reason: 1 a position outside the grid, 2 a non-finite momentum or weight, 3 a
+// negative id), its patch, the shared-memory bank class of its cell in the patch's field
+// tile (the tile address modulo 32), and its rank among the particles of the same patch
+// and class (an atomic add on that pair's counter). Writes the key patch * 32 + class to
+// holes[k0 + k] and the rank to aux[k0 + k]. The counters are npatch x 32 ints in the
+// Gauss scratch rho (zeroed by the caller); red holds {first invalid (index << 2 |
+// reason), largest id, largest |w| as its bits}, set to {~0, 0, 0} by the caller. None of
+// these is live state between steps, so a rejected load leaves the sim as it was.
+__global__ void __launch_bounds__(256) load_bin_kernel(const BatchDev* __restrict__ bd,
+                                                       long long m, long long k0) {
+    const SimDev& S = bd->sims[0];
+    int* cnt = reinterpret_cast<int*>(S.rho);
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(S.red);
+    int idmax = 0;
+    unsigned long long wmax = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long p = k0 + k;
+        int ic[3] = {0, 0, 0};
+        int code = 0;
+        for (int a = 0; a < S.dims; a++) {
+            const double v = reinterpret_cast<const double*>(S.axi[a])[k];
+            if (!isfinite(v) || v < 0.0 || v >= S.n[a] * S.d[a]) {
+                code = 1;
+                break;
+            }
+            ic[a] = (int)floor(cell_coord(v, S.d[a], S.n[a]));
+        }
+        const double w = reinterpret_cast<const double*>(S.aw)[k];
+        if (!code && (!isfinite(reinterpret_cast<const double*>(S.au[0])[k]) ||
+                      !isfinite(reinterpret_cast<const double*>(S.au[1])[k]) ||
+                      !isfinite(reinterpret_cast<const double*>(S.au[2])[k]) || !isfinite(w)))
+            code = 2;
+        const int id = S.aid[k];
+        if (!code && id < 0) code = 3;
+        if (code) {
+            atomicMin(&red[0], ((unsigned long long)p << 2) | (unsigned long long)code);
+            continue;
+        }
+        idmax = max(idmax, id);
+        wmax = max(wmax, (unsigned long long)__double_as_longlong(fabs(w)));
+        const int pc[3] = {ic[0] / S.P[0], ic[1] / S.P[1], ic[2] / S.P[2]};
+        const int pp = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
+        const int lx = ic[0] - pc[0] * S.P[0], ly = ic[1] - pc[1] * S.P[1];
+        const int lz = ic[2] - pc[2] * S.P[2];
+        const int key = pp * 32 + (((lz * S.BY + ly) * S.BX + lx) & 31);
+        S.holes[p] = key;
+        S.aux[p] = atomicAdd(&cnt[key], 1);
+    }
+    // largest id and |w| of the CTA, then one atomic each
+    __shared__ int s_id[32];
+    __shared__ unsigned long long s_w[32];
+    idmax = __reduce_max_sync(0xffffffffu, idmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_down_sync(0xffffffffu, wmax, o);
+        wmax = x > wmax ? x : wmax;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_id[wid] = idmax;
+        s_w[wid] = wmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+            idmax = max(idmax, s_id[i]);
+            wmax = s_w[i] > wmax ? s_w[i] : wmax;
+        }
+        atomicMax(&red[1], (unsigned long long)idmax);
+        atomicMax(&red[2], wmax);
+    }
+}
+
+// Pass 2, per particle of the call: its slot, the patch's base plus its place in the run
+// order (run r holds the r-th particle of every class present in the patch, classes in
+// order), so that the lanes of a warp read and add into different banks. The rank is
+// scrambled by a fixed bijection of [0, class count), r -> r * 1000003 mod count (the
+// multiplier is prime, so coprime to any smaller count): particles of one cell, which
+// tend to take consecutive ranks, land in different runs.
+__global__ void __launch_bounds__(256) load_slot_kernel(const BatchDev* __restrict__ bd,
+                                                        long long n) {
+    const SimDev& S = bd->sims[0];
+    const int* cnt = reinterpret_cast<const int*>(S.rho);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int key = S.holes[p];
+        const int pp = key >> 5, q = key & 31;
+        const int* nb = cnt + pp * 32;
+        const int c = nb[q];
+        int r = S.aux[p];
+        if (c < 1000003) r = (int)(((long long)r * 1000003LL) % c);
+        int off = 0;
+#pragma unroll 8
+        for (int t = 0; t < 32; t++) {
+            const int x = nb[t];
+            off += min(x, r) + ((t < q && x > r) ? 1 : 0);
+        }
+        S.holes[p] = S.pbase[pp] + off;
+    }
+}
+
+// Pass 3, one chunk: each particle converted to the sim's representation (FP64: position
+// in cell units; FP32 and double-word: the packed cell index plus the offset in the cell)
+// and stored in its slot holes[k0 + k]. Free slots were cleared beforehand (id -1).
 template <typename T>
 __global__ void __launch_bounds__(256) load_scatter_kernel(const BatchDev* __restrict__ bd,
-                                                           long long m) {
+                                                           long long m, long long k0) {
     const SimDev& S = bd->sims[0];
     const int dims = S.dims;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
          k += (long long)gridDim.x * blockDim.x) {
-        const long long dst = S.holes[k];
+        const long long dst = S.holes[k0 + k];
         int cellv = 0;
         for (int a = 0; a < dims; a++) {
             const double c =
@@ -638,10 +743,23 @@ static int elementwise_grid(long long n) {
     return (int)(want < 8LL * nsm ? want : 8LL * nsm);
 }
 
-cudaError_t launch_load_scatter(const BatchDev* bd, long long m, int prec, cudaStream_t s) {
+cudaError_t launch_load_bin(const BatchDev* bd, long long m, long long k0, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    load_bin_kernel<<<elementwise_grid(m), 256, 0, s>>>(bd, m, k0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_slot(const BatchDev* bd, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    load_slot_kernel<<<elementwise_grid(n), 256, 0, s>>>(bd, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_scatter(const BatchDev* bd, long long m, long long k0, int prec,
+                                cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const int grid = elementwise_grid(m);
-    PIC_DISPATCH(prec, (load_scatter_kernel<T><<<grid, 256, 0, s>>>(bd, m)));
+    PIC_DISPATCH(prec, (load_scatter_kernel<T><<<grid, 256, 0, s>>>(bd, m, k0)));
     return cudaGetLastError();
 }
 

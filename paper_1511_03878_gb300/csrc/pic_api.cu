@@ -496,13 +496,6 @@ double load_real(int prec, const void* a, long long i) {
     return (double)static_cast<const df64*>(a)[i];
 }
 
-uint64_t mix64(uint64_t x) {
-    x += 0x9E3779B97F4A7C15ULL;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
-    return x ^ (x >> 31);
-}
-
 }  // namespace
 
 // ===================================================================== C ABI
@@ -588,47 +581,6 @@ extern "C" pic_status pic_create(const pic_config* cfg, void* dev_arena, size_t 
                    [&] { return create_body(cfg, dev_arena, arena_bytes, cuda_stream, out); });
 }
 
-// Host threads of the particle load: binning and laying out millions of particles is
-// the bulk of loading a sim, and it splits into independent ranges.
-static int load_threads(long long n) {
-    if (n < (1LL << 16)) return 1;
-    const unsigned hc = std::thread::hardware_concurrency();
-    return (int)std::max(1u, std::min(hc == 0 ? 4u : hc, 32u));
-}
-
-// f(begin, end, t) on nt contiguous ranges of [0, n), in parallel. A range whose thread
-// cannot be started runs on the calling thread, so every range runs exactly once. An
-// exception in any range is rethrown on the calling thread after all ranges finished.
-template <typename F>
-static void parallel_ranges(long long n, int nt, F&& f) {
-    if (nt <= 1) {
-        f(0LL, n, 0);
-        return;
-    }
-    std::vector<std::thread> th;
-    std::vector<std::exception_ptr> errs(nt);
-    th.reserve(nt);
-    const long long chunk = (n + nt - 1) / nt;
-    for (int t = 0; t < nt; t++) {
-        const long long b = std::min(n, (long long)t * chunk), e = std::min(n, b + chunk);
-        auto run = [&f, &errs, b, e, t] {
-            try {
-                f(b, e, t);
-            } catch (...) {
-                errs[t] = std::current_exception();
-            }
-        };
-        try {
-            th.emplace_back(run);
-        } catch (const std::system_error&) {
-            run();
-        }
-    }
-    for (auto& x : th) x.join();
-    for (auto& x : errs)
-        if (x) std::rethrow_exception(x);
-}
-
 static pic_status load_particles_body(pic_sim* s, long long n, const double* x,
                                       const double* y, const double* z, const double* ux,
                                       const double* uy, const double* uz, const double* w,
@@ -640,11 +592,15 @@ static pic_status load_particles_body(pic_sim* s, long long n, const double* x,
     if (n > 0 && (!x || !y || !ux || !uy || !uz || !w || !id || (S.dims == 3 && !z)))
         return fail(&s->err, PIC_ERR_INVALID, "null particle array");
     CK(cudaStreamSynchronize(s->stream), "sync before load");
+    // every return waits for the stream, so no copy from the caller's arrays outlives
+    // the call
+    struct Drain {
+        cudaStream_t st;
+        ~Drain() { cudaStreamSynchronize(st); }
+    } drain{s->stream};
     const int dims = S.dims;
     const double* pos[3] = {x, y, z};
     const double* mom[3] = {ux, uy, uz};
-    const int nt = load_threads(n);
-    const long long n1 = std::max(n, 1LL);
     // the caller's arrays go to the device as they are, in chunks that fit the repack
     // scratch (FP64 values, so a 4-byte precision takes half its slots per chunk)
     const size_t es = elem_size(S.prec);
@@ -663,90 +619,38 @@ static pic_status load_particles_body(pic_sim* s, long long n, const double* x,
             e = cudaMemcpyAsync(S.aid, id + k0, m * sizeof(int), cudaMemcpyHostToDevice, s->stream);
         return e;
     };
-    // chunk 0 needs nothing from the host's binning: a helper thread copies it while the
-    // host validates and orders (from pageable memory a copy occupies its calling thread).
-    // Every return waits for it and for the stream, so no copy outlives the call.
-    cudaError_t early = cudaSuccess;
-    int dev = 0;
-    CK(cudaGetDevice(&dev), "device");
-    std::thread early_copy;
-    if (n > 0)
-        early_copy = std::thread([&, dev] {
-            early = cudaSetDevice(dev);
-            if (early == cudaSuccess) early = copy_chunk(0, std::min(chunk, n));
-        });
-    struct Drain {
-        std::thread& t;
-        cudaStream_t st;
-        void join() {
-            if (t.joinable()) t.join();
+    // pass 1 on the device, chunk by chunk: validation, patch and bank class, rank within
+    // (patch, class); only scratch is written (see load_bin_kernel)
+    const size_t ccount_bytes = (size_t)S.npatch * 32 * sizeof(int);
+    std::vector<int> ccount(S.npatch * 32, 0);
+    unsigned long long red[3] = {~0ULL, 0ULL, 0ULL};
+    if (n > 0) {
+        CK(cudaMemsetAsync(S.rho, 0, ccount_bytes, s->stream), "zero counters");
+        CK(cudaMemcpyAsync(S.red, red, sizeof(red), cudaMemcpyHostToDevice, s->stream),
+           "init reductions");
+        for (long long k0 = 0; k0 < n; k0 += chunk) {
+            const long long m = std::min(chunk, n - k0);
+            CK(copy_chunk(k0, m), "copy particles");
+            CK(launch_load_bin(s->L.db, m, k0, s->stream), "bin particles");
         }
-        ~Drain() {
-            join();
-            cudaStreamSynchronize(st);
-        }
-    } drain{early_copy, s->stream};
-    // per particle: its patch and the shared-memory bank class of its cell in the patch's
-    // field tile (the tile address modulo 32); uninitialised, every entry is written
-    std::unique_ptr<int[]> patch(new int[n1]);
-    std::unique_ptr<unsigned char[]> cls(new unsigned char[n1]);
-    // per thread: patch counts, largest id, largest |w|, first invalid particle (index, code)
-    std::vector<std::vector<int>> tcount(nt, std::vector<int>(S.npatch, 0));
-    std::vector<int> tmaxid(nt, -1);
-    std::vector<double> twmax(nt, 0.0);
-    std::vector<long long> tbad(nt, -1);
-    std::vector<int> tcode(nt, 0);
-    parallel_ranges(n, nt, [&](long long b, long long e, int t) {
-        std::vector<int>& cnt = tcount[t];
-        int mid = -1;
-        double wm = 0.0;
-        for (long long p = b; p < e; p++) {
-            int ic[3] = {0, 0, 0};
-            int code = 0;
-            for (int a = 0; a < dims; a++) {
-                const double v = pos[a][p];
-                if (!std::isfinite(v) || v < 0.0 || v >= S.n[a] * S.d[a]) {
-                    code = 1;
-                    break;
-                }
-                ic[a] = (int)std::floor(cell_coord(v, S.d[a], S.n[a]));
-            }
-            if (!code && (!std::isfinite(ux[p]) || !std::isfinite(uy[p]) ||
-                          !std::isfinite(uz[p]) || !std::isfinite(w[p])))
-                code = 2;
-            if (!code && id[p] < 0) code = 3;
-            if (code) {
-                tbad[t] = p;
-                tcode[t] = code;
-                return;  // the first invalid particle of this range
-            }
-            mid = std::max(mid, id[p]);
-            wm = std::max(wm, std::fabs(w[p]));
-            const int pc[3] = {ic[0] / S.P[0], ic[1] / S.P[1], ic[2] / S.P[2]};
-            const int pp = pc[0] + S.np[0] * (pc[1] + S.np[1] * pc[2]);
-            const long long lx = ic[0] - pc[0] * S.P[0], ly = ic[1] - pc[1] * S.P[1];
-            const long long lz = ic[2] - pc[2] * S.P[2];
-            patch[p] = pp;
-            cls[p] = (unsigned char)(((lz * S.BY + ly) * S.BX + lx) & 31);
-            cnt[pp]++;
-        }
-        tmaxid[t] = mid;
-        twmax[t] = wm;
-    });
-    for (int t = 0; t < nt; t++) {  // the first invalid particle overall
-        if (tbad[t] < 0) continue;
-        if (tcode[t] == 1) return fail(&s->err, PIC_ERR_INVALID, "particle position outside the grid");
-        if (tcode[t] == 2) return fail(&s->err, PIC_ERR_NUMERIC, "non-finite particle momentum or weight");
+        CK(cudaMemcpyAsync(red, S.red, sizeof(red), cudaMemcpyDeviceToHost, s->stream),
+           "read reductions");
+        CK(cudaMemcpyAsync(ccount.data(), S.rho, ccount_bytes, cudaMemcpyDeviceToHost, s->stream),
+           "read counters");
+        CK(cudaStreamSynchronize(s->stream), "bin particles");
+    }
+    if (red[0] != ~0ULL) {  // the first invalid particle of the call
+        const int code = (int)(red[0] & 3ULL);
+        if (code == 1) return fail(&s->err, PIC_ERR_INVALID, "particle position outside the grid");
+        if (code == 2) return fail(&s->err, PIC_ERR_NUMERIC, "non-finite particle momentum or weight");
         return fail(&s->err, PIC_ERR_INVALID, "negative particle id");
     }
     std::vector<int> counts(S.npatch, 0);
-    int maxid = -1;
+    for (int p = 0; p < S.npatch; p++)
+        for (int q = 0; q < 32; q++) counts[p] += ccount[p * 32 + q];
+    const int maxid = n > 0 ? (int)red[1] : -1;
     double wmax = 0.0;
-    for (int t = 0; t < nt; t++) {
-        maxid = std::max(maxid, tmaxid[t]);
-        wmax = std::max(wmax, twmax[t]);
-        for (int p = 0; p < S.npatch; p++) counts[p] += tcount[t][p];
-    }
+    std::memcpy(&wmax, &red[2], sizeof(wmax));
     // per-patch capacity: the free slots are shared half by count, half evenly; every
     // capacity is rounded up to kSlotAlign so that all bases stay aligned
     const long long spare = S.ucap - n;
@@ -764,82 +668,26 @@ static pic_status load_particles_body(pic_sim* s, long long n, const double* x,
     }
     if (acc > S.capacity || macc > S.mtotal)
         return fail(&s->err, PIC_ERR_CAPACITY, "capacity split failed");
-    // stable binning (thread t's particles of patch p follow those of threads < t), then
-    // per patch a fixed pseudo-random order, so that the lanes of a warp rarely share a
-    // cell (spreads shared-memory atomics), and an interleave of the 32 bank classes:
-    // run r of the patch's slots holds the r-th particle of every class that has one, in
-    // class order, so the lanes of a warp read and add into different banks. The result
-    // is each particle's slot.
-    std::unique_ptr<int[]> order(new int[n1]), slot(new int[n1]);
-    {
-        std::vector<long long> start(S.npatch);
-        long long a = 0;
-        for (int p = 0; p < S.npatch; p++) {
-            start[p] = a;
-            a += counts[p];
-        }
-        std::vector<std::vector<long long>> cursor(nt, std::vector<long long>(S.npatch));
-        for (int p = 0; p < S.npatch; p++) {
-            long long c = start[p];
-            for (int t = 0; t < nt; t++) {
-                cursor[t][p] = c;
-                c += tcount[t][p];
-            }
-        }
-        parallel_ranges(n, nt, [&](long long b, long long e, int t) {
-            std::vector<long long>& cur = cursor[t];
-            for (long long p = b; p < e; p++) order[cur[patch[p]]++] = (int)p;
-        });
-        parallel_ranges(S.npatch, nt, [&](long long pb0, long long pb1, int) {
-            std::vector<int> list;
-            std::vector<unsigned char> lc;
-            for (long long p = pb0; p < pb1; p++) {
-                int* seg = order.get() + start[p];
-                const long long c = counts[p];
-                // Fisher-Yates; the draw in [0, k] is the high word of a 64-bit hash times k + 1
-                for (long long k = c - 1; k > 0; k--) {
-                    const uint64_t h = mix64(((uint64_t)p << 32) ^ (uint64_t)k);
-                    const long long r =
-                        (long long)(((unsigned __int128)h * (uint64_t)(k + 1)) >> 64);
-                    std::swap(seg[k], seg[r]);
-                }
-                // each class's particles in the shuffled order, then emitted run by run
-                lc.resize(c);
-                int nb[32] = {0}, off[32], fill[32];
-                for (long long k = 0; k < c; k++) nb[lc[k] = cls[seg[k]]]++;
-                int maxnb = 0;
-                for (int q = 0, o = 0; q < 32; q++) {
-                    off[q] = fill[q] = o;
-                    o += nb[q];
-                    maxnb = std::max(maxnb, nb[q]);
-                }
-                list.resize(c);
-                for (long long k = 0; k < c; k++) list[fill[lc[k]]++] = seg[k];
-                int next = pbase[p];
-                for (int r = 0; r < maxnb; r++)
-                    for (int q = 0; q < 32; q++)
-                        if (nb[q] > r) slot[list[off[q] + r]] = next++;
-            }
-        });
-    }
-    // device side: clear every slot (zero state, id -1), then per chunk the particles'
-    // slots; the device converts the chunk and places it
-    drain.join();
-    CK(early, "copy particles");
+    // the load is accepted: from here on the sim's state is replaced
+    const size_t pb = S.npatch * sizeof(int);
+    CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
+    // pass 2: every particle's slot (patch base plus its place in the bank-class run order)
+    CK(launch_load_slot(s->L.db, n, s->stream), "order particles");
+    // pass 3: clear every slot (zero state, id -1), then per chunk the device converts and
+    // places the particles; the last chunk of pass 1 is still staged, so it goes first
     for (int a = 0; a < dims; a++) CK(cudaMemsetAsync(S.xi[a], 0, cap * es, s->stream), "clear x");
     for (int a = 0; a < 3; a++) CK(cudaMemsetAsync(S.u[a], 0, cap * es, s->stream), "clear u");
     CK(cudaMemsetAsync(S.w, 0, cap * es, s->stream), "clear w");
     CK(cudaMemsetAsync(S.id, 0xFF, cap * sizeof(int), s->stream), "clear id");
     if (S.prec != PIC_FP64) CK(cudaMemsetAsync(S.cell, 0, cap * sizeof(int), s->stream), "clear cell");
-    for (long long k0 = 0; k0 < n; k0 += chunk) {
-        const long long m = std::min(chunk, n - k0);
-        if (k0 > 0) CK(copy_chunk(k0, m), "copy particles");
-        CK(cudaMemcpyAsync(S.holes, slot.get() + k0, m * sizeof(int), cudaMemcpyHostToDevice,
-                           s->stream), "copy slots");
-        CK(launch_load_scatter(s->L.db, m, S.prec, s->stream), "place particles");
+    if (n > 0) {
+        const long long last = ((n - 1) / chunk) * chunk;
+        for (long long k0 = last; k0 >= 0; k0 -= chunk) {
+            const long long m = std::min(chunk, n - k0);
+            if (k0 != last) CK(copy_chunk(k0, m), "copy particles");
+            CK(launch_load_scatter(s->L.db, m, k0, S.prec, s->stream), "place particles");
+        }
     }
-    const size_t pb = S.npatch * sizeof(int);
-    CK(cudaMemcpyAsync(S.pbase, pbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pbase");
     CK(cudaMemcpyAsync(S.pcap, pcap.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcap");
     CK(cudaMemcpyAsync(S.pcount, counts.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy pcount");
     CK(cudaMemcpyAsync(S.mbase, mbase.data(), pb, cudaMemcpyHostToDevice, s->stream), "copy mbase");

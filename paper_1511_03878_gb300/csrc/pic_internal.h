@@ -192,7 +192,10 @@ cudaError_t launch_bounded_wait_selftest(int* status, cudaStream_t s);
 // particle load, one chunk: m particles of the caller's FP64 arrays staged in the repack
 // scratch (positions axi, momenta au, weights aw, ids aid; slots in holes), converted to
 // the sim's representation and stored in their slots
-cudaError_t launch_load_scatter(const BatchDev* bd, long long m, int prec, cudaStream_t s);
+cudaError_t launch_load_bin(const BatchDev* bd, long long m, long long k0, cudaStream_t s);
+cudaError_t launch_load_slot(const BatchDev* bd, long long n, cudaStream_t s);
+cudaError_t launch_load_scatter(const BatchDev* bd, long long m, long long k0, int prec,
+                                cudaStream_t s);
 // field load: E staged in J[0] and B in J[1] (three ncell arrays each, x fastest) to the
 // padded F (E, B) and H (B) of generation 0 in the sim's precision
 cudaError_t launch_load_fields(const SimDev* sd, long long fstride, int prec, cudaStream_t s);
