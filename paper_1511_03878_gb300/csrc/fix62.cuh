@@ -123,6 +123,46 @@ __device__ __forceinline__ void fix_field_tile(double* F, int pl, int* s_emax) {
     }
 }
 
+// v 2^-k as a double with integer operations only (the mantissa truncated to 53 bits; 0
+// below the normal range), for |v| < 2^62: the gathered fields' return to FP64 off the
+// FP64 pipe
+__device__ __forceinline__ double fix_to_f64_int(long long v, int k) {
+    const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)a);  // 64 for a = 0
+    const unsigned long long m = a << (lz & 63);  // leading bit at 63
+    const int e = 1086 - lz - k;                  // biased exponent of a 2^-k
+    const unsigned long long bits = sgn | ((((unsigned long long)(e - 1)) << 52) + (m >> 11));
+    return (a == 0 || e <= 0) ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// round(c w) for doubles c (a charge constant) and w (a weight) whose product's magnitude
+// is below 2^61, with integer operations only: the 53-bit mantissas multiplied in 32-bit
+// halves, the product's high 64 bits shifted into place and rounded to nearest
+__device__ __forceinline__ long long mul_to_fixed(double c, double w) {
+    const unsigned long long bc = (unsigned long long)__double_as_longlong(c);
+    const unsigned long long bw = (unsigned long long)__double_as_longlong(w);
+    const int ec = (int)((bc >> 52) & 0x7FF), ew = (int)((bw >> 52) & 0x7FF);
+    if (ec == 0 || ew == 0) return 0;  // zero (or below the fixed point's quantum)
+    const unsigned long long mc = (bc & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    const unsigned long long mw = (bw & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    const unsigned ch = (unsigned)(mc >> 32), cl = (unsigned)mc;
+    const unsigned wh = (unsigned)(mw >> 32), wl = (unsigned)mw;
+    // T = floor(mc mw / 2^42): high-by-high (below 2^42) times 2^22, the cross products
+    // shifted by 10, the low-by-low product's high word shifted by 10 (its low word
+    // is below 2^-10 of a unit of T)
+    const unsigned long long hh = (unsigned long long)ch * wh;
+    const unsigned long long cross = (unsigned long long)ch * wl + (unsigned long long)cl * wh +
+                                     (unsigned long long)__umulhi(cl, wl);
+    const unsigned long long T = (hh << 22) + (cross >> 10);
+    // c w = mc mw 2^(ec + ew - 2150) = T 2^(ec + ew - 2108); |c w| < 2^61 keeps the
+    // shift at 3 or more
+    const int sh = max(2108 - ec - ew, 1);
+    if (sh >= 64) return 0;
+    const long long q = (long long)((T + (1ULL << (sh - 1))) >> sh);
+    return ((bc ^ bw) >> 63) ? -q : q;
+}
+
 // A 2^62 weight split as S = h 2^31 + l (0 <= l < 2^31; S >= 0, so h >= 0)
 struct W31 {
     int h, l;

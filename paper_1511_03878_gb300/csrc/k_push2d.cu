@@ -77,37 +77,6 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
             jatomic(jy + JX + k, jprod<JT>(by2, wx0));
             wx0 = wx1, wx1 = wx2;
         }
-    } else if constexpr (std::is_same<T, double>::value && std::is_same<JT, long long>::value) {
-        // FP64 with the int64 tile: the 21 tap products in integer arithmetic, with the
-        // weights (all in [-1, 1]) in 2^62 fixed point and the charge factors already
-        // carrying the tile's 2^k; the FP64 pipe, which bounds this kernel, only forms the
-        // weights
-        long long WY[3], WX[3], WZ[3], SX[3], AX[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            WY[k] = f64_to_fixed_shift(wy[k], 62);
-            WX[k] = f64_to_fixed_shift(wx[k], 62);
-            WZ[k] = f64_to_fixed_shift(wz[k], 62);
-            SX[k] = f64_to_fixed_shift(S0x[k], 62);
-            AX[k] = f64_to_fixed_shift(a[k], 62);
-        }
-        const long long CX1 = f64_to_fixed(ax1), CX2 = f64_to_fixed(ax2);
-        const long long CY1 = f64_to_fixed(by1), CY2 = f64_to_fixed(by2);
-        const long long CZ = f64_to_fixed(qz);
-#pragma unroll
-        for (int l = 0; l < 3; l++) {
-            jatomic(jx + l * JX + 0, fixmul62(CX1, WY[l]));
-            jatomic(jx + l * JX + 1, fixmul62(CX2, WY[l]));
-            const long long QWY = fixmul62(CZ, WY[l]), QWZ = fixmul62(CZ, WZ[l]);
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                jatomic(jz + l * JX + k, fixmul62(QWY, SX[k]) + fixmul62(QWZ, AX[k]));
-        }
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            jatomic(jy + 0 * JX + k, fixmul62(CY1, WX[k]));
-            jatomic(jy + 1 * JX + k, fixmul62(CY2, WX[k]));
-        }
     } else {
 #pragma unroll
         for (int l = 0; l < 3; l++) {
@@ -128,7 +97,7 @@ __device__ __forceinline__ void deposit2d_fast(JT* jx, JT* jy, JT* jz, int JX, c
 }
 
 // General 2D Esirkepov deposition on the five-node stencil with per-node predicates
-// (used for FP64 and FP32, where it needs fewer registers than the four-node window).
+// (used for FP32, where it needs fewer registers than the four-node window).
 template <typename T, typename JT>
 __device__ __forceinline__ void deposit2d_general5(JT* jx, JT* jy, JT* jz, int JX, const T S0x[3],
                                                    const T S0y[3], T dx1, T dy1, int sx, int sy,
@@ -489,7 +458,7 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                             const long long v = gather9_fix(
                                 Fi + c * pl + (yp ? typ : tyd) * BX + (xp ? txp : txd), BX, gx, gy);
                             r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5;
-                            r5 = scaled_to_f64(v, fix_field_exp(s_femax[c]));
+                            r5 = fix_to_f64_int(v, fix_field_exp(s_femax[c]));
                         }
                         E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
                     }
@@ -509,10 +478,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                 }
                 long long QX = 0, QY = 0, QZ = 0;
                 if (ok) {
-                    // charge factors (carrying the tile's 2^k) as integers
-                    QX = __double2ll_rn(cjxs * w);
-                    QY = __double2ll_rn(cjys * w);
-                    QZ = __double2ll_rn(cjzs * w * vz);
+                    // charge factors (carrying the tile's 2^k) as integers, formed on the
+                    // integer units: q w d_a/dt for Jx, Jy and q w v_z for Jz
+                    QX = mul_to_fixed(cjxs, w);
+                    QY = mul_to_fixed(cjys, w);
+                    QZ = fixmul62(mul_to_fixed(cjzs, w), f64_to_fixed_shift(vz, 62));
                     // ---- boundaries, destination patch (decisions on the integer floors) and
                     // the new state, stored before the deposit so that only the shapes and
                     // charge factors stay live through it
