@@ -206,7 +206,7 @@ enum {
                                    particles added by splitting, when out_bytes
                                    allows                                         */
     PIC_DIAG_EX_AXIS = 7,       /* nx float64: Ex on the row (and plane) ny/2      */
-    PIC_DIAG_QUEUE = 8          /* int32 m, then m x 4 int32 {sim, patch, first,
+    PIC_DIAG_QUEUE = 8,         /* int32 m, then m x 4 int32 {sim, patch, first,
                                    count}: the work items of the last step's queue
                                    (built from the patch counts at the start of that
                                    step): full chunks of `chunk` particles in patch
@@ -216,6 +216,10 @@ enum {
                                    static mapping one item per non-empty patch in patch
                                    order. Sec. 3: load = SP count, so the largest loads
                                    are handed out first                          */
+    PIC_DIAG_SLOTS = 9          /* n int32, sorted by id as PIC_DIAG_PARTICLES: each
+                                   SP's slot within its patch's range (0 = the patch's
+                                   first slot), the order in which work items take a
+                                   patch's SP (Sec. 3.1: a patch owns its SP)   */
 };
 pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);
 

@@ -20,7 +20,7 @@ PIC_FP64, PIC_FP32, PIC_DF64 = 0, 1, 2
 PIC_MAP_QUEUE, PIC_MAP_STATIC = 0, 1
 (PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_FIELDS, PIC_DIAG_PARTICLES,
  PIC_DIAG_NUM_PARTICLES, PIC_DIAG_PATCH_COUNTS, PIC_DIAG_STEP, PIC_DIAG_EX_AXIS,
- PIC_DIAG_QUEUE) = range(9)
+ PIC_DIAG_QUEUE, PIC_DIAG_SLOTS) = range(10)
 
 STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
                 -3: "PIC_ERR_CAPACITY", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NUMERIC",
@@ -463,6 +463,11 @@ class Sim:
         b = pic_diag(self.h, PIC_DIAG_QUEUE, cap)
         m = int(np.frombuffer(b[:4], dtype=np.int32)[0])
         return np.frombuffer(b[4:4 + 16 * m], dtype=np.int32).reshape(m, 4).copy()
+
+    def slots(self):
+        """Each particle's slot within its patch, in id order (as particles())."""
+        n = self.num_particles()
+        return np.frombuffer(pic_diag(self.h, PIC_DIAG_SLOTS, 4 * n), dtype=np.int32).copy()
 
     def chunk_used(self) -> int:
         return int(self.cfg.chunk) if self.cfg.chunk > 0 else 2048

@@ -973,6 +973,25 @@ static pic_status diag_body(pic_sim* s, int kind, void* out, size_t out_bytes, s
             if (written) *written = b;
             return PIC_OK;
         }
+        case PIC_DIAG_SLOTS: {
+            CK(read_counts(), "read counts");
+            long long n = 0;
+            for (int c : counts) n += c;
+            if (!need((size_t)n * sizeof(int))) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+            std::vector<int> hid(S.capacity), pbase(S.npatch);
+            CK(cudaMemcpy(hid.data(), S.id, S.capacity * sizeof(int), cudaMemcpyDeviceToHost), "read id");
+            CK(cudaMemcpy(pbase.data(), S.pbase, S.npatch * sizeof(int), cudaMemcpyDeviceToHost),
+               "read pbase");
+            std::vector<std::pair<int, int>> live;  // (id, slot within the patch)
+            live.reserve(n);
+            for (int p = 0; p < S.npatch; p++)
+                for (int c = 0; c < counts[p]; c++) live.emplace_back(hid[(long long)pbase[p] + c], c);
+            std::sort(live.begin(), live.end());
+            int* o = static_cast<int*>(out);
+            for (long long k = 0; k < n; k++) o[k] = live[k].second;
+            if (written) *written = (size_t)n * sizeof(int);
+            return PIC_OK;
+        }
         case PIC_DIAG_QUEUE: {
             int nitems = 0;
             CK(cudaMemcpy(&nitems, s->L.B.nitems, sizeof(int), cudaMemcpyDeviceToHost),
