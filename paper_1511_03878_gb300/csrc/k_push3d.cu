@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(Push3DShape<T>::threads, Push3DShape<T>::min_b
                                         (xp ? tp[0] : td[0]);
                         const long long v = gather27_fix(Fi + c * vol + off, BX, BXY, gx, gy, gz);
                         r0 = r1, r1 = r2, r2 = r3, r3 = r4, r4 = r5;
-                        r5 = scaled_to_f64(v, fix_field_exp(s_femax[c]));
+                        r5 = fix_to_f64_int(v, fix_field_exp(s_femax[c]));
                     }
                     const double E[3] = {r0, r1, r2}, B[3] = {r3, r4, r5};
                     const double ig = boris(eps, E, B, u);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(Push3DShape<T>::threads, Push3DShape<T>::min_b
                         sh[a] = icn[a] + (h1 ? 1 : 0) - np_[a];
                         ok = ok && sh[a] >= -1 && sh[a] <= 1;
                         shape62(h1 ? F1 - kOne62 : F1, S1[a]);
-                        Q[a] = __double2ll_rn(cjs[a] * w);  // charge factor, tile scale included
+                        Q[a] = mul_to_fixed(cjs[a], w);  // charge factor, tile scale included
                     }
                     // ---- boundaries, destination patch and the new state, stored before
                     // the deposit: periodic, except a moving-window x axis (this step's
