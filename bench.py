@@ -206,7 +206,7 @@ def workload(nx, ny, kind="lwfa", total=64 * 2 ** 20, order=2, start="full"):
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic.md")
 # the sources a particle kernel is built from (the digest in the traffic table)
 KERNEL_SOURCES = {2: ("k_push2d.cu", "fix62.cuh", "pic_device.cuh", "df64.cuh", "pic_internal.h"),
-                  3: ("k_push3d.cu", "pic_device.cuh", "df64.cuh", "pic_internal.h")}
+                  3: ("k_push3d.cu", "fix62.cuh", "pic_device.cuh", "df64.cuh", "pic_internal.h")}
 
 
 def source_digest(dims):

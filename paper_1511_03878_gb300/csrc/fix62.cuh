@@ -156,10 +156,12 @@ __device__ __forceinline__ long long mul_to_fixed(double c, double w) {
                                      (unsigned long long)__umulhi(cl, wl);
     const unsigned long long T = (hh << 22) + (cross >> 10);
     // c w = mc mw 2^(ec + ew - 2150) = T 2^(ec + ew - 2108); |c w| < 2^61 keeps the
-    // shift at 3 or more
+    // shift at 3 or more; a shift above 64 leaves less than half a unit. The shift by
+    // one bit less comes first, then the rounding bit: T is up to 2^64, so adding half
+    // a unit before the shift could overflow.
     const int sh = max(2108 - ec - ew, 1);
-    if (sh >= 64) return 0;
-    const long long q = (long long)((T + (1ULL << (sh - 1))) >> sh);
+    if (sh > 64) return 0;
+    const long long q = (long long)(((T >> (sh - 1)) + 1ULL) >> 1);
     return ((bc ^ bw) >> 63) ? -q : q;
 }
 
