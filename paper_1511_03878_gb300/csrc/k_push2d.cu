@@ -396,11 +396,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             bool ok = false, leave = false;
             int dest = patch;
             if constexpr (std::is_same<T, double>::value) {
-                // ---- FP64: in-cell offsets, shapes and every deposit weight, running sum and
-                // tap product in 2^62 fixed point (integer units, 32 times the FP64 rate on
-                // this GPU); the gather, Boris, the move and the charge factors in FP64
-                // a field tile holding a non-finite value cannot be converted: its
-                // particles are reported and dropped like non-finite particles
+                // ---- FP64: in-cell offsets, shapes, the field gather, the charge factors and
+                // every deposit weight, running sum and tap product in 2^62 fixed point
+                // (integer units, 32 times the FP64 rate on this GPU); Boris and the move in
+                // FP64. A field tile holding a non-finite value cannot be converted: its
+                // particles are reported and dropped like non-finite particles.
                 const bool ftile_ok = s_femax[0] < 0x7FF && s_femax[1] < 0x7FF &&
                                       s_femax[2] < 0x7FF && s_femax[3] < 0x7FF &&
                                       s_femax[4] < 0x7FF && s_femax[5] < 0x7FF;

@@ -48,24 +48,16 @@ __device__ __forceinline__ T gather27(const T* __restrict__ f, int BX, int BXY, 
     return r;
 }
 
+// FP32 particle state: the packed cell and the offsets in it (the FP64 kernel reads its
+// positions directly)
 template <typename T>
-__device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T f[3],
-                                          double xi[3]) {
-    if constexpr (is_f64<T>::value) {
+__device__ __forceinline__ void split_pos(const SimDev& S, int slot, int i[3], T f[3]) {
+    const int c = S.cell[slot];
+    i[0] = c & 0x7FF;
+    i[1] = (c >> 11) & 0x7FF;
+    i[2] = (c >> 22) & 0x3FF;
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            xi[a] = reinterpret_cast<const double*>(S.xi[a])[slot];
-            i[a] = floor_to_int(xi[a]);  // integer floor, widened back exactly
-            f[a] = xi[a] - fixed_to_f64(i[a], 0);
-        }
-    } else {
-        const int c = S.cell[slot];
-        i[0] = c & 0x7FF;
-        i[1] = (c >> 11) & 0x7FF;
-        i[2] = (c >> 22) & 0x3FF;
-#pragma unroll
-        for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const T*>(S.xi[a])[slot];
-    }
+    for (int a = 0; a < 3; a++) f[a] = reinterpret_cast<const T*>(S.xi[a])[slot];
 }
 
 // 3D deposition when no axis changes its nearest node: S0 and DS live on stencil
@@ -252,7 +244,7 @@ __global__ void __launch_bounds__(Push3DShape<T>::threads, Push3DShape<T>::min_b
 #pragma unroll
                 for (int a = 0; a < 3; a++) nxi[a] = reinterpret_cast<const double*>(S.xi[a])[sl];
             } else {
-                split_pos<T>(S, sl, nic, nf, nxi);
+                split_pos<T>(S, sl, nic, nf);
             }
             nu[0] = U0[sl];
             nu[1] = U1[sl];

@@ -182,7 +182,9 @@ template <typename T>
 struct JType;
 template <>
 struct JType<double> {
-    using type = long long;  // int64 fixed point: FP64 shared atomics run on the FP64 pipe
+    // int64 fixed point (shared FP64 atomics would run on the FP64 pipe); each add is two
+    // native 32-bit atomics with the carry (jatomic)
+    using type = long long;
 };
 #ifndef PIC_F32_FIXED_TILE
 #define PIC_F32_FIXED_TILE 1
@@ -202,11 +204,8 @@ struct JType<df64> {
     using type = long long;  // int64 fixed-point shared-memory current (see jprod)
 };
 
-// 3D tile type: the same as 2D (int64 fixed point for FP64: shared FP64 atomics run on
-// the FP64 pipe). With the FP64 kernel's deposit loops rolled, the integer conversion of
-// the 54 to 144 contributions per particle is hidden: measured level with the FP64 tile
-// on the 3D stress case and 7 % faster on the 3D LWFA window (the FP64 tile with
-// unrolled loops was the faster of the unrolled pair, by 24 %).
+// 3D tile type: the same as 2D (the FP64 kernel forms its contributions in 2^62 fixed
+// point and adds them into the int64 tile).
 template <typename T>
 struct JType3D {
     using type = typename JType<T>::type;
