@@ -35,6 +35,21 @@ __device__ __forceinline__ T gather9(const T* __restrict__ f, int BX, const T Sx
     return r;
 }
 
+// FP32: the same gather for two components that share a stagger, interleaved in the
+// tile as float2 (Ex with By, Ey with Bx): one 64-bit shared load per tap serves both.
+__device__ __forceinline__ float2 gather9x2(const float2* __restrict__ f, int BX,
+                                            const float Sx[3], const float Sy[3]) {
+    float rx = 0.0f, ry = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const float2* row = f + b * BX;
+        const float2 a0 = row[0], a1 = row[1], a2 = row[2];
+        rx += Sy[b] * (Sx[0] * a0.x + Sx[1] * a1.x + Sx[2] * a2.x);
+        ry += Sy[b] * (Sx[0] * a0.y + Sx[1] * a1.y + Sx[2] * a2.y);
+    }
+    return make_float2(rx, ry);
+}
+
 // Esirkepov deposition, 2D, when the particle stays on its nearest nodes along both
 // axes (the common case): S0 and DS live on the stencil nodes 1..3 only, the running
 // sums have two non-zero entries, 6 + 6 + 9 shared-memory atomics.
@@ -309,20 +324,32 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
         JT* Jt = reinterpret_cast<JT*>(smem + ((fbytes + 127) & ~127));
         const int jplane = JX * JY;
 
-        for (int e = tid; e < 3 * JY * JW; e += blockDim.x) {
-            const int r = e / JW;  // component * JY + row
-            Jt[r * JX + (e - r * JW)] = JT(0);
-        }
+        // FP32 stages the six planes in the current tile's space, which is zeroed after
+        // they are interleaved into the field tile
+        constexpr bool kPaired = std::is_same<T, float>::value;
+        auto zero_j = [&] {
+            for (int e = tid; e < 3 * JY * JW; e += blockDim.x) {
+                const int r = e / JW;  // component * JY + row
+                Jt[r * JX + (e - r * JW)] = JT(0);
+            }
+        };
+        if constexpr (!kPaired) zero_j();
 
         if (item.x != loaded_sim || patch != loaded_patch || gen != loaded_gen) {
             if constexpr (std::is_same<T, double>::value) {
                 if (tid < 6) s_femax[tid] = 0;
             }
+            if constexpr (kPaired) {
+                // the previous item's atomics into the staging space come before the copy
+                fence_proxy_async_smem();
+                __syncthreads();
+            }
             if (tid == 0) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&mbar, (uint32_t)fbytes);
                 // box origin: interior index (px0 - 1, py0 - 1) = padded (px0, py0)
-                tma_load_3d(Ft, S.tmap + gen, &mbar, px0 - 1 + kGuard, py0 - 1 + kGuard, 0);
+                tma_load_3d(kPaired ? reinterpret_cast<void*>(Jt) : reinterpret_cast<void*>(Ft),
+                            S.tmap + gen, &mbar, px0 - 1 + kGuard, py0 - 1 + kGuard, 0);
             }
             const bool ok = mbar_wait_bounded(&mbar, phase);
             phase ^= 1u;
@@ -332,10 +359,24 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
             }
             if constexpr (std::is_same<T, double>::value)
                 fix_field_tile(reinterpret_cast<double*>(Ft), BX * BY, s_femax);
+            if constexpr (kPaired) {
+                // planes Ex Ey Ez Bx By Bz -> (Ex, By) pairs, (Ey, Bx) pairs, Ez, Bz
+                const int pl = BX * BY;
+                const float* St = reinterpret_cast<const float*>(Jt);
+                float2* FA = reinterpret_cast<float2*>(Ft);
+                for (int i = tid; i < pl; i += blockDim.x) {
+                    FA[i] = make_float2(St[i], St[4 * pl + i]);
+                    FA[pl + i] = make_float2(St[pl + i], St[3 * pl + i]);
+                    Ft[4 * pl + i] = St[2 * pl + i];
+                    Ft[5 * pl + i] = St[5 * pl + i];
+                }
+                __syncthreads();
+            }
             loaded_sim = item.x;
             loaded_patch = patch;
             loaded_gen = gen;
         }
+        if constexpr (kPaired) zero_j();
         __syncthreads();  // J tile zeroed (FP64: field tile converted)
 
         // per-sim constants in the working precision (precomputed on the host)
@@ -597,11 +638,11 @@ __global__ void __launch_bounds__(Push2DShape<T>::threads, Push2DShape<T>::min_b
                         }
                         E[0] = r0, E[1] = r1, E[2] = r2, B[0] = r3, B[1] = r4, B[2] = r5;
                     } else {
-                        E[0] = gather9(Ft + 0 * pl + typ * BX + txd, BX, Sxd, Syp);
-                        E[1] = gather9(Ft + 1 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                        E[2] = gather9(Ft + 2 * pl + typ * BX + txp, BX, Sxp, Syp);
-                        B[0] = gather9(Ft + 3 * pl + tyd * BX + txp, BX, Sxp, Syd);
-                        B[1] = gather9(Ft + 4 * pl + typ * BX + txd, BX, Sxd, Syp);
+                        const float2* FA = reinterpret_cast<const float2*>(Ft);
+                        const float2 exby = gather9x2(FA + typ * BX + txd, BX, Sxd, Syp);
+                        const float2 eybx = gather9x2(FA + pl + tyd * BX + txp, BX, Sxp, Syd);
+                        E[0] = exby.x, B[1] = exby.y, E[1] = eybx.x, B[0] = eybx.y;
+                        E[2] = gather9(Ft + 4 * pl + typ * BX + txp, BX, Sxp, Syp);
                         B[2] = gather9(Ft + 5 * pl + tyd * BX + txd, BX, Sxd, Syd);
                     }
 
@@ -790,7 +831,8 @@ template <typename T>
 static int smem_bytes_2d(int P0, int P1) {
     const int BX = ((P0 + 3) + 3) & ~3, BY = P1 + 3;
     const int fb = 6 * BX * BY * (int)sizeof(T);
-    const int jb = 3 * jrow2d<T>(P0) * (P1 + 5) * (int)sizeof(typename JType<T>::type);
+    int jb = 3 * jrow2d<T>(P0) * (P1 + 5) * (int)sizeof(typename JType<T>::type);
+    if (std::is_same<T, float>::value && jb < fb) jb = fb;  // FP32 stages the field tile there
     return ((fb + 127) & ~127) + jb;
 }
 

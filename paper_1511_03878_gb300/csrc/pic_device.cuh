@@ -125,6 +125,8 @@ __device__ __forceinline__ void shape3(df64 delta, df64 S[3]) {
 
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Relativistic Boris rotation (Boris 1970): u^{n-1/2} -> u^{n+1/2}; eps = q dt/(2m).
 // Returns 1/gamma^{n+1/2}.
@@ -136,12 +138,14 @@ __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     const T t0 = ei * B[0], t1 = ei * B[1], t2 = ei * B[2];
     const T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
     const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
-    const T up0 = um0 + (um1 * t2 - um2 * t1);
-    const T up1 = um1 + (um2 * t0 - um0 * t2);
-    const T up2 = um2 + (um0 * t1 - um1 * t0);
-    um0 += up1 * s2 - up2 * s1;
-    um1 += up2 * s0 - up0 * s2;
-    um2 += up0 * s1 - up1 * s0;
+    // each component of both cross-product updates as two fused multiply-adds into the
+    // running value (two roundings instead of the three of product, difference, sum)
+    const T up0 = fma_t(um1, t2, fma_t(-um2, t1, um0));
+    const T up1 = fma_t(um2, t0, fma_t(-um0, t2, um1));
+    const T up2 = fma_t(um0, t1, fma_t(-um1, t0, um2));
+    um0 = fma_t(up1, s2, fma_t(-up2, s1, um0));
+    um1 = fma_t(up2, s0, fma_t(-up0, s2, um1));
+    um2 = fma_t(up0, s1, fma_t(-up1, s0, um2));
     u[0] = um0 + eps * E[0];
     u[1] = um1 + eps * E[1];
     u[2] = um2 + eps * E[2];
