@@ -209,11 +209,51 @@ KERNEL_SOURCES = {2: ("k_push2d.cu", "fix62.cuh", "pic_device.cuh", "df64.cuh", 
                   3: ("k_push3d.cu", "fix62.cuh", "pic_device.cuh", "df64.cuh", "pic_internal.h")}
 
 
-def source_digest(dims):
+def code_only(text):
+    """C/C++/CUDA source without its comments, each whitespace run outside string and
+    character literals reduced to one newline (if it holds one) or one space: a comment
+    or layout edit leaves it as it was, a change to the code does not."""
+    out = []
+    i, n = 0, len(text)
+
+    def space(nl):
+        if out and out[-1] in " \n":
+            if nl:
+                out[-1] = "\n"
+        elif out:
+            out.append("\n" if nl else " ")
+
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            space(False)
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif c.isspace():
+            space(c == "\n")
+            i += 1
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out).strip()
+
+
+def source_digest(dims, root=None):
+    """First 16 hex digits of sha256 over the code of the kernel's sources (code_only)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[dims]:
-        with open(os.path.join(ROOT, "paper_1511_03878_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(root or ROOT, "paper_1511_03878_gb300", "csrc", f)) as fh:
+            h.update(code_only(fh.read()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

@@ -14,8 +14,9 @@ namespace pic {
 
 // Row stride of the 2D current tile, whose rows hold P0 + 5 nodes. The 4-byte (FP32) tile
 // is padded to the field tile's stride P0 + 4 modulo the 32 shared-memory banks: a
-// particle's field taps and current taps then sit in the same bank classes, so the bank
-// interleaving of the particle order spreads the loads and the atomics of a warp alike.
+// particle's scalar field taps (Ez, Bz) and current taps then sit in the same bank
+// classes, so the bank interleaving of the particle order spreads the loads and the
+// atomics of a warp alike (the float2 pairs put class c on banks 2c and 2c + 1).
 template <typename T>
 __host__ __device__ constexpr int jrow2d(int P0) {
     return sizeof(typename JType<T>::type) == 4 ? P0 + 4 + 32 : P0 + 5;

@@ -78,3 +78,28 @@ def test_lwfa_line_is_timed_on_the_developed_run():
     wf = bench.workload(2048, 32, "lwfa", start="full")
     assert len(wf["particles"]["x"]) == full
     assert w["params"]["ramp_x0"] == inputs.lwfa2d(nx=2048, ny=32)["params"]["ramp_x0"]
+
+
+def test_code_digest_ignores_comments_not_code():
+    a = 'int f(int x) {  // twice\n    return 2 * x; /* doubled */\n}\nconst char* s = "a // b";\n'
+    b = '/* header */\nint f(int x) {\n\n    return 2 * x;\n}   \nconst char* s = "a // b";'
+    c = 'int f(int x) {\n    return 3 * x;\n}\nconst char* s = "a // b";\n'
+    d = 'int f(int x) {\n    return 2 * x;\n}\nconst char* s = "a //  b";\n'
+    e = '#define K 1\nint f(int x) { return K * x; }\n'
+    f = '#define K 1 int f(int x) { return K * x; }\n'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)   # code changed
+    assert bench.code_only(a) != bench.code_only(d)   # a string literal changed
+    assert bench.code_only(e) != bench.code_only(f)   # a line break that ends a macro
+
+
+def test_traffic_table_covers_the_current_kernels():
+    """The committed ncu traffic rows of the default bench line's kernels were taken on
+    the current kernel code: a code change without a new capture fails here."""
+    assert bench.measured_traffic("push2d_kernel<double>", "lwfa2d-2048x512-ppc4-from-step1800",
+                                  (32, 32), 4096, 2) is not None
+    assert bench.measured_traffic("push2d_kernel<float>", "lwfa2d-2048x512-ppc4-from-step1800",
+                                  (32, 32), 4096, 2) is not None
+    assert bench.measured_traffic("push3d_kernel<float>",
+                                  "stress3d-256x128x128-lognormal1.5-n67108864",
+                                  (8, 8, 8), 8192, 3) is not None
