@@ -5,9 +5,9 @@
 // periodic or a moving window (particles leaving [0, nx) are absorbed, the shift is
 // applied in the particle store, contributions outside the window are dropped).
 // FP32 cells pack (ix | iy << 11 | iz << 22). The FP64 kernel runs everything but the Boris
-// push, the move and the charge factors in 2^62 fixed point on the integer units, as the
-// 2D one does (fix62.cuh): offsets, shapes, the 27-tap gather from a fixed-point copy of
-// the field tile, the Esirkepov weights and products.
+// push and the move in 2^62 fixed point on the integer units, as the 2D one does
+// (fix62.cuh): offsets, shapes, the 27-tap gather from a fixed-point copy of the field
+// tile, the charge factors, the Esirkepov weights and products.
 #include <cuda_runtime.h>
 
 #include "fix62.cuh"
@@ -261,9 +261,9 @@ __global__ void __launch_bounds__(Push3DShape<T>::threads, Push3DShape<T>::min_b
             bool leave = false;
             int dest = patch;
             if constexpr (is_f64<T>::value) {
-                // ---- FP64: offsets, shapes, gather, deposit weights and products in 2^62
-                // fixed point on the integer units; Boris, the move and the charge factors
-                // in FP64. A field tile holding a non-finite value cannot be converted: its
+                // ---- FP64: offsets, shapes, gather, charge factors, deposit weights and
+                // products in 2^62 fixed point on the integer units; Boris and the move in
+                // FP64. A field tile holding a non-finite value cannot be converted: its
                 // particles are reported and dropped like non-finite particles.
                 const bool ftile_ok = s_femax[0] < 0x7FF && s_femax[1] < 0x7FF &&
                                       s_femax[2] < 0x7FF && s_femax[3] < 0x7FF &&
