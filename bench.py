@@ -51,10 +51,10 @@ FLOPS_PER_PUSH_2D = 325
 FLOPS_PER_PUSH_3D = 742
 # The 2D FP64 kernel runs most of those flops as exact fixed-point integer arithmetic
 # (offsets, shapes, gather, deposit weights and products); the FP64 pipe keeps the Boris
-# push and the move, with the internals of rsqrt and division: 70 FP64-pipe
+# push and the move, with the internals of rsqrt and the reciprocal: 68 FP64-pipe
 # instructions per push (ncu, developed LWFA run). At 2 FP64 lane-operations per clock
 # per SM that is this kernel's own ceiling.
-FP64_PIPE_INSTR_PER_PUSH_2D = 70
+FP64_PIPE_INSTR_PER_PUSH_2D = 68
 GB300_SMS = 152
 
 

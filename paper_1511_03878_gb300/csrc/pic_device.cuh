@@ -127,6 +127,12 @@ __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+// 2/x. FP64: twice the correctly rounded reciprocal, the same value as the correctly
+// rounded quotient (doubling is exact) wherever 1/x is a normal number, here for x >= 1,
+// in fewer FP64-pipe instructions than the division. FP32 keeps the division, which
+// measured no slower.
+__device__ __forceinline__ double two_over_t(double x) { return 2.0 * __drcp_rn(x); }
+__device__ __forceinline__ float two_over_t(float x) { return 2.0f / x; }
 
 // Relativistic Boris rotation (Boris 1970): u^{n-1/2} -> u^{n+1/2}; eps = q dt/(2m).
 // Returns 1/gamma^{n+1/2}.
@@ -136,7 +142,7 @@ __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     const T ig = rsqrt_t(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
     const T ei = eps * ig;
     const T t0 = ei * B[0], t1 = ei * B[1], t2 = ei * B[2];
-    const T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    const T f = two_over_t(T(1) + t0 * t0 + t1 * t1 + t2 * t2);
     const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
     // each component of both cross-product updates as two fused multiply-adds into the
     // running value (two roundings instead of the three of product, difference, sum)
