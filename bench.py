@@ -212,7 +212,8 @@ KERNEL_SOURCES = {2: ("k_push2d.cu", "fix62.cuh", "pic_device.cuh", "df64.cuh", 
 def code_only(text):
     """C/C++/CUDA source without its comments, each whitespace run outside string and
     character literals reduced to one newline (if it holds one) or one space: a comment
-    or layout edit leaves it as it was, a change to the code does not."""
+    or layout edit leaves it as it was, a change to the code does not. Raw string
+    literals and digit separators are not recognised; the kernel sources use neither."""
     out = []
     i, n = 0, len(text)
 
