@@ -223,6 +223,28 @@ enum {
 };
 pic_status pic_diag(pic_sim* sim, int kind, void* out, size_t out_bytes, size_t* written);
 
+/* The step record without a wait: enqueues, on the sim's stream after the work already
+ * enqueued, a copy of the device step state and status word into a page-locked staging
+ * slot the library owns (slot 0 or 1, created on first use), then an event, and returns
+ * at once. pic_record_wait(sim, slot, ...) later waits for that event only. A caller
+ * that enqueues step k + 1 before it waits for step k's record keeps the device busy
+ * between steps. Enqueueing a slot again before its wait overwrites the record. The
+ * paper has no counterpart (host plumbing). Errors: PIC_ERR_INVALID (null sim, slot not
+ * 0 or 1); PIC_ERR_NOMEM (no page-locked memory or event); PIC_ERR_CUDA (the copy or
+ * the event could not be enqueued). */
+pic_status pic_step_record_async(pic_sim* sim, int slot);
+
+/* Waits for the record pic_step_record_async enqueued in `slot` and writes it to out as
+ * PIC_DIAG_STEP does (3 int64: steps taken, window shifts, capacity repacks; a 4th,
+ * particles removed by merging, and a 5th, particles added by splitting, when out_bytes
+ * allows; *written = bytes written). Returns the device status latched up to that
+ * record as pic_sync does (PIC_ERR_TIMEOUT, PIC_ERR_CAPACITY, PIC_ERR_NUMERIC, ...),
+ * and then writes nothing. Errors: PIC_ERR_INVALID (null sim or out, slot not 0 or 1,
+ * or no record pending in the slot); PIC_ERR_NOMEM (out_bytes < 24); PIC_ERR_CUDA. The
+ * paper has no counterpart. */
+pic_status pic_record_wait(pic_sim* sim, int slot, void* out, size_t out_bytes,
+                           size_t* written);
+
 /* Instrumentation (per-kernel timing): runs nsteps steps with one plain launch per
  * kernel (no graph) and CUDA events around each kernel on the sim's stream, then
  * synchronises. ms[0..7] receive the summed times in milliseconds of: work-queue

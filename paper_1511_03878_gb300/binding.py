@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_ERR_INVALID", -2: "PIC_ERR_NOMEM",
 
 # every symbol include/pic.h declares
 EXPORTS = ("pic_config_bytes", "pic_required_bytes", "pic_create", "pic_load_particles", "pic_load_fields",
-           "pic_step", "pic_sync", "pic_diag", "pic_profile", "pic_destroy", "pic_last_error",
+           "pic_step", "pic_sync", "pic_diag", "pic_step_record_async", "pic_record_wait",
+           "pic_profile", "pic_destroy", "pic_last_error",
            "pic_batch_required_bytes", "pic_batch_create", "pic_batch_step",
            "pic_batch_destroy", "pic_gauss_residual_2d_static", "pic_selftest_bounded_wait",
            "pic_hilbert_order", "pic_partition")
@@ -98,6 +99,11 @@ def lib():
         L.pic_sync.argtypes = [vp]
         L.pic_diag.restype = ctypes.c_int
         L.pic_diag.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.pic_step_record_async.restype = ctypes.c_int
+        L.pic_step_record_async.argtypes = [vp, ctypes.c_int]
+        L.pic_record_wait.restype = ctypes.c_int
+        L.pic_record_wait.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_size_t)]
         L.pic_profile.restype = ctypes.c_int
         L.pic_profile.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
         L.pic_destroy.restype = ctypes.c_int
@@ -258,6 +264,17 @@ def pic_diag(h, kind: int, nbytes: int) -> bytes:
     buf = ctypes.create_string_buffer(nbytes)
     written = ctypes.c_size_t(0)
     _check(lib().pic_diag(h, kind, buf, nbytes, ctypes.byref(written)), h)
+    return buf.raw[: written.value]
+
+
+def pic_step_record_async(h, slot: int):
+    _check(lib().pic_step_record_async(h, int(slot)), h)
+
+
+def pic_record_wait(h, slot: int, nbytes: int = 24) -> bytes:
+    buf = ctypes.create_string_buffer(nbytes)
+    written = ctypes.c_size_t(0)
+    _check(lib().pic_record_wait(h, int(slot), buf, nbytes, ctypes.byref(written)), h)
     return buf.raw[: written.value]
 
 
@@ -444,6 +461,15 @@ class Sim:
 
     def step_info(self):
         s, k, _ = np.frombuffer(pic_diag(self.h, PIC_DIAG_STEP, 24), dtype=np.int64)
+        return int(s), int(k)
+
+    def step_record_async(self, slot: int):
+        """Enqueue a copy of the step record into slot 0 or 1 without waiting."""
+        pic_step_record_async(self.h, slot)
+
+    def record_wait(self, slot: int):
+        """Wait for the record enqueued in `slot`: (steps taken, window shifts)."""
+        s, k, _ = np.frombuffer(pic_record_wait(self.h, slot), dtype=np.int64)
         return int(s), int(k)
 
     def merged(self) -> int:

@@ -67,6 +67,11 @@ struct pic_sim {
     cudaGraphExec_t gexec = nullptr;
     int push_grid = 0;
     int column_pts = 0;
+    // asynchronous step records: two page-locked slots (the device step state, then the
+    // status word) and their events, created on first use
+    unsigned char* rec_host = nullptr;
+    cudaEvent_t rec_ev[2] = {nullptr, nullptr};
+    bool rec_pending[2] = {false, false};
     std::string err;
 };
 
@@ -1073,8 +1078,83 @@ extern "C" pic_status pic_destroy(pic_sim* s) {
     cudaStreamSynchronize(s->stream);
     GraphOwner o{&s->cap0, &s->cap1, &s->ev_fork, &s->ev_join, &s->graph, &s->gexec};
     destroy_graph_owner(o);
+    for (cudaEvent_t& e : s->rec_ev)
+        if (e) cudaEventDestroy(e);
+    if (s->rec_host) cudaFreeHost(s->rec_host);
     delete s;
     return PIC_OK;
+}
+
+namespace {
+constexpr size_t kRecSlot = 64;  // StepState, then the status word
+static_assert(sizeof(StepState) + sizeof(int) <= kRecSlot, "record slot too small");
+}  // namespace
+
+static pic_status step_record_async_body(pic_sim* s, int slot) {
+    if (!s || (slot != 0 && slot != 1)) return PIC_ERR_INVALID;
+    if (!s->rec_host) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, 2 * kRecSlot, cudaHostAllocDefault) != cudaSuccess)
+            return fail(&s->err, PIC_ERR_NOMEM, "page-locked record slots");
+        s->rec_host = static_cast<unsigned char*>(h);
+    }
+    if (!s->rec_ev[slot] &&
+        cudaEventCreateWithFlags(&s->rec_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+        s->rec_ev[slot] = nullptr;
+        return fail(&s->err, PIC_ERR_NOMEM, "record event");
+    }
+    unsigned char* r = s->rec_host + slot * kRecSlot;
+    const SimDev& S = s->L.S;
+    CK(cudaMemcpyAsync(r, S.st, sizeof(StepState), cudaMemcpyDeviceToHost, s->stream),
+       "record copy");
+    CK(cudaMemcpyAsync(r + sizeof(StepState), S.status, sizeof(int), cudaMemcpyDeviceToHost,
+                       s->stream),
+       "record status copy");
+    CK(cudaEventRecord(s->rec_ev[slot], s->stream), "record event");
+    s->rec_pending[slot] = true;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_step_record_async(pic_sim* s, int slot) {
+    return guarded(s ? &s->err : nullptr, [&] { return step_record_async_body(s, slot); });
+}
+
+static pic_status record_wait_body(pic_sim* s, int slot, void* out, size_t out_bytes,
+                                   size_t* written) {
+    if (!s || !out || (slot != 0 && slot != 1)) return PIC_ERR_INVALID;
+    if (written) *written = 0;
+    if (!s->rec_pending[slot]) return fail(&s->err, PIC_ERR_INVALID, "no record pending");
+    CK(cudaEventSynchronize(s->rec_ev[slot]), "record wait");
+    s->rec_pending[slot] = false;
+    const unsigned char* r = s->rec_host + slot * kRecSlot;
+    StepState st;
+    int status = 0;
+    memcpy(&st, r, sizeof(st));
+    memcpy(&status, r + sizeof(StepState), sizeof(int));
+    pic_status rc = status_to_error(&s->err, status);
+    if (rc != PIC_OK) return rc;
+    if (out_bytes < 3 * sizeof(long long)) return fail(&s->err, PIC_ERR_NOMEM, "output too small");
+    long long* o = static_cast<long long*>(out);
+    o[0] = st.step;
+    o[1] = st.nshift;
+    o[2] = st.nrepack;
+    size_t wb = 3 * sizeof(long long);
+    if (out_bytes >= 4 * sizeof(long long)) {
+        o[3] = st.nmerged;
+        wb = 4 * sizeof(long long);
+    }
+    if (out_bytes >= 5 * sizeof(long long)) {
+        o[4] = st.nsplit;
+        wb = 5 * sizeof(long long);
+    }
+    if (written) *written = wb;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_record_wait(pic_sim* s, int slot, void* out, size_t out_bytes,
+                                      size_t* written) {
+    return guarded(s ? &s->err : nullptr,
+                   [&] { return record_wait_body(s, slot, out, out_bytes, written); });
 }
 
 extern "C" const char* pic_last_error(const pic_sim* s) {
