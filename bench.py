@@ -563,6 +563,21 @@ def run_gpu(args, w, precision, K, W, world, clocks=None, chunk=0, snapshot=Fals
     return out
 
 
+def pipelined_steps(sim, K):
+    """K steps, each with a read of its step record; step k + 1 is enqueued before the
+    host waits for step k's record (two record slots, alternating). Returns the records
+    (steps taken, window shifts) in step order."""
+    recs = []
+    for k in range(K):
+        sim.step(1)
+        sim.step_record_async(k & 1)
+        if k:
+            recs.append(sim.record_wait((k - 1) & 1))
+    if K:
+        recs.append(sim.record_wait((K - 1) & 1))
+    return recs
+
+
 def run_e2e(args, w, precision, K, chunk=0, world=1):
     """Same metric through the public C ABI with host buffers, all inside the timed
     region: load the particles and fields from pinned host arrays (H2D), then K steps,
@@ -596,13 +611,7 @@ def run_e2e(args, w, precision, K, chunk=0, world=1):
     t0 = time.perf_counter()
     sim.load(wp)
     tl = time.perf_counter()
-    for k in range(K):
-        sim.step(1)
-        sim.step_record_async(k & 1)
-        if k:
-            sim.record_wait((k - 1) & 1)
-    if K:
-        sim.record_wait((K - 1) & 1)
+    pipelined_steps(sim, K)
     ts = time.perf_counter()
     e = sim.energy()
     ax = sim.ex_axis()

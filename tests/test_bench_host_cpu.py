@@ -103,3 +103,38 @@ def test_traffic_table_covers_the_current_kernels():
     assert bench.measured_traffic("push3d_kernel<float>",
                                   "stress3d-256x128x128-lognormal1.5-n67108864",
                                   (8, 8, 8), 8192, 3) is not None
+
+
+class _FakeSim:
+    """Records the calls the end-to-end loop makes, with a device that runs in order."""
+
+    def __init__(self):
+        self.log = []
+        self.enqueued = 0
+        self.slots = {}
+
+    def step(self, n):
+        self.enqueued += n
+        self.log.append(("step", self.enqueued))
+
+    def step_record_async(self, slot):
+        assert slot not in self.slots  # a slot is reused only after its wait
+        self.slots[slot] = self.enqueued
+        self.log.append(("record", slot))
+
+    def record_wait(self, slot):
+        steps = self.slots.pop(slot)
+        self.log.append(("wait", slot))
+        return steps, 0
+
+
+def test_e2e_loop_waits_one_step_behind():
+    sim = _FakeSim()
+    recs = bench.pipelined_steps(sim, 5)
+    assert [r[0] for r in recs] == [1, 2, 3, 4, 5]
+    # steps enqueued when each wait starts: the wait for step k comes after step k + 1
+    # was enqueued (the last one after the last step)
+    steps_before = [max([a for w, a in sim.log[:i] if w == "step"], default=0)
+                    for i, (w, _) in enumerate(sim.log) if w == "wait"]
+    assert steps_before == [2, 3, 4, 5, 5]
+    assert bench.pipelined_steps(_FakeSim(), 0) == []
